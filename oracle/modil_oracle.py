@@ -1,0 +1,649 @@
+"""mODIL oracle: a plain, slow, FP64 restatement of the method on the CPU.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import or run
+this module.  It shares no code with the CUDA library (no kernels, headers,
+tables or helpers); the only module both sides use is the seeded input
+generator ``paper_2303_04679_gb300.inputs``, which holds none of the method's
+arithmetic.
+
+What is computed, and where the paper defines it:
+
+* Levels N_i = N / 2^(i-1) and the multigrid decomposition
+  u = M_L(u_1..u_L) = u_1 + T_1 u_2 + ... + T_1...T_{L-1} u_L, evaluated by
+  Horner's scheme (Section 2.2, the two displayed forms of M_L).
+* T_i: linear interpolation between consecutive grids, node-based (N+1
+  values per axis) and cell-based (N values per axis), whose 1-D matrices for
+  N = 8, 4, 2 are printed in Section 2.2.  Here each 1-D matrix is built
+  explicitly from its definition and applied along every axis (tensor product).
+  The transposed operator is the transposed matrix.
+* The ODIL loss: weighted sum of squared discrete residuals over the grid
+  plus squared mismatches at measurement points plus regularisers
+  (Section 2.1, the displayed loss for the wave equation, and the loss
+  formulas of Sections 3.1, 3.2, 3.4).
+* Its gradient by a hand-written reverse pass through the stencils and then
+  through the Horner chain (gw_{i+1} = T_i^T gw_i); the paper obtains it by
+  automatic differentiation (Section 2.1, end of Section 2.2).
+* Adam (Kingma and Ba, the optimiser named in Section 2.1).
+* Reference generators used only to make test data: an explicit finite-volume
+  Burgers solver and an implicit heat solver (Sections 3.2 and 3.4).
+
+Discretisation readings where the paper gives no formula are stated next to
+each function.  Nothing here is tuned for speed.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "interp_matrix", "prolong", "restrict", "compose", "compose_explicit",
+    "chain_grad", "level_shapes", "Problem", "burgers_residual",
+    "heat_conductivity", "heat_residual", "poisson_residual", "loss_terms",
+    "loss_grad_fine", "loss_grad_levels", "adam_step", "OracleState",
+    "oracle_step", "burgers_explicit_solve", "heat_implicit_solve",
+    "eo_flux",
+]
+
+
+# ---------------------------------------------------------------------------
+# Grids and the multigrid decomposition (Section 2.2)
+# ---------------------------------------------------------------------------
+
+def level_shapes(shape, n_levels, layout="cell"):
+    """Cells per axis of each level: N_i = N / 2^(i-1), i = 1..L.
+
+    For the node layout the arrays hold N_i + 1 values per axis.
+    """
+    shapes = []
+    for i in range(n_levels):
+        cells = []
+        for n in shape:
+            if n % (1 << i):
+                raise ValueError("grid cannot be halved that many times")
+            cells.append(n // (1 << i))
+        if layout == "node":
+            shapes.append(tuple(c + 1 for c in cells))
+        else:
+            shapes.append(tuple(cells))
+    return shapes
+
+
+def interp_matrix(n_coarse, layout="cell"):
+    """1-D linear interpolation matrix T from a grid of n_coarse cells to 2*n_coarse.
+
+    cell: values at cell centres.  A fine centre lies a quarter of a coarse
+    cell from its parent centre, so it takes 3/4 of the parent and 1/4 of the
+    nearer neighbour.  Beyond the first and last coarse centres the line
+    through the two outermost centres is extended (linear extrapolation),
+    which gives the printed boundary rows (5/4, -1/4).  A coarse grid of one
+    cell has no line to extend; both fine cells copy it (constant).
+    node: values at nodes; fine nodes on coarse nodes copy them and fine nodes
+    between two coarse nodes take their mean.
+    """
+    if layout == "node":
+        nc, nf = n_coarse + 1, 2 * n_coarse + 1
+        T = np.zeros((nf, nc))
+        for i in range(nf):
+            if i % 2 == 0:
+                T[i, i // 2] = 1.0
+            else:
+                T[i, i // 2] = 0.5
+                T[i, i // 2 + 1] = 0.5
+        return T
+    nc, nf = n_coarse, 2 * n_coarse
+    T = np.zeros((nf, nc))
+    xc = np.arange(nc) + 0.5            # coarse centres in coarse-cell units
+    for i in range(nf):
+        x = (i + 0.5) / 2.0             # fine centre in coarse-cell units
+        if nc == 1:
+            T[i, 0] = 1.0
+            continue
+        # the two coarse centres bracketing x, clamped to the end pairs
+        j = int(math.floor(x - 0.5))
+        j = min(max(j, 0), nc - 2)
+        t = (x - xc[j]) / (xc[j + 1] - xc[j])
+        T[i, j] += 1.0 - t
+        T[i, j + 1] += t
+    return T
+
+
+def _apply_axes(mats, a):
+    """Apply one matrix along each axis of ``a`` (tensor-product operator)."""
+    out = a
+    for ax, M in enumerate(mats):
+        out = np.moveaxis(np.tensordot(M, np.moveaxis(out, ax, 0), axes=(1, 0)), 0, ax)
+    return out
+
+
+def _cells(shape, layout):
+    return tuple(s - 1 for s in shape) if layout == "node" else tuple(shape)
+
+
+def prolong(c, layout="cell"):
+    """T_i c: interpolate a level to the next finer level (tensor product)."""
+    cells = _cells(c.shape, layout)
+    return _apply_axes([interp_matrix(n, layout) for n in cells], c)
+
+
+def restrict(f, layout="cell"):
+    """T_i^T f: the transposed interpolation applied to a fine-level array."""
+    if layout == "node":
+        cells = tuple((s - 1) // 2 for s in f.shape)
+    else:
+        cells = tuple(s // 2 for s in f.shape)
+    return _apply_axes([interp_matrix(n, layout).T for n in cells], f)
+
+
+def compose(levels, layout="cell"):
+    """Horner form: w_L = u_L, w_i = u_i + T_i w_{i+1}, u = w_1."""
+    w = np.array(levels[-1], dtype=np.float64)
+    for u in reversed(levels[:-1]):
+        w = np.asarray(u, dtype=np.float64) + prolong(w, layout)
+    return w
+
+
+def compose_explicit(levels, layout="cell"):
+    """Explicit sum u_1 + T_1 u_2 + T_1 T_2 u_3 + ... (first displayed form of M_L)."""
+    total = np.array(levels[0], dtype=np.float64)
+    for i in range(1, len(levels)):
+        term = np.array(levels[i], dtype=np.float64)
+        for _ in range(i):
+            term = prolong(term, layout)
+        total = total + term
+    return total
+
+
+def chain_grad(g_fine, n_levels, layout="cell"):
+    """Gradients of the loss with respect to every level from dL/du.
+
+    Reverse of the Horner chain: dL/du_1 = g, dL/du_{i+1} = T_i^T dL/du_i.
+    """
+    grads = [np.array(g_fine, dtype=np.float64)]
+    for _ in range(n_levels - 1):
+        grads.append(restrict(grads[-1], layout))
+    return grads
+
+
+# ---------------------------------------------------------------------------
+# Problem description
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Problem:
+    """One mODIL problem.
+
+    pde:    "burgers" (space-time, axes (t, x)), "heat" (axes (t, x)) or
+            "poisson" (d-dimensional, axes (..., y, x)).
+    shape:  fine cells per axis, slowest axis first.
+    coef:   burgers {"nu"}; heat {}; poisson {"f": right-hand side array}.
+    meas_*: measurement cells (flat index into the fine field), field index
+            and values; data term weight w_data / n_meas.
+    aux:    heat initial temperature profile (one value per x cell).
+    """
+    pde: str
+    shape: tuple
+    n_levels: int
+    layout: str = "cell"
+    coef: dict = field(default_factory=dict)
+    w_res: float = 1.0
+    w_data: float = 1.0
+    w_reg: float = 0.0
+    meas_cell: np.ndarray = None
+    meas_field: np.ndarray = None
+    meas_value: np.ndarray = None
+    aux: np.ndarray = None
+
+    @property
+    def n_fields(self):
+        return 1
+
+    def spacing(self):
+        """Grid spacings per axis (same order as shape)."""
+        if self.pde == "burgers":       # t in [0,1], x in [-1,1]
+            return (1.0 / self.shape[0], 2.0 / self.shape[1])
+        if self.pde == "heat":          # t in [0,1], x in [0,1]
+            return (1.0 / self.shape[0], 1.0 / self.shape[1])
+        if self.pde == "poisson":       # unit cube
+            return tuple(1.0 / n for n in self.shape)
+        raise ValueError(self.pde)
+
+
+# ---------------------------------------------------------------------------
+# Viscous Burgers, space-time finite volumes (Section 3.2)
+# ---------------------------------------------------------------------------
+# Reading.  Rows are time levels t_n = (n + 1/2) dt, columns are x cells.  The
+# residual of row n >= 1 is the implicit (backward Euler) finite-volume step
+#   r^n_i = (u^n_i - u^{n-1}_i)/dt + (F_{i+1/2} - F_{i-1/2})/dx
+#           - nu (u^n_{i+1} - 2 u^n_i + u^n_{i-1})/dx^2,
+# all spatial terms at row n.  Row 0 has no residual (only data constrain it).
+# F is a first-order upwind flux for f(u) = u^2/2: the Engquist-Osher flux
+# F(a, b) = max(a, 0)^2/2 + min(b, 0)^2/2, evaluated at interior faces from
+# the two adjacent cells.  The walls x = -1, 1 carry zero Dirichlet data:
+# the convective flux there is f(0) = 0 and the viscous term uses the odd
+# ghost u_{-1} = -u_0, u_{N} = -u_{N-1} (linear profile through zero at the wall).
+
+def eo_flux(a, b):
+    """Engquist-Osher flux for f(u) = u^2/2 and its two partial derivatives."""
+    ap = np.maximum(a, 0.0)
+    bm = np.minimum(b, 0.0)
+    return 0.5 * ap * ap + 0.5 * bm * bm, ap, bm
+
+
+def _ghost_odd(u):
+    """Pad the last axis with odd ghosts (zero value at the wall)."""
+    return np.concatenate([-u[..., :1], u, -u[..., -1:]], axis=-1)
+
+
+def burgers_residual(u, nu, dt, dx):
+    """Residuals r^n_i for rows n = 1..N_t-1, shape (N_t - 1, N_x)."""
+    un, uo = u[1:], u[:-1]
+    nx = u.shape[1]
+    F = np.zeros((un.shape[0], nx + 1))
+    F[:, 1:nx], _, _ = eo_flux(un[:, :-1], un[:, 1:])
+    ug = _ghost_odd(un)
+    lap = (ug[:, 2:] - 2.0 * un + ug[:, :-2]) / dx**2
+    return (un - uo) / dt + (F[:, 1:] - F[:, :-1]) / dx - nu * lap
+
+
+def _burgers_adjoint(u, lam, nu, dt, dx):
+    """dL/du given lam = dL/dr for the residual rows 1..N_t-1."""
+    g = np.zeros_like(u)
+    un = u[1:]
+    nx = u.shape[1]
+    # time difference
+    g[1:] += lam / dt
+    g[:-1] -= lam / dt
+    # flux difference: face f (1..nx-1) is east of cell f-1 and west of cell f
+    lamF = (lam[:, :-1] - lam[:, 1:]) / dx
+    _, dFa, dFb = eo_flux(un[:, :-1], un[:, 1:])
+    g[1:, :-1] += lamF * dFa
+    g[1:, 1:] += lamF * dFb
+    # viscous term, through the odd ghosts
+    lamD = -nu * lam / dx**2
+    gug = np.zeros((un.shape[0], nx + 2))
+    gug[:, 2:] += lamD
+    gug[:, :-2] += lamD
+    gug[:, 1:-1] += -2.0 * lamD
+    g[1:] += gug[:, 1:-1]
+    g[1:, 0] -= gug[:, 0]
+    g[1:, -1] -= gug[:, -1]
+    return g
+
+
+# ---------------------------------------------------------------------------
+# Heat conduction with unknown conductivity k(u) (Section 3.4)
+# ---------------------------------------------------------------------------
+# Reading.  Rows are time levels, columns x cells on [0,1] with cell-based
+# values.  Row m >= 1 carries the displayed implicit residual linking rows m-1
+# and m, with k at the face taken at the mean of the two neighbouring values of
+# row m.  Zero Dirichlet walls use the odd ghost, so the face value at a wall
+# is exactly 0.  Row 0 carries the initial condition as a residual
+# (u^0_i - u_init_i)/dt, i.e. a quadratic term on the initial values.
+# k is represented by nodal values q_0..q_{K} at u_j = j/K (K = 31 for 32
+# nodes), linear between nodes and constant outside [0, 1]:
+#   ubar = clamp(u, 0, 1), s = min(floor(K ubar), K-1), theta = K ubar - s,
+#   k = q_s + theta (q_{s+1} - q_s).
+# The regulariser is w_reg * sum_j (q_{j+1} - 2 q_j + q_{j-1})^2.
+
+def heat_conductivity(u, q):
+    """k(u), dk/du, segment index s and local coordinate theta."""
+    K = len(q) - 1
+    ub = np.clip(u, 0.0, 1.0)
+    s = np.minimum(np.floor(ub * K).astype(np.int64), K - 1)
+    th = ub * K - s
+    k = q[s] + th * (q[s + 1] - q[s])
+    dk = np.where((u >= 0.0) & (u <= 1.0), K * (q[s + 1] - q[s]), 0.0)
+    return k, dk, s, th
+
+
+def _heat_faces(un):
+    """Ghost-padded rows, face values (N_x + 1 faces) and face differences."""
+    ug = _ghost_odd(un)
+    uf = 0.5 * (ug[:, :-1] + ug[:, 1:])
+    du = ug[:, 1:] - ug[:, :-1]
+    return ug, uf, du
+
+
+def heat_residual(u, q, dt, dx, u_init, kfun=None):
+    """Residuals, shape (N_t, N_x): row 0 initial condition, rows >= 1 the PDE.
+
+    k is the nodal representation q unless ``kfun`` (face value -> k) is given.
+    """
+    r = np.empty_like(u)
+    r[0] = (u[0] - u_init) / dt
+    un, uo = u[1:], u[:-1]
+    _, uf, du = _heat_faces(un)
+    kf = heat_conductivity(uf, q)[0] if kfun is None else kfun(uf)
+    flux = kf * du / dx
+    r[1:] = (un - uo) / dt - (flux[:, 1:] - flux[:, :-1]) / dx
+    return r
+
+
+def _heat_adjoint(u, q, lam, dt, dx):
+    """dL/du and dL/dq given lam = dL/dr (shape of the residual array)."""
+    g = np.zeros_like(u)
+    gq = np.zeros_like(q)
+    g[0] += lam[0] / dt
+    li = lam[1:]
+    g[1:] += li / dt
+    g[:-1] -= li / dt
+    un = u[1:]
+    nx = u.shape[1]
+    ug, uf, du = _heat_faces(un)
+    kf, dkf, s, th = heat_conductivity(uf, q)
+    # r = ... - (flux_E - flux_W)/dx, flux_f = kf * du_f / dx
+    lamF = np.zeros((li.shape[0], nx + 1))
+    lamF[:, 1:] -= li / dx
+    lamF[:, :-1] += li / dx
+    lam_du = lamF * kf / dx
+    lam_k = lamF * du / dx
+    gug = np.zeros_like(ug)
+    gug[:, 1:] += lam_du
+    gug[:, :-1] -= lam_du
+    gug[:, 1:] += 0.5 * lam_k * dkf
+    gug[:, :-1] += 0.5 * lam_k * dkf
+    g[1:] += gug[:, 1:-1]
+    g[1:, 0] -= gug[:, 0]
+    g[1:, -1] -= gug[:, -1]
+    np.add.at(gq, s, lam_k * (1.0 - th))
+    np.add.at(gq, s + 1, lam_k * th)
+    return g, gq
+
+
+def _heat_reg(q):
+    d2 = q[2:] - 2.0 * q[1:-1] + q[:-2]
+    gq = np.zeros_like(q)
+    gq[2:] += 2.0 * d2
+    gq[1:-1] -= 4.0 * d2
+    gq[:-2] += 2.0 * d2
+    return float(np.sum(d2 * d2)), gq
+
+
+# ---------------------------------------------------------------------------
+# Poisson equation (Section 3.1)
+# ---------------------------------------------------------------------------
+# cell layout: finite volumes on [0,1]^d, value at cell centres; the Dirichlet
+# value b = 0 is imposed by quadratic extrapolation from the wall and the two
+# nearest centres: ghost = 8/3 b - 2 u_0 + 1/3 u_1.  Residual = discrete
+# Laplacian - f in every cell; loss w_res * h^d * sum r^2.
+# node layout: finite differences on the N+1 nodes per axis; residual at the
+# interior nodes; boundary nodes carry the term w_res * h^(d-1) * sum u^2
+# (the boundary integral of the displayed Poisson loss).
+
+def _poisson_ghost_pad(u, axis):
+    u0 = np.take(u, [0], axis=axis)
+    u1 = np.take(u, [1], axis=axis)
+    un = np.take(u, [-1], axis=axis)
+    un1 = np.take(u, [-2], axis=axis)
+    gl = -2.0 * u0 + u1 / 3.0
+    gr = -2.0 * un + un1 / 3.0
+    return np.concatenate([gl, u, gr], axis=axis)
+
+
+def poisson_residual(u, f, h, layout="cell"):
+    """Cell layout: Laplacian(u) - f in every cell.  Node: at interior nodes."""
+    d = u.ndim
+    if layout == "cell":
+        lap = np.zeros_like(u)
+        for ax in range(d):
+            p = _poisson_ghost_pad(u, ax)
+            n = u.shape[ax]
+            lap += (np.take(p, range(2, n + 2), axis=ax) - 2.0 * u
+                    + np.take(p, range(0, n), axis=ax)) / h[ax] ** 2
+        return lap - f
+    inner = tuple(slice(1, -1) for _ in range(d))
+    lap = np.zeros(tuple(s - 2 for s in u.shape))
+    for ax in range(d):
+        sp = [slice(1, -1)] * d
+        sm = [slice(1, -1)] * d
+        sp[ax] = slice(2, None)
+        sm[ax] = slice(0, -2)
+        lap += (u[tuple(sp)] - 2.0 * u[inner] + u[tuple(sm)]) / h[ax] ** 2
+    return lap - f[inner]
+
+
+def _poisson_boundary_mask(shape):
+    m = np.zeros(shape, dtype=bool)
+    for ax in range(len(shape)):
+        idx = [slice(None)] * len(shape)
+        idx[ax] = 0
+        m[tuple(idx)] = True
+        idx[ax] = -1
+        m[tuple(idx)] = True
+    return m
+
+
+def _poisson_adjoint(u, lam, h, layout):
+    d = u.ndim
+    g = np.zeros_like(u)
+    if layout == "cell":
+        for ax in range(d):
+            n = u.shape[ax]
+            c = lam / h[ax] ** 2
+            gp = np.zeros(tuple(s + 2 if a == ax else s for a, s in enumerate(u.shape)))
+            sl = [slice(None)] * d
+            sl[ax] = slice(2, n + 2)
+            gp[tuple(sl)] += c
+            sl[ax] = slice(0, n)
+            gp[tuple(sl)] += c
+            g += -2.0 * c
+            sl[ax] = slice(1, n + 1)
+            g += gp[tuple(sl)]
+            # ghost_l = -2 u_0 + u_1/3, ghost_r = -2 u_{n-1} + u_{n-2}/3
+            gl = np.take(gp, [0], axis=ax)
+            gr = np.take(gp, [n + 1], axis=ax)
+            for j, w in ((0, -2.0), (1, 1.0 / 3.0)):
+                sl = [slice(None)] * d
+                sl[ax] = slice(j, j + 1)
+                g[tuple(sl)] += w * gl
+                sl[ax] = slice(n - 1 - j, n - j)
+                g[tuple(sl)] += w * gr
+        return g
+    inner = tuple(slice(1, -1) for _ in range(d))
+    for ax in range(d):
+        c = lam / h[ax] ** 2
+        sp = [slice(1, -1)] * d
+        sm = [slice(1, -1)] * d
+        sp[ax] = slice(2, None)
+        sm[ax] = slice(0, -2)
+        g[tuple(sp)] += c
+        g[tuple(sm)] += c
+        g[inner] += -2.0 * c
+    return g
+
+
+# ---------------------------------------------------------------------------
+# Loss and gradient
+# ---------------------------------------------------------------------------
+
+def _data_term(p, u):
+    if p.meas_cell is None or len(p.meas_cell) == 0:
+        return 0.0, np.zeros_like(u)
+    flat = u.reshape(-1)
+    diff = flat[p.meas_cell] - p.meas_value
+    w = p.w_data / len(p.meas_cell)
+    g = np.zeros_like(flat)
+    np.add.at(g, p.meas_cell, 2.0 * w * diff)
+    return float(w * np.sum(diff * diff)), g.reshape(u.shape)
+
+
+def loss_terms(p, u, q=None):
+    """Loss components {"res", "data", "reg", "total"} of the composed field u."""
+    h = p.spacing()
+    dV = float(np.prod(h))
+    reg = 0.0
+    bnd = 0.0
+    if p.pde == "burgers":
+        r = burgers_residual(u, p.coef["nu"], h[0], h[1])
+    elif p.pde == "heat":
+        r = heat_residual(u, q, h[0], h[1], p.aux)
+        reg = p.w_reg * _heat_reg(q)[0]
+    elif p.pde == "poisson":
+        r = poisson_residual(u, p.coef["f"], h, p.layout)
+        if p.layout == "node":
+            hb = np.prod(h[1:]) if len(h) > 1 else 1.0
+            bnd = p.w_res * hb * float(np.sum(u[_poisson_boundary_mask(u.shape)] ** 2))
+    else:
+        raise ValueError(p.pde)
+    res = p.w_res * dV * float(np.sum(r * r)) + bnd
+    data, _ = _data_term(p, u)
+    return {"res": res, "data": data, "reg": reg, "total": res + data + reg}
+
+
+def loss_grad_fine(p, u, q=None):
+    """Loss terms and dL/du (and dL/dq for heat) at the composed fine field."""
+    h = p.spacing()
+    dV = float(np.prod(h))
+    terms = loss_terms(p, u, q)
+    gq = None
+    if p.pde == "burgers":
+        r = burgers_residual(u, p.coef["nu"], h[0], h[1])
+        g = _burgers_adjoint(u, 2.0 * p.w_res * dV * r, p.coef["nu"], h[0], h[1])
+    elif p.pde == "heat":
+        r = heat_residual(u, q, h[0], h[1], p.aux)
+        g, gq = _heat_adjoint(u, q, 2.0 * p.w_res * dV * r, h[0], h[1])
+        gq = gq + p.w_reg * _heat_reg(q)[1]
+    elif p.pde == "poisson":
+        r = poisson_residual(u, p.coef["f"], h, p.layout)
+        g = _poisson_adjoint(u, 2.0 * p.w_res * dV * r, h, p.layout)
+        if p.layout == "node":
+            hb = np.prod(h[1:]) if len(h) > 1 else 1.0
+            m = _poisson_boundary_mask(u.shape)
+            g = g + np.where(m, 2.0 * p.w_res * hb * u, 0.0)
+    else:
+        raise ValueError(p.pde)
+    _, gd = _data_term(p, u)
+    return terms, g + gd, gq
+
+
+def loss_grad_levels(p, levels, q=None):
+    """Loss terms and the gradient with respect to every level (and q)."""
+    u = compose(levels, p.layout)
+    terms, g, gq = loss_grad_fine(p, u, q)
+    return terms, chain_grad(g, len(levels), p.layout), gq
+
+
+# ---------------------------------------------------------------------------
+# Adam (Kingma and Ba, Algorithm 1)
+# ---------------------------------------------------------------------------
+
+def adam_step(x, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update at step t >= 1; returns new (x, m, v)."""
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mh = m / (1.0 - b1**t)
+    vh = v / (1.0 - b2**t)
+    return x - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+@dataclass
+class OracleState:
+    levels: list
+    m: list
+    v: list
+    q: np.ndarray = None
+    mq: np.ndarray = None
+    vq: np.ndarray = None
+    t: int = 0
+
+    @classmethod
+    def zeros_like_levels(cls, levels, q=None):
+        z = [np.zeros_like(a) for a in levels]
+        return cls([np.array(a, dtype=np.float64) for a in levels], z,
+                   [np.zeros_like(a) for a in levels],
+                   None if q is None else np.array(q, dtype=np.float64),
+                   None if q is None else np.zeros_like(q),
+                   None if q is None else np.zeros_like(q), 0)
+
+
+def oracle_step(p, st, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One mODIL optimiser step: loss and gradient at the current levels, then
+    Adam on every level and on q.  Returns the loss terms before the update."""
+    terms, grads, gq = loss_grad_levels(p, st.levels, st.q)
+    st.t += 1
+    for i, g in enumerate(grads):
+        st.levels[i], st.m[i], st.v[i] = adam_step(st.levels[i], st.m[i], st.v[i],
+                                                   g, st.t, lr, b1, b2, eps)
+    if st.q is not None:
+        st.q, st.mq, st.vq = adam_step(st.q, st.mq, st.vq, gq, st.t, lr, b1, b2, eps)
+    return terms
+
+
+# ---------------------------------------------------------------------------
+# Reference generators (test data only)
+# ---------------------------------------------------------------------------
+
+def burgers_explicit_solve(u0, nu, dx, t_out, cfl=0.4, bc="dirichlet"):
+    """March u_t + (u^2/2)_x = nu u_xx with forward Euler finite volumes.
+
+    Same flux as the residual (Engquist-Osher, zero convective flux through
+    the walls, odd viscous ghosts) or a periodic variant.  Returns the cell
+    averages at each time in ``t_out`` (linear interpolation between steps).
+    """
+    u = np.array(u0, dtype=np.float64)
+    t = 0.0
+    out = []
+    k = 0
+    t_out = list(t_out)
+    prev_t, prev_u = t, u.copy()
+    while k < len(t_out):
+        if t >= t_out[k]:
+            a = (t_out[k] - prev_t) / (t - prev_t) if t > prev_t else 1.0
+            out.append((1.0 - a) * prev_u + a * u)
+            k += 1
+            continue
+        umax = max(float(np.max(np.abs(u))), 1e-12)
+        dt = cfl * min(dx / umax, dx * dx / (2.0 * nu) if nu > 0 else np.inf)
+        if bc == "periodic":
+            ul = np.roll(u, 1)
+            ur = np.roll(u, -1)
+            Fe, _, _ = eo_flux(u, ur)
+            Fw = np.roll(Fe, 1)
+            lap = (ur - 2.0 * u + ul) / dx**2
+        else:
+            F = np.zeros(len(u) + 1)
+            F[1:-1], _, _ = eo_flux(u[:-1], u[1:])
+            Fe, Fw = F[1:], F[:-1]
+            ug = np.concatenate([[-u[0]], u, [-u[-1]]])
+            lap = (ug[2:] - 2.0 * u + ug[:-2]) / dx**2
+        prev_t, prev_u = t, u.copy()
+        u = u - dt * (Fe - Fw) / dx + dt * nu * lap
+        t += dt
+    return np.array(out)
+
+
+def heat_implicit_solve(u_init, nt, dt, dx, kfun, tol=1e-13, max_iter=200):
+    """Solve the heat residual rows to zero one time row after another.
+
+    Picard iteration: freeze k at the current iterate, solve the tridiagonal
+    linear system of the residual, repeat until the update is below tol.
+    ``kfun(u)`` returns the conductivity at face values u.
+    """
+    from scipy.linalg import solve_banded
+    nx = len(u_init)
+    u = np.zeros((nt, nx))
+    u[0] = u_init
+    for m in range(1, nt):
+        w = u[m - 1].copy()
+        for _ in range(max_iter):
+            wg = np.concatenate([[-w[0]], w, [-w[-1]]])
+            kf = kfun(0.5 * (wg[:-1] + wg[1:]))
+            kE, kW = kf[1:], kf[:-1]
+            c = dt / dx**2
+            ab = np.zeros((3, nx))
+            diag = 1.0 + c * (kE + kW)
+            diag[0] += c * kW[0]          # odd ghost on the left
+            diag[-1] += c * kE[-1]        # odd ghost on the right
+            ab[1] = diag
+            ab[0, 1:] = -c * kE[:-1]
+            ab[2, :-1] = -c * kW[1:]
+            wn = solve_banded((1, 1), ab, u[m - 1])
+            done = np.max(np.abs(wn - w)) < tol
+            w = wn
+            if done:
+                break
+        u[m] = w
+    return u

@@ -1,0 +1,180 @@
+"""Seeded synthetic inputs shared by the CUDA path's callers and the CPU oracle.
+
+This module draws random numbers and evaluates closed-form data profiles
+(initial conditions, analytic fields used as synthetic measurements).  It holds
+none of the method's arithmetic: no prolongation, no residual stencil, no loss,
+no gradient and no optimiser step.  Everything is a deterministic function of an
+integer seed (numpy PCG64 through ``np.random.default_rng``).
+
+Workload recipes follow the paper's problems (Section 3.2 Burgers
+reconstruction, Section 3.3 lid-driven cavity, Section 3.4 conductivity
+inference, Section 3.5 body shape) at the sizes of the configurations this
+library is measured on.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def make_rng(seed: int) -> np.random.Generator:
+    """PCG64 generator for an integer seed."""
+    return np.random.default_rng(int(seed))
+
+
+def level_shapes(shape, n_levels):
+    """Cells per axis on each level: N_i = N / 2^(i-1) (Section 2.2)."""
+    out = []
+    for i in range(n_levels):
+        s = tuple(int(n) >> i for n in shape)
+        if min(s) < 1 or any((int(n) >> i) << i != int(n) for n in shape):
+            raise ValueError(f"shape {shape} cannot be halved {n_levels - 1} times")
+        out.append(s)
+    return out
+
+
+def random_levels(shape, n_levels, n_fields, seed, fine_lo=-1.0, fine_hi=1.0,
+                  coarse_scale=0.5, dtype=np.float64):
+    """Random level values: list over fields of list over levels of arrays.
+
+    The fine level is uniform in [fine_lo, fine_hi]; coarser levels are
+    N(0, coarse_scale^2).  Values are rounded to ``dtype`` so that the FP32
+    device path and the FP64 oracle start from identical numbers.
+    """
+    rng = make_rng(seed)
+    shapes = level_shapes(shape, n_levels)
+    out = []
+    for _ in range(n_fields):
+        lv = []
+        for i, s in enumerate(shapes):
+            if i == 0:
+                a = rng.uniform(fine_lo, fine_hi, size=s)
+            else:
+                a = rng.normal(0.0, coarse_scale, size=s)
+            lv.append(a.astype(dtype).astype(np.float64))
+        out.append(lv)
+    return out
+
+
+def measurement_cells(n_cells, n_meas, seed):
+    """Distinct random flat cell indices (sampling without replacement)."""
+    rng = make_rng(seed)
+    return np.sort(rng.choice(int(n_cells), size=int(n_meas), replace=False)).astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# Viscous Burgers (space-time, x in [-1, 1], t in [0, 1])
+# --------------------------------------------------------------------------
+
+BURGERS_X = (-1.0, 1.0)
+BURGERS_T = (0.0, 1.0)
+
+
+def burgers_ic_amplitudes(seed, n_modes=4, sigma=0.5):
+    """Amplitudes a_k ~ N(0, sigma^2) of the initial condition."""
+    return make_rng(seed).normal(0.0, sigma, size=n_modes)
+
+
+def burgers_ic(x, amps):
+    """u(x, 0) = sum_k a_k sin(k pi (x + 1) / 2); zero at x = -1 and x = 1."""
+    x = np.asarray(x, dtype=np.float64)
+    u = np.zeros_like(x)
+    for k, a in enumerate(amps, start=1):
+        u += a * np.sin(k * math.pi * (x + 1.0) / 2.0)
+    return u
+
+
+def burgers_batch_instance(i, base_seed=0):
+    """Per-instance draw for the batched Burgers workload (512 instances).
+
+    Returns (nx, nt, nu, seed): N_x, N_t uniform in {64, 128, 256, 512},
+    nu log-uniform in [1e-3, 1e-1].
+    """
+    rng = make_rng(1_000_003 * (base_seed + 1) + i)
+    sizes = np.array([64, 128, 256, 512])
+    nx = int(rng.choice(sizes))
+    nt = int(rng.choice(sizes))
+    nu = float(10.0 ** rng.uniform(-3.0, -1.0))
+    return nx, nt, nu, int(rng.integers(0, 2**31 - 1))
+
+
+def burgers_smooth_field(nt, nx, amps, nu):
+    """Closed-form smooth space-time field used as synthetic Burgers data.
+
+    Each sine mode decays with its heat-equation rate, u = sum_k a_k
+    exp(-nu (k pi / 2)^2 t) sin(k pi (x+1)/2), sampled at cell centres.  It
+    is smooth, vanishes at the walls and starts at the Burgers initial
+    condition; it is a data profile, not a solution of the discrete problem.
+    """
+    dx = 2.0 / nx
+    dt = 1.0 / nt
+    x = -1.0 + (np.arange(nx) + 0.5) * dx
+    t = (np.arange(nt) + 0.5) * dt
+    u = np.zeros((nt, nx))
+    for k, a in enumerate(amps, start=1):
+        lam = nu * (k * math.pi / 2.0) ** 2
+        u += a * np.exp(-lam * t)[:, None] * np.sin(k * math.pi * (x + 1.0) / 2.0)[None, :]
+    return u
+
+
+# --------------------------------------------------------------------------
+# Heat conduction with unknown conductivity (x, t in [0, 1])
+# --------------------------------------------------------------------------
+
+HEAT_KNODES = 32
+
+
+def heat_g(x):
+    """g(x) = exp(-50 (x - 1/2)^2) (Section 3.4)."""
+    return np.exp(-50.0 * (np.asarray(x, dtype=np.float64) - 0.5) ** 2)
+
+
+def heat_ic(nx):
+    """Initial temperature u(x, 0) = g(x) - g(0) at the nx cell centres."""
+    x = (np.arange(nx) + 0.5) / nx
+    return heat_g(x) - heat_g(0.0)
+
+
+def heat_k_true(u):
+    """Reference conductivity k(u) = 0.02 exp(-20 (u - 1/2)^2) (Section 3.4)."""
+    u = np.asarray(u, dtype=np.float64)
+    return 0.02 * np.exp(-20.0 * (u - 0.5) ** 2)
+
+
+def heat_linear_series(nt, nx, k0=0.02, n_modes=64):
+    """Closed-form solution of u_t = k0 u_xx, u(0)=u(1)=0, u(x,0)=g(x)-g(0).
+
+    Sine series with coefficients from a 4096-point midpoint quadrature, sampled
+    at cell centres x_i = (i+1/2)/nx and rows t_n = (n+1/2)/nt.  Used as a
+    smooth synthetic temperature record of the right shape and magnitude.
+    """
+    xq = (np.arange(4096) + 0.5) / 4096
+    f = heat_g(xq) - heat_g(0.0)
+    x = (np.arange(nx) + 0.5) / nx
+    t = (np.arange(nt) + 0.5) / nt
+    u = np.zeros((nt, nx))
+    for n in range(1, n_modes + 1):
+        b = 2.0 * np.mean(f * np.sin(n * math.pi * xq))
+        u += b * np.exp(-k0 * (n * math.pi) ** 2 * t)[:, None] * np.sin(n * math.pi * x)[None, :]
+    return u
+
+
+def heat_measurements(nt, nx, frac=0.05, sigma=1e-3, seed=2, field=None):
+    """5 % of cells with Gaussian noise of standard deviation sigma.
+
+    ``field`` is the (nt, nx) temperature record to sample; by default the
+    closed-form constant-conductivity series.  Returns (cells, values).
+    """
+    if field is None:
+        field = heat_linear_series(nt, nx)
+    n = nt * nx
+    m = int(round(frac * n))
+    cells = measurement_cells(n, m, seed)
+    noise = make_rng(seed + 7919).normal(0.0, sigma, size=m)
+    return cells, field.reshape(-1)[cells] + noise
+
+
+def heat_k_init(value=0.02, n=HEAT_KNODES):
+    """Initial conductivity nodes q_j (uniform value)."""
+    return np.full(n, value, dtype=np.float64)

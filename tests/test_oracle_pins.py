@@ -1,0 +1,418 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with itself: each test checks a printed
+value, a closed form, a convergence order, an invariant or a finite-difference
+derivative, chosen so that a dropped term, a wrong sign or index, or a
+transposed operand in the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2303_04679_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden_matrices():
+    mats = {}
+    cur = None
+    with open(os.path.join(GOLDEN, "interp_matrices.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith(("node", "cell")):
+                parts = line.split()
+                num, den = parts[-1].split("/")
+                cur = (parts[0], parts[1])
+                mats[cur] = [float(num) / float(den), []]
+            else:
+                mats[cur][1].append([float(x) for x in line.split()])
+    return {k: v[0] * np.array(v[1]) for k, v in mats.items()}
+
+
+# --------------------------------------------------------------------------
+# Interpolation operators and the decomposition (Section 2.2)
+# --------------------------------------------------------------------------
+
+def test_interp_matrices_match_printed():
+    """The node and cell matrices for grids 8 -> 4 -> 2 printed in Section 2.2."""
+    g = _read_golden_matrices()
+    np.testing.assert_array_equal(o.interp_matrix(4, "node"), g[("node", "T1")])
+    np.testing.assert_array_equal(o.interp_matrix(2, "node"), g[("node", "T2")])
+    np.testing.assert_array_equal(o.interp_matrix(4, "cell"), g[("cell", "T1")])
+    np.testing.assert_array_equal(o.interp_matrix(2, "cell"), g[("cell", "T2")])
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 16, 64])
+def test_cell_interp_reproduces_linear_functions(n):
+    """Linear interpolation/extrapolation is exact on linear data (closed form)."""
+    xc = (np.arange(n) + 0.5) / n
+    xf = (np.arange(2 * n) + 0.5) / (2 * n)
+    a, b = 0.37, -1.9
+    np.testing.assert_allclose(o.interp_matrix(n) @ (a * xc + b), a * xf + b, rtol=0, atol=1e-14)
+    # rows sum to one: constants are preserved
+    np.testing.assert_allclose(o.interp_matrix(n).sum(axis=1), 1.0, atol=1e-15)
+
+
+def test_single_cell_level_is_injected():
+    np.testing.assert_array_equal(o.interp_matrix(1), [[1.0], [1.0]])
+
+
+def test_tensor_product_prolongation_bilinear_exact():
+    """2-D and 3-D prolongation reproduce bilinear/trilinear data exactly."""
+    for shape in [(4, 8), (2, 4, 8)]:
+        grids_c = np.meshgrid(*[(np.arange(n) + 0.5) / n for n in shape], indexing="ij")
+        grids_f = np.meshgrid(*[(np.arange(2 * n) + 0.5) / (2 * n) for n in shape], indexing="ij")
+        fc = 1.0 + sum((k + 1) * g for k, g in enumerate(grids_c)) + 0.5 * grids_c[0] * grids_c[-1]
+        ff = 1.0 + sum((k + 1) * g for k, g in enumerate(grids_f)) + 0.5 * grids_f[0] * grids_f[-1]
+        np.testing.assert_allclose(o.prolong(fc), ff, atol=1e-13)
+
+
+@pytest.mark.parametrize("layout,shape,L", [("cell", (16, 32), 4), ("cell", (8, 8, 16), 4),
+                                            ("node", (16, 16), 3), ("cell", (64,), 7)])
+def test_adjoint_identity_every_level_pair_and_chain(layout, shape, L):
+    """<T x, y> = <x, T^T y> for every level pair and <M x, y> = <x, M^T y>."""
+    rng = np.random.default_rng(1)
+    shapes = o.level_shapes(shape, L, layout)
+    for i in range(L - 1):
+        x = rng.normal(size=shapes[i + 1])
+        y = rng.normal(size=shapes[i])
+        lhs = np.vdot(o.prolong(x, layout), y)
+        rhs = np.vdot(x, o.restrict(y, layout))
+        assert abs(lhs - rhs) <= 1e-14 * (abs(lhs) + np.linalg.norm(x) * np.linalg.norm(y))
+    xs = [rng.normal(size=s) for s in shapes]
+    y = rng.normal(size=shapes[0])
+    lhs = np.vdot(o.compose(xs, layout), y)
+    rhs = sum(np.vdot(a, b) for a, b in zip(xs, o.chain_grad(y, L, layout)))
+    assert abs(lhs - rhs) <= 1e-13 * max(1.0, abs(lhs))
+
+
+@pytest.mark.parametrize("layout", ["cell", "node"])
+def test_horner_equals_explicit_sum(layout):
+    """The Horner form of M_L equals its explicit sum (Section 2.2)."""
+    rng = np.random.default_rng(2)
+    shapes = o.level_shapes((32, 32), 5, layout)
+    lv = [rng.normal(size=s) for s in shapes]
+    np.testing.assert_allclose(o.compose(lv, layout), o.compose_explicit(lv, layout), atol=1e-12)
+
+
+def test_one_level_is_plain_odil():
+    """L = 1: the decomposition is the identity and the gradient is dL/du."""
+    rng = np.random.default_rng(3)
+    u = rng.normal(size=(16, 16))
+    np.testing.assert_array_equal(o.compose([u]), u)
+    p = _burgers_problem((16, 16), 1, seed=3)
+    t1, g1, _ = o.loss_grad_levels(p, [u])
+    t2, g2, _ = o.loss_grad_fine(p, u)
+    assert t1["total"] == t2["total"]
+    np.testing.assert_array_equal(g1[0], g2)
+
+
+# --------------------------------------------------------------------------
+# Burgers (Section 3.2; viscous variant)
+# --------------------------------------------------------------------------
+
+def _burgers_problem(shape, L, seed=0, nu=0.01, n_meas=20):
+    nt, nx = shape
+    cells = inputs.measurement_cells(nt * nx, n_meas, seed)
+    vals = np.random.default_rng(seed + 1).normal(size=n_meas)
+    return o.Problem("burgers", shape, L, coef={"nu": nu}, w_res=1.0, w_data=1.0,
+                     meas_cell=cells, meas_value=vals)
+
+
+def _burgers_exact(x, t, A=0.7):
+    u = A * np.sin(math.pi * x) * np.exp(-t)
+    ut = -u
+    ux = A * math.pi * np.cos(math.pi * x) * np.exp(-t)
+    uxx = -(math.pi**2) * u
+    return u, ut, ux, uxx
+
+
+def test_burgers_residual_consistent_with_pde_first_order():
+    """Residual of a smooth field -> u_t + u u_x - nu u_xx at first order."""
+    nu = 0.05
+    errs = []
+    for n in (32, 64, 128, 256):
+        dt, dx = 1.0 / n, 2.0 / n
+        x = -1.0 + (np.arange(n) + 0.5) * dx
+        t = (np.arange(n) + 0.5) * dt
+        X, Tm = np.meshgrid(x, t)
+        u, ut, ux, uxx = _burgers_exact(X, Tm)
+        r = o.burgers_residual(u, nu, dt, dx)
+        R = (ut + u * ux - nu * uxx)[1:]
+        errs.append(np.max(np.abs(r - R)))
+    rates = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(1.7 < q < 2.3 for q in rates), (errs, rates)
+
+
+def test_burgers_constant_field_closed_form():
+    """Constant c: interior residual 0; wall cells see the zero wall flux and ghost."""
+    n, c, nu = 16, 0.8, 0.03
+    dt, dx = 1.0 / n, 2.0 / n
+    r = o.burgers_residual(np.full((n, n), c), nu, dt, dx)
+    np.testing.assert_allclose(r[:, 1:-1], 0.0, atol=1e-12)
+    np.testing.assert_allclose(r[:, 0], c * c / (2 * dx) + 2 * nu * c / dx**2, rtol=1e-13)
+    np.testing.assert_allclose(r[:, -1], -c * c / (2 * dx) + 2 * nu * c / dx**2, rtol=1e-13)
+
+
+def test_burgers_mass_balance_of_residual():
+    """sum_i r^n_i dx = (M^n - M^{n-1})/dt + 2 nu (u_0 + u_{N-1})/dx (telescoping)."""
+    rng = np.random.default_rng(5)
+    n, nu = 24, 0.02
+    dt, dx = 1.0 / n, 2.0 / n
+    u = rng.normal(size=(n, n))
+    r = o.burgers_residual(u, nu, dt, dx)
+    M = u.sum(axis=1) * dx
+    rhs = (M[1:] - M[:-1]) / dt + 2 * nu * (u[1:, 0] + u[1:, -1]) / dx
+    np.testing.assert_allclose(r.sum(axis=1) * dx, rhs, rtol=1e-11, atol=1e-11)
+
+
+def test_burgers_implicit_step_dissipates_energy():
+    """A row solved to zero residual has no more energy than the row before."""
+    from scipy.optimize import root
+    rng = np.random.default_rng(6)
+    n, nu = 32, 0.01
+    dx, dt = 2.0 / n, 0.05
+    x = -1.0 + (np.arange(n) + 0.5) * dx
+    for trial in range(5):
+        prev = inputs.burgers_ic(x, rng.normal(0, 0.5, 4))
+        sol = root(lambda w: o.burgers_residual(np.vstack([prev, w]), nu, dt, dx)[0],
+                   prev, method="hybr", tol=1e-13)
+        assert sol.success
+        assert np.sum(sol.x**2) <= np.sum(prev**2) + 1e-12
+
+
+def test_burgers_explicit_solver_invariants():
+    """Explicit solver: periodic mass conserved; Dirichlet energy non-increasing."""
+    n = 64
+    dx = 2.0 / n
+    x = -1.0 + (np.arange(n) + 0.5) * dx
+    u0 = inputs.burgers_ic(x, inputs.burgers_ic_amplitudes(11))
+    ts = np.linspace(0.0, 1.0, 21)
+    per = o.burgers_explicit_solve(u0 + 0.3, 0.01, dx, ts, bc="periodic")
+    np.testing.assert_allclose(per.sum(axis=1), (u0 + 0.3).sum(), rtol=1e-12)
+    dirich = o.burgers_explicit_solve(u0, 0.01, dx, ts)
+    E = np.sum(dirich**2, axis=1)
+    assert np.all(np.diff(E) <= 1e-12)
+
+
+# --------------------------------------------------------------------------
+# Heat with unknown conductivity (Section 3.4)
+# --------------------------------------------------------------------------
+
+def test_conductivity_interpolation_closed_form():
+    rng = np.random.default_rng(7)
+    q = rng.uniform(0.01, 0.03, 32)
+    nodes = np.arange(32) / 31.0
+    k, dk, _, _ = o.heat_conductivity(nodes[:-1] + 1e-15, q)
+    np.testing.assert_allclose(k, q[:-1], atol=1e-15)
+    # linear between nodes: midpoint is the mean, slope is the difference quotient
+    mid = (nodes[:-1] + nodes[1:]) / 2
+    k, dk, _, _ = o.heat_conductivity(mid, q)
+    np.testing.assert_allclose(k, (q[:-1] + q[1:]) / 2, atol=1e-15)
+    np.testing.assert_allclose(dk, 31 * (q[1:] - q[:-1]), rtol=1e-12)
+    # constant extrapolation outside [0, 1]
+    k, dk, _, _ = o.heat_conductivity(np.array([-0.5, 1.5, 1.0]), q)
+    np.testing.assert_allclose(k, [q[0], q[-1], q[-1]], atol=1e-15)
+    assert dk[0] == 0.0 and dk[1] == 0.0
+
+
+def test_heat_constant_k_is_textbook_implicit_euler():
+    rng = np.random.default_rng(8)
+    nt, nx, kap = 12, 16, 0.017
+    dt, dx = 1.0 / nt, 1.0 / nx
+    u = rng.uniform(-0.2, 1.2, size=(nt, nx))
+    init = rng.normal(size=nx)
+    r = o.heat_residual(u, np.full(32, kap), dt, dx, init)
+    ug = np.concatenate([-u[:, :1], u, -u[:, -1:]], axis=1)
+    lap = (ug[1:, 2:] - 2 * u[1:] + ug[1:, :-2]) / dx**2
+    np.testing.assert_allclose(r[1:], (u[1:] - u[:-1]) / dt - kap * lap, rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(r[0], (u[0] - init) / dt, rtol=1e-14)
+
+
+def test_heat_residual_consistent_with_pde():
+    """Smooth k and a smooth field: residual -> u_t - (k(u) u_x)_x.
+
+    Backward Euler in t (first order) plus central faces in x (second order):
+    the error ratio per halving lies between 2 and 4 and never stalls."""
+    kf = inputs.heat_k_true
+
+    def dk(v):
+        return kf(v) * (-40.0) * (v - 0.5)
+
+    errs = []
+    for n in (32, 64, 128, 256):
+        dt, dx = 1.0 / n, 1.0 / n
+        x = (np.arange(n) + 0.5) * dx
+        t = (np.arange(n) + 0.5) * dt
+        X, Tm = np.meshgrid(x, t)
+        u = 0.8 * np.sin(math.pi * X) * np.exp(-Tm / 2)
+        ut = -u / 2
+        ux = 0.8 * math.pi * np.cos(math.pi * X) * np.exp(-Tm / 2)
+        uxx = -(math.pi**2) * u
+        r = o.heat_residual(u, None, dt, dx, u[0], kfun=kf)
+        R = ut - dk(u) * ux**2 - kf(u) * uxx
+        errs.append(np.max(np.abs(r[1:] - R[1:])))
+        assert np.max(np.abs(r[0])) == 0.0
+    rates = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(1.8 < q < 4.2 for q in rates), (errs, rates)
+
+
+def test_heat_implicit_solve_zeroes_residual():
+    n = 32
+    dt, dx = 1.0 / n, 1.0 / n
+    init = inputs.heat_ic(n)
+    u = o.heat_implicit_solve(init, n, dt, dx, inputs.heat_k_true)
+    r = o.heat_residual(u, None, dt, dx, init, kfun=inputs.heat_k_true)
+    assert np.max(np.abs(r)) < 1e-9
+    # maximum principle of the implicit scheme: temperature stays within the initial range
+    assert u.max() <= init.max() + 1e-12 and u.min() >= -1e-12
+
+
+# --------------------------------------------------------------------------
+# Poisson (Section 3.1): exact discrete solution and second-order convergence
+# --------------------------------------------------------------------------
+
+def _u_ref(x):
+    v = np.prod([5 * (1 - xi) * xi for xi in x], axis=0)
+    return (v**5 / (1 + v**5)) ** 0.2
+
+
+@pytest.mark.parametrize("layout", ["cell", "node"])
+def test_poisson_paper_reference_is_exact_discrete_solution(layout):
+    n = 32
+    h = (1.0 / n, 1.0 / n)
+    if layout == "cell":
+        c = (np.arange(n) + 0.5) / n
+    else:
+        c = np.arange(n + 1) / n
+    X = np.meshgrid(c, c, indexing="ij")
+    u = _u_ref(X)
+    z = np.zeros_like(u)
+    f = o.poisson_residual(u, z, h, layout)
+    if layout == "node":
+        full = np.zeros_like(u)
+        full[1:-1, 1:-1] = f
+        f = full
+    p = o.Problem("poisson", (n, n), 1, layout=layout, coef={"f": f})
+    assert o.loss_terms(p, u)["total"] < 1e-24
+
+
+def _quadratic_minimiser(p, shape):
+    """Minimiser of a quadratic loss from its exact gradient: H u = -g(0)."""
+    n = int(np.prod(shape))
+    g0 = o.loss_grad_fine(p, np.zeros(shape))[1].reshape(-1)
+    H = np.empty((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        H[:, j] = o.loss_grad_fine(p, e.reshape(shape))[1].reshape(-1) - g0
+    return np.linalg.solve(H, -g0).reshape(shape)
+
+
+@pytest.mark.parametrize("layout", ["cell", "node"])
+def test_poisson_minimiser_converges_second_order(layout):
+    """Manufactured u = sin(pi x) sin(pi y): the loss minimiser is O(h^2) accurate."""
+    errs = []
+    for n in (8, 16, 32):
+        h = (1.0 / n, 1.0 / n)
+        c = (np.arange(n) + 0.5) / n if layout == "cell" else np.arange(n + 1) / n
+        X, Y = np.meshgrid(c, c, indexing="ij")
+        ue = np.sin(math.pi * X) * np.sin(math.pi * Y)
+        f = -2 * math.pi**2 * ue
+        p = o.Problem("poisson", (n, n), 1, layout=layout, coef={"f": f})
+        u = _quadratic_minimiser(p, ue.shape)
+        g = o.loss_grad_fine(p, u)[1]
+        assert np.max(np.abs(g)) < 1e-8
+        errs.append(np.max(np.abs(u - ue)))
+    rates = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(3.3 < q < 4.7 for q in rates), (errs, rates)
+
+
+# --------------------------------------------------------------------------
+# Gradients: central finite differences through levels, stencils and data
+# --------------------------------------------------------------------------
+
+def _fd_check(loss_fn, params, grads, h=1e-6, rtol=2e-6):
+    worst = 0.0
+    scale = max(np.max(np.abs(g)) for g in grads)
+    for a, g in zip(params, grads):
+        flat = a.reshape(-1)
+        gf = g.reshape(-1)
+        for j in range(flat.size):
+            old = flat[j]
+            step = h * max(1.0, abs(old))
+            flat[j] = old + step
+            lp = loss_fn()
+            flat[j] = old - step
+            lm = loss_fn()
+            flat[j] = old
+            fd = (lp - lm) / (2 * step)
+            worst = max(worst, abs(fd - gf[j]) / scale)
+    assert worst < rtol, worst
+
+
+def test_burgers_gradient_finite_differences():
+    p = _burgers_problem((8, 16), 3, seed=9, nu=0.04, n_meas=12)
+    lv = inputs.random_levels((8, 16), 3, 1, seed=9)[0]
+    _, grads, _ = o.loss_grad_levels(p, lv)
+    _fd_check(lambda: o.loss_terms(p, o.compose(lv))["total"], lv, grads)
+
+
+def test_heat_gradient_finite_differences():
+    nt, nx = 8, 16
+    rng = np.random.default_rng(10)
+    cells = inputs.measurement_cells(nt * nx, 10, 10)
+    p = o.Problem("heat", (nt, nx), 3, w_res=1.0, w_data=2.0, w_reg=0.3,
+                  meas_cell=cells, meas_value=rng.uniform(0, 1, 10), aux=inputs.heat_ic(nx))
+    lv = inputs.random_levels((nt, nx), 3, 1, seed=10, fine_lo=-0.1, fine_hi=1.1,
+                              coarse_scale=0.1)[0]
+    q = rng.uniform(0.01, 0.03, 32)
+    _, grads, gq = o.loss_grad_levels(p, lv, q)
+    _fd_check(lambda: o.loss_terms(p, o.compose(lv), q)["total"], lv + [q], grads + [gq])
+
+
+def test_poisson_gradient_finite_differences():
+    rng = np.random.default_rng(11)
+    for layout in ("cell", "node"):
+        n = 8
+        sh = (n, n) if layout == "cell" else (n + 1, n + 1)
+        f = rng.normal(size=sh)
+        p = o.Problem("poisson", (n, n), 3, layout=layout, coef={"f": f})
+        lv = [rng.normal(size=s) for s in o.level_shapes((n, n), 3, layout)]
+        _, grads, _ = o.loss_grad_levels(p, lv)
+        _fd_check(lambda: o.loss_terms(p, o.compose(lv, layout))["total"], lv, grads)
+
+
+# --------------------------------------------------------------------------
+# Adam
+# --------------------------------------------------------------------------
+
+def test_adam_constant_gradient_closed_form():
+    """Constant g: bias correction gives m_hat = g, v_hat = g^2 at every step,
+    so x_t = x_0 - t lr g / (|g| + eps)."""
+    rng = np.random.default_rng(12)
+    g = rng.normal(size=50) * np.logspace(-9, 2, 50)
+    x0 = rng.normal(size=50)
+    x, m, v = x0.copy(), np.zeros(50), np.zeros(50)
+    lr, eps = 5e-3, 1e-8
+    for t in range(1, 8):
+        x, m, v = o.adam_step(x, m, v, g, t, lr, eps=eps)
+        np.testing.assert_allclose(x, x0 - t * lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-15)
+
+
+def test_adam_two_steps_by_hand():
+    """Two steps with g = 1 then g = -2 (b1 = 0.9, b2 = 0.999, eps = 0)."""
+    x, m, v = np.array([0.0]), np.array([0.0]), np.array([0.0])
+    x, m, v = o.adam_step(x, m, v, np.array([1.0]), 1, 0.1, eps=0.0)
+    assert abs(x[0] + 0.1) < 1e-15
+    x, m, v = o.adam_step(x, m, v, np.array([-2.0]), 2, 0.1, eps=0.0)
+    # m = 0.9*0.1 + 0.1*(-2) = -0.11, mhat = -0.11/0.19; v = 0.999*0.001 + 0.001*4
+    mh = -0.11 / 0.19
+    vh = (0.000999 + 0.004) / (1 - 0.999**2)
+    assert abs(x[0] - (-0.1 - 0.1 * mh / math.sqrt(vh))) < 1e-14
