@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Throughput of one mODIL optimiser step on the GPU (and of the CPU oracle).
+
+Workload: conductivity inference in 1-D transient heat conduction
+(u_t = (k(u) u_x)_x, paper Section 3.4) on a 512 (x) by 512 (t) grid in FP32,
+7 multigrid levels, the temperature plus 32 conductivity nodes as unknowns,
+5 % of the cells measured with Gaussian noise sigma = 1e-3, a second-difference
+regulariser on the nodes, Adam.  A step is one loss+gradient evaluation of
+every level followed by the Adam update of every level and of the nodes.
+
+Timing: W untimed warm-up steps, then K steps each timed with CUDA events on
+the problem's stream; before every timed step a 256 MiB buffer is written so
+the step starts with a cold L2 (the working set, 11 MB, would otherwise stay
+resident).  One JSON line is printed by rank 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl modil|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mODIL loss+grad evals/s"
+UNIT = "evals/s"
+WORKLOAD = "heat conductivity inference, 512x512 space-time, 7 levels, FP32, Adam"
+ALG_BYTES_PER_PARAM = 32     # p, m (FP32) and v (FP64), read and written
+ALG_BYTES_PER_MEAS = 8       # cell index + value
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="modil", choices=["modil", "reference"])
+    ap.add_argument("--tile", default="16x64")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=50)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def workload_sizes(w):
+    nt, nx = w["shape"]
+    params = sum((nt >> l) * (nx >> l) for l in range(w["n_levels"])) + len(w["knodes"])
+    fine = nt * nx
+    return params, fine
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        return max(n) if n else 1
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_setup(w):
+    import oracle as o
+    from paper_2303_04679_gb300 import inputs
+    f32 = lambda a: np.asarray(a, np.float64).astype(np.float32).astype(np.float64)  # noqa: E731
+    prob = o.Problem("heat", w["shape"], w["n_levels"], w_res=w["w_res"], w_data=w["w_data"],
+                     w_reg=w["w_reg"], meas_cell=w["meas_cell"], meas_value=f32(w["meas_value"]),
+                     aux=f32(w["aux"]))
+    levels = [np.zeros(s) for s in inputs.level_shapes(w["shape"], w["n_levels"])]
+    st = o.OracleState.zeros_like_levels(levels, f32(w["knodes"]))
+    return o, prob, st
+
+
+def time_oracle(w, seconds, max_steps=None):
+    o, prob, st = oracle_setup(w)
+    o.oracle_step(prob, st, w["lr"])  # warm-up (imports, BLAS pools)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        o.oracle_step(prob, st, w["lr"])
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_steps and n >= max_steps):
+            break
+    return n, el
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    # each timed step is one full oracle step on the whole workload; the run
+    # stops early after ~150 s and reports the steps it timed
+    _, _, _ = oracle_setup(w)
+    o, prob, st = oracle_setup(w)
+    for _ in range(max(args.warmup, 1) if args.warmup < 3 else 3):
+        o.oracle_step(prob, st, w["lr"])
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.steps):
+        o.oracle_step(prob, st, w["lr"])
+        n += 1
+        if time.perf_counter() - t0 > 150.0:
+            break
+    el = time.perf_counter() - t0
+    value = n / el
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} full oracle Adam steps of the workload ({cpu_model()})"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def make_desc(modil, w, tile):
+    ty, tx = (int(v) for v in tile.split("x"))
+    return modil.Desc("heat", w["shape"], w["n_levels"], "f32", w_res=w["w_res"],
+                      w_data=w["w_data"], w_reg=w["w_reg"], meas_cell=w["meas_cell"],
+                      meas_value=w["meas_value"], aux=w["aux"], knodes=w["knodes"], lr=w["lr"],
+                      tile=(ty, tx))
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def main():
+    args = parse()
+    from paper_2303_04679_gb300 import inputs
+    w = inputs.heat_workload()
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2303_04679_gb300 import modil
+
+    params, fine = workload_sizes(w)
+    n_meas = len(w["meas_cell"])
+    step_alg_bytes = params * ALG_BYTES_PER_PARAM + n_meas * ALG_BYTES_PER_MEAS
+    fine_alg_bytes = fine * ALG_BYTES_PER_PARAM + n_meas * ALG_BYTES_PER_MEAS
+
+    prob = modil.Problem(make_desc(modil, w, args.tile))
+    stream = prob.stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    launches = prob.launches_per_step()
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+
+    for _ in range(args.warmup):
+        flush_l2()
+        prob.step(1, read_loss=False)
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.25)
+    wall0 = time.perf_counter()
+    for a, b in evs:
+        flush_l2()
+        a.record(stream)
+        prob.step(1, read_loss=False)
+        b.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    terms = prob.eval_loss()[0]
+
+    # per-kernel device times of a step launched kernel by kernel (cold L2)
+    prof = []
+    for _ in range(max(1, args.profile_steps)):
+        flush_l2()
+        torch.cuda.synchronize()
+        prof.append(prob.profile_step())
+    prof = np.array(prof)
+    kern_ms = prof.mean(axis=0)
+    names = ["fine_tile_fused"] + [f"restrict_adam_L{l + 1}" for l in range(1, w["n_levels"])] + ["finalize"]
+    dom = int(np.argmax(kern_ms))
+    peak, peak_kind = measured_peak()
+    dom_bytes = fine_alg_bytes if dom == 0 else None
+    achieved = dom_bytes / (kern_ms[dom] * 1e-3) / 1e9 if dom_bytes else None
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            from paper_2303_04679_gb300 import build as bld
+            tj = json.load(open(tfile))
+            if tj.get("source_hash") == bld.source_hash():
+                traffic = tj.get("fine_tile_fused_bytes_per_launch")
+        except Exception:
+            traffic = None
+    prob.close()
+
+    # end to end through the public API, host buffers, copies inside the timed region
+    e2e_steps = min(args.steps, 2000)
+    levels0 = [torch.zeros(s, dtype=torch.float32).pin_memory()
+               for s in inputs.level_shapes(w["shape"], w["n_levels"])]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p2 = modil.Problem(make_desc(modil, w, args.tile))
+    for lvl, a in enumerate(levels0):
+        modil._check(modil.LIB.modil_write_level(p2._h, 0, 0, lvl, a.data_ptr(),
+                                                 a.numel() * 4, 0))
+    for _ in range(e2e_steps):
+        p2.step(1, read_loss=True)
+    field = p2.read_field()
+    e2e_s = time.perf_counter() - t0
+    p2.close()
+    h2d = (sum(a.numel() * 4 for a in levels0) + n_meas * 8 + w["shape"][1] * 4 +
+           len(w["knodes"]) * 4)
+    d2h = 32 * e2e_steps + field.nbytes
+
+    value = world * args.steps / (tot_ms * 1e-3)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(w["shape"]), "levels": w["n_levels"],
+                   "params": params, "measurements": n_meas, "tile": args.tile,
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "fine_cells_per_s": value * fine,
+        "effective_step_GBps": step_alg_bytes * value / world / 1e9,
+        "hbm_frac_step": step_alg_bytes * value / world / 1e9 / peak,
+        "step_ms_median": statistics.median(step_ms),
+        "wall_s": wall,
+        "loss_final": float(terms[0]),
+        "kernel_ms": {n: float(v) for n, v in zip(names, kern_ms)},
+        "roofline": {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "alg_bytes_per_launch": dom_bytes},
+        "clocks": clocks,
+        "gpu_launches": launches * args.steps,
+        "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+                "steps": e2e_steps, "note": "create + upload + steps with loss read back + field read"},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, el = time_oracle(w, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": n / el, "unit": UNIT, "cores": blas_threads(),
+                               "kind": "oracle",
+                               "sample": f"{n} full oracle Adam steps of the workload in {el:.1f} s "
+                                         f"({cpu_model()}, {os.cpu_count()} host cores)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * modil.h -- C ABI of the GB300 mODIL library (libmodil.so).
+ *
+ * mODIL (multiresolution Optimizing a DIscrete Loss) solves a PDE problem,
+ * forward or inverse, by minimising a discrete loss with a gradient-based
+ * optimiser.  The unknown field on the fine grid is the multigrid
+ * decomposition u = M_L(u_1, ..., u_L) = u_1 + T_1 (u_2 + ... T_{L-1} u_L)
+ * of per-level arrays u_i on grids N_i = N / 2^(i-1) (paper, Section 2.2,
+ * the two displayed forms of M_L); T_i is cell-based linear interpolation
+ * (Section 2.2, the 8x4 and 4x2 matrices).  The loss is the weighted sum of
+ * squared discrete residuals plus squared data mismatches plus regularisers
+ * (Section 2.1 displayed loss; Sections 3.2 and 3.4).  One optimiser step
+ * composes the field, evaluates the residuals, reduces the loss, runs the
+ * adjoint of the stencils and of the prolongations, and applies Adam
+ * (Section 2.1) to every level.  Everything in a step runs in this library's
+ * CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point:
+ *  - Return value: MODIL_OK or a negative modil_status.  No call aborts the
+ *    process.  modil_last_error() gives a message for the calling thread.
+ *  - Grids are row-major with the LAST axis fastest.  Space-time problems use
+ *    axes (t, x); 2-D problems (y, x); 3-D problems (z, y, x).
+ *  - Every pointer passed in stays owned by the caller.  modil_create copies
+ *    what it needs (measurements, coefficients, initial values) before
+ *    returning.
+ *  - The library's device memory is one arena.  The caller may supply it
+ *    (arena != NULL, at least modil_arena_bytes() bytes, 256-byte aligned,
+ *    e.g. a torch uint8 tensor) and then owns it; with arena == NULL the
+ *    library allocates it with cudaMalloc and modil_destroy frees it.
+ *  - Work is issued on the stream given to modil_create / modil_set_stream
+ *    (a cudaStream_t; NULL is the legacy default stream).  Calls that return
+ *    numbers to host memory synchronise that stream first; the others are
+ *    asynchronous.
+ *  - Device-side failures (non-finite loss) are latched in device memory and
+ *    reported as MODIL_ERR_NONFINITE by the next call that returns numbers.
+ */
+#ifndef MODIL_H
+#define MODIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct modil_problem modil_problem; /* opaque, library-owned */
+
+typedef enum {
+  MODIL_OK = 0,
+  MODIL_ERR_ARG = -1,         /* invalid argument or descriptor            */
+  MODIL_ERR_OOM = -2,         /* device or host allocation failed          */
+  MODIL_ERR_CUDA = -3,        /* a CUDA runtime call failed                */
+  MODIL_ERR_UNSUPPORTED = -4, /* valid request this build does not handle  */
+  MODIL_ERR_NONFINITE = -5,   /* loss became NaN or Inf                     */
+  MODIL_ERR_STATE = -6        /* call not valid in the problem's state      */
+} modil_status;
+
+/* PDE families (paper Section 3). */
+enum {
+  MODIL_PDE_BURGERS = 1, /* viscous Burgers u_t + (u^2/2)_x = nu u_xx, axes (t, x),
+                            x in [-1, 1], t in [0, 1]; Section 3.2 with viscosity   */
+  MODIL_PDE_HEAT = 2     /* u_t = (k(u) u_x)_x with unknown k, axes (t, x) on [0,1]^2;
+                            Section 3.4, the displayed implicit scheme              */
+};
+
+enum { MODIL_F32 = 0, MODIL_F64 = 1 };
+
+#define MODIL_MAX_LEVELS 10
+#define MODIL_MAX_FIELDS 5
+#define MODIL_MAX_KNODES 64
+
+/* Loss terms reported by the eval/step calls (doubles, in this order). */
+enum { MODIL_TERM_TOTAL = 0, MODIL_TERM_RES = 1, MODIL_TERM_DATA = 2, MODIL_TERM_REG = 3,
+       MODIL_NTERMS = 4 };
+
+typedef struct {
+  int pde;      /* MODIL_PDE_*                                                   */
+  int dtype;    /* MODIL_F32 or MODIL_F64: storage and stencil arithmetic       */
+  int ndim;     /* 2 for the space-time families                                */
+  int shape[3]; /* fine cells per axis, slowest first; unused entries 0         */
+  int n_levels; /* L >= 1; every axis must be divisible by 2^(L-1); 1 = ODIL    */
+  double coef[4]; /* BURGERS: coef[0] = nu.  HEAT: unused.                       */
+  double w_res;   /* residual weight: w_res * dV * sum r^2                       */
+  double w_data;  /* data weight: w_data / n_meas * sum (u - y)^2                */
+  double w_reg;   /* HEAT: w_reg * sum_j (q_{j+1} - 2 q_j + q_{j-1})^2           */
+  int n_meas;     /* number of measurements (0 allowed)                          */
+  const int32_t* meas_cell;  /* flat fine-grid cell index per measurement       */
+  const int32_t* meas_field; /* field index per measurement, or NULL (field 0)  */
+  const double* meas_value;  /* measured value                                  */
+  int n_aux;                 /* HEAT: initial temperature, one per x cell       */
+  const double* aux;
+  int n_knodes;              /* HEAT: conductivity nodes q_0..q_{K}, K+1 <= 64  */
+  const double* knodes;      /* initial q (copied)                              */
+  double adam_lr, adam_beta1, adam_beta2, adam_eps;
+  int tile[2];               /* fine tile (rows, cols); 0 = library default    */
+} modil_desc;
+
+/* Device bytes needed for a batch of n problems described by descs[0..n-1]. */
+modil_status modil_arena_bytes(const modil_desc* descs, int n, size_t* bytes);
+
+/* Create a batch of n >= 1 independent problems of one PDE family and dtype.
+ * All levels start at zero, Adam moments at zero, step count 0.
+ * arena: caller-owned device buffer of modil_arena_bytes() bytes or NULL.
+ * stream: cudaStream_t for all work of this problem.  */
+modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t arena_bytes,
+                          void* stream, modil_problem** out);
+
+/* Wait for the problem's stream, then free the problem (and the arena if the
+ * library allocated it).  NULL is a no-op. */
+void modil_destroy(modil_problem* p);
+
+modil_status modil_set_stream(modil_problem* p, void* stream);
+
+/* Number of instances, fields, levels and cells per axis of a level. */
+modil_status modil_level_shape(const modil_problem* p, int instance, int level, int shape[3]);
+
+/* Copy one level (field, level 0 = finest) in or out; bytes must equal the
+ * level size in the problem's dtype.  *_on_device selects device or host
+ * memory for src/dst.  Writing a level also resets nothing else.  */
+modil_status modil_write_level(modil_problem* p, int instance, int field, int level,
+                               const void* src, size_t bytes, int src_on_device);
+modil_status modil_read_level(modil_problem* p, int instance, int field, int level, void* dst,
+                              size_t bytes, int dst_on_device);
+/* Gradient dL/du_level from the last modil_eval_grad (or the last step). */
+modil_status modil_read_grad(modil_problem* p, int instance, int field, int level, void* dst,
+                             size_t bytes, int dst_on_device);
+/* Composed fine field M_L(u_1..u_L), computed on the device. */
+modil_status modil_read_field(modil_problem* p, int instance, int field, void* dst,
+                              size_t bytes, int dst_on_device);
+/* HEAT conductivity nodes q (doubles on the host) and their gradient. */
+modil_status modil_write_knodes(modil_problem* p, int instance, const double* q, int n);
+modil_status modil_read_knodes(modil_problem* p, int instance, double* q, int n);
+modil_status modil_read_kgrad(modil_problem* p, int instance, double* gq, int n);
+
+/* Loss of the current levels.  terms: n_instances * MODIL_NTERMS doubles on
+ * the host (synchronises), or NULL.  */
+modil_status modil_eval_loss(modil_problem* p, double* terms);
+/* Loss and gradient for every level (read with modil_read_grad). */
+modil_status modil_eval_grad(modil_problem* p, double* terms);
+/* n_steps Adam steps of every instance.  terms (nullable) receives the loss
+ * terms evaluated at the start of the last step.  Asynchronous when NULL. */
+modil_status modil_step(modil_problem* p, int n_steps, double* terms);
+/* Kernel launches one modil_step issues (the fused fine-tile kernel, one
+ * restriction+Adam kernel per coarser level, one finalising kernel). */
+modil_status modil_launches_per_step(const modil_problem* p, int* n);
+
+/* One Adam step issued kernel by kernel with a CUDA event between launches;
+ * ms[k] receives the device time of launch k (order as above).  Synchronises.
+ * max_kernels: capacity of ms; *n_kernels: launches timed. */
+modil_status modil_profile_step(modil_problem* p, float* ms, int max_kernels, int* n_kernels);
+
+/* Steps taken so far (the Adam step counter t). */
+modil_status modil_step_count(const modil_problem* p, long long* t);
+
+/* Zero the Adam moments and the step counter of every instance. */
+modil_status modil_reset_optimizer(modil_problem* p);
+
+/* Last error message of the calling thread ("" if none). */
+const char* modil_last_error(void);
+
+/* Library version string. */
+const char* modil_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MODIL_H */

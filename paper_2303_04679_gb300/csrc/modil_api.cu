@@ -1,0 +1,654 @@
+// C ABI of the mODIL library: problem planning, the device arena, uploads,
+// the per-step launch sequence (optionally captured once in a CUDA graph and
+// replayed) and read-back.  The declarations and their contracts are in
+// include/modil.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/modil.h"
+#include "launch.h"
+#include "modil_dev.cuh"
+
+using namespace modil;
+
+namespace {
+
+thread_local std::string g_err;
+
+modil_status fail(modil_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(MODIL_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct InstPlan {
+  int nlev = 1, nfield = 1, nk = 0;
+  int n[MODIL_MAXL][3] = {};
+  int nt[MODIL_MAXL][3] = {};
+  long long lev_size[MODIL_MAXL] = {};
+};
+
+// Everything derived from the descriptors before any device memory exists.
+struct Plan {
+  int n_inst = 0, pde = 0, dtype = 0, ndim = 2, nfield = 1, cfg = 1, max_lev = 1, nk = 0;
+  int npart = 2;
+  size_t esz = 4;
+  std::vector<InstPlan> inst;
+  std::vector<DevInst> dev;
+  std::vector<int> tile_inst[MODIL_MAXL];
+  long long n_param = 0;   // elements of one level arena (all instances, fields, levels)
+  long long n_fine = 0;    // elements of the composed-field scratch
+  long long n_k = 0;       // conductivity nodes over all instances
+  long long n_aux = 0;
+  // measurements, grouped into runs of equal (tile, cell)
+  std::vector<int> run_ptr, run_cell, run_field, run_beg;
+  std::vector<double> meas_val;
+  size_t pyr_elems = 0;
+  // arena offsets (bytes)
+  size_t o_p0, o_p1, o_m, o_v, o_g, o_uf, o_kq, o_km, o_kv, o_kg, o_aux, o_part, o_rptr, o_rcell,
+      o_rfield, o_rbeg, o_mval, o_inst, o_st, o_ti[MODIL_MAXL], total;
+};
+
+int find_cfg(int ty, int tx) {
+  for (int c = 0; c < kNumTileCfg; ++c)
+    if (kTileCfg[c][0] == ty && kTileCfg[c][1] == tx) return c;
+  return -1;
+}
+
+modil_status make_plan(const modil_desc* d, int n, Plan& P) {
+  if (!d || n < 1) return fail(MODIL_ERR_ARG, "descs is NULL or n < 1");
+  P = Plan();
+  P.n_inst = n;
+  P.pde = d[0].pde;
+  P.dtype = d[0].dtype;
+  P.ndim = d[0].ndim;
+  if (P.pde != MODIL_PDE_BURGERS && P.pde != MODIL_PDE_HEAT)
+    return fail(MODIL_ERR_UNSUPPORTED, "unknown pde " + std::to_string(P.pde));
+  if (P.dtype != MODIL_F32 && P.dtype != MODIL_F64) return fail(MODIL_ERR_ARG, "dtype");
+  if (P.ndim != 2) return fail(MODIL_ERR_UNSUPPORTED, "space-time families are 2-D");
+  P.esz = P.dtype == MODIL_F64 ? 8 : 4;
+  P.nfield = 1;
+  // tile configuration (same for the batch)
+  int ty = d[0].tile[0], tx = d[0].tile[1];
+  if (ty == 0 && tx == 0) { ty = 16; tx = 64; }
+  P.cfg = find_cfg(ty, tx);
+  if (P.cfg < 0) return fail(MODIL_ERR_ARG, "unsupported tile shape");
+  const int TY = kTileCfg[P.cfg][0], TX = kTileCfg[P.cfg][1];
+
+  P.inst.resize(n);
+  P.dev.resize(n);
+  long long off = 0, foff = 0, koff = 0, aoff = 0;
+  for (int i = 0; i < n; ++i) {
+    const modil_desc& q = d[i];
+    if (q.pde != P.pde || q.dtype != P.dtype || q.ndim != P.ndim)
+      return fail(MODIL_ERR_ARG, "a batch must share pde, dtype and ndim");
+    if (q.tile[0] != d[0].tile[0] || q.tile[1] != d[0].tile[1])
+      return fail(MODIL_ERR_ARG, "a batch must share the tile shape");
+    const int ny = q.shape[0], nx = q.shape[1];
+    if (ny < 1 || nx < 1) return fail(MODIL_ERR_ARG, "shape must be positive");
+    if (q.n_levels < 1 || q.n_levels > MODIL_MAXL) return fail(MODIL_ERR_ARG, "n_levels");
+    const int L = q.n_levels;
+    if ((ny % (1 << (L - 1))) || (nx % (1 << (L - 1))))
+      return fail(MODIL_ERR_ARG, "every axis must be divisible by 2^(n_levels-1)");
+    if ((long long)ny * nx > (1LL << 30)) return fail(MODIL_ERR_ARG, "grid too large");
+    if (P.pde == MODIL_PDE_BURGERS && ny < 2) return fail(MODIL_ERR_ARG, "Burgers needs >= 2 rows");
+    if (P.pde == MODIL_PDE_HEAT) {
+      if (q.n_aux != nx || !q.aux) return fail(MODIL_ERR_ARG, "heat needs aux[nx] (initial profile)");
+      if (q.n_knodes < 2 || q.n_knodes > MODIL_MAXK || !q.knodes)
+        return fail(MODIL_ERR_ARG, "heat needs 2..64 conductivity nodes");
+    }
+    if (q.n_meas < 0 || (q.n_meas > 0 && (!q.meas_cell || !q.meas_value)))
+      return fail(MODIL_ERR_ARG, "measurement arrays");
+    if (!(q.adam_lr >= 0) || !(q.adam_beta1 >= 0 && q.adam_beta1 < 1) ||
+        !(q.adam_beta2 >= 0 && q.adam_beta2 < 1) || !(q.adam_eps >= 0))
+      return fail(MODIL_ERR_ARG, "Adam parameters");
+    InstPlan& ip = P.inst[i];
+    DevInst& D = P.dev[i];
+    std::memset(&D, 0, sizeof(D));
+    ip.nlev = L;
+    ip.nfield = 1;
+    ip.nk = P.pde == MODIL_PDE_HEAT ? q.n_knodes : 0;
+    P.nk = std::max(P.nk, ip.nk);
+    P.max_lev = std::max(P.max_lev, L);
+    D.nlev = L;
+    D.nfield = 1;
+    D.nk = ip.nk;
+    D.ndim = 2;
+    for (int l = 0; l < L; ++l) {
+      ip.n[l][0] = 1;
+      ip.n[l][1] = ny >> l;
+      ip.n[l][2] = nx >> l;
+      const int tyl = l == 0 ? TY : kLevTY, txl = l == 0 ? TX : kLevTX;
+      ip.nt[l][0] = 1;
+      ip.nt[l][1] = (ip.n[l][1] + tyl - 1) / tyl;
+      ip.nt[l][2] = (ip.n[l][2] + txl - 1) / txl;
+      ip.lev_size[l] = (long long)ip.n[l][1] * ip.n[l][2];
+      for (int a = 0; a < 3; ++a) { D.n[l][a] = ip.n[l][a]; D.nt[l][a] = ip.nt[l][a]; }
+      D.tile_base[l] = (int)P.tile_inst[l].size();
+      const int ntl = ip.nt[l][1] * ip.nt[l][2];
+      for (int t = 0; t < ntl; ++t) P.tile_inst[l].push_back(i);
+      D.off[0][l] = off;
+      off += ip.lev_size[l];
+    }
+    D.fine_off[0] = foff;
+    foff += ip.lev_size[0];
+    D.k_off = koff;
+    koff += ip.nk;
+    D.aux_off = aoff;
+    aoff += (P.pde == MODIL_PDE_HEAT) ? nx : 0;
+    double dV;
+    if (P.pde == MODIL_PDE_BURGERS) {
+      D.h[0] = 1.0; D.h[1] = 1.0 / ny; D.h[2] = 2.0 / nx;
+    } else {
+      D.h[0] = 1.0; D.h[1] = 1.0 / ny; D.h[2] = 1.0 / nx;
+    }
+    dV = D.h[1] * D.h[2];
+    for (int c = 0; c < 4; ++c) D.coef[c] = q.coef[c];
+    D.w_res_dV = q.w_res * dV;
+    D.w_data_n = q.n_meas > 0 ? q.w_data / q.n_meas : 0.0;
+    D.w_reg = q.w_reg;
+    D.lr = q.adam_lr; D.b1 = q.adam_beta1; D.b2 = q.adam_beta2; D.eps = q.adam_eps;
+    // pyramid bound of this instance (unclipped worst case, clipped by level size)
+    {
+      long long hy = TY + 4, hx = TX + 4, tot = 0;
+      for (int l = 1; l < L; ++l) {
+        hy = std::min<long long>((hy + 7) / 2, ip.n[l][1]);
+        hx = std::min<long long>((hx + 7) / 2, ip.n[l][2]);
+        tot += hy * hx;
+      }
+      P.pyr_elems = std::max<size_t>(P.pyr_elems, (size_t)tot);
+    }
+  }
+  P.n_param = off;
+  P.n_fine = foff;
+  P.n_k = koff;
+  P.n_aux = aoff;
+  P.npart = 2 + P.nk;
+
+  // measurements -> runs sorted by (global fine tile, cell)
+  const int nft = (int)P.tile_inst[0].size();
+  struct M { int tile, cell, field; double val; };
+  std::vector<M> all;
+  for (int i = 0; i < n; ++i) {
+    const modil_desc& q = d[i];
+    const int ny = q.shape[0], nx = q.shape[1];
+    for (int k = 0; k < q.n_meas; ++k) {
+      const int c = q.meas_cell[k];
+      const int f = q.meas_field ? q.meas_field[k] : 0;
+      if (c < 0 || (long long)c >= (long long)ny * nx) return fail(MODIL_ERR_ARG, "measurement cell out of range");
+      if (f != 0) return fail(MODIL_ERR_ARG, "measurement field out of range");
+      if (!std::isfinite(q.meas_value[k])) return fail(MODIL_ERR_ARG, "measurement value not finite");
+      const int y = c / nx, x = c % nx;
+      const int t = P.dev[i].tile_base[0] + (y / TY) * P.inst[i].nt[0][2] + (x / TX);
+      all.push_back({t, c, f, q.meas_value[k]});
+    }
+  }
+  std::stable_sort(all.begin(), all.end(), [](const M& a, const M& b) {
+    if (a.tile != b.tile) return a.tile < b.tile;
+    if (a.field != b.field) return a.field < b.field;
+    return a.cell < b.cell;
+  });
+  P.run_ptr.assign(nft + 1, 0);
+  for (size_t k = 0; k < all.size(); ++k) {
+    const bool start = k == 0 || all[k].tile != all[k - 1].tile || all[k].cell != all[k - 1].cell ||
+                       all[k].field != all[k - 1].field;
+    if (start) {
+      P.run_cell.push_back(all[k].cell);
+      P.run_field.push_back(all[k].field);
+      P.run_beg.push_back((int)k);
+      P.run_ptr[all[k].tile + 1]++;
+    }
+    P.meas_val.push_back(all[k].val);
+  }
+  P.run_beg.push_back((int)all.size());
+  for (int t = 0; t < nft; ++t) P.run_ptr[t + 1] += P.run_ptr[t];
+
+  // arena layout
+  size_t o = 0;
+  auto take = [&](size_t bytes) { const size_t r = o; o = align256(o + std::max<size_t>(bytes, 1)); return r; };
+  P.o_p0 = take(P.esz * P.n_param);
+  P.o_p1 = take(P.esz * P.n_param);
+  P.o_m = take(P.esz * P.n_param);
+  P.o_v = take(8 * P.n_param);
+  P.o_g = take(P.esz * P.n_param);
+  P.o_uf = take(P.esz * P.n_fine);
+  P.o_kq = take(P.esz * P.n_k);
+  P.o_km = take(P.esz * P.n_k);
+  P.o_kv = take(8 * P.n_k);
+  P.o_kg = take(P.esz * P.n_k);
+  P.o_aux = take(P.esz * P.n_aux);
+  P.o_part = take(8 * (size_t)nft * P.npart);
+  P.o_rptr = take(4 * P.run_ptr.size());
+  P.o_rcell = take(4 * P.run_cell.size());
+  P.o_rfield = take(4 * P.run_field.size());
+  P.o_rbeg = take(4 * P.run_beg.size());
+  P.o_mval = take(P.esz * P.meas_val.size());
+  P.o_inst = take(sizeof(DevInst) * n);
+  P.o_st = take(sizeof(InstState) * n);
+  for (int l = 0; l < MODIL_MAXL; ++l) P.o_ti[l] = take(4 * P.tile_inst[l].size());
+  P.total = o;
+  return MODIL_OK;
+}
+
+}  // namespace
+
+struct modil_problem {
+  Plan plan;
+  void* arena = nullptr;
+  bool own_arena = false;
+  cudaStream_t stream = nullptr;
+  Arena<float> A32{};
+  Arena<double> A64{};
+  long long steps = 0;  // host mirror of the device step counter (all instances)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool use_graph = true;
+};
+
+namespace {
+
+template <class T>
+void fill_arena(modil_problem* p, Arena<T>& A) {
+  const Plan& P = p->plan;
+  char* b = static_cast<char*>(p->arena);
+  A.p[0] = reinterpret_cast<T*>(b + P.o_p0);
+  A.p[1] = reinterpret_cast<T*>(b + P.o_p1);
+  A.m = reinterpret_cast<T*>(b + P.o_m);
+  A.v = reinterpret_cast<double*>(b + P.o_v);
+  A.g = reinterpret_cast<T*>(b + P.o_g);
+  A.ufine = reinterpret_cast<T*>(b + P.o_uf);
+  A.kq = reinterpret_cast<T*>(b + P.o_kq);
+  A.km = reinterpret_cast<T*>(b + P.o_km);
+  A.kv = reinterpret_cast<double*>(b + P.o_kv);
+  A.kg = reinterpret_cast<T*>(b + P.o_kg);
+  A.aux = reinterpret_cast<const T*>(b + P.o_aux);
+  A.part = reinterpret_cast<double*>(b + P.o_part);
+  A.run_ptr = reinterpret_cast<const int*>(b + P.o_rptr);
+  A.run_cell = reinterpret_cast<const int*>(b + P.o_rcell);
+  A.run_field = reinterpret_cast<const int*>(b + P.o_rfield);
+  A.run_beg = reinterpret_cast<const int*>(b + P.o_rbeg);
+  A.meas_val = reinterpret_cast<const T*>(b + P.o_mval);
+  A.inst = reinterpret_cast<const DevInst*>(b + P.o_inst);
+  A.st = reinterpret_cast<InstState*>(b + P.o_st);
+  for (int l = 0; l < MODIL_MAXL; ++l) {
+    A.tile_inst[l] = reinterpret_cast<const int*>(b + P.o_ti[l]);
+    A.ntiles[l] = (int)P.tile_inst[l].size();
+  }
+  A.npart = P.npart;
+  A.n_inst = P.n_inst;
+}
+
+template <class T>
+std::vector<T> convert(const std::vector<double>& v) {
+  return std::vector<T>(v.begin(), v.end());
+}
+
+modil_status upload(modil_problem* p, size_t off, const void* src, size_t bytes) {
+  if (bytes == 0) return MODIL_OK;
+  CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(p->arena) + off, src, bytes, cudaMemcpyHostToDevice,
+                           p->stream));
+  return MODIL_OK;
+}
+
+// One pass of the method: the fused fine-tile kernel, the restriction/Adam
+// kernel of each coarser level, and the finalising kernel.  With ev != NULL an
+// event is recorded after every launch (ev[0] before the first).
+template <class T>
+modil_status run_pass_t(modil_problem* p, Arena<T>& A, int mode, cudaEvent_t* ev, int* nev) {
+  const Plan& P = p->plan;
+  int k = 0;
+  if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+  CUDA_TRY(launch_fine_st<T>(A, P.pde, P.cfg, mode, P.pyr_elems, p->stream));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+  if (mode == MODE_GRAD || mode == MODE_STEP)
+    for (int l = 1; l < P.max_lev; ++l) {
+      CUDA_TRY(launch_level<T>(A, l, mode, p->stream));
+      if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+    }
+  if (mode != MODE_COMPOSE) {
+    CUDA_TRY(launch_finalize<T>(A, mode, p->stream));
+    if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+  }
+  if (nev) *nev = k;
+  return MODIL_OK;
+}
+
+modil_status run_pass(modil_problem* p, int mode, cudaEvent_t* ev = nullptr, int* nev = nullptr) {
+  return p->plan.dtype == MODIL_F64 ? run_pass_t<double>(p, p->A64, mode, ev, nev)
+                                    : run_pass_t<float>(p, p->A32, mode, ev, nev);
+}
+
+int kernels_per_step(const Plan& P) { return 1 + (P.max_lev - 1) + 1; }
+
+modil_status read_terms(modil_problem* p, double* terms) {
+  CUDA_TRY(cudaStreamSynchronize(p->stream));
+  const Plan& P = p->plan;
+  std::vector<InstState> st(P.n_inst);
+  CUDA_TRY(cudaMemcpy(st.data(), static_cast<char*>(p->arena) + P.o_st,
+                      sizeof(InstState) * P.n_inst, cudaMemcpyDeviceToHost));
+  bool bad = false;
+  for (int i = 0; i < P.n_inst; ++i) {
+    if (terms)
+      for (int j = 0; j < MODIL_NTERMS; ++j) terms[i * MODIL_NTERMS + j] = st[i].terms[j];
+    bad |= st[i].nonfinite != 0;
+  }
+  if (bad) return fail(MODIL_ERR_NONFINITE, "loss became non-finite");
+  return MODIL_OK;
+}
+
+modil_status check_level(const modil_problem* p, int inst, int field, int level, size_t bytes,
+                         long long* off, long long* count) {
+  if (!p) return fail(MODIL_ERR_ARG, "problem is NULL");
+  const Plan& P = p->plan;
+  if (inst < 0 || inst >= P.n_inst) return fail(MODIL_ERR_ARG, "instance out of range");
+  if (field < 0 || field >= P.nfield) return fail(MODIL_ERR_ARG, "field out of range");
+  if (level < 0 || level >= P.inst[inst].nlev) return fail(MODIL_ERR_ARG, "level out of range");
+  const long long cnt = P.inst[inst].lev_size[level];
+  if (bytes != (size_t)cnt * P.esz) return fail(MODIL_ERR_ARG, "byte count does not match the level");
+  *off = P.dev[inst].off[field][level];
+  *count = cnt;
+  return MODIL_OK;
+}
+
+modil_status copy_dev(modil_problem* p, void* dst, const void* src, size_t bytes, cudaMemcpyKind k) {
+  CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, k, p->stream));
+  if (k == cudaMemcpyDeviceToHost || k == cudaMemcpyHostToDevice) CUDA_TRY(cudaStreamSynchronize(p->stream));
+  return MODIL_OK;
+}
+
+void drop_graph(modil_problem* p) {
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->gexec = nullptr;
+  p->graph = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+modil_status modil_arena_bytes(const modil_desc* descs, int n, size_t* bytes) {
+  if (!bytes) return fail(MODIL_ERR_ARG, "bytes is NULL");
+  Plan P;
+  modil_status s = make_plan(descs, n, P);
+  if (s != MODIL_OK) return s;
+  *bytes = P.total;
+  return MODIL_OK;
+}
+
+modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t arena_bytes,
+                          void* stream, modil_problem** out) {
+  if (!out) return fail(MODIL_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  modil_problem* p = new (std::nothrow) modil_problem();
+  if (!p) return fail(MODIL_ERR_OOM, "host allocation");
+  modil_status s = make_plan(descs, n, p->plan);
+  if (s != MODIL_OK) { delete p; return s; }
+  Plan& P = p->plan;
+  p->stream = static_cast<cudaStream_t>(stream);
+  p->use_graph = (stream != nullptr) && !std::getenv("MODIL_NO_GRAPH");
+  if (arena) {
+    if (arena_bytes < P.total) { delete p; return fail(MODIL_ERR_ARG, "arena too small"); }
+    if (reinterpret_cast<uintptr_t>(arena) & 255) { delete p; return fail(MODIL_ERR_ARG, "arena not 256-byte aligned"); }
+    p->arena = arena;
+  } else {
+    cudaError_t e = cudaMalloc(&p->arena, P.total);
+    if (e != cudaSuccess) { delete p; return fail(MODIL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+    p->own_arena = true;
+  }
+  fill_arena(p, p->A32);
+  fill_arena(p, p->A64);
+  auto bail = [&](modil_status st) { modil_destroy(p); return st; };
+  cudaError_t e = cudaMemsetAsync(p->arena, 0, P.total, p->stream);
+  if (e != cudaSuccess) return bail(fail(MODIL_ERR_CUDA, cudaGetErrorString(e)));
+  // host-side staging of the read-only tables
+  std::vector<double> kq, aux;
+  for (int i = 0; i < n; ++i) {
+    if (P.inst[i].nk) kq.insert(kq.end(), descs[i].knodes, descs[i].knodes + P.inst[i].nk);
+    if (P.pde == MODIL_PDE_HEAT) aux.insert(aux.end(), descs[i].aux, descs[i].aux + descs[i].n_aux);
+  }
+  modil_status st = MODIL_OK;
+  if (P.dtype == MODIL_F64) {
+    st = upload(p, P.o_kq, kq.data(), 8 * kq.size());
+    if (st == MODIL_OK) st = upload(p, P.o_aux, aux.data(), 8 * aux.size());
+    if (st == MODIL_OK) st = upload(p, P.o_mval, P.meas_val.data(), 8 * P.meas_val.size());
+  } else {
+    auto kq32 = convert<float>(kq), aux32 = convert<float>(aux), mv32 = convert<float>(P.meas_val);
+    st = upload(p, P.o_kq, kq32.data(), 4 * kq32.size());
+    if (st == MODIL_OK) st = upload(p, P.o_aux, aux32.data(), 4 * aux32.size());
+    if (st == MODIL_OK) st = upload(p, P.o_mval, mv32.data(), 4 * mv32.size());
+    if (st == MODIL_OK) {
+      e = cudaStreamSynchronize(p->stream);
+      if (e != cudaSuccess) st = fail(MODIL_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
+  if (st == MODIL_OK) st = upload(p, P.o_rptr, P.run_ptr.data(), 4 * P.run_ptr.size());
+  if (st == MODIL_OK) st = upload(p, P.o_rcell, P.run_cell.data(), 4 * P.run_cell.size());
+  if (st == MODIL_OK) st = upload(p, P.o_rfield, P.run_field.data(), 4 * P.run_field.size());
+  if (st == MODIL_OK) st = upload(p, P.o_rbeg, P.run_beg.data(), 4 * P.run_beg.size());
+  if (st == MODIL_OK) st = upload(p, P.o_inst, P.dev.data(), sizeof(DevInst) * n);
+  for (int l = 0; l < MODIL_MAXL && st == MODIL_OK; ++l)
+    st = upload(p, P.o_ti[l], P.tile_inst[l].data(), 4 * P.tile_inst[l].size());
+  if (st != MODIL_OK) return bail(st);
+  e = P.dtype == MODIL_F64 ? launch_reset<double>(p->A64, p->stream) : launch_reset<float>(p->A32, p->stream);
+  if (e != cudaSuccess) return bail(fail(MODIL_ERR_CUDA, cudaGetErrorString(e)));
+  e = P.dtype == MODIL_F64 ? prepare_fine_st<double>(P.pde, P.cfg, P.pyr_elems)
+                           : prepare_fine_st<float>(P.pde, P.cfg, P.pyr_elems);
+  if (e != cudaSuccess) return bail(fail(MODIL_ERR_CUDA, std::string("kernel setup: ") + cudaGetErrorString(e)));
+  e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return bail(fail(MODIL_ERR_CUDA, cudaGetErrorString(e)));
+  *out = p;
+  return MODIL_OK;
+}
+
+void modil_destroy(modil_problem* p) {
+  if (!p) return;
+  drop_graph(p);
+  cudaStreamSynchronize(p->stream);  // no kernel may still use the arena
+  if (p->own_arena && p->arena) cudaFree(p->arena);
+  delete p;
+}
+
+modil_status modil_set_stream(modil_problem* p, void* stream) {
+  if (!p) return fail(MODIL_ERR_ARG, "problem is NULL");
+  drop_graph(p);
+  p->stream = static_cast<cudaStream_t>(stream);
+  p->use_graph = (stream != nullptr) && !std::getenv("MODIL_NO_GRAPH");
+  return MODIL_OK;
+}
+
+modil_status modil_level_shape(const modil_problem* p, int instance, int level, int shape[3]) {
+  if (!p || !shape) return fail(MODIL_ERR_ARG, "NULL argument");
+  const Plan& P = p->plan;
+  if (instance < 0 || instance >= P.n_inst) return fail(MODIL_ERR_ARG, "instance out of range");
+  if (level < 0 || level >= P.inst[instance].nlev) return fail(MODIL_ERR_ARG, "level out of range");
+  shape[0] = P.inst[instance].n[level][1];
+  shape[1] = P.inst[instance].n[level][2];
+  shape[2] = 0;
+  return MODIL_OK;
+}
+
+modil_status modil_write_level(modil_problem* p, int instance, int field, int level,
+                               const void* src, size_t bytes, int src_on_device) {
+  long long off, cnt;
+  modil_status s = check_level(p, instance, field, level, bytes, &off, &cnt);
+  if (s != MODIL_OK) return s;
+  if (!src) return fail(MODIL_ERR_ARG, "src is NULL");
+  const int cur = (int)(p->steps & 1);
+  char* dst = static_cast<char*>(p->arena) + (cur ? p->plan.o_p1 : p->plan.o_p0) + off * p->plan.esz;
+  return copy_dev(p, dst, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+}
+
+static modil_status read_arr(modil_problem* p, size_t base, int instance, int field, int level,
+                             void* dst, size_t bytes, int dst_on_device) {
+  long long off, cnt;
+  modil_status s = check_level(p, instance, field, level, bytes, &off, &cnt);
+  if (s != MODIL_OK) return s;
+  if (!dst) return fail(MODIL_ERR_ARG, "dst is NULL");
+  const char* src = static_cast<const char*>(p->arena) + base + off * p->plan.esz;
+  return copy_dev(p, dst, src, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+}
+
+modil_status modil_read_level(modil_problem* p, int instance, int field, int level, void* dst,
+                              size_t bytes, int dst_on_device) {
+  if (!p) return fail(MODIL_ERR_ARG, "problem is NULL");
+  const int cur = (int)(p->steps & 1);
+  return read_arr(p, cur ? p->plan.o_p1 : p->plan.o_p0, instance, field, level, dst, bytes, dst_on_device);
+}
+
+modil_status modil_read_grad(modil_problem* p, int instance, int field, int level, void* dst,
+                             size_t bytes, int dst_on_device) {
+  if (!p) return fail(MODIL_ERR_ARG, "problem is NULL");
+  return read_arr(p, p->plan.o_g, instance, field, level, dst, bytes, dst_on_device);
+}
+
+modil_status modil_read_field(modil_problem* p, int instance, int field, void* dst, size_t bytes,
+                              int dst_on_device) {
+  long long off, cnt;
+  modil_status s = check_level(p, instance, field, 0, bytes, &off, &cnt);
+  if (s != MODIL_OK) return s;
+  if (!dst) return fail(MODIL_ERR_ARG, "dst is NULL");
+  s = run_pass(p, MODE_COMPOSE);
+  if (s != MODIL_OK) return s;
+  const char* src = static_cast<const char*>(p->arena) + p->plan.o_uf +
+                    p->plan.dev[instance].fine_off[field] * p->plan.esz;
+  return copy_dev(p, dst, src, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+}
+
+static modil_status knode_io(modil_problem* p, int instance, double* q, int n, size_t base, bool write) {
+  if (!p || !q) return fail(MODIL_ERR_ARG, "NULL argument");
+  const Plan& P = p->plan;
+  if (instance < 0 || instance >= P.n_inst) return fail(MODIL_ERR_ARG, "instance out of range");
+  if (n != P.inst[instance].nk || n == 0) return fail(MODIL_ERR_ARG, "node count does not match");
+  char* dev = static_cast<char*>(p->arena) + base + P.dev[instance].k_off * P.esz;
+  if (P.dtype == MODIL_F64) {
+    return copy_dev(p, write ? (void*)dev : (void*)q, write ? (const void*)q : (const void*)dev, 8 * n,
+                    write ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+  }
+  std::vector<float> tmp(n);
+  if (write) {
+    for (int j = 0; j < n; ++j) tmp[j] = (float)q[j];
+    return copy_dev(p, dev, tmp.data(), 4 * n, cudaMemcpyHostToDevice);
+  }
+  modil_status s = copy_dev(p, tmp.data(), dev, 4 * n, cudaMemcpyDeviceToHost);
+  for (int j = 0; j < n; ++j) q[j] = tmp[j];
+  return s;
+}
+
+modil_status modil_write_knodes(modil_problem* p, int instance, const double* q, int n) {
+  return knode_io(p, instance, const_cast<double*>(q), n, p ? p->plan.o_kq : 0, true);
+}
+modil_status modil_read_knodes(modil_problem* p, int instance, double* q, int n) {
+  return knode_io(p, instance, q, n, p ? p->plan.o_kq : 0, false);
+}
+modil_status modil_read_kgrad(modil_problem* p, int instance, double* gq, int n) {
+  return knode_io(p, instance, gq, n, p ? p->plan.o_kg : 0, false);
+}
+
+modil_status modil_eval_loss(modil_problem* p, double* terms) {
+  if (!p) return fail(MODIL_ERR_ARG, "problem is NULL");
+  modil_status s = run_pass(p, MODE_LOSS);
+  if (s != MODIL_OK) return s;
+  return terms ? read_terms(p, terms) : MODIL_OK;
+}
+
+modil_status modil_eval_grad(modil_problem* p, double* terms) {
+  if (!p) return fail(MODIL_ERR_ARG, "problem is NULL");
+  modil_status s = run_pass(p, MODE_GRAD);
+  if (s != MODIL_OK) return s;
+  return terms ? read_terms(p, terms) : MODIL_OK;
+}
+
+modil_status modil_step(modil_problem* p, int n_steps, double* terms) {
+  if (!p) return fail(MODIL_ERR_ARG, "problem is NULL");
+  if (n_steps < 0) return fail(MODIL_ERR_ARG, "n_steps < 0");
+  for (int i = 0; i < n_steps; ++i) {
+    if (p->use_graph) {
+      if (!p->gexec) {
+        CUDA_TRY(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+        modil_status s = run_pass(p, MODE_STEP);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+        if (s != MODIL_OK) { if (g) cudaGraphDestroy(g); return s; }
+        if (e != cudaSuccess) return fail(MODIL_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        p->graph = g;
+        e = cudaGraphInstantiate(&p->gexec, g, 0);
+        if (e != cudaSuccess) { drop_graph(p); return fail(MODIL_ERR_CUDA, cudaGetErrorString(e)); }
+      }
+      CUDA_TRY(cudaGraphLaunch(p->gexec, p->stream));
+    } else {
+      modil_status s = run_pass(p, MODE_STEP);
+      if (s != MODIL_OK) return s;
+    }
+    p->steps++;
+  }
+  return terms ? read_terms(p, terms) : MODIL_OK;
+}
+
+modil_status modil_launches_per_step(const modil_problem* p, int* n) {
+  if (!p || !n) return fail(MODIL_ERR_ARG, "NULL argument");
+  *n = kernels_per_step(p->plan);
+  return MODIL_OK;
+}
+
+modil_status modil_profile_step(modil_problem* p, float* ms, int max_kernels, int* n_kernels) {
+  if (!p || !ms || !n_kernels) return fail(MODIL_ERR_ARG, "NULL argument");
+  const int nk = kernels_per_step(p->plan);
+  if (max_kernels < nk) return fail(MODIL_ERR_ARG, "ms[] too short");
+  std::vector<cudaEvent_t> ev(nk + 1, nullptr);
+  for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
+  int nev = 0;
+  modil_status s = run_pass(p, MODE_STEP, ev.data(), &nev);
+  if (s == MODIL_OK) {
+    p->steps++;
+    cudaError_t e = cudaEventSynchronize(ev[nev - 1]);
+    for (int k = 0; k + 1 < nev && e == cudaSuccess; ++k) e = cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
+    if (e != cudaSuccess) s = fail(MODIL_ERR_CUDA, cudaGetErrorString(e));
+    *n_kernels = nev - 1;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return s;
+}
+
+modil_status modil_step_count(const modil_problem* p, long long* t) {
+  if (!p || !t) return fail(MODIL_ERR_ARG, "NULL argument");
+  *t = p->steps;
+  return MODIL_OK;
+}
+
+modil_status modil_reset_optimizer(modil_problem* p) {
+  if (!p) return fail(MODIL_ERR_ARG, "problem is NULL");
+  const Plan& P = p->plan;
+  char* b = static_cast<char*>(p->arena);
+  // keep the current levels: move them into buffer 0 if they live in buffer 1
+  if (p->steps & 1) CUDA_TRY(cudaMemcpyAsync(b + P.o_p0, b + P.o_p1, P.esz * P.n_param, cudaMemcpyDeviceToDevice, p->stream));
+  CUDA_TRY(cudaMemsetAsync(b + P.o_m, 0, P.esz * P.n_param, p->stream));
+  CUDA_TRY(cudaMemsetAsync(b + P.o_v, 0, 8 * P.n_param, p->stream));
+  CUDA_TRY(cudaMemsetAsync(b + P.o_km, 0, P.esz * P.n_k, p->stream));
+  CUDA_TRY(cudaMemsetAsync(b + P.o_kv, 0, 8 * P.n_k, p->stream));
+  cudaError_t e = P.dtype == MODIL_F64 ? launch_reset<double>(p->A64, p->stream) : launch_reset<float>(p->A32, p->stream);
+  if (e != cudaSuccess) return fail(MODIL_ERR_CUDA, cudaGetErrorString(e));
+  p->steps = 0;
+  return MODIL_OK;
+}
+
+const char* modil_last_error(void) { return g_err.c_str(); }
+
+const char* modil_version(void) { return "modil-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// Device-side data structures and helpers of the mODIL library.
+//
+// Memory model.  One arena holds every instance of a batch:
+//   p[2]  level values, ping-pong: a step reads p[t & 1] and writes p[(t+1) & 1]
+//         so that tiles composing the field never see a half-updated level;
+//   m     Adam first moment (storage type T);
+//   v     Adam second moment, always FP64;
+//   g     dL/du per level (also the input of the next level's restriction);
+// all four indexed by DevInst::off[field][level] (element offsets, row-major,
+// last axis fastest).  Conductivity nodes (heat) have their own small arrays.
+// Per fine tile the kernels write FP64 partial sums (residual, data and the
+// conductivity-node gradient) that one finalising block per instance adds in
+// a fixed order, so every result is bit-reproducible run to run.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MODIL_MAXL 10
+#define MODIL_MAXF 5
+#define MODIL_MAXK 64
+#define MODIL_NT 256  // threads per block of the tile kernels
+
+namespace modil {
+
+enum Mode { MODE_LOSS = 0, MODE_GRAD = 1, MODE_STEP = 2, MODE_COMPOSE = 3 };
+enum Pde { PDE_BURGERS = 1, PDE_HEAT = 2 };
+
+// Per-instance description (read-only on the device).
+struct DevInst {
+  int nlev, nfield, nk, ndim;
+  int n[MODIL_MAXL][3];        // cells per axis per level, slowest first (2-D: n[l][0] = 1)
+  int nt[MODIL_MAXL][3];       // tiles per axis per level
+  int tile_base[MODIL_MAXL];   // global tile index of this instance's first tile per level
+  long long off[MODIL_MAXF][MODIL_MAXL];  // element offsets of (field, level) arrays
+  long long fine_off[MODIL_MAXF];         // offset in the composed-field scratch
+  long long k_off;             // offset of the conductivity nodes
+  long long aux_off;           // offset of the heat initial profile
+  double h[3];                 // spacing per axis (same order as n)
+  double coef[4];              // PDE coefficients (Burgers: nu)
+  double w_res_dV;             // w_res * cell volume
+  double w_data_n;             // w_data / n_meas
+  double w_reg;                // regulariser weight (heat)
+  double lr, b1, b2, eps;      // Adam
+};
+
+// Per-instance mutable state.
+struct InstState {
+  long long t;        // completed Adam steps
+  double b1t, b2t;    // beta1^t, beta2^t
+  double terms[4];    // total, residual, data, regulariser of the last evaluation
+  int nonfinite;      // latched when a loss is NaN/Inf
+  int pad;
+};
+
+template <class T>
+struct Arena {
+  T* p[2];
+  T* m;
+  double* v;
+  T* g;
+  T* ufine;            // composed-field scratch (MODE_COMPOSE)
+  T* kq;               // conductivity nodes (heat), Adam moments and gradient
+  T* km;
+  double* kv;
+  T* kg;
+  const T* aux;        // heat initial profiles
+  double* part;        // per fine tile partial sums, npart each
+  const int* run_ptr;  // per global fine tile: first measurement run
+  const int* run_cell; // flat fine cell of each run (within its instance)
+  const int* run_field;
+  const int* run_beg;  // first value of each run; run r spans [run_beg[r], run_beg[r+1])
+  const T* meas_val;
+  const DevInst* inst;
+  InstState* st;
+  const int* tile_inst[MODIL_MAXL];  // instance owning each global tile of level l
+  int ntiles[MODIL_MAXL];
+  int npart;
+  int n_inst;
+};
+
+// ---------------------------------------------------------------------------
+// Interpolation taps (cell-based linear interpolation, printed 1-D matrices)
+// ---------------------------------------------------------------------------
+
+// Fine cell i of a grid refined from nc coarse cells takes w0*c[j0] + w1*c[j1].
+template <class T>
+__device__ __forceinline__ void prolong_taps(int i, int nc, int& j0, int& j1, T& w0, T& w1) {
+  if (nc == 1) { j0 = 0; j1 = 0; w0 = T(1); w1 = T(0); return; }
+  const int j = i >> 1;
+  const int jn = (i & 1) ? j + 1 : j - 1;
+  if (jn < 0) { j0 = 0; j1 = 1; w0 = T(1.25); w1 = T(-0.25); }
+  else if (jn >= nc) { j0 = nc - 1; j1 = nc - 2; w0 = T(1.25); w1 = T(-0.25); }
+  else { j0 = j; j1 = jn; w0 = T(0.75); w1 = T(0.25); }
+}
+
+// Column j of the interpolation matrix (coarse j <- fine cells): the transposed
+// operator gathers at most six fine values (nc = 3, j = 1).  Returns the tap count.
+template <class T>
+__device__ __forceinline__ int restrict_taps(int j, int nc, int* idx, T* w) {
+  if (nc == 1) { idx[0] = 0; w[0] = T(1); idx[1] = 1; w[1] = T(1); return 2; }
+  int c = 0;
+  // even fine cell 2j: parent j (weight 5/4 at the first coarse cell, else 3/4)
+  idx[c] = 2 * j; w[c] = (j == 0) ? T(1.25) : T(0.75); ++c;
+  // odd fine cell 2j+1: parent j (5/4 at the last coarse cell, else 3/4)
+  idx[c] = 2 * j + 1; w[c] = (j == nc - 1) ? T(1.25) : T(0.75); ++c;
+  // odd fine cell 2j-1 has parent j-1 and neighbour j
+  if (j >= 1) { idx[c] = 2 * j - 1; w[c] = T(0.25); ++c; }
+  // even fine cell 2j+2 has parent j+1 and neighbour j
+  if (j <= nc - 2) { idx[c] = 2 * j + 2; w[c] = T(0.25); ++c; }
+  // boundary extrapolation rows reach one cell further
+  if (j == 1) { idx[c] = 0; w[c] = T(-0.25); ++c; }
+  if (j == nc - 2) { idx[c] = 2 * nc - 1; w[c] = T(-0.25); ++c; }
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Adam.  The second moment is accumulated in FP64; the rest in T.
+// ---------------------------------------------------------------------------
+struct AdamCoef {
+  double lr, b1, b2, eps, c1, c2;  // c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
+};
+
+__device__ __forceinline__ void adam_update(float& p, float& m, double& v, float g,
+                                            const AdamCoef& c) {
+  const float b1 = (float)c.b1;
+  m = b1 * m + (1.0f - b1) * g;
+  const double gd = (double)g;
+  v = fma(c.b2, v, (1.0 - c.b2) * (gd * gd));
+  const float mh = m * (float)c.c1;
+  const float den = sqrtf((float)v * (float)c.c2) + (float)c.eps;
+  p = p - (float)c.lr * (mh / den);
+}
+
+__device__ __forceinline__ void adam_update(double& p, double& m, double& v, double g,
+                                            const AdamCoef& c) {
+  m = c.b1 * m + (1.0 - c.b1) * g;
+  v = c.b2 * v + (1.0 - c.b2) * (g * g);
+  const double mh = m * c.c1;
+  const double den = sqrt(v * c.c2) + c.eps;
+  p = p - c.lr * (mh / den);
+}
+
+__device__ __forceinline__ AdamCoef adam_coef(const DevInst& D, const InstState& S) {
+  AdamCoef c;
+  c.lr = D.lr; c.b1 = D.b1; c.b2 = D.b2; c.eps = D.eps;
+  c.c1 = 1.0 / (1.0 - S.b1t * D.b1);
+  c.c2 = 1.0 / (1.0 - S.b2t * D.b2);
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Reductions (fixed order: deterministic)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Sum over the block; every thread gets the result.  scratch: >= NT/32 doubles.
+template <int NT>
+__device__ __forceinline__ double block_sum(double x, double* scratch) {
+  x = warp_sum(x);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) scratch[w] = x;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) s += scratch[i];
+  return s;
+}
+
+// Copy a POD struct from global to shared memory with the whole block.
+template <class S>
+__device__ __forceinline__ void block_copy(S* dst, const S* src) {
+  static_assert(sizeof(S) % 4 == 0, "POD size");
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(S) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+}  // namespace modil

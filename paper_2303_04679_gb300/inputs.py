@@ -178,3 +178,27 @@ def heat_measurements(nt, nx, frac=0.05, sigma=1e-3, seed=2, field=None):
 def heat_k_init(value=0.02, n=HEAT_KNODES):
     """Initial conductivity nodes q_j (uniform value)."""
     return np.full(n, value, dtype=np.float64)
+
+
+def heat_workload(nt=512, nx=512, n_levels=7, seed=2):
+    """Conductivity inference on a 512 (x) by 512 (t) grid with 7 levels.
+
+    5 % of the cells carry measurements with Gaussian noise (sigma = 1e-3) of
+    the closed-form constant-conductivity temperature record; the initial
+    profile is g(x) - g(0); 32 conductivity nodes start at 0.02.
+    """
+    cells, vals = heat_measurements(nt, nx, 0.05, 1e-3, seed)
+    return dict(shape=(nt, nx), n_levels=n_levels, meas_cell=cells, meas_value=vals,
+                aux=heat_ic(nx), knodes=heat_k_init(), w_res=1.0, w_data=1.0, w_reg=1e-4,
+                lr=1e-3)
+
+
+def burgers_workload(nt=64, nx=64, n_levels=4, seed=0, n_meas=200, nu=0.01):
+    """Burgers reconstruction on 64 x 64 with 4 levels and 200 measurement cells.
+
+    Returns the cells and the amplitudes of the initial condition; the
+    measured values come from a reference solve done by the caller.
+    """
+    cells = measurement_cells(nt * nx, n_meas, seed)
+    return dict(shape=(nt, nx), n_levels=n_levels, meas_cell=cells, nu=nu,
+                amps=burgers_ic_amplitudes(seed), w_res=1.0, w_data=1.0, lr=5e-3)

@@ -1,0 +1,299 @@
+"""Thin Python binding of libmodil.so (argument marshalling only).
+
+Every step of the method runs in the library's CUDA kernels; this module only
+converts Python/numpy/torch arguments into the C ABI declared in
+``include/modil.h``.  There is no CPU fallback: if the shared library is
+missing, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libmodil.so")
+
+PDE_BURGERS = 1
+PDE_HEAT = 2
+F32 = 0
+F64 = 1
+NTERMS = 4
+TERM_NAMES = ("total", "res", "data", "reg")
+MAX_LEVELS = 10
+
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_UNSUPPORTED",
+          -5: "ERR_NONFINITE", -6: "ERR_STATE"}
+
+
+class ModilError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class modil_desc(C.Structure):
+    _fields_ = [
+        ("pde", C.c_int), ("dtype", C.c_int), ("ndim", C.c_int), ("shape", C.c_int * 3),
+        ("n_levels", C.c_int), ("coef", C.c_double * 4), ("w_res", C.c_double),
+        ("w_data", C.c_double), ("w_reg", C.c_double), ("n_meas", C.c_int),
+        ("meas_cell", C.POINTER(C.c_int32)), ("meas_field", C.POINTER(C.c_int32)),
+        ("meas_value", C.POINTER(C.c_double)), ("n_aux", C.c_int),
+        ("aux", C.POINTER(C.c_double)), ("n_knodes", C.c_int),
+        ("knodes", C.POINTER(C.c_double)), ("adam_lr", C.c_double),
+        ("adam_beta1", C.c_double), ("adam_beta2", C.c_double), ("adam_eps", C.c_double),
+        ("tile", C.c_int * 2),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmodil.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    sig = {
+        "modil_arena_bytes": ([C.POINTER(modil_desc), C.c_int, C.POINTER(C.c_size_t)], C.c_int),
+        "modil_create": ([C.POINTER(modil_desc), C.c_int, P, C.c_size_t, P, C.POINTER(P)], C.c_int),
+        "modil_destroy": ([P], None),
+        "modil_set_stream": ([P, P], C.c_int),
+        "modil_level_shape": ([P, C.c_int, C.c_int, C.POINTER(C.c_int)], C.c_int),
+        "modil_write_level": ([P, C.c_int, C.c_int, C.c_int, P, C.c_size_t, C.c_int], C.c_int),
+        "modil_read_level": ([P, C.c_int, C.c_int, C.c_int, P, C.c_size_t, C.c_int], C.c_int),
+        "modil_read_grad": ([P, C.c_int, C.c_int, C.c_int, P, C.c_size_t, C.c_int], C.c_int),
+        "modil_read_field": ([P, C.c_int, C.c_int, P, C.c_size_t, C.c_int], C.c_int),
+        "modil_write_knodes": ([P, C.c_int, C.POINTER(C.c_double), C.c_int], C.c_int),
+        "modil_read_knodes": ([P, C.c_int, C.POINTER(C.c_double), C.c_int], C.c_int),
+        "modil_read_kgrad": ([P, C.c_int, C.POINTER(C.c_double), C.c_int], C.c_int),
+        "modil_eval_loss": ([P, C.POINTER(C.c_double)], C.c_int),
+        "modil_eval_grad": ([P, C.POINTER(C.c_double)], C.c_int),
+        "modil_step": ([P, C.c_int, C.POINTER(C.c_double)], C.c_int),
+        "modil_step_count": ([P, C.POINTER(C.c_longlong)], C.c_int),
+        "modil_launches_per_step": ([P, C.POINTER(C.c_int)], C.c_int),
+        "modil_profile_step": ([P, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)], C.c_int),
+        "modil_reset_optimizer": ([P], C.c_int),
+        "modil_last_error": ([], C.c_char_p),
+        "modil_version": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+LIB = _load()
+
+
+def _check(code):
+    if code != 0:
+        raise ModilError(code, LIB.modil_last_error().decode())
+
+
+def _dptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+class Desc:
+    """One problem description; keeps its numpy buffers alive for the C struct."""
+
+    def __init__(self, pde, shape, n_levels, dtype="f32", coef=(), w_res=1.0, w_data=1.0,
+                 w_reg=0.0, meas_cell=None, meas_value=None, meas_field=None, aux=None,
+                 knodes=None, lr=5e-3, beta1=0.9, beta2=0.999, eps=1e-8, tile=(0, 0)):
+        self.pde = {"burgers": PDE_BURGERS, "heat": PDE_HEAT}.get(pde, pde)
+        self.dtype = {"f32": F32, "f64": F64}.get(dtype, dtype)
+        self.shape = tuple(int(s) for s in shape)
+        self.n_levels = int(n_levels)
+        self._cell = None if meas_cell is None else np.ascontiguousarray(meas_cell, np.int32)
+        self._val = None if meas_value is None else np.ascontiguousarray(meas_value, np.float64)
+        self._field = None if meas_field is None else np.ascontiguousarray(meas_field, np.int32)
+        self._aux = None if aux is None else np.ascontiguousarray(aux, np.float64)
+        self._knodes = None if knodes is None else np.ascontiguousarray(knodes, np.float64)
+        d = modil_desc()
+        d.pde, d.dtype, d.ndim = self.pde, self.dtype, len(self.shape)
+        for i, s in enumerate(self.shape):
+            d.shape[i] = s
+        d.n_levels = self.n_levels
+        for i, c in enumerate(coef):
+            d.coef[i] = float(c)
+        d.w_res, d.w_data, d.w_reg = float(w_res), float(w_data), float(w_reg)
+        d.n_meas = 0 if self._cell is None else len(self._cell)
+        d.meas_cell = _dptr(self._cell, C.c_int32)
+        d.meas_value = _dptr(self._val, C.c_double)
+        d.meas_field = _dptr(self._field, C.c_int32)
+        d.n_aux = 0 if self._aux is None else len(self._aux)
+        d.aux = _dptr(self._aux, C.c_double)
+        d.n_knodes = 0 if self._knodes is None else len(self._knodes)
+        d.knodes = _dptr(self._knodes, C.c_double)
+        d.adam_lr, d.adam_beta1, d.adam_beta2, d.adam_eps = lr, beta1, beta2, eps
+        d.tile[0], d.tile[1] = int(tile[0]), int(tile[1])
+        self.c = d
+
+    @property
+    def np_dtype(self):
+        return np.float64 if self.dtype == F64 else np.float32
+
+
+def _desc_array(descs):
+    arr = (modil_desc * len(descs))()
+    for i, d in enumerate(descs):
+        arr[i] = d.c
+    return arr
+
+
+def arena_bytes(descs):
+    out = C.c_size_t(0)
+    _check(LIB.modil_arena_bytes(_desc_array(descs), len(descs), C.byref(out)))
+    return out.value
+
+
+class Problem:
+    """A batch of mODIL problems living on the current CUDA device.
+
+    arena="torch" lets PyTorch own the device memory (a uint8 tensor);
+    arena="library" makes the library cudaMalloc it.  ``stream`` is a
+    torch.cuda.Stream (default: a new one, so steps replay as a CUDA graph).
+    """
+
+    def __init__(self, descs, arena="torch", stream=None):
+        import torch
+        if isinstance(descs, Desc):
+            descs = [descs]
+        self.descs = list(descs)
+        self._arr = _desc_array(self.descs)
+        self.n = len(self.descs)
+        self.np_dtype = self.descs[0].np_dtype
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        nbytes = arena_bytes(self.descs)
+        self._arena = None
+        aptr = None
+        if arena == "torch":
+            self._arena = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._arena.data_ptr()
+            aptr = (base + 255) & ~255
+        self._h = C.c_void_p()
+        _check(LIB.modil_create(self._arr, self.n, aptr, nbytes, self.stream.cuda_stream,
+                                C.byref(self._h)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            LIB.modil_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- shapes ----------------------------------------------------------
+    def level_shape(self, level, instance=0):
+        s = (C.c_int * 3)()
+        _check(LIB.modil_level_shape(self._h, instance, level, s))
+        return (s[0], s[1])
+
+    def n_levels(self, instance=0):
+        return self.descs[instance].n_levels
+
+    # -- level I/O (host numpy or device torch tensors) ---------------------
+    def write_level(self, level, values, field=0, instance=0):
+        if hasattr(values, "data_ptr"):
+            _check(LIB.modil_write_level(self._h, instance, field, level, values.data_ptr(),
+                                         values.numel() * values.element_size(), 1))
+            return
+        a = np.ascontiguousarray(values, dtype=self.np_dtype)
+        _check(LIB.modil_write_level(self._h, instance, field, level, a.ctypes.data, a.nbytes, 0))
+
+    def write_levels(self, levels, field=0, instance=0):
+        for i, a in enumerate(levels):
+            self.write_level(i, a, field, instance)
+
+    def _read(self, fn, level, field, instance, shape):
+        out = np.empty(shape, dtype=self.np_dtype)
+        _check(fn(self._h, instance, field, level, out.ctypes.data, out.nbytes, 0))
+        return out
+
+    def read_level(self, level, field=0, instance=0):
+        return self._read(LIB.modil_read_level, level, field, instance, self.level_shape(level, instance))
+
+    def read_levels(self, field=0, instance=0):
+        return [self.read_level(l, field, instance) for l in range(self.n_levels(instance))]
+
+    def read_grad(self, level, field=0, instance=0):
+        return self._read(LIB.modil_read_grad, level, field, instance, self.level_shape(level, instance))
+
+    def read_grads(self, field=0, instance=0):
+        return [self.read_grad(l, field, instance) for l in range(self.n_levels(instance))]
+
+    def read_field(self, field=0, instance=0):
+        out = np.empty(self.level_shape(0, instance), dtype=self.np_dtype)
+        _check(LIB.modil_read_field(self._h, instance, field, out.ctypes.data, out.nbytes, 0))
+        return out
+
+    def write_knodes(self, q, instance=0):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        _check(LIB.modil_write_knodes(self._h, instance, _dptr(q, C.c_double), len(q)))
+
+    def _kio(self, fn, instance):
+        q = np.empty(len(self.descs[instance]._knodes), dtype=np.float64)
+        _check(fn(self._h, instance, _dptr(q, C.c_double), len(q)))
+        return q
+
+    def read_knodes(self, instance=0):
+        return self._kio(LIB.modil_read_knodes, instance)
+
+    def read_kgrad(self, instance=0):
+        return self._kio(LIB.modil_read_kgrad, instance)
+
+    # -- evaluation and steps ------------------------------------------------
+    def _terms(self):
+        return np.zeros(self.n * NTERMS, dtype=np.float64)
+
+    def eval_loss(self):
+        t = self._terms()
+        _check(LIB.modil_eval_loss(self._h, _dptr(t, C.c_double)))
+        return t.reshape(self.n, NTERMS)
+
+    def eval_grad(self):
+        t = self._terms()
+        _check(LIB.modil_eval_grad(self._h, _dptr(t, C.c_double)))
+        return t.reshape(self.n, NTERMS)
+
+    def step(self, n=1, read_loss=True):
+        if read_loss:
+            t = self._terms()
+            _check(LIB.modil_step(self._h, int(n), _dptr(t, C.c_double)))
+            return t.reshape(self.n, NTERMS)
+        _check(LIB.modil_step(self._h, int(n), None))
+        return None
+
+    def step_count(self):
+        t = C.c_longlong()
+        _check(LIB.modil_step_count(self._h, C.byref(t)))
+        return t.value
+
+    def launches_per_step(self):
+        n = C.c_int()
+        _check(LIB.modil_launches_per_step(self._h, C.byref(n)))
+        return n.value
+
+    def profile_step(self):
+        """One step launched kernel by kernel; returns the device ms of each launch."""
+        cap = 64
+        ms = (C.c_float * cap)()
+        n = C.c_int()
+        _check(LIB.modil_profile_step(self._h, ms, cap, C.byref(n)))
+        return [ms[i] for i in range(n.value)]
+
+    def reset_optimizer(self):
+        _check(LIB.modil_reset_optimizer(self._h))
+
+
+def version():
+    return LIB.modil_version().decode()

@@ -1,0 +1,81 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/modil.h declares, and validates descriptors."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(modil_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def mod():
+    from paper_2303_04679_gb300 import build
+    build.build()
+    from paper_2303_04679_gb300 import modil
+    return modil
+
+
+def test_library_exports_every_declared_symbol(mod):
+    names = _declared()
+    assert len(names) >= 19
+    missing = [n for n in sorted(names) if not hasattr(mod.LIB, n)]
+    assert not missing, missing
+
+
+def test_version_string(mod):
+    assert "sm_103a" in mod.version()
+
+
+def _heat(mod, shape=(64, 64), L=4, **kw):
+    nt, nx = shape
+    return mod.Desc("heat", shape, L, aux=np.zeros(nx), knodes=np.full(32, 0.02), **kw)
+
+
+def test_arena_bytes_grows_with_problem(mod):
+    a = mod.arena_bytes([_heat(mod, (64, 64), 4)])
+    b = mod.arena_bytes([_heat(mod, (128, 128), 4)])
+    c = mod.arena_bytes([_heat(mod, (64, 64), 4), _heat(mod, (64, 64), 4)])
+    assert 0 < a < b and a < c
+    # p0, p1, m, g (4 B) + v (8 B) per parameter at least
+    P = sum((64 >> l) ** 2 for l in range(4))
+    assert a >= 24 * P
+
+
+@pytest.mark.parametrize("bad", [
+    dict(shape=(60, 64), L=4),        # 60 not divisible by 8
+    dict(shape=(64, 64), L=11),       # too many levels
+    dict(shape=(64, 64), L=0),
+])
+def test_arena_bytes_rejects_bad_grids(mod, bad):
+    with pytest.raises(mod.ModilError) as e:
+        mod.arena_bytes([_heat(mod, bad["shape"], bad["L"])])
+    assert e.value.code == -1
+
+
+def test_rejects_bad_measurements_and_mixed_batches(mod):
+    d = mod.Desc("burgers", (16, 16), 2, coef=(0.01,), meas_cell=[0, 300], meas_value=[1.0, 2.0])
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([d])
+    d = mod.Desc("burgers", (16, 16), 2, coef=(0.01,), meas_cell=[3], meas_value=[np.nan])
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([d])
+    a = mod.Desc("burgers", (16, 16), 2, coef=(0.01,))
+    b = mod.Desc("burgers", (16, 16), 2, coef=(0.01,), dtype="f64")
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([a, b])
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([mod.Desc("heat", (16, 16), 2)])  # no initial profile / nodes
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([mod.Desc("burgers", (16, 16), 2, tile=(7, 7))])
