@@ -156,6 +156,31 @@ modil_status modil_step_count(const modil_problem* p, long long* t);
 /* Zero the Adam moments and the step counter of every instance. */
 modil_status modil_reset_optimizer(modil_problem* p);
 
+/* Loss and gradient of ONE problem with no device allocation at all.
+ * The paper has no counterpart: this is an interface for callers that cannot
+ * allocate device memory -- plug-ins whose host application owns every device
+ * allocation through its own pool, loops that must not allocate once running
+ * (cudaMalloc can synchronise the device), or code that only holds the
+ * buffers it was given.  The working memory (per-tile partial sums, problem
+ * tables, measurement runs) lives in one file-scope __device__ array of 8 MiB
+ * that every GPU loading the library keeps until the process exits.
+ *   desc:   one problem, as for modil_create (read on the host).
+ *   levels: device, all levels of field 0 back to back (level 0 first, each
+ *           row-major), dtype of desc.  Conductivity nodes come from desc.
+ *   grads:  device output, dL/du of every level, same layout as levels.
+ *   terms:  host output, MODIL_NTERMS doubles.  kgrad: host output of n_knodes
+ *           doubles (heat) or NULL.
+ *   stream: cudaStream_t; the call synchronises it before returning.
+ * Returns MODIL_ERR_ARG if the problem needs more than the 8 MiB of working
+ * memory.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array, which keeps the last call's contents (every
+ * value a call reads is written by that call first), so calls that overlap on
+ * the GPU -- on different streams or threads -- race and must be serialised
+ * by the caller.  Calls no cudaMalloc, cudaFree or allocating routine. */
+modil_status modil_eval_grad_noalloc(const modil_desc* desc, const void* levels, void* grads,
+                                     double* terms, double* kgrad, void* stream);
+
 /* Last error message of the calling thread ("" if none). */
 const char* modil_last_error(void);
 

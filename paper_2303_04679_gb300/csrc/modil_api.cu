@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -652,3 +653,140 @@ const char* modil_last_error(void) { return g_err.c_str(); }
 const char* modil_version(void) { return "modil-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Loss and gradient without any device allocation.
+//
+// Some callers cannot allocate device memory: a host application or framework
+// that owns every device allocation through its own pool (and forbids raw
+// cudaMalloc from plug-ins), code that must not allocate once it is running
+// (real-time loops, which cudaMalloc would stall by synchronising the device),
+// or a caller that holds only the buffers it was handed.  For them this entry
+// point keeps its working memory -- the per-tile partial sums, the problem
+// tables and the measurement runs -- in one file-scope __device__ array of
+// kNoAllocScratchBytes.  Every GPU that loads the library holds the array until
+// the process exits.  In host code the array's name is only a host-side
+// stand-in, so the device address is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+modil_status noalloc_scratch(void** out) {
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(MODIL_ERR_UNSUPPORTED, "device ordinal too large");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(MODIL_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MODIL_OK;
+}
+
+template <class T>
+modil_status noalloc_run(const Plan& P, const modil_desc* d, const void* levels, void* grads,
+                         double* terms, double* kgrad, cudaStream_t s) {
+  void* base = nullptr;
+  modil_status st = noalloc_scratch(&base);
+  if (st != MODIL_OK) return st;
+  // compact layout of what the kernels read or write besides levels and grads
+  size_t o = 0;
+  auto take = [&](size_t bytes) { const size_t r = o; o = align256(o + std::max<size_t>(bytes, 1)); return r; };
+  const size_t nft = P.tile_inst[0].size();
+  const size_t o_kq = take(sizeof(T) * P.n_k), o_kg = take(sizeof(T) * P.n_k);
+  const size_t o_aux = take(sizeof(T) * P.n_aux);
+  const size_t o_part = take(8 * nft * P.npart);
+  const size_t o_rptr = take(4 * P.run_ptr.size()), o_rcell = take(4 * P.run_cell.size());
+  const size_t o_rfield = take(4 * P.run_field.size()), o_rbeg = take(4 * P.run_beg.size());
+  const size_t o_mval = take(sizeof(T) * P.meas_val.size());
+  const size_t o_inst = take(sizeof(DevInst)), o_st = take(sizeof(InstState));
+  size_t o_ti[MODIL_MAXL];
+  for (int l = 0; l < MODIL_MAXL; ++l) o_ti[l] = take(4 * P.tile_inst[l].size());
+  if (o > kNoAllocScratchBytes)
+    return fail(MODIL_ERR_ARG, "problem needs " + std::to_string(o) + " scratch bytes; the allocation-free "
+                "entry point holds at most " + std::to_string(kNoAllocScratchBytes));
+  char* b = static_cast<char*>(base);
+  auto up = [&](size_t off, const void* src, size_t bytes) -> modil_status {
+    if (bytes) CUDA_TRY(cudaMemcpyAsync(b + off, src, bytes, cudaMemcpyHostToDevice, s));
+    return MODIL_OK;
+  };
+  std::vector<T> kq(d->n_knodes > 0 && P.nk ? d->knodes : nullptr,
+                    d->n_knodes > 0 && P.nk ? d->knodes + P.nk : nullptr);
+  std::vector<T> aux(P.n_aux ? d->aux : nullptr, P.n_aux ? d->aux + P.n_aux : nullptr);
+  std::vector<T> mv(P.meas_val.begin(), P.meas_val.end());
+  InstState st0;
+  std::memset(&st0, 0, sizeof(st0));
+  st0.b1t = 1.0;
+  st0.b2t = 1.0;
+  if ((st = up(o_kq, kq.data(), sizeof(T) * kq.size())) != MODIL_OK) return st;
+  if ((st = up(o_aux, aux.data(), sizeof(T) * aux.size())) != MODIL_OK) return st;
+  if ((st = up(o_rptr, P.run_ptr.data(), 4 * P.run_ptr.size())) != MODIL_OK) return st;
+  if ((st = up(o_rcell, P.run_cell.data(), 4 * P.run_cell.size())) != MODIL_OK) return st;
+  if ((st = up(o_rfield, P.run_field.data(), 4 * P.run_field.size())) != MODIL_OK) return st;
+  if ((st = up(o_rbeg, P.run_beg.data(), 4 * P.run_beg.size())) != MODIL_OK) return st;
+  if ((st = up(o_mval, mv.data(), sizeof(T) * mv.size())) != MODIL_OK) return st;
+  if ((st = up(o_inst, P.dev.data(), sizeof(DevInst))) != MODIL_OK) return st;
+  if ((st = up(o_st, &st0, sizeof(st0))) != MODIL_OK) return st;
+  for (int l = 0; l < MODIL_MAXL; ++l)
+    if ((st = up(o_ti[l], P.tile_inst[l].data(), 4 * P.tile_inst[l].size())) != MODIL_OK) return st;
+  Arena<T> A{};
+  A.p[0] = const_cast<T*>(static_cast<const T*>(levels));
+  A.p[1] = nullptr;
+  A.g = static_cast<T*>(grads);
+  A.kq = reinterpret_cast<T*>(b + o_kq);
+  A.kg = reinterpret_cast<T*>(b + o_kg);
+  A.aux = reinterpret_cast<const T*>(b + o_aux);
+  A.part = reinterpret_cast<double*>(b + o_part);
+  A.run_ptr = reinterpret_cast<const int*>(b + o_rptr);
+  A.run_cell = reinterpret_cast<const int*>(b + o_rcell);
+  A.run_field = reinterpret_cast<const int*>(b + o_rfield);
+  A.run_beg = reinterpret_cast<const int*>(b + o_rbeg);
+  A.meas_val = reinterpret_cast<const T*>(b + o_mval);
+  A.inst = reinterpret_cast<const DevInst*>(b + o_inst);
+  A.st = reinterpret_cast<InstState*>(b + o_st);
+  for (int l = 0; l < MODIL_MAXL; ++l) {
+    A.tile_inst[l] = reinterpret_cast<const int*>(b + o_ti[l]);
+    A.ntiles[l] = (int)P.tile_inst[l].size();
+  }
+  A.npart = P.npart;
+  A.n_inst = 1;
+  CUDA_TRY((prepare_fine_st<T>(P.pde, P.cfg, P.pyr_elems)));
+  CUDA_TRY(launch_fine_st<T>(A, P.pde, P.cfg, MODE_GRAD, P.pyr_elems, s));
+  for (int l = 1; l < P.max_lev; ++l) CUDA_TRY(launch_level<T>(A, l, MODE_GRAD, s));
+  CUDA_TRY(launch_finalize<T>(A, MODE_GRAD, s));
+  InstState out;
+  CUDA_TRY(cudaMemcpyAsync(&out, b + o_st, sizeof(out), cudaMemcpyDeviceToHost, s));
+  std::vector<T> kg(P.nk);
+  if (kgrad && P.nk) CUDA_TRY(cudaMemcpyAsync(kg.data(), b + o_kg, sizeof(T) * P.nk, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (int j = 0; j < MODIL_NTERMS; ++j) terms[j] = out.terms[j];
+  if (kgrad)
+    for (int j = 0; j < P.nk; ++j) kgrad[j] = (double)kg[j];
+  if (out.nonfinite) return fail(MODIL_ERR_NONFINITE, "loss became non-finite");
+  return MODIL_OK;
+}
+
+}  // namespace
+
+extern "C" modil_status modil_eval_grad_noalloc(const modil_desc* desc, const void* levels,
+                                                void* grads, double* terms, double* kgrad,
+                                                void* stream) {
+  if (!desc || !levels || !grads || !terms) return fail(MODIL_ERR_ARG, "NULL argument");
+  Plan P;
+  modil_status s = make_plan(desc, 1, P);
+  if (s != MODIL_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return P.dtype == MODIL_F64 ? noalloc_run<double>(P, desc, levels, grads, terms, kgrad, st)
+                              : noalloc_run<float>(P, desc, levels, grads, terms, kgrad, st);
+}

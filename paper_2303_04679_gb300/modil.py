@@ -72,6 +72,8 @@ def _load():
         "modil_launches_per_step": ([P, C.POINTER(C.c_int)], C.c_int),
         "modil_profile_step": ([P, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)], C.c_int),
         "modil_reset_optimizer": ([P], C.c_int),
+        "modil_eval_grad_noalloc": ([C.POINTER(modil_desc), P, P, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), P], C.c_int),
         "modil_last_error": ([], C.c_char_p),
         "modil_version": ([], C.c_char_p),
     }
@@ -293,6 +295,24 @@ class Problem:
 
     def reset_optimizer(self):
         _check(LIB.modil_reset_optimizer(self._h))
+
+
+def eval_grad_noalloc(desc, levels, grads, stream=None):
+    """Loss and gradient of one problem with no device allocation.
+
+    ``levels`` and ``grads`` are device tensors holding all levels back to back
+    (level 0 first); returns (terms, kgrad).  The library keeps its working
+    memory in a fixed 8 MiB device array, for callers that cannot allocate.
+    """
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    terms = np.zeros(NTERMS, dtype=np.float64)
+    nk = 0 if desc._knodes is None else len(desc._knodes)
+    kg = np.zeros(max(nk, 1), dtype=np.float64)
+    _check(LIB.modil_eval_grad_noalloc(C.byref(desc.c), levels.data_ptr(), grads.data_ptr(),
+                                       _dptr(terms, C.c_double),
+                                       _dptr(kg, C.c_double) if nk else None, s.cuda_stream))
+    return terms, kg[:nk]
 
 
 def version():
