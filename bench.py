@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="modil", choices=["modil", "reference"])
-    ap.add_argument("--tile", default="16x64")
+    ap.add_argument("--tile", default="16x32")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=50)
@@ -289,7 +289,8 @@ def main():
         prof.append(prob.profile_step())
     prof = np.array(prof)
     kern_ms = prof.mean(axis=0)
-    names = ["fine_tile_fused"] + [f"restrict_adam_L{l + 1}" for l in range(1, w["n_levels"])] + ["finalize"]
+    names = (["fine_tile_fused"] + [f"restrict_adam_L{l + 1}" for l in range(1, len(kern_ms) - 1)]
+             + ["coarse_tail"])
     dom = int(np.argmax(kern_ms))
     peak, peak_kind = measured_peak()
     dom_bytes = fine_alg_bytes if dom == 0 else None

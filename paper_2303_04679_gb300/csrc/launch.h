@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <algorithm>
+
 #include "modil_dev.cuh"
 
 namespace modil {
@@ -12,19 +14,39 @@ namespace modil {
 constexpr int kNumTileCfg = 5;
 constexpr int kTileCfg[kNumTileCfg][2] = {{16, 32}, {16, 64}, {8, 64}, {32, 32}, {8, 128}};
 // Tile of the restriction kernels (coarse levels), rows x cols.
-constexpr int kLevTY = 8, kLevTX = 64;
+constexpr int kLevTY = 8, kLevTX = 32;
+
+// Levels with at most this many cells are finished by the per-instance tail
+// kernel (FP32 / FP64 problems).
+constexpr int kTailCellsF32 = 4096;
+constexpr int kTailCellsF64 = 1024;
+
+// What the tail kernel of a batch needs (maxima over the instances).
+struct TailPlan {
+  int level_kernels = 0;     // restriction kernels between the fine kernel and the tail
+  size_t prev_cells = 0;     // cells of the level just above the tail levels
+  size_t tail_cells = 0;     // cells of the tail levels
+  size_t smem_bytes = 0;     // dynamic shared memory of a tail block
+};
+// Blocks per instance of the tail kernel (one thread-block cluster).
+constexpr int kTailC = 8;
 
 size_t fine_st_smem_bytes(int cfg, size_t pyr_elems, int elem_bytes);
 template <class T>
 cudaError_t prepare_fine_st(int pde, int cfg, size_t pyr_elems);
 template <class T>
-cudaError_t launch_fine_st(const Arena<T>& A, int pde, int cfg, int mode, size_t pyr_elems,
-                           cudaStream_t s);
+cudaError_t launch_fine_st(const Arena<T>& A, int pde, int cfg, int mode, int cur,
+                           size_t pyr_elems, cudaStream_t s);
 template <class T>
-cudaError_t launch_level(const Arena<T>& A, int level, int mode, cudaStream_t s);
+cudaError_t launch_level(const Arena<T>& A, int level, int mode, int cur, cudaStream_t s);
+size_t tail_smem_bytes(const TailPlan& tp, int elem_bytes);
+size_t tail_instance_bytes(int L, int ts, const int (*n)[3], int elem_bytes);
 template <class T>
-cudaError_t launch_finalize(const Arena<T>& A, int mode, cudaStream_t s);
+cudaError_t prepare_tail(const TailPlan& tp);
+template <class T>
+cudaError_t launch_tail(const Arena<T>& A, int mode, int cur, const TailPlan& tp, cudaStream_t s);
 template <class T>
 cudaError_t launch_reset(const Arena<T>& A, cudaStream_t s);
+cudaError_t launch_delay(long long ns, cudaStream_t s);
 
 }  // namespace modil

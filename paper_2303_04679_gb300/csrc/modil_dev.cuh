@@ -1,8 +1,9 @@
 // Device-side data structures and helpers of the mODIL library.
 //
 // Memory model.  One arena holds every instance of a batch:
-//   p[2]  level values, ping-pong: a step reads p[t & 1] and writes p[(t+1) & 1]
-//         so that tiles composing the field never see a half-updated level;
+//   p[2]  level values, ping-pong: step t reads p[t & 1] and writes p[(t+1) & 1]
+//         so that tiles composing the field never see a half-updated level
+//         (the buffer index is a kernel argument; the host keeps t);
 //   m     Adam first moment (storage type T);
 //   v     Adam second moment, always FP64;
 //   g     dL/du per level (also the input of the next level's restriction);
@@ -29,6 +30,8 @@ enum Pde { PDE_BURGERS = 1, PDE_HEAT = 2 };
 // Per-instance description (read-only on the device).
 struct DevInst {
   int nlev, nfield, nk, ndim;
+  int tail;                    // first level finished by the per-instance tail kernel
+  int ntile0;                  // fine tiles of this instance
   int n[MODIL_MAXL][3];        // cells per axis per level, slowest first (2-D: n[l][0] = 1)
   int nt[MODIL_MAXL][3];       // tiles per axis per level
   int tile_base[MODIL_MAXL];   // global tile index of this instance's first tile per level
@@ -48,10 +51,21 @@ struct DevInst {
 struct InstState {
   long long t;        // completed Adam steps
   double b1t, b2t;    // beta1^t, beta2^t
+  double c1, c2;      // bias corrections of step t+1: 1/(1-beta1^(t+1)), 1/(1-beta2^(t+1))
   double terms[4];    // total, residual, data, regulariser of the last evaluation
   int nonfinite;      // latched when a loss is NaN/Inf
   int pad;
 };
+
+// Advance the step counter and precompute the next step's bias corrections
+// (one thread; keeps FP64 divisions out of the per-cell code).
+__device__ __forceinline__ void advance_step(InstState& S, double b1, double b2) {
+  S.t += 1;
+  S.b1t *= b1;
+  S.b2t *= b2;
+  S.c1 = 1.0 / (1.0 - S.b1t * b1);
+  S.c2 = 1.0 / (1.0 - S.b2t * b2);
+}
 
 template <class T>
 struct Arena {
@@ -71,8 +85,10 @@ struct Arena {
   const int* run_field;
   const int* run_beg;  // first value of each run; run r spans [run_beg[r], run_beg[r+1])
   const T* meas_val;
+  const T* run_v0;     // first value of each run (meas_val[run_beg[r]])
   const DevInst* inst;
   InstState* st;
+  int* counter;        // per instance: fine tiles done in the current launch
   const int* tile_inst[MODIL_MAXL];  // instance owning each global tile of level l
   int ntiles[MODIL_MAXL];
   int npart;
@@ -83,15 +99,22 @@ struct Arena {
 // Interpolation taps (cell-based linear interpolation, printed 1-D matrices)
 // ---------------------------------------------------------------------------
 
-// Fine cell i of a grid refined from nc coarse cells takes w0*c[j0] + w1*c[j1].
+// Fine cell i of a grid refined from nc coarse cells takes w0*c[j0] + w1*c[j1]:
+// 3/4 of its parent j = i/2 and 1/4 of the nearer neighbour; past the first
+// or last coarse centre the line through the two outermost centres is
+// extended (5/4 and -1/4 of the parent and its inner neighbour); a single
+// coarse cell is copied.  Written with selects only (no divergent branches).
 template <class T>
 __device__ __forceinline__ void prolong_taps(int i, int nc, int& j0, int& j1, T& w0, T& w1) {
-  if (nc == 1) { j0 = 0; j1 = 0; w0 = T(1); w1 = T(0); return; }
   const int j = i >> 1;
-  const int jn = (i & 1) ? j + 1 : j - 1;
-  if (jn < 0) { j0 = 0; j1 = 1; w0 = T(1.25); w1 = T(-0.25); }
-  else if (jn >= nc) { j0 = nc - 1; j1 = nc - 2; w0 = T(1.25); w1 = T(-0.25); }
-  else { j0 = j; j1 = jn; w0 = T(0.75); w1 = T(0.25); }
+  const int s = (i & 1) ? 1 : -1;
+  const int jn = j + s;
+  const bool out = (jn < 0) || (jn >= nc);
+  const bool one = (nc == 1);
+  j0 = j;
+  j1 = one ? 0 : (out ? j - s : jn);
+  w0 = one ? T(1) : (out ? T(1.25) : T(0.75));
+  w1 = one ? T(0) : (out ? T(-0.25) : T(0.25));
 }
 
 // Column j of the interpolation matrix (coarse j <- fine cells): the transposed
@@ -119,17 +142,18 @@ __device__ __forceinline__ int restrict_taps(int j, int nc, int* idx, T* w) {
 // ---------------------------------------------------------------------------
 struct AdamCoef {
   double lr, b1, b2, eps, c1, c2;  // c1 = 1/(1-b1^t), c2 = 1/(1-b2^t)
+  float lrf, b1f, omb1f, omb2f, epsf, c1f, c2f;
 };
 
+// The second moment is accumulated in FP64 (one FMA per cell: GB300 runs FP64
+// at 1/64 of the FP32 rate); the square of the gradient, the first moment and
+// the update are FP32.
 __device__ __forceinline__ void adam_update(float& p, float& m, double& v, float g,
                                             const AdamCoef& c) {
-  const float b1 = (float)c.b1;
-  m = b1 * m + (1.0f - b1) * g;
-  const double gd = (double)g;
-  v = fma(c.b2, v, (1.0 - c.b2) * (gd * gd));
-  const float mh = m * (float)c.c1;
-  const float den = sqrtf((float)v * (float)c.c2) + (float)c.eps;
-  p = p - (float)c.lr * (mh / den);
+  m = c.b1f * m + c.omb1f * g;
+  v = fma(c.b2, v, (double)(c.omb2f * (g * g)));
+  const float den = sqrtf((float)v * c.c2f) + c.epsf;
+  p = p - c.lrf * ((m * c.c1f) / den);
 }
 
 __device__ __forceinline__ void adam_update(double& p, double& m, double& v, double g,
@@ -144,9 +168,35 @@ __device__ __forceinline__ void adam_update(double& p, double& m, double& v, dou
 __device__ __forceinline__ AdamCoef adam_coef(const DevInst& D, const InstState& S) {
   AdamCoef c;
   c.lr = D.lr; c.b1 = D.b1; c.b2 = D.b2; c.eps = D.eps;
-  c.c1 = 1.0 / (1.0 - S.b1t * D.b1);
-  c.c2 = 1.0 / (1.0 - S.b2t * D.b2);
+  c.c1 = S.c1;
+  c.c2 = S.c2;
+  c.lrf = (float)c.lr; c.b1f = (float)c.b1; c.omb1f = (float)(1.0 - c.b1);
+  c.omb2f = (float)(1.0 - c.b2); c.epsf = (float)c.eps; c.c1f = (float)c.c1; c.c2f = (float)c.c2;
   return c;
+}
+
+// Compensated FP32 sum of two (hi, lo) pairs (Knuth's two-sum on the high
+// parts, low parts added): about 48 significant bits with FP32 instructions.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bp = s - hi;
+  float e = (hi - (s - bp)) + (bh - bp);
+  e += lo + bl;
+  const float t = s + e;
+  lo = e - (t - s);
+  hi = t;
+}
+
+// Warp sum in compensated FP32; lane 0's result is the deterministic one.
+__device__ __forceinline__ double warp_sum_ff(float x) {
+  float hi = x, lo = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+    ff_add(hi, lo, bh, bl);
+  }
+  return (double)hi + (double)lo;
 }
 
 // ---------------------------------------------------------------------------
@@ -170,6 +220,51 @@ __device__ __forceinline__ double block_sum(double x, double* scratch) {
 #pragma unroll
   for (int i = 0; i < NT / 32; ++i) s += scratch[i];
   return s;
+}
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Every kernel of a step is launched with
+// programmatic stream serialisation.  Protocol: a kernel may read, before
+// pdl_wait(), only data that no kernel writes or that was last written two or
+// more launches earlier; it calls pdl_wait() and then pdl_trigger(), so its
+// successor's prologue starts only after this kernel's predecessor finished.
+// Without the launch attribute both instructions are no-ops.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Asynchronous global -> shared copies (4 or 8 bytes, any aligned element).
+__device__ __forceinline__ void cp_async(float* dst, const float* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async(double* dst, const double* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Block sum of per-thread FP32 values in compensated FP32, fixed order;
+// every thread gets the result.  scratch: >= NT/16 floats.
+template <int NT>
+__device__ __forceinline__ double block_sum_ff(float x, float* scratch) {
+  float hi = x, lo = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+    ff_add(hi, lo, bh, bl);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { scratch[2 * w] = hi; scratch[2 * w + 1] = lo; }
+  __syncthreads();
+  float sh = scratch[0], sl = scratch[1];
+#pragma unroll
+  for (int i = 1; i < NT / 32; ++i) ff_add(sh, sl, scratch[2 * i], scratch[2 * i + 1]);
+  return (double)sh + (double)sl;
 }
 
 // Copy a POD struct from global to shared memory with the whole block.
