@@ -87,14 +87,14 @@ constexpr int kLevFY = 2 * kLevTY + 4, kLevFX = 2 * kLevTX + 4;  // staged fine 
 
 template <class T>
 __global__ void __launch_bounds__(MODIL_NT)
-k_level(Arena<T> A, int l, int mode, int cur) {
+k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   static_assert(kLevTY * kLevTX == MODIL_NT, "one coarse cell per thread");
   __shared__ DevInst D;
   __shared__ __align__(16) T fineS[kLevFY * kLevFX];
   __shared__ __align__(16) T H[kLevFY * kLevTX];
   const int gt = blockIdx.x;
   const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[l][gt];
-  block_copy(&D, A.inst + ii);
+  load_inst(&D, A, ii);
   __syncthreads();
   const int ny = D.n[l][1], nx = D.n[l][2];
   const int fy = D.n[l - 1][1], fx = D.n[l - 1][2];
@@ -188,7 +188,7 @@ __host__ __device__ inline void tail_layout(int L, int ts, const int (*n)[3], Ta
 
 template <class T>
 __global__ void __cluster_dims__(kTailC, 1, 1) __launch_bounds__(kTailNT)
-k_tail(Arena<T> A, int mode, int cur) {
+k_tail(const __grid_constant__ Arena<T> A, int mode, int cur) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ DevInst D;
   __shared__ TailLayout TL;
@@ -199,7 +199,7 @@ k_tail(Arena<T> A, int mode, int cur) {
   const int r = (int)cluster.block_rank();
   const int ii = blockIdx.x / kTailC;
   const int tid = threadIdx.x;
-  block_copy(&D, A.inst + ii);
+  load_inst(&D, A, ii);
   __syncthreads();
   if (tid == 0) tail_layout(D.nlev, D.tail, D.n, TL);
   __syncthreads();
@@ -291,11 +291,18 @@ k_tail(Arena<T> A, int mode, int cur) {
                                [&](int k, T g) { dst[k] = g; });
     }
     cluster.sync();
+    // every block has read the bias-correction powers: advance them now (off the
+    // critical path of the remaining levels)
+    if (l == ts && mode == MODE_STEP && r == 0 && tid == 0) advance_step(S, D.b1, D.b2);
   }
-  if (!levels) cluster.sync();  // partial sums visible cluster-wide
+  if (!levels) {
+    cluster.sync();  // partial sums visible cluster-wide; powers read by all blocks
+    if (mode == MODE_STEP && r == 0 && tid == 0) advance_step(S, D.b1, D.b2);
+  }
 
   // ---- block 0: loss terms, dL/dq, Adam on the nodes -------------------------
   if (r == 0) {
+    __shared__ double d2s[MODIL_MAXK];
     for (int j = tid; j < nk; j += kTailNT) qs[j] = (double)A.kq[D.k_off + j];
     if (tid < nterm) {
       double v[kTailC];
@@ -307,32 +314,39 @@ k_tail(Arena<T> A, int mode, int cur) {
       chunk[tid] = a;
     }
     __syncthreads();
-    if (tid == 0) {
-      double reg = 0.0;
-      for (int j = 1; j + 1 < nk; ++j) {
-        const double d2 = qs[j + 1] - 2.0 * qs[j] + qs[j - 1];
-        reg += d2 * d2;
+    // second differences d2_j = q_{j+1} - 2 q_j + q_{j-1}, j = 1 .. nk-2, in parallel
+    double dd = 0.0;
+    if (tid < MODIL_MAXK) {
+      d2s[tid] = 0.0;
+      if (tid >= 1 && tid + 1 < nk) {
+        dd = qs[tid + 1] - 2.0 * qs[tid] + qs[tid - 1];
+        d2s[tid] = dd;
       }
-      reg *= D.w_reg;
+    }
+    double reg = 0.0;
+    if (tid < 64) {
+      reg = warp_sum(dd * dd);
+      if ((tid & 31) == 0) chunk[nterm + (tid >> 5)] = reg;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double rg = D.w_reg * (chunk[nterm] + chunk[nterm + 1]);
       const double res = D.w_res_dV * chunk[0];
       const double dat = D.w_data_n * chunk[1];
-      const double tot = res + dat + reg;
+      const double tot = res + dat + rg;
       S.terms[0] = tot;
       S.terms[1] = res;
       S.terms[2] = dat;
-      S.terms[3] = reg;
+      S.terms[3] = rg;
       if (!isfinite(tot)) S.nonfinite = 1;
     }
     if (mode != MODE_LOSS)
       for (int j = tid; j < nk; j += kTailNT) {
         const AdamCoef ac = acS;
-        double g = chunk[2 + j];
-        // d/dq_j of w_reg * sum_i d2_i^2, d2_i = q_{i+1} - 2 q_i + q_{i-1}
-        for (int i = j - 1; i <= j + 1; ++i) {
-          if (i < 1 || i + 1 >= nk) continue;
-          const double d2 = qs[i + 1] - 2.0 * qs[i] + qs[i - 1];
-          g += D.w_reg * 2.0 * d2 * ((i == j) ? -2.0 : 1.0);
-        }
+        // d/dq_j of w_reg * sum_i d2_i^2 = 2 w_reg (d2_{j-1} - 2 d2_j + d2_{j+1})
+        const double dm = (j >= 1) ? d2s[j - 1] : 0.0;
+        const double dp = (j + 1 < MODIL_MAXK) ? d2s[j + 1] : 0.0;
+        const double g = chunk[2 + j] + 2.0 * D.w_reg * (dm - 2.0 * d2s[j] + dp);
         A.kg[D.k_off + j] = (T)g;
         if (mode == MODE_STEP) {
           T p = (T)qs[j];
@@ -370,14 +384,12 @@ k_tail(Arena<T> A, int mode, int cur) {
       }
     }
   }
-  // every block has read the bias-correction powers and no block still reads
-  // another block's shared memory
+  // no block may exit while another still reads its shared memory
   cluster.sync();
-  if (mode == MODE_STEP && r == 0 && tid == 0) advance_step(S, D.b1, D.b2);
 }
 
 template <class T>
-__global__ void k_reset(Arena<T> A) {
+__global__ void k_reset(const __grid_constant__ Arena<T> A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < A.n_inst) {
     InstState s;

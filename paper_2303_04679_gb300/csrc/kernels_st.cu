@@ -93,7 +93,7 @@ __device__ __forceinline__ T eo_flux(T a, T b, T& da, T& db) {
 
 template <class T, int PDE, int TY, int TX>
 __global__ void __launch_bounds__(MODIL_NT)
-k_fine_st(Arena<T> A, int mode, int cur) {
+k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
   using G = StGeom<TY, TX>;
   using S = StSmem<T, TY, TX>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -127,7 +127,7 @@ k_fine_st(Arena<T> A, int mode, int cur) {
   const int gt = blockIdx.x;
   // ---- prologue: data no kernel of a step writes -----------------------------
   const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[0][gt];
-  block_copy(&D, A.inst + ii);
+  load_inst(&D, A, ii);
   const int rb = A.run_ptr[gt], re = A.run_ptr[gt + 1];
   const int nrun = min(re - rb, TY * TX);  // runs hold distinct cells of the tile
   __syncthreads();
@@ -222,12 +222,12 @@ k_fine_st(Arena<T> A, int mode, int cur) {
   __syncthreads();
 
   // ---- 1. Horner on the pyramid: w_l += T w_{l+1}, coarse to fine ----------
-  for (int l = L - 2; l >= 0; --l) {
+  auto horner_level = [&](int l, int first, int stride) {
     const int nyc = D.n[l + 1][1], nxc = D.n[l + 1][2];
     const T* wc = pyr + poff[l + 1];
     const int cw = wid[l + 1], cly = loy[l + 1], clx = lox[l + 1];
     const int nreg = (l == 0) ? G::UH * G::UW : hgt[l] * wid[l];
-    for (int idx = tid; idx < nreg; idx += MODIL_NT) {
+    for (int idx = first; idx < nreg; idx += stride) {
       int y, x;
       if (l == 0) {
         const int ry = idx / G::UW, rx = idx - ry * G::UW;
@@ -249,6 +249,17 @@ k_fine_st(Arena<T> A, int mode, int cur) {
       T* dst = (l == 0) ? uR + idx : pyr + poff[l] + idx;
       *dst += add;
     }
+  };
+  // the small coarse regions (levels >= 2) by one warp, warp-synchronously
+  if (tid < 32) {
+    for (int l = L - 2; l >= 2; --l) {
+      horner_level(l, tid, 32);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int l = min(1, L - 2); l >= 0; --l) {
+    horner_level(l, tid, MODIL_NT);
     __syncthreads();
   }
 

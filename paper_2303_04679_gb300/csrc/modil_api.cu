@@ -321,6 +321,7 @@ void fill_arena(modil_problem* p, Arena<T>& A) {
   }
   A.npart = P.npart;
   A.n_inst = P.n_inst;
+  A.inst0 = P.dev[0];
 }
 
 template <class T>
@@ -813,6 +814,7 @@ modil_status noalloc_run(const Plan& P, const modil_desc* d, const void* levels,
   }
   A.npart = P.npart;
   A.n_inst = 1;
+  A.inst0 = P.dev[0];
   CUDA_TRY((prepare_fine_st<T>(P.pde, P.cfg, P.pyr_elems)));
   CUDA_TRY(prepare_tail<T>(P.tail));
   CUDA_TRY(launch_fine_st<T>(A, P.pde, P.cfg, MODE_GRAD, 0, P.pyr_elems, s));

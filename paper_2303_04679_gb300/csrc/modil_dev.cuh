@@ -87,6 +87,7 @@ struct Arena {
   const T* meas_val;
   const T* run_v0;     // first value of each run (meas_val[run_beg[r]])
   const DevInst* inst;
+  DevInst inst0;       // copy of instance 0 in the kernel parameters (read when n_inst == 1)
   InstState* st;
   int* counter;        // per instance: fine tiles done in the current launch
   const int* tile_inst[MODIL_MAXL];  // instance owning each global tile of level l
@@ -267,6 +268,12 @@ __device__ __forceinline__ double block_sum_ff(float x, float* scratch) {
   return (double)sh + (double)sl;
 }
 
+// The descriptor of instance ii into shared memory: from the kernel
+// parameters for a single instance (no global-memory round trip), else from
+// the descriptor table.
+template <class AR>
+__device__ __forceinline__ void load_inst(DevInst* dst, const AR& A, int ii);
+
 // Copy a POD struct from global to shared memory with the whole block.
 template <class S>
 __device__ __forceinline__ void block_copy(S* dst, const S* src) {
@@ -274,6 +281,12 @@ __device__ __forceinline__ void block_copy(S* dst, const S* src) {
   const int* s = reinterpret_cast<const int*>(src);
   int* d = reinterpret_cast<int*>(dst);
   for (int i = threadIdx.x; i < (int)(sizeof(S) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+template <class AR>
+__device__ __forceinline__ void load_inst(DevInst* dst, const AR& A, int ii) {
+  if (A.n_inst == 1) block_copy(dst, &A.inst0);
+  else block_copy(dst, A.inst + ii);
 }
 
 }  // namespace modil
