@@ -44,7 +44,7 @@ __all__ = [
     "heat_conductivity", "heat_residual", "poisson_residual", "loss_terms",
     "loss_grad_fine", "loss_grad_levels", "adam_step", "OracleState",
     "oracle_step", "burgers_explicit_solve", "heat_implicit_solve",
-    "eo_flux",
+    "eo_flux", "ns2d_residuals", "ns2d_fields_residual_jacobian_grad",
 ]
 
 
@@ -198,7 +198,7 @@ class Problem:
 
     @property
     def n_fields(self):
-        return 1
+        return 3 if self.pde == "ns2d" else 1
 
     def spacing(self):
         """Grid spacings per axis (same order as shape)."""
@@ -206,7 +206,7 @@ class Problem:
             return (1.0 / self.shape[0], 2.0 / self.shape[1])
         if self.pde == "heat":          # t in [0,1], x in [0,1]
             return (1.0 / self.shape[0], 1.0 / self.shape[1])
-        if self.pde == "poisson":       # unit cube
+        if self.pde in ("poisson", "ns2d"):  # unit square / cube
             return tuple(1.0 / n for n in self.shape)
         raise ValueError(self.pde)
 
@@ -456,10 +456,125 @@ def _poisson_adjoint(u, lam, h, layout):
 
 
 # ---------------------------------------------------------------------------
+# Steady incompressible Navier-Stokes, lid-driven cavity (Section 3.3)
+# ---------------------------------------------------------------------------
+# Reading.  Collocated cell-centred finite volumes on [0,1]^2, N x N cells,
+# fields u, v, p, axes (y, x).  No-slip walls by ghost cells: the wall value
+# is the mean of the ghost and the adjacent cell (lid u = 1 at y = 1), zero
+# normal pressure gradient (ghost p = adjacent p).  Momentum residuals use
+# conservative central convection with face-averaged velocities (zero mass
+# flux through walls), the central pressure gradient and the 5-point viscous
+# term with 1/Re.  The continuity residual uses Rhie-Chow face velocities at
+# interior faces,
+#   U_e = (u_P + u_E)/2 - tau [ (p_E - p_P)/h - (g_P + g_E)/2 ],  g = (p_E - p_W)/(2h),
+# tau = tau_factor * h, and zero flux through walls.  The pressure level is
+# fixed by one extra residual p(0, 0).  Everything is polynomial in the
+# unknowns (no branches), so the residual accepts complex input.
+
+def _ns2d_pad(u, v, p, lid=1.0):
+    n0, n1 = u.shape
+    U = np.zeros((n0 + 2, n1 + 2), dtype=u.dtype)
+    V = np.zeros_like(U)
+    Pp = np.zeros_like(U)
+    U[1:-1, 1:-1], V[1:-1, 1:-1], Pp[1:-1, 1:-1] = u, v, p
+    U[1:-1, 0], U[1:-1, -1] = -u[:, 0], -u[:, -1]
+    U[0, 1:-1], U[-1, 1:-1] = -u[0, :], 2.0 * lid - u[-1, :]
+    V[1:-1, 0], V[1:-1, -1] = -v[:, 0], -v[:, -1]
+    V[0, 1:-1], V[-1, 1:-1] = -v[0, :], -v[-1, :]
+    Pp[1:-1, 0], Pp[1:-1, -1] = p[:, 0], p[:, -1]
+    Pp[0, 1:-1], Pp[-1, 1:-1] = p[0, :], p[-1, :]
+    return U, V, Pp
+
+
+def ns2d_residuals(u, v, p, Re, h, tau_factor=1.0, lid=1.0):
+    """Residuals (r_u, r_v, r_c) on every cell and the gauge residual p(0,0)."""
+    n0, n1 = u.shape
+    U, V, Pp = _ns2d_pad(u, v, p, lid)
+    C = (slice(1, -1), slice(1, -1))
+    E = (slice(1, -1), slice(2, None))
+    W = (slice(1, -1), slice(0, -2))
+    N = (slice(2, None), slice(1, -1))
+    S = (slice(0, -2), slice(1, -1))
+    jj, ii = np.meshgrid(np.arange(n0), np.arange(n1), indexing="ij")
+    me, mw, mn, ms = ii < n1 - 1, ii > 0, jj < n0 - 1, jj > 0   # interior faces
+    nu = 1.0 / Re
+    ue, uw, un, us = (U[C] + U[E]) / 2, (U[W] + U[C]) / 2, (U[C] + U[N]) / 2, (U[S] + U[C]) / 2
+    ve, vw, vn, vs = (V[C] + V[E]) / 2, (V[W] + V[C]) / 2, (V[C] + V[N]) / 2, (V[S] + V[C]) / 2
+    conv_u = (np.where(me, ue * ue, 0) - np.where(mw, uw * uw, 0)
+              + np.where(mn, vn * un, 0) - np.where(ms, vs * us, 0)) / h
+    conv_v = (np.where(me, ue * ve, 0) - np.where(mw, uw * vw, 0)
+              + np.where(mn, vn * vn, 0) - np.where(ms, vs * vs, 0)) / h
+    lap_u = (U[E] + U[W] + U[N] + U[S] - 4 * U[C]) / h**2
+    lap_v = (V[E] + V[W] + V[N] + V[S] - 4 * V[C]) / h**2
+    gx = (Pp[E] - Pp[W]) / (2 * h)
+    gy = (Pp[N] - Pp[S]) / (2 * h)
+    ru = conv_u + gx - nu * lap_u
+    rv = conv_v + gy - nu * lap_v
+    tau = tau_factor * h
+    # Rhie-Chow face velocities at interior faces (index of the face's west/south cell)
+    Ux = (u[:, :-1] + u[:, 1:]) / 2 - tau * ((p[:, 1:] - p[:, :-1]) / h - (gx[:, :-1] + gx[:, 1:]) / 2)
+    Vy = (v[:-1, :] + v[1:, :]) / 2 - tau * ((p[1:, :] - p[:-1, :]) / h - (gy[:-1, :] + gy[1:, :]) / 2)
+    Fx = np.zeros((n0, n1 + 1), dtype=Ux.dtype)
+    Fy = np.zeros((n0 + 1, n1), dtype=Vy.dtype)
+    Fx[:, 1:-1] = Ux
+    Fy[1:-1, :] = Vy
+    rc = (Fx[:, 1:] - Fx[:, :-1] + Fy[1:, :] - Fy[:-1, :]) / h
+    return ru, rv, rc, p[0, 0]
+
+
+def ns2d_fields_residual_jacobian_grad(u, v, p, lam_u, lam_v, lam_c, Re, h, tau_factor=1.0,
+                                       lid=1.0, eps=1e-30):
+    """J^T lambda for the three residual fields, J by complex-step differentiation.
+
+    Every residual reads unknowns at most 2 cells away along each axis, so the
+    unknowns of one field on cells (a, b) mod 5 never share a residual: one
+    complex evaluation per (field, a, b) perturbs all of them at once and
+    yields their Jacobian columns exactly (the imaginary part of r(w + i eps e)
+    is eps dr/dw to rounding, with no subtraction).  75 evaluations in all.
+    """
+    n0, n1 = u.shape
+    base = [np.asarray(u, complex), np.asarray(v, complex), np.asarray(p, complex)]
+    grads = [np.zeros((n0, n1)) for _ in range(3)]
+    jj, ii = np.meshgrid(np.arange(n0), np.arange(n1), indexing="ij")
+    for f in range(3):
+        for a in range(5):
+            for b in range(5):
+                w = [x.copy() for x in base]
+                sel = ((jj % 5) == a) & ((ii % 5) == b)
+                w[f] = w[f] + 1j * eps * sel
+                ru, rv, rc, _ = ns2d_residuals(w[0], w[1], w[2], Re, h, tau_factor, lid)
+                # the perturbed cell in each residual's 5 x 5 neighbourhood
+                dj = ((a - jj + 2) % 5) - 2
+                di = ((b - ii + 2) % 5) - 2
+                tj, ti = jj + dj, ii + di
+                ok = (tj >= 0) & (tj < n0) & (ti >= 0) & (ti < n1)
+                contrib = (ru.imag * lam_u + rv.imag * lam_v + rc.imag * lam_c) / eps
+                np.add.at(grads[f], (tj[ok], ti[ok]), contrib[ok])
+    return grads
+
+
+# ---------------------------------------------------------------------------
 # Loss and gradient
 # ---------------------------------------------------------------------------
 
 def _data_term(p, u):
+    """Data term of one field u, or of a list of fields (meas_field selects)."""
+    if isinstance(u, (list, tuple)):
+        if p.meas_cell is None or len(p.meas_cell) == 0:
+            return 0.0, [np.zeros_like(x) for x in u]
+        mf = np.zeros(len(p.meas_cell), int) if p.meas_field is None else np.asarray(p.meas_field)
+        w = p.w_data / len(p.meas_cell)
+        total = 0.0
+        gs = []
+        for f, x in enumerate(u):
+            sel = mf == f
+            flat = x.reshape(-1)
+            diff = flat[p.meas_cell[sel]] - p.meas_value[sel]
+            g = np.zeros_like(flat)
+            np.add.at(g, p.meas_cell[sel], 2.0 * w * diff)
+            total += float(w * np.sum(diff * diff))
+            gs.append(g.reshape(x.shape))
+        return total, gs
     if p.meas_cell is None or len(p.meas_cell) == 0:
         return 0.0, np.zeros_like(u)
     flat = u.reshape(-1)
@@ -486,6 +601,10 @@ def loss_terms(p, u, q=None):
         if p.layout == "node":
             hb = np.prod(h[1:]) if len(h) > 1 else 1.0
             bnd = p.w_res * hb * float(np.sum(u[_poisson_boundary_mask(u.shape)] ** 2))
+    elif p.pde == "ns2d":
+        ru, rv, rc, rg = ns2d_residuals(u[0], u[1], u[2], p.coef["Re"], h[0],
+                                        p.coef.get("tau", 1.0))
+        r = np.concatenate([ru.ravel(), rv.ravel(), rc.ravel(), [rg]])
     else:
         raise ValueError(p.pde)
     res = p.w_res * dV * float(np.sum(r * r)) + bnd
@@ -513,6 +632,15 @@ def loss_grad_fine(p, u, q=None):
             hb = np.prod(h[1:]) if len(h) > 1 else 1.0
             m = _poisson_boundary_mask(u.shape)
             g = g + np.where(m, 2.0 * p.w_res * hb * u, 0.0)
+    elif p.pde == "ns2d":
+        Re, tf = p.coef["Re"], p.coef.get("tau", 1.0)
+        ru, rv, rc, rg = ns2d_residuals(u[0], u[1], u[2], Re, h[0], tf)
+        c = 2.0 * p.w_res * dV
+        g = ns2d_fields_residual_jacobian_grad(u[0], u[1], u[2], c * ru, c * rv, c * rc, Re,
+                                               h[0], tf)
+        g[2][0, 0] += c * rg
+        _, gd = _data_term(p, list(u))
+        return terms, [a + b for a, b in zip(g, gd)], gq
     else:
         raise ValueError(p.pde)
     _, gd = _data_term(p, u)
@@ -520,7 +648,14 @@ def loss_grad_fine(p, u, q=None):
 
 
 def loss_grad_levels(p, levels, q=None):
-    """Loss terms and the gradient with respect to every level (and q)."""
+    """Loss terms and the gradient with respect to every level (and q).
+
+    Multi-field problems take and return a list over fields of level lists.
+    """
+    if p.n_fields > 1:
+        u = [compose(lv, p.layout) for lv in levels]
+        terms, g, gq = loss_grad_fine(p, u, q)
+        return terms, [chain_grad(gf, len(lv), p.layout) for gf, lv in zip(g, levels)], gq
     u = compose(levels, p.layout)
     terms, g, gq = loss_grad_fine(p, u, q)
     return terms, chain_grad(g, len(levels), p.layout), gq
@@ -551,6 +686,10 @@ class OracleState:
 
     @classmethod
     def zeros_like_levels(cls, levels, q=None):
+        if levels and isinstance(levels[0], (list, tuple)):  # several fields
+            return cls([[np.array(a, dtype=np.float64) for a in lv] for lv in levels],
+                       [[np.zeros_like(a) for a in lv] for lv in levels],
+                       [[np.zeros_like(a) for a in lv] for lv in levels], None, None, None, 0)
         z = [np.zeros_like(a) for a in levels]
         return cls([np.array(a, dtype=np.float64) for a in levels], z,
                    [np.zeros_like(a) for a in levels],
@@ -564,6 +703,12 @@ def oracle_step(p, st, lr, b1=0.9, b2=0.999, eps=1e-8):
     Adam on every level and on q.  Returns the loss terms before the update."""
     terms, grads, gq = loss_grad_levels(p, st.levels, st.q)
     st.t += 1
+    if p.n_fields > 1:
+        for f, gf in enumerate(grads):
+            for i, g in enumerate(gf):
+                st.levels[f][i], st.m[f][i], st.v[f][i] = adam_step(
+                    st.levels[f][i], st.m[f][i], st.v[f][i], g, st.t, lr, b1, b2, eps)
+        return terms
     for i, g in enumerate(grads):
         st.levels[i], st.m[i], st.v[i] = adam_step(st.levels[i], st.m[i], st.v[i],
                                                    g, st.t, lr, b1, b2, eps)

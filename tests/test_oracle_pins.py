@@ -416,3 +416,64 @@ def test_adam_two_steps_by_hand():
     mh = -0.11 / 0.19
     vh = (0.000999 + 0.004) / (1 - 0.999**2)
     assert abs(x[0] - (-0.1 - 0.1 * mh / math.sqrt(vh))) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# Lid-driven cavity, steady Navier-Stokes (Section 3.3)
+# --------------------------------------------------------------------------
+
+def test_ns2d_fluid_at_rest_closed_form():
+    """u = v = 0, p = c: only the lid shears the top row, -2/(Re h^2) in r_u."""
+    n, Re, c = 12, 100.0, 0.7
+    h = 1.0 / n
+    z = np.zeros((n, n))
+    ru, rv, rc, rg = o.ns2d_residuals(z, z, np.full((n, n), c), Re, h)
+    np.testing.assert_allclose(ru[:-1], 0.0, atol=1e-12)
+    np.testing.assert_allclose(ru[-1], -2.0 / (Re * h * h), rtol=1e-13)
+    np.testing.assert_allclose(rv, 0.0, atol=1e-12)
+    np.testing.assert_allclose(rc, 0.0, atol=1e-12)
+    assert rg == c
+
+
+def test_ns2d_interior_consistency_second_order():
+    """Smooth fields: interior residuals -> (u^2)_x + (uv)_y + p_x - nu lap u,
+    (uv)_x + (v^2)_y + p_y - nu lap v and u_x + v_y at second order."""
+    import sympy as sp
+    X, Y = sp.symbols("x y")
+    uu = sp.sin(2 * X) * sp.cos(3 * Y) + 0.3
+    vv = sp.cos(X + 0.5) * sp.sin(2 * Y) - 0.2
+    pp = sp.exp(X * Y) * sp.cos(X)
+    Re = 50.0
+    nu = 1.0 / Re
+    ex_u = sp.diff(uu * uu, X) + sp.diff(uu * vv, Y) + sp.diff(pp, X) - nu * (sp.diff(uu, X, 2) + sp.diff(uu, Y, 2))
+    ex_v = sp.diff(uu * vv, X) + sp.diff(vv * vv, Y) + sp.diff(pp, Y) - nu * (sp.diff(vv, X, 2) + sp.diff(vv, Y, 2))
+    ex_c = sp.diff(uu, X) + sp.diff(vv, Y)
+    fs = [sp.lambdify((X, Y), e, "numpy") for e in (uu, vv, pp, ex_u, ex_v, ex_c)]
+    errs = []
+    for n in (32, 64, 128, 256):
+        h = 1.0 / n
+        c = (np.arange(n) + 0.5) * h
+        Yg, Xg = np.meshgrid(c, c, indexing="ij")
+        u, v, p = fs[0](Xg, Yg), fs[1](Xg, Yg), fs[2](Xg, Yg)
+        ru, rv, rc, _ = o.ns2d_residuals(u, v, p, Re, h)
+        k = max(3, n // 8)
+        sl = (slice(k, -k), slice(k, -k))
+        e = max(np.max(np.abs(ru - fs[3](Xg, Yg))[sl]), np.max(np.abs(rv - fs[4](Xg, Yg))[sl]),
+                np.max(np.abs(rc - fs[5](Xg, Yg))[sl]))
+        errs.append(e)
+    rates = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(3.3 < q < 4.7 for q in rates), (errs, rates)
+
+
+def test_ns2d_gradient_finite_differences():
+    n, L = 8, 3
+    rng = np.random.default_rng(21)
+    cells = inputs.measurement_cells(n * n, 14, 21)
+    fields = (np.arange(14) % 2).astype(np.int32)
+    p = o.Problem("ns2d", (n, n), L, coef={"Re": 100.0, "tau": 1.0}, w_res=1.0, w_data=3.0,
+                  meas_cell=cells, meas_field=fields, meas_value=rng.normal(size=14))
+    lv = inputs.random_levels((n, n), L, 3, seed=21, coarse_scale=0.3)
+    _, grads, _ = o.loss_grad_levels(p, lv)
+    flat_params = [a for f in lv for a in f]
+    flat_grads = [g for f in grads for g in f]
+    _fd_check(lambda: o.loss_terms(p, [o.compose(f) for f in lv])["total"], flat_params, flat_grads)
