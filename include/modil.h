@@ -60,8 +60,11 @@ typedef enum {
 enum {
   MODIL_PDE_BURGERS = 1, /* viscous Burgers u_t + (u^2/2)_x = nu u_xx, axes (t, x),
                             x in [-1, 1], t in [0, 1]; Section 3.2 with viscosity   */
-  MODIL_PDE_HEAT = 2     /* u_t = (k(u) u_x)_x with unknown k, axes (t, x) on [0,1]^2;
+  MODIL_PDE_HEAT = 2,    /* u_t = (k(u) u_x)_x with unknown k, axes (t, x) on [0,1]^2;
                             Section 3.4, the displayed implicit scheme              */
+  MODIL_PDE_NS2D = 3     /* steady incompressible Navier-Stokes, lid-driven cavity on
+                            [0,1]^2 (square grid), fields 0 = u, 1 = v, 2 = p; collocated
+                            finite volumes with Rhie-Chow continuity; Section 3.3   */
 };
 
 enum { MODIL_F32 = 0, MODIL_F64 = 1 };
@@ -80,7 +83,8 @@ typedef struct {
   int ndim;     /* 2 for the space-time families                                */
   int shape[3]; /* fine cells per axis, slowest first; unused entries 0         */
   int n_levels; /* L >= 1; every axis must be divisible by 2^(L-1); 1 = ODIL    */
-  double coef[4]; /* BURGERS: coef[0] = nu.  HEAT: unused.                       */
+  double coef[4]; /* BURGERS: coef[0] = nu.  HEAT: unused.  NS2D: coef[0] = Re,
+                     coef[1] = Rhie-Chow factor (tau = coef[1] * h)               */
   double w_res;   /* residual weight: w_res * dV * sum r^2                       */
   double w_data;  /* data weight: w_data / n_meas * sum (u - y)^2                */
   double w_reg;   /* HEAT: w_reg * sum_j (q_{j+1} - 2 q_j + q_{j-1})^2           */
@@ -93,7 +97,9 @@ typedef struct {
   int n_knodes;              /* HEAT: conductivity nodes q_0..q_{K}, K+1 <= 64  */
   const double* knodes;      /* initial q (copied)                              */
   double adam_lr, adam_beta1, adam_beta2, adam_eps;
-  int tile[2];               /* fine tile (rows, cols); 0 = library default    */
+  int tile[2];               /* fine tile (rows, cols); 0 = library default.
+                                Burgers/heat: 16x32 16x64 8x64 32x32 8x128;
+                                NS2D: 8x32 16x32                                 */
 } modil_desc;
 
 /* Device bytes needed for a batch of n problems described by descs[0..n-1]. */
@@ -149,6 +155,23 @@ modil_status modil_launches_per_step(const modil_problem* p, int* n);
  * ms[k] receives the device time of launch k (order as above).  Synchronises.
  * max_kernels: capacity of ms; *n_kernels: launches timed. */
 modil_status modil_profile_step(modil_problem* p, float* ms, int max_kernels, int* n_kernels);
+
+/* ---- caller-owned parameters (e.g. a torch.autograd.Function) -------------
+ * The layout of all levels of a batch in one buffer ("parameter vector"):
+ * instance-major, then field, then level (finest first), each level
+ * row-major; modil_param_count gives its length in elements of the dtype and
+ * modil_level_offset the element offset of one level.  The evaluation is the
+ * same as modil_eval_loss / modil_eval_grad (paper Section 2.1 loss, Section
+ * 2.2 decomposition) but reads the levels from `levels` (device) instead of
+ * the problem's own copy; the heat conductivity nodes come from the problem.
+ *   modil_loss_fwd: loss terms (host, n_instances * MODIL_NTERMS, synchronises).
+ *   modil_loss_bwd: grads (device, parameter-vector layout) = grad_out * dL/dlevels;
+ *                   asynchronous on the problem's stream. */
+modil_status modil_param_count(const modil_problem* p, long long* n);
+modil_status modil_level_offset(const modil_problem* p, int instance, int field, int level,
+                                long long* offset);
+modil_status modil_loss_fwd(modil_problem* p, const void* levels, double* terms);
+modil_status modil_loss_bwd(modil_problem* p, const void* levels, double grad_out, void* grads);
 
 /* Steps taken so far (the Adam step counter t). */
 modil_status modil_step_count(const modil_problem* p, long long* t);

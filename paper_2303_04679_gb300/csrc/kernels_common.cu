@@ -96,6 +96,7 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[l][gt];
   load_inst(&D, A, ii);
   __syncthreads();
+  const int nf = D.nfield;
   const int ny = D.n[l][1], nx = D.n[l][2];
   const int fy = D.n[l - 1][1], fx = D.n[l - 1][2];
   const int local = gt - D.tile_base[l];
@@ -103,46 +104,56 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   const int y0 = ty * kLevTY, x0 = tx * kLevTX;
   const int ch = min(kLevTY, ny - y0), cw = min(kLevTX, nx - x0);
   const bool store_g = (mode != MODE_STEP) || (l < D.nlev - 1);
-  const long long off = D.off[0][l];
   // Prologue: this level's parameters and moments were last written by the
   // same kernel one step earlier, two or more launches back.
   const int oy = threadIdx.x / cw, ox = threadIdx.x - (threadIdx.x / cw) * cw;
   const bool mine = threadIdx.x < ch * cw;
-  const long long o = off + (long long)(y0 + oy) * nx + (x0 + ox);
-  T pv = T(0), mv = T(0);
-  double vv = 0.0;
-  if (mode == MODE_STEP && mine) {
-    pv = A.p[cur][o];
-    mv = A.m[o];
-    vv = A.v[o];
+  const long long e = (long long)(y0 + oy) * nx + (x0 + ox);
+  T pv[MODIL_MAXF], mv[MODIL_MAXF];
+  double vv[MODIL_MAXF];
+#pragma unroll
+  for (int f = 0; f < MODIL_MAXF; ++f) {
+    pv[f] = T(0); mv[f] = T(0); vv[f] = 0.0;
+    if (f < nf && mode == MODE_STEP && mine) {
+      const long long o = D.off[f][l] + e;
+      pv[f] = A.p[cur][o];
+      mv[f] = A.m[o];
+      vv[f] = A.v[o];
+    }
   }
   __shared__ AdamCoef acS;
   if (threadIdx.x == 0) acS = adam_coef(D, A.st[ii]);  // once per block: no per-thread FP64
   pdl_wait();
   pdl_trigger();
-  // stage the finer level's gradient over the tile's footprint
   const int fy0 = max(0, 2 * y0 - 2), fy1 = min(fy, 2 * (y0 + ch) + 2);
   const int fx0 = max(0, 2 * x0 - 2), fx1 = min(fx, 2 * (x0 + cw) + 2);
   const int fw = fx1 - fx0, fh = fy1 - fy0;
-  const T* __restrict__ gf = A.g + D.off[0][l - 1];
-  for (int i = threadIdx.x; i < fw * fh; i += MODIL_NT) {
-    const int r = i / fw, c = i - r * fw;
-    cp_async(fineS + r * kLevFX + c, gf + (long long)(fy0 + r) * fx + (fx0 + c));
+#pragma unroll
+  for (int f = 0; f < MODIL_MAXF; ++f) {
+    if (f >= nf) break;
+    // stage field f of the finer level's gradient over the tile's footprint
+    const T* __restrict__ gf = A.g + D.off[f][l - 1];
+    for (int i = threadIdx.x; i < fw * fh; i += MODIL_NT) {
+      const int r = i / fw, c = i - r * fw;
+      cp_async(fineS + r * kLevFX + c, gf + (long long)(fy0 + r) * fx + (fx0 + c));
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const AdamCoef ac = acS;
+    const long long o = D.off[f][l] + e;
+    restrict_sep<T, MODIL_NT>(fineS, kLevFX, fy0, fh, fx0, fw, H, y0, ch, x0, cw, ny, nx,
+                              [&](int k, T g) {
+                                // k == threadIdx.x: each thread finishes its own cell
+                                if (store_g) A.g[o] = g;
+                                if (mode == MODE_STEP) {
+                                  adam_update(pv[f], mv[f], vv[f], g, ac);
+                                  A.p[cur ^ 1][o] = pv[f];
+                                  A.m[o] = mv[f];
+                                  A.v[o] = vv[f];
+                                }
+                              });
+    __syncthreads();  // fineS and H are reused by the next field
   }
-  cp_async_wait_all();
-  __syncthreads();
-  const AdamCoef ac = acS;
-  restrict_sep<T, MODIL_NT>(fineS, kLevFX, fy0, fh, fx0, fw, H, y0, ch, x0, cw, ny, nx,
-                            [&](int k, T g) {
-                              // k == threadIdx.x: each thread finishes its own cell
-                              if (store_g) A.g[o] = g;
-                              if (mode == MODE_STEP) {
-                                adam_update(pv, mv, vv, g, ac);
-                                A.p[cur ^ 1][o] = pv;
-                                A.m[o] = mv;
-                                A.v[o] = vv;
-                              }
-                            });
 }
 
 // ---------------------------------------------------------------------------
@@ -160,15 +171,17 @@ constexpr int kTailNT = 256;
 // Shared-memory layout of one tail block (identical on host and device).
 struct TailLayout {
   int rp[MODIL_MAXL];       // rows per block of each tail level
-  int own_off[MODIL_MAXL];  // offset of the block's own rows of each level
-  int own_cells;            // cells owned by one block (upper bound)
+  int own_off[MODIL_MAXL];  // offset of the block's own rows of each level (one field)
+  int own_cells;            // cells of one field owned by one block (upper bound)
+  int nf;                   // fields
   int st_elems, h_elems;    // staging of the level above, separable scratch
   size_t bytes(int esz) const {
-    return 8 * (size_t)own_cells + (size_t)esz * (3 * (size_t)own_cells + st_elems + h_elems) + 64;
+    const size_t oc = (size_t)own_cells * nf;
+    return 8 * oc + (size_t)esz * (3 * oc + st_elems + h_elems) + 64;
   }
 };
 
-__host__ __device__ inline void tail_layout(int L, int ts, const int (*n)[3], TailLayout& t) {
+__host__ __device__ inline void tail_layout(int L, int ts, const int (*n)[3], int nf, TailLayout& t) {
   int acc = 0, st = 0, h = 0;
   for (int l = 0; l < MODIL_MAXL; ++l) { t.rp[l] = 0; t.own_off[l] = 0; }
   for (int l = ts; l < L; ++l) {
@@ -182,6 +195,7 @@ __host__ __device__ inline void tail_layout(int L, int ts, const int (*n)[3], Ta
     h = max(h, rows * nx);
   }
   t.own_cells = acc;
+  t.nf = nf;
   t.st_elems = st;
   t.h_elems = h;
 }
@@ -201,32 +215,34 @@ k_tail(const __grid_constant__ Arena<T> A, int mode, int cur) {
   const int tid = threadIdx.x;
   load_inst(&D, A, ii);
   __syncthreads();
-  if (tid == 0) tail_layout(D.nlev, D.tail, D.n, TL);
+  if (tid == 0) tail_layout(D.nlev, D.tail, D.n, D.nfield, TL);
   __syncthreads();
   const int L = D.nlev, ts = D.tail;
   const bool levels = (mode == MODE_GRAD || mode == MODE_STEP) && ts < L;
-  const int oc = TL.own_cells;
+  const int nf = D.nfield;
+  const int oc = TL.own_cells;  // per field; field f of the own arrays starts at f * oc
   double* vS = reinterpret_cast<double*>(smem);
-  T* gO = reinterpret_cast<T*>(smem + 8 * (size_t)oc);
-  T* pS = gO + oc;
-  T* mS = pS + oc;
-  T* Pst = mS + oc;
+  T* gO = reinterpret_cast<T*>(smem + 8 * (size_t)oc * nf);
+  T* pS = gO + oc * nf;
+  T* mS = pS + oc * nf;
+  T* Pst = mS + oc * nf;
   T* H = Pst + TL.st_elems;
 
   // Prologue: the tail levels' parameters and moments and the bias-correction
   // powers were last written by this kernel one step earlier.
   if (mode == MODE_STEP && levels) {
-    for (int l = ts; l < L; ++l) {
-      const int ny = D.n[l][1], nx = D.n[l][2];
-      const int a = r * TL.rp[l], b = min(ny, a + TL.rp[l]);
-      for (int i = tid; i < (b > a ? (b - a) * nx : 0); i += kTailNT) {
-        const long long o = D.off[0][l] + (long long)a * nx + i;
-        const int k = TL.own_off[l] + i;
-        cp_async(pS + k, A.p[cur] + o);
-        cp_async(mS + k, A.m + o);
-        cp_async(vS + k, A.v + o);
+    for (int f = 0; f < nf; ++f)
+      for (int l = ts; l < L; ++l) {
+        const int ny = D.n[l][1], nx = D.n[l][2];
+        const int a = r * TL.rp[l], b = min(ny, a + TL.rp[l]);
+        for (int i = tid; i < (b > a ? (b - a) * nx : 0); i += kTailNT) {
+          const long long o = D.off[f][l] + (long long)a * nx + i;
+          const int k = f * oc + TL.own_off[l] + i;
+          cp_async(pS + k, A.p[cur] + o);
+          cp_async(mS + k, A.m + o);
+          cp_async(vS + k, A.v + o);
+        }
       }
-    }
   }
   InstState& S = A.st[ii];
   __shared__ AdamCoef acS;
@@ -272,23 +288,26 @@ k_tail(const __grid_constant__ Arena<T> A, int mode, int cur) {
     if (b > a) {
       const int pa = max(0, 2 * a - 2), pb = min(fy, 2 * b + 2);
       const int prow = pb - pa;
-      if (l == ts) {
-        const T* src = A.g + D.off[0][l - 1] + (long long)pa * fx;
-        for (int i = tid; i < prow * fx; i += kTailNT) cp_async(Pst + i, src + i);
-        cp_async_wait_all();
-      } else {
-        const int rpp = TL.rp[l - 1];
-        for (int i = tid; i < prow * fx; i += kTailNT) {
-          const int y = pa + i / fx, x = i - (i / fx) * fx;
-          const int owner = y / rpp;
-          const T* rem = cluster.map_shared_rank(gO, owner);
-          Pst[i] = rem[TL.own_off[l - 1] + (y - owner * rpp) * fx + x];
+      for (int f = 0; f < nf; ++f) {
+        if (l == ts) {
+          const T* src = A.g + D.off[f][l - 1] + (long long)pa * fx;
+          for (int i = tid; i < prow * fx; i += kTailNT) cp_async(Pst + i, src + i);
+          cp_async_wait_all();
+        } else {
+          const int rpp = TL.rp[l - 1];
+          for (int i = tid; i < prow * fx; i += kTailNT) {
+            const int y = pa + i / fx, x = i - (i / fx) * fx;
+            const int owner = y / rpp;
+            const T* rem = cluster.map_shared_rank(gO, owner);
+            Pst[i] = rem[f * oc + TL.own_off[l - 1] + (y - owner * rpp) * fx + x];
+          }
         }
+        __syncthreads();
+        T* dst = gO + f * oc + TL.own_off[l];
+        restrict_sep<T, kTailNT>(Pst, fx, pa, prow, 0, fx, H, a, b - a, 0, nx, ny, nx,
+                                 [&](int k, T g) { dst[k] = g; });
+        __syncthreads();  // Pst and H are reused by the next field
       }
-      __syncthreads();
-      T* dst = gO + TL.own_off[l];
-      restrict_sep<T, kTailNT>(Pst, fx, pa, prow, 0, fx, H, a, b - a, 0, nx, ny, nx,
-                               [&](int k, T g) { dst[k] = g; });
     }
     cluster.sync();
     // every block has read the bias-correction powers: advance them now (off the
@@ -364,12 +383,13 @@ k_tail(const __grid_constant__ Arena<T> A, int mode, int cur) {
   if (levels) {
     cp_async_wait_all();
     __syncthreads();
+    for (int f = 0; f < nf; ++f)
     for (int l = ts; l < L; ++l) {
       const int ny = D.n[l][1], nx = D.n[l][2];
       const int a = r * TL.rp[l], b = min(ny, a + TL.rp[l]);
       for (int i = tid; i < (b > a ? (b - a) * nx : 0); i += kTailNT) {
-        const int k = TL.own_off[l] + i;
-        const long long o = D.off[0][l] + (long long)a * nx + i;
+        const int k = f * oc + TL.own_off[l] + i;
+        const long long o = D.off[f][l] + (long long)a * nx + i;
         const T g = gO[k];
         if (mode != MODE_STEP || l < L - 1) A.g[o] = g;
         if (mode == MODE_STEP) {
@@ -443,9 +463,9 @@ cudaError_t launch_level(const Arena<T>& A, int level, int mode, int cur, cudaSt
 size_t tail_smem_bytes(const TailPlan& tp, int elem) { return tp.smem_bytes; }
 
 // Shared-memory bytes the tail blocks of one instance need.
-size_t tail_instance_bytes(int L, int ts, const int (*n)[3], int elem) {
+size_t tail_instance_bytes(int L, int ts, const int (*n)[3], int nf, int elem) {
   TailLayout t;
-  tail_layout(L, ts, n, t);
+  tail_layout(L, ts, n, nf, t);
   return t.bytes(elem);
 }
 

@@ -416,7 +416,7 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
       const int oy = idx / TX, ox = idx - oy * TX;
       if (oy >= hy || ox >= hx) continue;
       const long long e = (long long)(y0 + oy) * nx + (x0 + ox);
-      const T g = gS[idx];
+      const T g = gS[idx] * (T)A.gscale;
       Gp[e] = g;
       if (mode == MODE_STEP) {
         T p = pS[idx];

@@ -11,8 +11,8 @@
 namespace modil {
 
 // Tile configurations of the fused fine kernel: (rows, cols).
-constexpr int kNumTileCfg = 5;
-constexpr int kTileCfg[kNumTileCfg][2] = {{16, 32}, {16, 64}, {8, 64}, {32, 32}, {8, 128}};
+constexpr int kNumTileCfg = 6;
+constexpr int kTileCfg[kNumTileCfg][2] = {{16, 32}, {16, 64}, {8, 64}, {32, 32}, {8, 128}, {8, 32}};
 // Tile of the restriction kernels (coarse levels), rows x cols.
 constexpr int kLevTY = 8, kLevTX = 32;
 
@@ -37,10 +37,16 @@ cudaError_t prepare_fine_st(int pde, int cfg, size_t pyr_elems);
 template <class T>
 cudaError_t launch_fine_st(const Arena<T>& A, int pde, int cfg, int mode, int cur,
                            size_t pyr_elems, cudaStream_t s);
+size_t fine_ns2d_smem_bytes(int cfg, size_t pyr_elems, int elem_bytes);
+template <class T>
+cudaError_t prepare_fine_ns2d(int cfg, size_t pyr_elems);
+template <class T>
+cudaError_t launch_fine_ns2d(const Arena<T>& A, int cfg, int mode, int cur, size_t pyr_elems,
+                             cudaStream_t s);
 template <class T>
 cudaError_t launch_level(const Arena<T>& A, int level, int mode, int cur, cudaStream_t s);
 size_t tail_smem_bytes(const TailPlan& tp, int elem_bytes);
-size_t tail_instance_bytes(int L, int ts, const int (*n)[3], int elem_bytes);
+size_t tail_instance_bytes(int L, int ts, const int (*n)[3], int nf, int elem_bytes);
 template <class T>
 cudaError_t prepare_tail(const TailPlan& tp);
 template <class T>

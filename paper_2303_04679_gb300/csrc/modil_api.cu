@@ -80,17 +80,24 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   P.pde = d[0].pde;
   P.dtype = d[0].dtype;
   P.ndim = d[0].ndim;
-  if (P.pde != MODIL_PDE_BURGERS && P.pde != MODIL_PDE_HEAT)
+  if (P.pde != MODIL_PDE_BURGERS && P.pde != MODIL_PDE_HEAT && P.pde != MODIL_PDE_NS2D)
     return fail(MODIL_ERR_UNSUPPORTED, "unknown pde " + std::to_string(P.pde));
   if (P.dtype != MODIL_F32 && P.dtype != MODIL_F64) return fail(MODIL_ERR_ARG, "dtype");
-  if (P.ndim != 2) return fail(MODIL_ERR_UNSUPPORTED, "space-time families are 2-D");
+  if (P.ndim != 2) return fail(MODIL_ERR_UNSUPPORTED, "these PDE families are 2-D");
   P.esz = P.dtype == MODIL_F64 ? 8 : 4;
-  P.nfield = 1;
+  P.nfield = (P.pde == MODIL_PDE_NS2D) ? 3 : 1;
   // tile configuration (same for the batch)
   int ty = d[0].tile[0], tx = d[0].tile[1];
-  if (ty == 0 && tx == 0) { ty = 16; tx = 32; }
+  if (ty == 0 && tx == 0) {
+    ty = (P.pde == MODIL_PDE_NS2D) ? 8 : 16;
+    tx = 32;
+  }
   P.cfg = find_cfg(ty, tx);
   if (P.cfg < 0) return fail(MODIL_ERR_ARG, "unsupported tile shape");
+  if (P.pde == MODIL_PDE_NS2D && P.cfg != 0 && P.cfg != 5)
+    return fail(MODIL_ERR_ARG, "NS2D tiles are 8x32 or 16x32");
+  if (P.pde != MODIL_PDE_NS2D && P.cfg == 5)
+    return fail(MODIL_ERR_ARG, "unsupported tile shape");
   const int TY = kTileCfg[P.cfg][0], TX = kTileCfg[P.cfg][1];
 
   P.inst.resize(n);
@@ -110,6 +117,11 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
       return fail(MODIL_ERR_ARG, "every axis must be divisible by 2^(n_levels-1)");
     if ((long long)ny * nx > (1LL << 30)) return fail(MODIL_ERR_ARG, "grid too large");
     if (P.pde == MODIL_PDE_BURGERS && ny < 2) return fail(MODIL_ERR_ARG, "Burgers needs >= 2 rows");
+    if (P.pde == MODIL_PDE_NS2D) {
+      if (ny != nx) return fail(MODIL_ERR_ARG, "the cavity grid must be square");
+      if (!(q.coef[0] > 0)) return fail(MODIL_ERR_ARG, "NS2D needs coef[0] = Re > 0");
+      if (!(q.coef[1] >= 0)) return fail(MODIL_ERR_ARG, "NS2D needs coef[1] = tau factor >= 0");
+    }
     if (P.pde == MODIL_PDE_HEAT) {
       if (q.n_aux != nx || !q.aux) return fail(MODIL_ERR_ARG, "heat needs aux[nx] (initial profile)");
       if (q.n_knodes < 2 || q.n_knodes > MODIL_MAXK || !q.knodes)
@@ -124,12 +136,12 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
     DevInst& D = P.dev[i];
     std::memset(&D, 0, sizeof(D));
     ip.nlev = L;
-    ip.nfield = 1;
+    ip.nfield = P.nfield;
     ip.nk = P.pde == MODIL_PDE_HEAT ? q.n_knodes : 0;
     P.nk = std::max(P.nk, ip.nk);
     P.max_lev = std::max(P.max_lev, L);
     D.nlev = L;
-    D.nfield = 1;
+    D.nfield = P.nfield;
     D.nk = ip.nk;
     D.ndim = 2;
     // first level small enough for the per-instance tail kernel
@@ -147,7 +159,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
         P.tail.prev_cells = std::max(P.tail.prev_cells, (size_t)(ny >> (tail - 1)) * (nx >> (tail - 1)));
       int nn[MODIL_MAXL][3] = {};
       for (int l = 0; l < L; ++l) { nn[l][0] = 1; nn[l][1] = ny >> l; nn[l][2] = nx >> l; }
-      P.tail.smem_bytes = std::max(P.tail.smem_bytes, tail_instance_bytes(L, tail, nn, (int)P.esz));
+      P.tail.smem_bytes = std::max(P.tail.smem_bytes, tail_instance_bytes(L, tail, nn, P.nfield, (int)P.esz));
     }
     for (int l = 0; l < L; ++l) {
       ip.n[l][0] = 1;
@@ -164,11 +176,15 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
       if (l == 0) D.ntile0 = ntl;
       if (l == 0 || l < tail)
         for (int t = 0; t < ntl; ++t) P.tile_inst[l].push_back(i);
-      D.off[0][l] = off;
-      off += ip.lev_size[l];
     }
-    D.fine_off[0] = foff;
-    foff += ip.lev_size[0];
+    for (int f = 0; f < P.nfield; ++f) {
+      for (int l = 0; l < L; ++l) {
+        D.off[f][l] = off;
+        off += ip.lev_size[l];
+      }
+      D.fine_off[f] = foff;
+      foff += ip.lev_size[0];
+    }
     D.k_off = koff;
     koff += ip.nk;
     D.aux_off = aoff;
@@ -187,7 +203,8 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
     D.lr = q.adam_lr; D.b1 = q.adam_beta1; D.b2 = q.adam_beta2; D.eps = q.adam_eps;
     // pyramid bound of this instance (unclipped worst case, clipped by level size)
     {
-      long long hy = TY + 4, hx = TX + 4, tot = 0;
+      const int hu = (P.pde == MODIL_PDE_NS2D) ? 4 : 2;  // halo of the composed field
+      long long hy = TY + 2 * hu, hx = TX + 2 * hu, tot = 0;
       for (int l = 1; l < L; ++l) {
         hy = std::min<long long>((hy + 7) / 2, ip.n[l][1]);
         hx = std::min<long long>((hx + 7) / 2, ip.n[l][2]);
@@ -216,7 +233,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
       const int c = q.meas_cell[k];
       const int f = q.meas_field ? q.meas_field[k] : 0;
       if (c < 0 || (long long)c >= (long long)ny * nx) return fail(MODIL_ERR_ARG, "measurement cell out of range");
-      if (f != 0) return fail(MODIL_ERR_ARG, "measurement field out of range");
+      if (f < 0 || f >= P.nfield) return fail(MODIL_ERR_ARG, "measurement field out of range");
       if (!std::isfinite(q.meas_value[k])) return fail(MODIL_ERR_ARG, "measurement value not finite");
       const int y = c / nx, x = c % nx;
       const int t = P.dev[i].tile_base[0] + (y / TY) * P.inst[i].nt[0][2] + (x / TX);
@@ -321,6 +338,7 @@ void fill_arena(modil_problem* p, Arena<T>& A) {
   }
   A.npart = P.npart;
   A.n_inst = P.n_inst;
+  A.gscale = 1.0f;
   A.inst0 = P.dev[0];
 }
 
@@ -347,7 +365,10 @@ modil_status run_pass_t(modil_problem* p, Arena<T>& A, int mode, int cur, cudaEv
   const Plan& P = p->plan;
   int k = 0;
   if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
-  CUDA_TRY(launch_fine_st<T>(A, P.pde, P.cfg, mode, cur, P.pyr_elems, p->stream));
+  if (P.pde == MODIL_PDE_NS2D)
+    CUDA_TRY(launch_fine_ns2d<T>(A, P.cfg, mode, cur, P.pyr_elems, p->stream));
+  else
+    CUDA_TRY(launch_fine_st<T>(A, P.pde, P.cfg, mode, cur, P.pyr_elems, p->stream));
   if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
   if (mode == MODE_GRAD || mode == MODE_STEP)
     for (int l = 1; l < P.max_tail; ++l) {
@@ -413,6 +434,20 @@ void drop_graph(modil_problem* p) {
     p->gexec[c] = nullptr;
     p->graph[c] = nullptr;
   }
+}
+
+}  // namespace
+
+namespace {
+// A pass over caller-owned levels (and gradient buffer), scaled gradient.
+template <class T>
+modil_status external_pass(modil_problem* p, Arena<T> A, const void* levels, void* grads,
+                                  double scale, int mode) {
+  A.p[0] = const_cast<T*>(static_cast<const T*>(levels));
+  A.p[1] = nullptr;
+  if (grads) A.g = static_cast<T*>(grads);
+  A.gscale = (float)scale;
+  return run_pass_t<T>(p, A, mode, 0, nullptr, nullptr);
 }
 
 }  // namespace
@@ -487,8 +522,12 @@ modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t ar
   if (st != MODIL_OK) return bail(st);
   e = P.dtype == MODIL_F64 ? launch_reset<double>(p->A64, p->stream) : launch_reset<float>(p->A32, p->stream);
   if (e != cudaSuccess) return bail(fail(MODIL_ERR_CUDA, cudaGetErrorString(e)));
-  e = P.dtype == MODIL_F64 ? prepare_fine_st<double>(P.pde, P.cfg, P.pyr_elems)
-                           : prepare_fine_st<float>(P.pde, P.cfg, P.pyr_elems);
+  if (P.pde == MODIL_PDE_NS2D)
+    e = P.dtype == MODIL_F64 ? prepare_fine_ns2d<double>(P.cfg, P.pyr_elems)
+                             : prepare_fine_ns2d<float>(P.cfg, P.pyr_elems);
+  else
+    e = P.dtype == MODIL_F64 ? prepare_fine_st<double>(P.pde, P.cfg, P.pyr_elems)
+                             : prepare_fine_st<float>(P.pde, P.cfg, P.pyr_elems);
   if (e == cudaSuccess)
     e = P.dtype == MODIL_F64 ? prepare_tail<double>(P.tail) : prepare_tail<float>(P.tail);
   if (e != cudaSuccess) return bail(fail(MODIL_ERR_CUDA, std::string("kernel setup: ") + cudaGetErrorString(e)));
@@ -670,6 +709,39 @@ modil_status modil_profile_step(modil_problem* p, float* ms, int max_kernels, in
   return s;
 }
 
+modil_status modil_loss_fwd(modil_problem* p, const void* levels, double* terms) {
+  if (!p || !levels) return fail(MODIL_ERR_ARG, "NULL argument");
+  modil_status s = p->plan.dtype == MODIL_F64
+                       ? external_pass<double>(p, p->A64, levels, nullptr, 1.0, MODE_LOSS)
+                       : external_pass<float>(p, p->A32, levels, nullptr, 1.0, MODE_LOSS);
+  if (s != MODIL_OK) return s;
+  return terms ? read_terms(p, terms) : MODIL_OK;
+}
+
+modil_status modil_loss_bwd(modil_problem* p, const void* levels, double grad_out, void* grads) {
+  if (!p || !levels || !grads) return fail(MODIL_ERR_ARG, "NULL argument");
+  return p->plan.dtype == MODIL_F64
+             ? external_pass<double>(p, p->A64, levels, grads, grad_out, MODE_GRAD)
+             : external_pass<float>(p, p->A32, levels, grads, grad_out, MODE_GRAD);
+}
+
+modil_status modil_param_count(const modil_problem* p, long long* n) {
+  if (!p || !n) return fail(MODIL_ERR_ARG, "NULL argument");
+  *n = p->plan.n_param;
+  return MODIL_OK;
+}
+
+modil_status modil_level_offset(const modil_problem* p, int instance, int field, int level,
+                                long long* offset) {
+  if (!p || !offset) return fail(MODIL_ERR_ARG, "NULL argument");
+  const Plan& P = p->plan;
+  if (instance < 0 || instance >= P.n_inst) return fail(MODIL_ERR_ARG, "instance out of range");
+  if (field < 0 || field >= P.nfield) return fail(MODIL_ERR_ARG, "field out of range");
+  if (level < 0 || level >= P.inst[instance].nlev) return fail(MODIL_ERR_ARG, "level out of range");
+  *offset = P.dev[instance].off[field][level];
+  return MODIL_OK;
+}
+
 modil_status modil_step_count(const modil_problem* p, long long* t) {
   if (!p || !t) return fail(MODIL_ERR_ARG, "NULL argument");
   *t = p->steps;
@@ -814,10 +886,13 @@ modil_status noalloc_run(const Plan& P, const modil_desc* d, const void* levels,
   }
   A.npart = P.npart;
   A.n_inst = 1;
+  A.gscale = 1.0f;
   A.inst0 = P.dev[0];
-  CUDA_TRY((prepare_fine_st<T>(P.pde, P.cfg, P.pyr_elems)));
+  if (P.pde == MODIL_PDE_NS2D) CUDA_TRY((prepare_fine_ns2d<T>(P.cfg, P.pyr_elems)));
+  else CUDA_TRY((prepare_fine_st<T>(P.pde, P.cfg, P.pyr_elems)));
   CUDA_TRY(prepare_tail<T>(P.tail));
-  CUDA_TRY(launch_fine_st<T>(A, P.pde, P.cfg, MODE_GRAD, 0, P.pyr_elems, s));
+  if (P.pde == MODIL_PDE_NS2D) CUDA_TRY(launch_fine_ns2d<T>(A, P.cfg, MODE_GRAD, 0, P.pyr_elems, s));
+  else CUDA_TRY(launch_fine_st<T>(A, P.pde, P.cfg, MODE_GRAD, 0, P.pyr_elems, s));
   for (int l = 1; l < P.max_tail; ++l) CUDA_TRY(launch_level<T>(A, l, MODE_GRAD, 0, s));
   CUDA_TRY(launch_tail<T>(A, MODE_GRAD, 0, P.tail, s));
   InstState out;

@@ -25,7 +25,7 @@
 namespace modil {
 
 enum Mode { MODE_LOSS = 0, MODE_GRAD = 1, MODE_STEP = 2, MODE_COMPOSE = 3 };
-enum Pde { PDE_BURGERS = 1, PDE_HEAT = 2 };
+enum Pde { PDE_BURGERS = 1, PDE_HEAT = 2, PDE_NS2D = 3 };
 
 // Per-instance description (read-only on the device).
 struct DevInst {
@@ -94,6 +94,7 @@ struct Arena {
   int ntiles[MODIL_MAXL];
   int npart;
   int n_inst;
+  float gscale;        // factor on the written fine gradient (d loss / d output), 1 normally
 };
 
 // ---------------------------------------------------------------------------

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libmodil.so")
 
 PDE_BURGERS = 1
 PDE_HEAT = 2
+PDE_NS2D = 3
 F32 = 0
 F64 = 1
 NTERMS = 4
@@ -72,6 +73,10 @@ def _load():
         "modil_launches_per_step": ([P, C.POINTER(C.c_int)], C.c_int),
         "modil_profile_step": ([P, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)], C.c_int),
         "modil_reset_optimizer": ([P], C.c_int),
+        "modil_param_count": ([P, C.POINTER(C.c_longlong)], C.c_int),
+        "modil_level_offset": ([P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_longlong)], C.c_int),
+        "modil_loss_fwd": ([P, P, C.POINTER(C.c_double)], C.c_int),
+        "modil_loss_bwd": ([P, P, C.c_double, P], C.c_int),
         "modil_eval_grad_noalloc": ([C.POINTER(modil_desc), P, P, C.POINTER(C.c_double),
                                      C.POINTER(C.c_double), P], C.c_int),
         "modil_last_error": ([], C.c_char_p),
@@ -102,7 +107,7 @@ class Desc:
     def __init__(self, pde, shape, n_levels, dtype="f32", coef=(), w_res=1.0, w_data=1.0,
                  w_reg=0.0, meas_cell=None, meas_value=None, meas_field=None, aux=None,
                  knodes=None, lr=5e-3, beta1=0.9, beta2=0.999, eps=1e-8, tile=(0, 0)):
-        self.pde = {"burgers": PDE_BURGERS, "heat": PDE_HEAT}.get(pde, pde)
+        self.pde = {"burgers": PDE_BURGERS, "heat": PDE_HEAT, "ns2d": PDE_NS2D}.get(pde, pde)
         self.dtype = {"f32": F32, "f64": F64}.get(dtype, dtype)
         self.shape = tuple(int(s) for s in shape)
         self.n_levels = int(n_levels)
@@ -134,6 +139,10 @@ class Desc:
     @property
     def np_dtype(self):
         return np.float64 if self.dtype == F64 else np.float32
+
+    @property
+    def n_fields(self):
+        return 3 if self.pde == PDE_NS2D else 1
 
 
 def _desc_array(descs):
@@ -216,6 +225,10 @@ class Problem:
         for i, a in enumerate(levels):
             self.write_level(i, a, field, instance)
 
+    def write_fields(self, levels_per_field, instance=0):
+        for f, lv in enumerate(levels_per_field):
+            self.write_levels(lv, f, instance)
+
     def _read(self, fn, level, field, instance, shape):
         out = np.empty(shape, dtype=self.np_dtype)
         _check(fn(self._h, instance, field, level, out.ctypes.data, out.nbytes, 0))
@@ -292,6 +305,26 @@ class Problem:
         n = C.c_int()
         _check(LIB.modil_profile_step(self._h, ms, cap, C.byref(n)))
         return [ms[i] for i in range(n.value)]
+
+    def param_count(self):
+        n = C.c_longlong()
+        _check(LIB.modil_param_count(self._h, C.byref(n)))
+        return n.value
+
+    def level_offset(self, level, field=0, instance=0):
+        o = C.c_longlong()
+        _check(LIB.modil_level_offset(self._h, instance, field, level, C.byref(o)))
+        return o.value
+
+    def loss_fwd(self, levels):
+        """Loss terms of caller-owned levels (device tensor, parameter-vector layout)."""
+        t = self._terms()
+        _check(LIB.modil_loss_fwd(self._h, levels.data_ptr(), _dptr(t, C.c_double)))
+        return t.reshape(self.n, NTERMS)
+
+    def loss_bwd(self, levels, grad_out, grads):
+        """grads <- grad_out * dL/dlevels (device tensors, parameter-vector layout)."""
+        _check(LIB.modil_loss_bwd(self._h, levels.data_ptr(), float(grad_out), grads.data_ptr()))
 
     def reset_optimizer(self):
         _check(LIB.modil_reset_optimizer(self._h))
