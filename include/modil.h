@@ -173,6 +173,12 @@ modil_status modil_level_offset(const modil_problem* p, int instance, int field,
 modil_status modil_loss_fwd(modil_problem* p, const void* levels, double* terms);
 modil_status modil_loss_bwd(modil_problem* p, const void* levels, double grad_out, void* grads);
 
+/* Persistent launch of the fine-tile kernel (Burgers, heat): on != 0 launches
+ * as many blocks as fit on the GPU at once, each taking tiles of all
+ * instances from an atomic queue until it is empty (useful for batches of
+ * uneven instances); on == 0 launches one block per tile (default). */
+modil_status modil_set_persistent(modil_problem* p, int on);
+
 /* Steps taken so far (the Adam step counter t). */
 modil_status modil_step_count(const modil_problem* p, long long* t);
 

@@ -471,8 +471,7 @@ size_t tail_instance_bytes(int L, int ts, const int (*n)[3], int nf, int elem) {
 
 template <class T>
 cudaError_t prepare_tail(const TailPlan& tp) {
-  return cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tp.smem_bytes);
+  return raise_smem_limit(k_tail<T>, tp.smem_bytes);
 }
 
 template <class T>

@@ -463,10 +463,8 @@ cudaError_t launch_fine_ns2d(const Arena<T>& A, int cfg, int mode, int cur, size
 template <class T>
 cudaError_t prepare_fine_ns2d(int cfg, size_t pyr) {
   if (cfg == 0)
-    return cudaFuncSetAttribute(k_fine_ns2d<T, 16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)NsSmem<T, 16, 32>::bytes(pyr));
-  return cudaFuncSetAttribute(k_fine_ns2d<T, 8, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)NsSmem<T, 8, 32>::bytes(pyr));
+    return raise_smem_limit(k_fine_ns2d<T, 16, 32>, NsSmem<T, 16, 32>::bytes(pyr));
+  return raise_smem_limit(k_fine_ns2d<T, 8, 32>, NsSmem<T, 8, 32>::bytes(pyr));
 }
 
 size_t fine_ns2d_smem_bytes(int cfg, size_t pyr, int elem) {

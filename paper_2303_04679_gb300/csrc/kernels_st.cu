@@ -27,6 +27,8 @@
 //     r = (u^n_i - u^{n-1}_i)/dt
 //         - [k_{i+1/2}(u^n_{i+1}-u^n_i) - k_{i-1/2}(u^n_i-u^n_{i-1})]/dx^2,
 //     k_{i+1/2} = k((u^n_i + u^n_{i+1})/2), k piecewise linear in the nodes q.
+#include <algorithm>
+
 #include "launch.h"
 #include "modil_dev.cuh"
 
@@ -124,7 +126,10 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
   __shared__ AdamCoef acS[1];
 
   const int tid = threadIdx.x;
-  const int gt = blockIdx.x;
+  // One tile; `first` is the block's first tile (the only one that waits on
+  // the previous launch).  A persistent launch calls it for every tile it
+  // takes from the queue, an ordinary launch once for tile blockIdx.x.
+  auto tile = [&](const int gt, const bool first) {
   // ---- prologue: data no kernel of a step writes -----------------------------
   const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[0][gt];
   load_inst(&D, A, ii);
@@ -211,8 +216,10 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
         cp_async(icS + (x - (x0 - G::HU)), A.aux + D.aux_off + x);
   }
 
-  pdl_wait();
-  pdl_trigger();
+  if (first) {
+    pdl_wait();
+    pdl_trigger();
+  }
   if (tid == 0) *acS = adam_coef(D, A.st[ii]);  // once per block: no per-thread FP64
   for (int l = pre; l < L; ++l) stage_level(l);
   // the nodes are stepped by the tail kernel, the previous launch
@@ -486,7 +493,37 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
       }
     }
   }
+  };  // tile
 
+  if (!A.persistent) {
+    tile(blockIdx.x, true);
+    return;
+  }
+  // persistent launch: take tiles from the queue until it is empty
+  __shared__ int s_tile;
+  bool first = true;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(A.queue, 1);
+    __syncthreads();
+    const int gt = s_tile;
+    __syncthreads();
+    if (gt >= A.ntiles[0]) break;
+    tile(gt, first);
+    first = false;
+    __syncthreads();  // shared memory is reused by the next tile
+  }
+  if (first) {  // no tile: still complete the dependency protocol
+    pdl_wait();
+    pdl_trigger();
+  }
+  // the last block out rewinds the queue for the next launch
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(A.queue + 1, 1) == (int)gridDim.x - 1) {
+      A.queue[0] = 0;
+      A.queue[1] = 0;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -496,7 +533,7 @@ template <class T, int PDE, int TY, int TX>
 static cudaError_t launch_one(const Arena<T>& A, int mode, int cur, size_t pyr, cudaStream_t s) {
   const size_t smem = StSmem<T, TY, TX>::bytes(pyr);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(A.ntiles[0]);
+  cfg.gridDim = dim3(A.persistent ? std::min(A.ntiles[0], A.persistent) : A.ntiles[0]);
   cfg.blockDim = dim3(MODIL_NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -521,11 +558,9 @@ template <class T, int TY, int TX>
 static cudaError_t prepare_cfg(int pde, size_t pyr) {
   const int smem = (int)StSmem<T, TY, TX>::bytes(pyr);
   if (pde == PDE_BURGERS)
-    return cudaFuncSetAttribute(k_fine_st<T, PDE_BURGERS, TY, TX>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return raise_smem_limit(k_fine_st<T, PDE_BURGERS, TY, TX>, (size_t)smem);
   if (pde == PDE_HEAT)
-    return cudaFuncSetAttribute(k_fine_st<T, PDE_HEAT, TY, TX>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return raise_smem_limit(k_fine_st<T, PDE_HEAT, TY, TX>, (size_t)smem);
   return cudaErrorInvalidValue;
 }
 
@@ -552,6 +587,30 @@ cudaError_t launch_fine_st(const Arena<T>& A, int pde, int cfg, int mode, int cu
     case 2: return launch_cfg<T, 8, 64>(A, pde, mode, cur, pyr, s);
     case 3: return launch_cfg<T, 32, 32>(A, pde, mode, cur, pyr, s);
     case 4: return launch_cfg<T, 8, 128>(A, pde, mode, cur, pyr, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class T, int PDE, int TY, int TX>
+static cudaError_t occ(size_t pyr, int* n) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_fine_st<T, PDE, TY, TX>, MODIL_NT,
+                                                       StSmem<T, TY, TX>::bytes(pyr));
+}
+
+template <class T, int TY, int TX>
+static cudaError_t occ_pde(int pde, size_t pyr, int* n) {
+  return pde == PDE_HEAT ? occ<T, PDE_HEAT, TY, TX>(pyr, n) : occ<T, PDE_BURGERS, TY, TX>(pyr, n);
+}
+
+// Resident fine-kernel blocks per SM (sizes the persistent launch).
+cudaError_t fine_st_blocks_per_sm(int pde, int cfg, size_t pyr, int elem, int* n) {
+  const bool d = (elem == 8);
+  switch (cfg) {
+    case 0: return d ? occ_pde<double, 16, 32>(pde, pyr, n) : occ_pde<float, 16, 32>(pde, pyr, n);
+    case 1: return d ? occ_pde<double, 16, 64>(pde, pyr, n) : occ_pde<float, 16, 64>(pde, pyr, n);
+    case 2: return d ? occ_pde<double, 8, 64>(pde, pyr, n) : occ_pde<float, 8, 64>(pde, pyr, n);
+    case 3: return d ? occ_pde<double, 32, 32>(pde, pyr, n) : occ_pde<float, 32, 32>(pde, pyr, n);
+    case 4: return d ? occ_pde<double, 8, 128>(pde, pyr, n) : occ_pde<float, 8, 128>(pde, pyr, n);
     default: return cudaErrorInvalidValue;
   }
 }

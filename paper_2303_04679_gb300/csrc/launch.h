@@ -32,6 +32,7 @@ struct TailPlan {
 constexpr int kTailC = 8;
 
 size_t fine_st_smem_bytes(int cfg, size_t pyr_elems, int elem_bytes);
+cudaError_t fine_st_blocks_per_sm(int pde, int cfg, size_t pyr_elems, int elem_bytes, int* n);
 template <class T>
 cudaError_t prepare_fine_st(int pde, int cfg, size_t pyr_elems);
 template <class T>

@@ -64,7 +64,7 @@ struct Plan {
   size_t pyr_elems = 0;
   // arena offsets (bytes)
   size_t o_p0, o_p1, o_m, o_v, o_g, o_uf, o_kq, o_km, o_kv, o_kg, o_aux, o_part, o_rptr, o_rcell,
-      o_rfield, o_rbeg, o_mval, o_rv0, o_inst, o_st, o_cnt, o_ti[MODIL_MAXL], total;
+      o_rfield, o_rbeg, o_mval, o_rv0, o_inst, o_st, o_cnt, o_q, o_ti[MODIL_MAXL], total;
 };
 
 int find_cfg(int ty, int tx) {
@@ -285,6 +285,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   P.o_inst = take(sizeof(DevInst) * n);
   P.o_st = take(sizeof(InstState) * n);
   P.o_cnt = take(sizeof(int) * n);
+  P.o_q = take(2 * sizeof(int));
   for (int l = 0; l < MODIL_MAXL; ++l) P.o_ti[l] = take(4 * P.tile_inst[l].size());
   P.total = o;
   return MODIL_OK;
@@ -332,6 +333,8 @@ void fill_arena(modil_problem* p, Arena<T>& A) {
   A.inst = reinterpret_cast<const DevInst*>(b + P.o_inst);
   A.st = reinterpret_cast<InstState*>(b + P.o_st);
   A.counter = reinterpret_cast<int*>(b + P.o_cnt);
+  A.queue = reinterpret_cast<int*>(b + P.o_q);
+  A.persistent = 0;
   for (int l = 0; l < MODIL_MAXL; ++l) {
     A.tile_inst[l] = reinterpret_cast<const int*>(b + P.o_ti[l]);
     A.ntiles[l] = (int)P.tile_inst[l].size();
@@ -725,6 +728,25 @@ modil_status modil_loss_bwd(modil_problem* p, const void* levels, double grad_ou
              : external_pass<float>(p, p->A32, levels, grads, grad_out, MODE_GRAD);
 }
 
+modil_status modil_set_persistent(modil_problem* p, int on) {
+  if (!p) return fail(MODIL_ERR_ARG, "problem is NULL");
+  const Plan& P = p->plan;
+  if (P.pde == MODIL_PDE_NS2D && on) return fail(MODIL_ERR_UNSUPPORTED, "persistent launch: Burgers/heat only");
+  int grid = 0;
+  if (on) {
+    int dev = 0, sms = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int per_sm = 0;
+    CUDA_TRY(fine_st_blocks_per_sm(P.pde, P.cfg, P.pyr_elems, (int)P.esz, &per_sm));
+    grid = std::max(1, per_sm) * sms;
+  }
+  drop_graph(p);  // the launch configuration is part of the captured graph
+  p->A32.persistent = grid;
+  p->A64.persistent = grid;
+  return MODIL_OK;
+}
+
 modil_status modil_param_count(const modil_problem* p, long long* n) {
   if (!p || !n) return fail(MODIL_ERR_ARG, "NULL argument");
   *n = p->plan.n_param;
@@ -829,6 +851,7 @@ modil_status noalloc_run(const Plan& P, const modil_desc* d, const void* levels,
   const size_t o_rv0 = take(sizeof(T) * P.run_v0.size());
   const size_t o_inst = take(sizeof(DevInst)), o_st = take(sizeof(InstState));
   const size_t o_cnt = take(sizeof(int));
+  const size_t o_q = take(2 * sizeof(int));
   size_t o_ti[MODIL_MAXL];
   for (int l = 0; l < MODIL_MAXL; ++l) o_ti[l] = take(4 * P.tile_inst[l].size());
   if (o > kNoAllocScratchBytes)
@@ -861,6 +884,7 @@ modil_status noalloc_run(const Plan& P, const modil_desc* d, const void* levels,
   if ((st = up(o_inst, P.dev.data(), sizeof(DevInst))) != MODIL_OK) return st;
   if ((st = up(o_st, &st0, sizeof(st0))) != MODIL_OK) return st;
   CUDA_TRY(cudaMemsetAsync(b + o_cnt, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(b + o_q, 0, 2 * sizeof(int), s));
   for (int l = 0; l < MODIL_MAXL; ++l)
     if ((st = up(o_ti[l], P.tile_inst[l].data(), 4 * P.tile_inst[l].size())) != MODIL_OK) return st;
   Arena<T> A{};
@@ -880,6 +904,8 @@ modil_status noalloc_run(const Plan& P, const modil_desc* d, const void* levels,
   A.inst = reinterpret_cast<const DevInst*>(b + o_inst);
   A.st = reinterpret_cast<InstState*>(b + o_st);
   A.counter = reinterpret_cast<int*>(b + o_cnt);
+  A.queue = reinterpret_cast<int*>(b + o_q);
+  A.persistent = 0;
   for (int l = 0; l < MODIL_MAXL; ++l) {
     A.tile_inst[l] = reinterpret_cast<const int*>(b + o_ti[l]);
     A.ntiles[l] = (int)P.tile_inst[l].size();

@@ -95,6 +95,8 @@ struct Arena {
   int npart;
   int n_inst;
   float gscale;        // factor on the written fine gradient (d loss / d output), 1 normally
+  int persistent;      // 0: one fine block per tile; > 0: grid size of the persistent launch
+  int* queue;          // persistent launch: next tile, blocks finished
 };
 
 // ---------------------------------------------------------------------------
@@ -222,6 +224,19 @@ __device__ __forceinline__ double block_sum(double x, double* scratch) {
 #pragma unroll
   for (int i = 0; i < NT / 32; ++i) s += scratch[i];
   return s;
+}
+
+// Raise (never lower) a kernel's dynamic shared-memory limit.  The limit is
+// a property of the kernel for the whole process, shared by every problem
+// that launches it, so a smaller problem created later must not cut it
+// below what an earlier, larger problem launches with.
+template <class K>
+inline cudaError_t raise_smem_limit(K kernel, size_t bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 // ---------------------------------------------------------------------------

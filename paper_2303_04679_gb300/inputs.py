@@ -202,3 +202,25 @@ def burgers_workload(nt=64, nx=64, n_levels=4, seed=0, n_meas=200, nu=0.01):
     cells = measurement_cells(nt * nx, n_meas, seed)
     return dict(shape=(nt, nx), n_levels=n_levels, meas_cell=cells, nu=nu,
                 amps=burgers_ic_amplitudes(seed), w_res=1.0, w_data=1.0, lr=5e-3)
+
+
+def burgers_batch(n=512, base_seed=0, meas_frac=0.005):
+    """The batched Burgers workload: n instances of uneven size.
+
+    Per instance (seeded by its index): N_x, N_t in {64, 128, 256, 512}, nu
+    log-uniform in [1e-3, 1e-1], 0.5 % of the cells measured (values of the
+    closed-form decaying sine field of the instance's initial condition),
+    L = log2(min(N_x, N_t) / 8) + 1 levels (coarsest grid at least 8 cells).
+    Returns a list of dicts (shape = (N_t, N_x)).
+    """
+    out = []
+    for i in range(n):
+        nx, nt, nu, seed = burgers_batch_instance(i, base_seed)
+        L = int(math.log2(min(nx, nt) // 8)) + 1
+        m = max(1, int(round(meas_frac * nt * nx)))
+        cells = measurement_cells(nt * nx, m, seed)
+        amps = burgers_ic_amplitudes(seed)
+        field = burgers_smooth_field(nt, nx, amps, nu)
+        out.append(dict(shape=(nt, nx), n_levels=L, nu=nu, meas_cell=cells,
+                        meas_value=field.reshape(-1)[cells], seed=seed))
+    return out

@@ -73,6 +73,7 @@ def _load():
         "modil_launches_per_step": ([P, C.POINTER(C.c_int)], C.c_int),
         "modil_profile_step": ([P, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)], C.c_int),
         "modil_reset_optimizer": ([P], C.c_int),
+        "modil_set_persistent": ([P, C.c_int], C.c_int),
         "modil_param_count": ([P, C.POINTER(C.c_longlong)], C.c_int),
         "modil_level_offset": ([P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_longlong)], C.c_int),
         "modil_loss_fwd": ([P, P, C.POINTER(C.c_double)], C.c_int),
@@ -107,6 +108,10 @@ class Desc:
     def __init__(self, pde, shape, n_levels, dtype="f32", coef=(), w_res=1.0, w_data=1.0,
                  w_reg=0.0, meas_cell=None, meas_value=None, meas_field=None, aux=None,
                  knodes=None, lr=5e-3, beta1=0.9, beta2=0.999, eps=1e-8, tile=(0, 0)):
+        self.kwargs = dict(pde=pde, shape=shape, n_levels=n_levels, dtype=dtype, coef=coef,
+                           w_res=w_res, w_data=w_data, w_reg=w_reg, meas_cell=meas_cell,
+                           meas_value=meas_value, meas_field=meas_field, aux=aux, knodes=knodes,
+                           lr=lr, beta1=beta1, beta2=beta2, eps=eps, tile=tile)
         self.pde = {"burgers": PDE_BURGERS, "heat": PDE_HEAT, "ns2d": PDE_NS2D}.get(pde, pde)
         self.dtype = {"f32": F32, "f64": F64}.get(dtype, dtype)
         self.shape = tuple(int(s) for s in shape)
@@ -325,6 +330,9 @@ class Problem:
     def loss_bwd(self, levels, grad_out, grads):
         """grads <- grad_out * dL/dlevels (device tensors, parameter-vector layout)."""
         _check(LIB.modil_loss_bwd(self._h, levels.data_ptr(), float(grad_out), grads.data_ptr()))
+
+    def set_persistent(self, on=True):
+        _check(LIB.modil_set_persistent(self._h, 1 if on else 0))
 
     def reset_optimizer(self):
         _check(LIB.modil_reset_optimizer(self._h))
