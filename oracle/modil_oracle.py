@@ -44,7 +44,8 @@ __all__ = [
     "heat_conductivity", "heat_residual", "poisson_residual", "loss_terms",
     "loss_grad_fine", "loss_grad_levels", "adam_step", "OracleState",
     "oracle_step", "burgers_explicit_solve", "heat_implicit_solve",
-    "eo_flux", "ns2d_residuals", "ns2d_fields_residual_jacobian_grad",
+    "eo_flux", "ns2d_residuals", "ns2d_fields_residual_jacobian_grad", "ns3d_residuals",
+    "ns3d_chi", "ns3d_residual_jacobian_grad",
 ]
 
 
@@ -198,7 +199,7 @@ class Problem:
 
     @property
     def n_fields(self):
-        return 3 if self.pde == "ns2d" else 1
+        return {"ns2d": 3, "ns3d": 5}.get(self.pde, 1)
 
     def spacing(self):
         """Grid spacings per axis (same order as shape)."""
@@ -208,6 +209,8 @@ class Problem:
             return (1.0 / self.shape[0], 1.0 / self.shape[1])
         if self.pde in ("poisson", "ns2d"):  # unit square / cube
             return tuple(1.0 / n for n in self.shape)
+        if self.pde == "ns3d":              # [0,1] (z) x [0,1] (y) x [0,2] (x)
+            return (1.0 / self.shape[0], 1.0 / self.shape[1], 2.0 / self.shape[2])
         raise ValueError(self.pde)
 
 
@@ -554,6 +557,133 @@ def ns2d_fields_residual_jacobian_grad(u, v, p, lam_u, lam_v, lam_c, Re, h, tau_
 
 
 # ---------------------------------------------------------------------------
+# Penalised steady Navier-Stokes in 3-D, body shape (Section 3.5, eq_nschi3)
+# ---------------------------------------------------------------------------
+# Reading.  Fields u, v, w, p, chihat on (z, y, x) cells of [0,1] x [0,1] x
+# [0,2], flow along x.  chi = 1 / (1 + exp(-(chihat + 5))).  Residuals follow
+# the cavity discretisation (Section 3.3 reading) in 3-D with the spacings of
+# each axis:
+#   momentum:  r = (1 - chi) (conv + grad p - (D/Re) lap) + lambda chi u_c
+#   continuity: sum over axes of Rhie-Chow face fluxes.
+# Boundaries by ghost cells: inlet x = 0 with u = (1, 0, 0) and zero normal
+# pressure gradient; outlet x = 2 with p = 0 (odd ghost) and zero-gradient
+# velocity; free-slip walls in y and z (odd ghost for the normal component,
+# even ghosts for the tangential ones and p).  Convective and mass fluxes
+# through x-boundary faces use the boundary values (inlet velocity, outlet
+# cell value), through walls they vanish.  Polynomial in u, v, w, p and
+# analytic in chihat, so complex input is accepted.
+
+def ns3d_chi(ch):
+    return 1.0 / (1.0 + np.exp(-(ch + 5.0)))
+
+
+def _ns3d_pad(f, kind):
+    """Pad one field with its ghost cells; kind in u, v, w, p."""
+    nz, ny, nx = f.shape
+    P = np.zeros((nz + 2, ny + 2, nx + 2), dtype=f.dtype)
+    P[1:-1, 1:-1, 1:-1] = f
+    c = P[1:-1, 1:-1, :]
+    # x: inlet (low) / outlet (high)
+    if kind == "u":
+        c[:, :, 0] = 2.0 - f[:, :, 0]
+    elif kind in ("v", "w"):
+        c[:, :, 0] = -f[:, :, 0]
+    else:
+        c[:, :, 0] = f[:, :, 0]
+    c[:, :, -1] = -f[:, :, -1] if kind == "p" else f[:, :, -1]
+    # y walls: v normal, others even; z walls: w normal
+    sy = -1.0 if kind == "v" else 1.0
+    P[1:-1, 0, 1:-1] = sy * f[:, 0, :]
+    P[1:-1, -1, 1:-1] = sy * f[:, -1, :]
+    sz = -1.0 if kind == "w" else 1.0
+    P[0, 1:-1, 1:-1] = sz * f[0, :, :]
+    P[-1, 1:-1, 1:-1] = sz * f[-1, :, :]
+    return P
+
+
+def ns3d_residuals(u, v, w, p, ch, Re, D, lam, h, tau_factor=1.0):
+    """(r_u, r_v, r_w, r_c) on every cell; h = (hz, hy, hx)."""
+    hz, hy, hx = h
+    nz, ny, nx = u.shape
+    U, V, W, Pp = _ns3d_pad(u, "u"), _ns3d_pad(v, "v"), _ns3d_pad(w, "w"), _ns3d_pad(p, "p")
+    C = (slice(1, -1),) * 3
+    def sh(a, dz, dy, dx):
+        return a[1 + dz:a.shape[0] - 1 + dz, 1 + dy:a.shape[1] - 1 + dy, 1 + dx:a.shape[2] - 1 + dx]
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    mn, ms = jj < ny - 1, jj > 0
+    mt, mb = kk < nz - 1, kk > 0
+    nu = D / Re
+    chi = ns3d_chi(ch)
+    # face normal velocities (face averages; x-boundary faces get the boundary value)
+    Ue, Uw = (U[C] + sh(U, 0, 0, 1)) / 2, (sh(U, 0, 0, -1) + U[C]) / 2
+    Vn, Vs = np.where(mn, (V[C] + sh(V, 0, 1, 0)) / 2, 0), np.where(ms, (sh(V, 0, -1, 0) + V[C]) / 2, 0)
+    Wt, Wb = np.where(mt, (W[C] + sh(W, 1, 0, 0)) / 2, 0), np.where(mb, (sh(W, -1, 0, 0) + W[C]) / 2, 0)
+    res = []
+    for F in (U, V, W):
+        fe, fw = (F[C] + sh(F, 0, 0, 1)) / 2, (sh(F, 0, 0, -1) + F[C]) / 2
+        fn, fs = (F[C] + sh(F, 0, 1, 0)) / 2, (sh(F, 0, -1, 0) + F[C]) / 2
+        ft, fb = (F[C] + sh(F, 1, 0, 0)) / 2, (sh(F, -1, 0, 0) + F[C]) / 2
+        conv = (Ue * fe - Uw * fw) / hx + (Vn * fn - Vs * fs) / hy + (Wt * ft - Wb * fb) / hz
+        lap = ((sh(F, 0, 0, 1) - 2 * F[C] + sh(F, 0, 0, -1)) / hx**2
+               + (sh(F, 0, 1, 0) - 2 * F[C] + sh(F, 0, -1, 0)) / hy**2
+               + (sh(F, 1, 0, 0) - 2 * F[C] + sh(F, -1, 0, 0)) / hz**2)
+        res.append((conv, lap, F[C]))
+    gx = (sh(Pp, 0, 0, 1) - sh(Pp, 0, 0, -1)) / (2 * hx)
+    gy = (sh(Pp, 0, 1, 0) - sh(Pp, 0, -1, 0)) / (2 * hy)
+    gz = (sh(Pp, 1, 0, 0) - sh(Pp, -1, 0, 0)) / (2 * hz)
+    out = []
+    for (conv, lap, f), g in zip(res, (gx, gy, gz)):
+        out.append((1.0 - chi) * (conv + g - nu * lap) + lam * chi * f)
+    # continuity: Rhie-Chow at interior faces, boundary values at x ends, 0 at walls
+    def rc_faces(vel, pres, gr, hh, axis):
+        a0 = [slice(None)] * 3
+        a1 = [slice(None)] * 3
+        a0[axis] = slice(None, -1)
+        a1[axis] = slice(1, None)
+        a0, a1 = tuple(a0), tuple(a1)
+        return (vel[a0] + vel[a1]) / 2 - tau_factor * hh * ((pres[a1] - pres[a0]) / hh - (gr[a0] + gr[a1]) / 2)
+    Fx = np.zeros((nz, ny, nx + 1), dtype=np.result_type(u, p))
+    Fx[:, :, 1:-1] = rc_faces(u, p, gx, hx, 2)
+    Fx[:, :, 0] = 1.0
+    Fx[:, :, -1] = u[:, :, -1]
+    Fy = np.zeros((nz, ny + 1, nx), dtype=Fx.dtype)
+    Fy[:, 1:-1, :] = rc_faces(v, p, gy, hy, 1)
+    Fz = np.zeros((nz + 1, ny, nx), dtype=Fx.dtype)
+    Fz[1:-1, :, :] = rc_faces(w, p, gz, hz, 0)
+    rcont = ((Fx[:, :, 1:] - Fx[:, :, :-1]) / hx + (Fy[:, 1:, :] - Fy[:, :-1, :]) / hy
+             + (Fz[1:, :, :] - Fz[:-1, :, :]) / hz)
+    return out[0], out[1], out[2], rcont
+
+
+def ns3d_residual_jacobian_grad(fields, lams, coef, h, eps=1e-30):
+    """J^T lambda for the four residual fields by complex-step differentiation;
+    5 x 5 x 5 colouring (reach 2 along each axis), 5 fields: 625 evaluations."""
+    nz, ny, nx = fields[0].shape
+    base = [np.asarray(f, complex) for f in fields]
+    grads = [np.zeros((nz, ny, nx)) for _ in range(5)]
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for f in range(5):
+        for a in range(5):
+            for b in range(5):
+                for c in range(5):
+                    sel = ((kk % 5) == a) & ((jj % 5) == b) & ((ii % 5) == c)
+                    if not sel.any():
+                        continue
+                    wv = list(base)
+                    wv[f] = base[f] + 1j * eps * sel
+                    rs = ns3d_residuals(*wv, coef["Re"], coef["D"], coef["lam"], h,
+                                        coef.get("tau", 1.0))
+                    contrib = sum(r.imag * l for r, l in zip(rs, lams)) / eps
+                    dk = ((a - kk + 2) % 5) - 2
+                    dj = ((b - jj + 2) % 5) - 2
+                    di = ((c - ii + 2) % 5) - 2
+                    tk, tj, ti = kk + dk, jj + dj, ii + di
+                    ok = (tk >= 0) & (tk < nz) & (tj >= 0) & (tj < ny) & (ti >= 0) & (ti < nx)
+                    np.add.at(grads[f], (tk[ok], tj[ok], ti[ok]), contrib[ok])
+    return grads
+
+
+# ---------------------------------------------------------------------------
 # Loss and gradient
 # ---------------------------------------------------------------------------
 
@@ -605,6 +735,9 @@ def loss_terms(p, u, q=None):
         ru, rv, rc, rg = ns2d_residuals(u[0], u[1], u[2], p.coef["Re"], h[0],
                                         p.coef.get("tau", 1.0))
         r = np.concatenate([ru.ravel(), rv.ravel(), rc.ravel(), [rg]])
+    elif p.pde == "ns3d":
+        rs = ns3d_residuals(*u, p.coef["Re"], p.coef["D"], p.coef["lam"], h, p.coef.get("tau", 1.0))
+        r = np.concatenate([x.ravel() for x in rs])
     else:
         raise ValueError(p.pde)
     res = p.w_res * dV * float(np.sum(r * r)) + bnd
@@ -639,6 +772,12 @@ def loss_grad_fine(p, u, q=None):
         g = ns2d_fields_residual_jacobian_grad(u[0], u[1], u[2], c * ru, c * rv, c * rc, Re,
                                                h[0], tf)
         g[2][0, 0] += c * rg
+        _, gd = _data_term(p, list(u))
+        return terms, [a + b for a, b in zip(g, gd)], gq
+    elif p.pde == "ns3d":
+        rs = ns3d_residuals(*u, p.coef["Re"], p.coef["D"], p.coef["lam"], h, p.coef.get("tau", 1.0))
+        c = 2.0 * p.w_res * dV
+        g = ns3d_residual_jacobian_grad(u, [c * x for x in rs], p.coef, h)
         _, gd = _data_term(p, list(u))
         return terms, [a + b for a, b in zip(g, gd)], gq
     else:

@@ -477,3 +477,97 @@ def test_ns2d_gradient_finite_differences():
     flat_params = [a for f in lv for a in f]
     flat_grads = [g for f in grads for g in f]
     _fd_check(lambda: o.loss_terms(p, [o.compose(f) for f in lv])["total"], flat_params, flat_grads)
+
+
+# --------------------------------------------------------------------------
+# Penalised Navier-Stokes in 3-D, body shape (Section 3.5)
+# --------------------------------------------------------------------------
+
+def _ns3d_h(sh):
+    return (1.0 / sh[0], 1.0 / sh[1], 2.0 / sh[2])
+
+
+def test_ns3d_uniform_inflow_is_a_solution_away_from_the_body():
+    """u = (1,0,0), p = 0, no body: only lambda chi u remains (chi ~ 1e-13)."""
+    sh = (6, 5, 10)
+    one, z = np.ones(sh), np.zeros(sh)
+    ch = np.full(sh, -25.0)
+    ru, rv, rw, rc = o.ns3d_residuals(one, z, z, z, ch, 60.0, 0.4, 1.0, _ns3d_h(sh))
+    chi = o.ns3d_chi(ch)
+    np.testing.assert_allclose(ru, chi, atol=1e-12)
+    for r in (rv, rw, rc):
+        np.testing.assert_allclose(r, 0.0, atol=1e-10)
+
+
+def test_ns3d_inside_the_body_only_penalisation_remains():
+    """chi = 1 (chihat large): momentum residual = lambda u exactly."""
+    rng = np.random.default_rng(30)
+    sh = (4, 5, 6)
+    u, v, w, p = [rng.normal(size=sh) for _ in range(4)]
+    ch = np.full(sh, 60.0)
+    ru, rv, rw, _ = o.ns3d_residuals(u, v, w, p, ch, 60.0, 0.4, 0.7, _ns3d_h(sh))
+    np.testing.assert_allclose(ru, 0.7 * u, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(rv, 0.7 * v, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(rw, 0.7 * w, rtol=1e-12, atol=1e-12)
+
+
+def test_ns3d_mass_balance():
+    """sum r_c dV = (outlet flux - inlet flux) over the x ends (walls carry none)."""
+    rng = np.random.default_rng(31)
+    sh = (5, 6, 8)
+    hz, hy, hx = _ns3d_h(sh)
+    f = [rng.normal(size=sh) for _ in range(5)]
+    rc = o.ns3d_residuals(*f, 60.0, 0.4, 1.0, (hz, hy, hx))[3]
+    lhs = rc.sum() * hx * hy * hz
+    rhs = hy * hz * (f[0][:, :, -1].sum() - sh[0] * sh[1] * 1.0)
+    assert abs(lhs - rhs) < 1e-10 * max(1.0, abs(rhs))
+
+
+def test_ns3d_interior_consistency_second_order():
+    """Smooth fields, no body: interior residuals -> conservative NS with D/Re."""
+    import sympy as sp
+    X, Y, Z = sp.symbols("x y z")
+    uu = 1 + 0.3 * sp.sin(X) * sp.cos(2 * Y) * sp.cos(Z)
+    vv = 0.2 * sp.cos(X + Y) * sp.sin(Z + 0.3)
+    ww = -0.1 * sp.sin(2 * Z) * sp.cos(X - Y)
+    pp = sp.exp(0.3 * X) * sp.sin(Y + Z)
+    nu = 0.4 / 60.0
+    fields = (uu, vv, ww)
+    lapl = lambda f: sp.diff(f, X, 2) + sp.diff(f, Y, 2) + sp.diff(f, Z, 2)  # noqa: E731
+    ex = []
+    for f, g in zip(fields, (sp.diff(pp, X), sp.diff(pp, Y), sp.diff(pp, Z))):
+        ex.append(sp.diff(uu * f, X) + sp.diff(vv * f, Y) + sp.diff(ww * f, Z) + g - nu * lapl(f))
+    ex.append(sp.diff(uu, X) + sp.diff(vv, Y) + sp.diff(ww, Z))
+    fn = [sp.lambdify((X, Y, Z), e, "numpy") for e in (uu, vv, ww, pp)]
+    en = [sp.lambdify((X, Y, Z), e, "numpy") for e in ex]
+    errs = []
+    for n in (16, 32, 64):
+        sh = (n, n, 2 * n)  # equal spacing in all axes
+        hz, hy, hx = 1.0 / n, 1.0 / n, 2.0 / (2 * n)
+        zc = (np.arange(n) + 0.5) * hz
+        yc = (np.arange(n) + 0.5) * hy
+        xc = (np.arange(2 * n) + 0.5) * hx
+        Zg, Yg, Xg = np.meshgrid(zc, yc, xc, indexing="ij")
+        f = [g(Xg, Yg, Zg) * np.ones(sh) for g in fn] + [np.full(sh, -40.0)]
+        rs = o.ns3d_residuals(*f, 60.0, 0.4, 1.0, (hz, hy, hx))
+        k = 3
+        sl = (slice(k, -k),) * 3
+        errs.append(max(np.max(np.abs(r - e(Xg, Yg, Zg))[sl]) for r, e in zip(rs, en)))
+    rates = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(3.2 < q < 4.8 for q in rates), (errs, rates)
+
+
+def test_ns3d_gradient_finite_differences():
+    sh, L = (4, 4, 8), 2
+    rng = np.random.default_rng(32)
+    n = int(np.prod(sh))
+    cells = inputs.measurement_cells(n, 12, 32)
+    mf = (np.arange(12) % 3).astype(np.int32)
+    p = o.Problem("ns3d", sh, L, coef={"Re": 60.0, "D": 0.4, "lam": 1.0, "tau": 1.0},
+                  w_res=1.0, w_data=2.0, meas_cell=cells, meas_field=mf,
+                  meas_value=rng.normal(size=12))
+    lv = inputs.random_levels(sh, L, 5, seed=32, coarse_scale=0.3)
+    _, grads, _ = o.loss_grad_levels(p, lv)
+    flat_params = [a for f in lv for a in f]
+    flat_grads = [g for f in grads for g in f]
+    _fd_check(lambda: o.loss_terms(p, [o.compose(f) for f in lv])["total"], flat_params, flat_grads)
