@@ -62,9 +62,16 @@ enum {
                             x in [-1, 1], t in [0, 1]; Section 3.2 with viscosity   */
   MODIL_PDE_HEAT = 2,    /* u_t = (k(u) u_x)_x with unknown k, axes (t, x) on [0,1]^2;
                             Section 3.4, the displayed implicit scheme              */
-  MODIL_PDE_NS2D = 3     /* steady incompressible Navier-Stokes, lid-driven cavity on
+  MODIL_PDE_NS2D = 3,    /* steady incompressible Navier-Stokes, lid-driven cavity on
                             [0,1]^2 (square grid), fields 0 = u, 1 = v, 2 = p; collocated
                             finite volumes with Rhie-Chow continuity; Section 3.3   */
+  MODIL_PDE_NS3D = 4     /* steady Navier-Stokes past a body in 3-D with the body as
+                            a penalisation field (Section 3.5, the penalised momentum
+                            equation): axes (z, y, x) on [0,1] x [0,1] x [0,2], fields
+                            0 = u, 1 = v, 2 = w (velocity along x, y, z), 3 = p,
+                            4 = chihat with body fraction chi = 1/(1+exp(-(chihat+5)));
+                            inlet x = 0 (u = (1,0,0)), outlet x = 2 (p = 0), free-slip
+                            walls in y and z; ndim = 3                               */
 };
 
 enum { MODIL_F32 = 0, MODIL_F64 = 1 };
@@ -80,11 +87,13 @@ enum { MODIL_TERM_TOTAL = 0, MODIL_TERM_RES = 1, MODIL_TERM_DATA = 2, MODIL_TERM
 typedef struct {
   int pde;      /* MODIL_PDE_*                                                   */
   int dtype;    /* MODIL_F32 or MODIL_F64: storage and stencil arithmetic       */
-  int ndim;     /* 2 for the space-time families                                */
+  int ndim;     /* 2 for BURGERS, HEAT and NS2D; 3 for NS3D                     */
   int shape[3]; /* fine cells per axis, slowest first; unused entries 0         */
   int n_levels; /* L >= 1; every axis must be divisible by 2^(L-1); 1 = ODIL    */
   double coef[4]; /* BURGERS: coef[0] = nu.  HEAT: unused.  NS2D: coef[0] = Re,
-                     coef[1] = Rhie-Chow factor (tau = coef[1] * h)               */
+                     coef[1] = Rhie-Chow factor (tau = coef[1] * h).  NS3D:
+                     coef[0] = Re, coef[1] = D (viscosity D/Re), coef[2] = lambda
+                     (penalisation), coef[3] = Rhie-Chow factor                   */
   double w_res;   /* residual weight: w_res * dV * sum r^2                       */
   double w_data;  /* data weight: w_data / n_meas * sum (u - y)^2                */
   double w_reg;   /* HEAT: w_reg * sum_j (q_{j+1} - 2 q_j + q_{j-1})^2           */
@@ -99,7 +108,7 @@ typedef struct {
   double adam_lr, adam_beta1, adam_beta2, adam_eps;
   int tile[2];               /* fine tile (rows, cols); 0 = library default.
                                 Burgers/heat: 16x32 16x64 8x64 32x32 8x128;
-                                NS2D: 8x32 16x32                                 */
+                                NS2D: 8x32 16x32.  NS3D: 0 only (4x8x16 cells)  */
 } modil_desc;
 
 /* Device bytes needed for a batch of n problems described by descs[0..n-1]. */
@@ -118,7 +127,8 @@ void modil_destroy(modil_problem* p);
 
 modil_status modil_set_stream(modil_problem* p, void* stream);
 
-/* Number of instances, fields, levels and cells per axis of a level. */
+/* Cells per axis of a level, slowest first: 2-D problems fill shape[0..1]
+ * and set shape[2] = 0, 3-D problems fill all three. */
 modil_status modil_level_shape(const modil_problem* p, int instance, int level, int shape[3]);
 
 /* Copy one level (field, level 0 = finest) in or out; bytes must equal the

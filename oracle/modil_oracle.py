@@ -45,7 +45,7 @@ __all__ = [
     "loss_grad_fine", "loss_grad_levels", "adam_step", "OracleState",
     "oracle_step", "burgers_explicit_solve", "heat_implicit_solve",
     "eo_flux", "ns2d_residuals", "ns2d_fields_residual_jacobian_grad", "ns3d_residuals",
-    "ns3d_chi", "ns3d_residual_jacobian_grad",
+    "ns3d_chi", "ns3d_residual_jacobian_grad", "ns3d_fine_grad_colours",
 ]
 
 
@@ -655,17 +655,25 @@ def ns3d_residuals(u, v, w, p, ch, Re, D, lam, h, tau_factor=1.0):
     return out[0], out[1], out[2], rcont
 
 
-def ns3d_residual_jacobian_grad(fields, lams, coef, h, eps=1e-30):
+def ns3d_residual_jacobian_grad(fields, lams, coef, h, eps=1e-30, colours=None):
     """J^T lambda for the four residual fields by complex-step differentiation;
-    5 x 5 x 5 colouring (reach 2 along each axis), 5 fields: 625 evaluations."""
+    5 x 5 x 5 colouring (reach 2 along each axis), 5 fields: 625 evaluations.
+
+    colours: optional list of (field, a, b, c); only those colour classes are
+    evaluated, so the result is exact on the cells (k, j, i) = (a, b, c) mod 5
+    of those fields and zero elsewhere (a sample of a grid too large for all
+    625 evaluations)."""
     nz, ny, nx = fields[0].shape
     base = [np.asarray(f, complex) for f in fields]
     grads = [np.zeros((nz, ny, nx)) for _ in range(5)]
     kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    todo = None if colours is None else set(tuple(x) for x in colours)
     for f in range(5):
         for a in range(5):
             for b in range(5):
                 for c in range(5):
+                    if todo is not None and (f, a, b, c) not in todo:
+                        continue
                     sel = ((kk % 5) == a) & ((jj % 5) == b) & ((ii % 5) == c)
                     if not sel.any():
                         continue
@@ -681,6 +689,18 @@ def ns3d_residual_jacobian_grad(fields, lams, coef, h, eps=1e-30):
                     ok = (tk >= 0) & (tk < nz) & (tj >= 0) & (tj < ny) & (ti >= 0) & (ti < nx)
                     np.add.at(grads[f], (tk[ok], tj[ok], ti[ok]), contrib[ok])
     return grads
+
+
+def ns3d_fine_grad_colours(p, u, colours):
+    """dL/du of the body problem on the cells of the given colour classes
+    (field, a, b, c): exact there, zero elsewhere; for grids where the full
+    625-evaluation Jacobian is too slow."""
+    h = p.spacing()
+    c = 2.0 * p.w_res * float(np.prod(h))
+    rs = ns3d_residuals(*u, p.coef["Re"], p.coef["D"], p.coef["lam"], h, p.coef.get("tau", 1.0))
+    g = ns3d_residual_jacobian_grad(u, [c * x for x in rs], p.coef, h, colours=colours)
+    _, gd = _data_term(p, list(u))
+    return [a + b for a, b in zip(g, gd)]
 
 
 # ---------------------------------------------------------------------------

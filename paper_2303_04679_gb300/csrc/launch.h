@@ -46,6 +46,17 @@ cudaError_t launch_fine_ns2d(const Arena<T>& A, int cfg, int mode, int cur, size
                              cudaStream_t s);
 template <class T>
 cudaError_t launch_level(const Arena<T>& A, int level, int mode, int cur, cudaStream_t s);
+// 3-D penalised Navier-Stokes: fine tile 4 x 8 x 16 cells, coarse tile 2 x 8 x 16.
+constexpr int k3TZ = 4, k3TY = 8, k3TX = 16;
+constexpr int k3LZ = 2, k3LY = 8, k3LX = 16;
+template <class T>
+cudaError_t prepare_ns3d(size_t pyr_elems);
+template <class T>
+cudaError_t launch_compose3(const Arena<T>& A, int cur, size_t pyr_elems, cudaStream_t s);
+template <class T>
+cudaError_t launch_resid3(const Arena<T>& A, int mode, int cur, cudaStream_t s);
+template <class T>
+cudaError_t launch_level3(const Arena<T>& A, int level, int mode, int cur, cudaStream_t s);
 size_t tail_smem_bytes(const TailPlan& tp, int elem_bytes);
 size_t tail_instance_bytes(int L, int ts, const int (*n)[3], int nf, int elem_bytes);
 template <class T>

@@ -80,14 +80,18 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   P.pde = d[0].pde;
   P.dtype = d[0].dtype;
   P.ndim = d[0].ndim;
-  if (P.pde != MODIL_PDE_BURGERS && P.pde != MODIL_PDE_HEAT && P.pde != MODIL_PDE_NS2D)
+  if (P.pde != MODIL_PDE_BURGERS && P.pde != MODIL_PDE_HEAT && P.pde != MODIL_PDE_NS2D &&
+      P.pde != MODIL_PDE_NS3D)
     return fail(MODIL_ERR_UNSUPPORTED, "unknown pde " + std::to_string(P.pde));
   if (P.dtype != MODIL_F32 && P.dtype != MODIL_F64) return fail(MODIL_ERR_ARG, "dtype");
-  if (P.ndim != 2) return fail(MODIL_ERR_UNSUPPORTED, "these PDE families are 2-D");
+  const bool three = P.pde == MODIL_PDE_NS3D;
+  if (P.ndim != (three ? 3 : 2))
+    return fail(MODIL_ERR_ARG, three ? "NS3D needs ndim = 3" : "this PDE family is 2-D (ndim = 2)");
   P.esz = P.dtype == MODIL_F64 ? 8 : 4;
-  P.nfield = (P.pde == MODIL_PDE_NS2D) ? 3 : 1;
+  P.nfield = (P.pde == MODIL_PDE_NS2D) ? 3 : (three ? 5 : 1);
   // tile configuration (same for the batch)
   int ty = d[0].tile[0], tx = d[0].tile[1];
+  if (three && (ty != 0 || tx != 0)) return fail(MODIL_ERR_ARG, "NS3D takes the library tile (tile = 0)");
   if (ty == 0 && tx == 0) {
     ty = (P.pde == MODIL_PDE_NS2D) ? 8 : 16;
     tx = 32;
@@ -109,13 +113,20 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
       return fail(MODIL_ERR_ARG, "a batch must share pde, dtype and ndim");
     if (q.tile[0] != d[0].tile[0] || q.tile[1] != d[0].tile[1])
       return fail(MODIL_ERR_ARG, "a batch must share the tile shape");
-    const int ny = q.shape[0], nx = q.shape[1];
-    if (ny < 1 || nx < 1) return fail(MODIL_ERR_ARG, "shape must be positive");
+    // 2-D problems: (1, ny, nx); 3-D: (nz, ny, nx)
+    const int nz = three ? q.shape[0] : 1;
+    const int ny = three ? q.shape[1] : q.shape[0], nx = three ? q.shape[2] : q.shape[1];
+    if (nz < 1 || ny < 1 || nx < 1) return fail(MODIL_ERR_ARG, "shape must be positive");
     if (q.n_levels < 1 || q.n_levels > MODIL_MAXL) return fail(MODIL_ERR_ARG, "n_levels");
     const int L = q.n_levels;
-    if ((ny % (1 << (L - 1))) || (nx % (1 << (L - 1))))
+    if ((three && (nz % (1 << (L - 1)))) || (ny % (1 << (L - 1))) || (nx % (1 << (L - 1))))
       return fail(MODIL_ERR_ARG, "every axis must be divisible by 2^(n_levels-1)");
-    if ((long long)ny * nx > (1LL << 30)) return fail(MODIL_ERR_ARG, "grid too large");
+    if ((long long)nz * ny * nx > (1LL << 30)) return fail(MODIL_ERR_ARG, "grid too large");
+    if (three) {
+      if (!(q.coef[0] > 0)) return fail(MODIL_ERR_ARG, "NS3D needs coef[0] = Re > 0");
+      if (!(q.coef[1] >= 0) || !(q.coef[2] >= 0) || !(q.coef[3] >= 0))
+        return fail(MODIL_ERR_ARG, "NS3D needs D, lambda and the Rhie-Chow factor >= 0");
+    }
     if (P.pde == MODIL_PDE_BURGERS && ny < 2) return fail(MODIL_ERR_ARG, "Burgers needs >= 2 rows");
     if (P.pde == MODIL_PDE_NS2D) {
       if (ny != nx) return fail(MODIL_ERR_ARG, "the cavity grid must be square");
@@ -143,12 +154,14 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
     D.nlev = L;
     D.nfield = P.nfield;
     D.nk = ip.nk;
-    D.ndim = 2;
-    // first level small enough for the per-instance tail kernel
+    D.ndim = three ? 3 : 2;
+    // first level small enough for the per-instance tail kernel (2-D only: the
+    // 3-D levels are all restricted by the level kernel, the tail finalises)
     const long long tcap = P.dtype == MODIL_F64 ? kTailCellsF64 : kTailCellsF32;
     int tail = L;
-    for (int l = 1; l < L; ++l)
-      if ((long long)(ny >> l) * (nx >> l) <= tcap) { tail = l; break; }
+    if (!three)
+      for (int l = 1; l < L; ++l)
+        if ((long long)(ny >> l) * (nx >> l) <= tcap) { tail = l; break; }
     D.tail = tail;
     P.max_tail = std::max(P.max_tail, tail);
     {
@@ -158,21 +171,29 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
       if (tail < L)
         P.tail.prev_cells = std::max(P.tail.prev_cells, (size_t)(ny >> (tail - 1)) * (nx >> (tail - 1)));
       int nn[MODIL_MAXL][3] = {};
-      for (int l = 0; l < L; ++l) { nn[l][0] = 1; nn[l][1] = ny >> l; nn[l][2] = nx >> l; }
+      for (int l = 0; l < L; ++l) { nn[l][0] = nz >> l; nn[l][1] = ny >> l; nn[l][2] = nx >> l; }
       P.tail.smem_bytes = std::max(P.tail.smem_bytes, tail_instance_bytes(L, tail, nn, P.nfield, (int)P.esz));
     }
     for (int l = 0; l < L; ++l) {
-      ip.n[l][0] = 1;
+      ip.n[l][0] = three ? nz >> l : 1;
       ip.n[l][1] = ny >> l;
       ip.n[l][2] = nx >> l;
-      const int tyl = l == 0 ? TY : kLevTY, txl = l == 0 ? TX : kLevTX;
-      ip.nt[l][0] = 1;
+      int tzl = 1, tyl, txl;
+      if (three) {
+        tzl = l == 0 ? k3TZ : k3LZ;
+        tyl = l == 0 ? k3TY : k3LY;
+        txl = l == 0 ? k3TX : k3LX;
+      } else {
+        tyl = l == 0 ? TY : kLevTY;
+        txl = l == 0 ? TX : kLevTX;
+      }
+      ip.nt[l][0] = (ip.n[l][0] + tzl - 1) / tzl;
       ip.nt[l][1] = (ip.n[l][1] + tyl - 1) / tyl;
       ip.nt[l][2] = (ip.n[l][2] + txl - 1) / txl;
-      ip.lev_size[l] = (long long)ip.n[l][1] * ip.n[l][2];
+      ip.lev_size[l] = (long long)ip.n[l][0] * ip.n[l][1] * ip.n[l][2];
       for (int a = 0; a < 3; ++a) { D.n[l][a] = ip.n[l][a]; D.nt[l][a] = ip.nt[l][a]; }
       D.tile_base[l] = (int)P.tile_inst[l].size();
-      const int ntl = ip.nt[l][1] * ip.nt[l][2];
+      const int ntl = ip.nt[l][0] * ip.nt[l][1] * ip.nt[l][2];
       if (l == 0) D.ntile0 = ntl;
       if (l == 0 || l < tail)
         for (int t = 0; t < ntl; ++t) P.tile_inst[l].push_back(i);
@@ -189,20 +210,41 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
     koff += ip.nk;
     D.aux_off = aoff;
     aoff += (P.pde == MODIL_PDE_HEAT) ? nx : 0;
-    double dV;
     if (P.pde == MODIL_PDE_BURGERS) {
       D.h[0] = 1.0; D.h[1] = 1.0 / ny; D.h[2] = 2.0 / nx;
+    } else if (three) {
+      D.h[0] = 1.0 / nz; D.h[1] = 1.0 / ny; D.h[2] = 2.0 / nx;
     } else {
       D.h[0] = 1.0; D.h[1] = 1.0 / ny; D.h[2] = 1.0 / nx;
     }
-    dV = D.h[1] * D.h[2];
+    const double dV = D.h[0] * D.h[1] * D.h[2];
     for (int c = 0; c < 4; ++c) D.coef[c] = q.coef[c];
     D.w_res_dV = q.w_res * dV;
     D.w_data_n = q.n_meas > 0 ? q.w_data / q.n_meas : 0.0;
     D.w_reg = q.w_reg;
     D.lr = q.adam_lr; D.b1 = q.adam_beta1; D.b2 = q.adam_beta2; D.eps = q.adam_eps;
     // pyramid bound of this instance (unclipped worst case, clipped by level size)
-    {
+    if (three) {
+      // exact: per axis the largest region over the tile positions; the axes
+      // are independent, so the product of the maxima is the largest box
+      long long tot = 0;
+      const int tdim[3] = {k3TZ, k3TY, k3TX};
+      for (int l = 0; l < L; ++l) {
+        long long box = 1;
+        for (int a = 0; a < 3; ++a) {
+          const int n0 = ip.n[0][a], nl = ip.n[l][a], k = (1 << (l + 1)) - 2;
+          int mx = 0;
+          for (int s0 = 0; s0 < n0; s0 += tdim[a]) {
+            const int lo = std::max(0, (s0 - k) >> l);
+            const int hi = std::min(nl - 1, (std::min(n0, s0 + tdim[a]) - 1 + k) >> l);
+            mx = std::max(mx, hi - lo + 1);
+          }
+          box *= mx;
+        }
+        tot += box;
+      }
+      P.pyr_elems = std::max<size_t>(P.pyr_elems, (size_t)tot);
+    } else {
       const int hu = (P.pde == MODIL_PDE_NS2D) ? 4 : 2;  // halo of the composed field
       long long hy = TY + 2 * hu, hx = TX + 2 * hu, tot = 0;
       for (int l = 1; l < L; ++l) {
@@ -228,15 +270,18 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   std::vector<M> all;
   for (int i = 0; i < n; ++i) {
     const modil_desc& q = d[i];
-    const int ny = q.shape[0], nx = q.shape[1];
+    const InstPlan& ip = P.inst[i];
+    const int nz = ip.n[0][0], ny = ip.n[0][1], nx = ip.n[0][2];
+    const int tz = three ? k3TZ : 1, ty3 = three ? k3TY : TY, tx3 = three ? k3TX : TX;
     for (int k = 0; k < q.n_meas; ++k) {
       const int c = q.meas_cell[k];
       const int f = q.meas_field ? q.meas_field[k] : 0;
-      if (c < 0 || (long long)c >= (long long)ny * nx) return fail(MODIL_ERR_ARG, "measurement cell out of range");
+      if (c < 0 || (long long)c >= (long long)nz * ny * nx)
+        return fail(MODIL_ERR_ARG, "measurement cell out of range");
       if (f < 0 || f >= P.nfield) return fail(MODIL_ERR_ARG, "measurement field out of range");
       if (!std::isfinite(q.meas_value[k])) return fail(MODIL_ERR_ARG, "measurement value not finite");
-      const int y = c / nx, x = c % nx;
-      const int t = P.dev[i].tile_base[0] + (y / TY) * P.inst[i].nt[0][2] + (x / TX);
+      const int z = c / (ny * nx), y = (c / nx) % ny, x = c % nx;
+      const int t = P.dev[i].tile_base[0] + ((z / tz) * ip.nt[0][1] + (y / ty3)) * ip.nt[0][2] + (x / tx3);
       all.push_back({t, c, f, q.meas_value[k]});
     }
   }
@@ -368,14 +413,26 @@ modil_status run_pass_t(modil_problem* p, Arena<T>& A, int mode, int cur, cudaEv
   const Plan& P = p->plan;
   int k = 0;
   if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
-  if (P.pde == MODIL_PDE_NS2D)
+  if (P.pde == MODIL_PDE_NS3D) {
+    CUDA_TRY(launch_compose3<T>(A, cur, P.pyr_elems, p->stream));
+    if (mode == MODE_COMPOSE) {
+      if (nev) *nev = k;
+      return MODIL_OK;
+    }
+    if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+    CUDA_TRY(launch_resid3<T>(A, mode, cur, p->stream));
+  } else if (P.pde == MODIL_PDE_NS2D) {
     CUDA_TRY(launch_fine_ns2d<T>(A, P.cfg, mode, cur, P.pyr_elems, p->stream));
-  else
+  } else {
     CUDA_TRY(launch_fine_st<T>(A, P.pde, P.cfg, mode, cur, P.pyr_elems, p->stream));
+  }
   if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
   if (mode == MODE_GRAD || mode == MODE_STEP)
     for (int l = 1; l < P.max_tail; ++l) {
-      CUDA_TRY(launch_level<T>(A, l, mode, cur, p->stream));
+      if (P.pde == MODIL_PDE_NS3D)
+        CUDA_TRY(launch_level3<T>(A, l, mode, cur, p->stream));
+      else
+        CUDA_TRY(launch_level<T>(A, l, mode, cur, p->stream));
       if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
     }
   if (mode != MODE_COMPOSE) {
@@ -392,7 +449,9 @@ modil_status run_pass(modil_problem* p, int mode, cudaEvent_t* ev = nullptr, int
                                     : run_pass_t<float>(p, p->A32, mode, cur, ev, nev);
 }
 
-int kernels_per_step(const Plan& P) { return 1 + (P.max_tail - 1) + 1; }
+int kernels_per_step(const Plan& P) {
+  return (P.pde == MODIL_PDE_NS3D ? 2 : 1) + (P.max_tail - 1) + 1;
+}
 
 modil_status read_terms(modil_problem* p, double* terms) {
   CUDA_TRY(cudaStreamSynchronize(p->stream));
@@ -525,7 +584,9 @@ modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t ar
   if (st != MODIL_OK) return bail(st);
   e = P.dtype == MODIL_F64 ? launch_reset<double>(p->A64, p->stream) : launch_reset<float>(p->A32, p->stream);
   if (e != cudaSuccess) return bail(fail(MODIL_ERR_CUDA, cudaGetErrorString(e)));
-  if (P.pde == MODIL_PDE_NS2D)
+  if (P.pde == MODIL_PDE_NS3D)
+    e = P.dtype == MODIL_F64 ? prepare_ns3d<double>(P.pyr_elems) : prepare_ns3d<float>(P.pyr_elems);
+  else if (P.pde == MODIL_PDE_NS2D)
     e = P.dtype == MODIL_F64 ? prepare_fine_ns2d<double>(P.cfg, P.pyr_elems)
                              : prepare_fine_ns2d<float>(P.cfg, P.pyr_elems);
   else
@@ -561,9 +622,13 @@ modil_status modil_level_shape(const modil_problem* p, int instance, int level, 
   const Plan& P = p->plan;
   if (instance < 0 || instance >= P.n_inst) return fail(MODIL_ERR_ARG, "instance out of range");
   if (level < 0 || level >= P.inst[instance].nlev) return fail(MODIL_ERR_ARG, "level out of range");
-  shape[0] = P.inst[instance].n[level][1];
-  shape[1] = P.inst[instance].n[level][2];
-  shape[2] = 0;
+  if (P.ndim == 3) {
+    for (int a = 0; a < 3; ++a) shape[a] = P.inst[instance].n[level][a];
+  } else {
+    shape[0] = P.inst[instance].n[level][1];
+    shape[1] = P.inst[instance].n[level][2];
+    shape[2] = 0;
+  }
   return MODIL_OK;
 }
 
@@ -731,7 +796,8 @@ modil_status modil_loss_bwd(modil_problem* p, const void* levels, double grad_ou
 modil_status modil_set_persistent(modil_problem* p, int on) {
   if (!p) return fail(MODIL_ERR_ARG, "problem is NULL");
   const Plan& P = p->plan;
-  if (P.pde == MODIL_PDE_NS2D && on) return fail(MODIL_ERR_UNSUPPORTED, "persistent launch: Burgers/heat only");
+  if ((P.pde == MODIL_PDE_NS2D || P.pde == MODIL_PDE_NS3D) && on)
+    return fail(MODIL_ERR_UNSUPPORTED, "persistent launch: Burgers/heat only");
   int grid = 0;
   if (on) {
     int dev = 0, sms = 0;
@@ -942,6 +1008,8 @@ extern "C" modil_status modil_eval_grad_noalloc(const modil_desc* desc, const vo
   Plan P;
   modil_status s = make_plan(desc, 1, P);
   if (s != MODIL_OK) return s;
+  if (P.pde == MODIL_PDE_NS3D)
+    return fail(MODIL_ERR_UNSUPPORTED, "the allocation-free entry point takes the 2-D families");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   return P.dtype == MODIL_F64 ? noalloc_run<double>(P, desc, levels, grads, terms, kgrad, st)
                               : noalloc_run<float>(P, desc, levels, grads, terms, kgrad, st);

@@ -224,3 +224,84 @@ def burgers_batch(n=512, base_seed=0, meas_frac=0.005):
         out.append(dict(shape=(nt, nx), n_levels=L, nu=nu, meas_cell=cells,
                         meas_value=field.reshape(-1)[cells], seed=seed))
     return out
+
+
+# --------------------------------------------------------------------------
+# Body shape in 3-D (Section 3.5): (z, y, x) cells of [0,1] x [0,1] x [0,2]
+# --------------------------------------------------------------------------
+
+NS3D_COEF = dict(Re=60.0, D=0.4, lam=1.0, tau=1.0)
+
+
+def ns3d_ellipsoid(seed):
+    """Seeded axis-aligned ellipsoid: centre (x, y, z) in [0.4, 0.6] x
+    [0.35, 0.65]^2, semi-axes in [0.1, 0.25]."""
+    rng = make_rng(seed)
+    centre = np.array([rng.uniform(0.4, 0.6), rng.uniform(0.35, 0.65), rng.uniform(0.35, 0.65)])
+    axes = rng.uniform(0.1, 0.25, size=3)
+    return centre, axes
+
+
+def ns3d_body_fraction(shape, centre, axes, sub=4):
+    """Volume fraction of the ellipsoid in each cell from sub^3 point samples
+    per cell (the reference body fraction chi_ref in [0, 1])."""
+    nz, ny, nx = shape
+    hz, hy, hx = 1.0 / nz, 1.0 / ny, 2.0 / nx
+    off = (np.arange(sub) + 0.5) / sub
+    z = ((np.arange(nz)[:, None] + off[None, :]) * hz).reshape(-1)
+    y = ((np.arange(ny)[:, None] + off[None, :]) * hy).reshape(-1)
+    x = ((np.arange(nx)[:, None] + off[None, :]) * hx).reshape(-1)
+    cx, cy, cz = centre
+    ax, ay, az = axes
+    inside = (((z[:, None, None] - cz) / az) ** 2 + ((y[None, :, None] - cy) / ay) ** 2
+              + ((x[None, None, :] - cx) / ax) ** 2) <= 1.0
+    return inside.reshape(nz, sub, ny, sub, nx, sub).mean(axis=(1, 3, 5))
+
+
+def ns3d_wake_velocity(z, y, x, centre, axes):
+    """Closed-form synthetic wake behind the body: a Gaussian velocity
+    deficit along x that widens downstream, small inward cross-flow."""
+    cx, cy, cz = centre
+    r0 = float(np.mean(axes[1:]))
+    s = r0 * (1.0 + 0.5 * np.maximum(x - cx, 0.0))
+    r2 = (y - cy) ** 2 + (z - cz) ** 2
+    deficit = 0.6 * (r0 / s) ** 2 * np.exp(-r2 / (s * s))
+    u = 1.0 - deficit
+    v = -0.1 * deficit * (y - cy) / s
+    w = -0.1 * deficit * (z - cz) / s
+    return u, v, w
+
+
+def ns3d_slab(shape, seed, centre, axes):
+    """Wake measurements on a 32 x 32 x 4 slab: y and z every (n/32)-th cell,
+    4 consecutive x planes from a seeded x in [1.2, 1.6]; u, v and w each.
+    Returns (cells, fields, values) with fields 0, 1, 2 = u, v, w."""
+    nz, ny, nx = shape
+    rng = make_rng(seed + 104729)
+    x0 = int(rng.uniform(1.2, 1.6) / (2.0 / nx))
+    x0 = min(x0, nx - 4)
+    sz, sy = max(1, nz // 32), max(1, ny // 32)
+    kz = np.arange(0, nz, sz)[:32]
+    ky = np.arange(0, ny, sy)[:32]
+    kx = np.arange(x0, x0 + 4)
+    K, J, I = np.meshgrid(kz, ky, kx, indexing="ij")
+    cell = ((K * ny + J) * nx + I).reshape(-1).astype(np.int32)
+    zc = (K.reshape(-1) + 0.5) / nz
+    yc = (J.reshape(-1) + 0.5) / ny
+    xc = (I.reshape(-1) + 0.5) * (2.0 / nx)
+    u, v, w = ns3d_wake_velocity(zc, yc, xc, centre, axes)
+    cells = np.concatenate([cell, cell, cell])
+    fields = np.repeat(np.arange(3, dtype=np.int32), len(cell))
+    return cells, fields, np.concatenate([u, v, w])
+
+
+def ns3d_workload(n=128, n_levels=8, seed=5):
+    """Body-shape inference on n^3 cells, 8 levels (128 -> 1), Re = 60,
+    D = 0.4, lambda = 1: a seeded ellipsoid and its 32 x 32 x 4 wake slab
+    (3 x 4096 velocity samples)."""
+    shape = (n, n, n)
+    centre, axes = ns3d_ellipsoid(seed)
+    cells, fields, vals = ns3d_slab(shape, seed, centre, axes)
+    return dict(shape=shape, n_levels=n_levels, meas_cell=cells, meas_field=fields,
+                meas_value=vals, centre=centre, axes=axes, coef=dict(NS3D_COEF),
+                w_res=1.0, w_data=1.0, lr=1e-3)

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libmodil.so")
 PDE_BURGERS = 1
 PDE_HEAT = 2
 PDE_NS2D = 3
+PDE_NS3D = 4
 F32 = 0
 F64 = 1
 NTERMS = 4
@@ -112,7 +113,8 @@ class Desc:
                            w_res=w_res, w_data=w_data, w_reg=w_reg, meas_cell=meas_cell,
                            meas_value=meas_value, meas_field=meas_field, aux=aux, knodes=knodes,
                            lr=lr, beta1=beta1, beta2=beta2, eps=eps, tile=tile)
-        self.pde = {"burgers": PDE_BURGERS, "heat": PDE_HEAT, "ns2d": PDE_NS2D}.get(pde, pde)
+        self.pde = {"burgers": PDE_BURGERS, "heat": PDE_HEAT, "ns2d": PDE_NS2D,
+                    "ns3d": PDE_NS3D}.get(pde, pde)
         self.dtype = {"f32": F32, "f64": F64}.get(dtype, dtype)
         self.shape = tuple(int(s) for s in shape)
         self.n_levels = int(n_levels)
@@ -147,7 +149,7 @@ class Desc:
 
     @property
     def n_fields(self):
-        return 3 if self.pde == PDE_NS2D else 1
+        return {PDE_NS2D: 3, PDE_NS3D: 5}.get(self.pde, 1)
 
 
 def _desc_array(descs):
@@ -212,7 +214,7 @@ class Problem:
     def level_shape(self, level, instance=0):
         s = (C.c_int * 3)()
         _check(LIB.modil_level_shape(self._h, instance, level, s))
-        return (s[0], s[1])
+        return (s[0], s[1], s[2]) if s[2] else (s[0], s[1])
 
     def n_levels(self, instance=0):
         return self.descs[instance].n_levels

@@ -17,20 +17,23 @@ def rnd(a, dtype):
 class Case:
     def __init__(self, pde, shape, L, dtype="f32", seed=0, n_meas=50, nu=0.01, w_res=1.0,
                  w_data=1.0, w_reg=0.0, lr=5e-3, tile=(0, 0), duplicate=0, n_knodes=32,
-                 fine_lo=None, fine_hi=None, coarse_scale=None, Re=100.0, tau=1.0):
+                 fine_lo=None, fine_hi=None, coarse_scale=None, Re=100.0, tau=1.0, D=0.4,
+                 lam=1.0, chi_shift=-5.0):
         self.pde, self.shape, self.L, self.dtype = pde, tuple(shape), L, dtype
         self.npd = np.float64 if dtype == "f64" else np.float32
-        nt, nx = shape
+        nx = shape[-1]
+        ncell = int(np.prod(shape))
         rng = np.random.default_rng(seed + 17)
-        n_meas = min(n_meas, nt * nx)
-        cells = inputs.measurement_cells(nt * nx, n_meas, seed)
+        n_meas = min(n_meas, ncell)
+        cells = inputs.measurement_cells(ncell, n_meas, seed)
         if duplicate:
             cells = np.concatenate([cells, cells[:duplicate]]).astype(np.int32)
         vals = rnd(rng.uniform(-0.5, 1.2, size=len(cells)), self.npd)
-        self.nf = 3 if pde == "ns2d" else 1
+        self.nf = {"ns2d": 3, "ns3d": 5}.get(pde, 1)
         mfield = None
-        if pde == "ns2d":
-            mfield = (rng.integers(0, 2, size=len(cells))).astype(np.int32)  # u or v samples
+        if pde in ("ns2d", "ns3d"):
+            # velocity samples: u or v (cavity), u, v or w (body)
+            mfield = (rng.integers(0, 2 if pde == "ns2d" else 3, size=len(cells))).astype(np.int32)
             vals = rnd(rng.normal(0.0, 0.3, size=len(cells)), self.npd)
         self.aux = None
         self.q = None
@@ -43,19 +46,24 @@ class Case:
         lo = lo if fine_lo is None else fine_lo
         hi = hi if fine_hi is None else fine_hi
         cs = cs if coarse_scale is None else coarse_scale
-        if pde == "ns2d":
+        if pde in ("ns2d", "ns3d"):
             lo, hi, cs = -0.5, 0.5, 0.2
             lo = lo if fine_lo is None else fine_lo
             hi = hi if fine_hi is None else fine_hi
             cs = cs if coarse_scale is None else coarse_scale
-            self.levels = inputs.random_levels(shape, L, 3, seed, lo, hi, cs, dtype=self.npd)
+            self.levels = inputs.random_levels(shape, L, self.nf, seed, lo, hi, cs, dtype=self.npd)
+            if pde == "ns3d":
+                # body-fraction logits around chihat = -5 (chi near 1/2) so that
+                # both the flow and the penalisation terms are exercised
+                self.levels[4][0] = rnd(self.levels[4][0] * 8.0 + chi_shift, self.npd)
         else:
             self.levels = inputs.random_levels(shape, L, 1, seed, lo, hi, cs, dtype=self.npd)[0]
-        coef = {"nu": nu} if pde == "burgers" else ({"Re": Re, "tau": tau} if pde == "ns2d" else {})
+        coef = {"burgers": {"nu": nu}, "ns2d": {"Re": Re, "tau": tau},
+                "ns3d": {"Re": Re, "D": D, "lam": lam, "tau": tau}}.get(pde, {})
         self.oracle = o.Problem(pde, self.shape, L, coef=coef, w_res=w_res, w_data=w_data,
                                 w_reg=w_reg, meas_cell=cells, meas_value=vals, aux=self.aux,
                                 meas_field=mfield)
-        dcoef = (nu,) if pde == "burgers" else ((Re, tau) if pde == "ns2d" else ())
+        dcoef = {"burgers": (nu,), "ns2d": (Re, tau), "ns3d": (Re, D, lam, tau)}.get(pde, ())
         self.desc_kw = dict(pde=pde, shape=self.shape, n_levels=L, dtype=dtype,
                             coef=dcoef, w_res=w_res, w_data=w_data,
                             w_reg=w_reg, meas_cell=cells, meas_value=vals, meas_field=mfield,

@@ -79,3 +79,31 @@ def test_rejects_bad_measurements_and_mixed_batches(mod):
         mod.arena_bytes([mod.Desc("heat", (16, 16), 2)])  # no initial profile / nodes
     with pytest.raises(mod.ModilError):
         mod.arena_bytes([mod.Desc("burgers", (16, 16), 2, tile=(7, 7))])
+
+
+def _body(mod, shape=(16, 16, 32), L=3, **kw):
+    return mod.Desc("ns3d", shape, L, coef=(60.0, 0.4, 1.0, 1.0), **kw)
+
+
+def test_ns3d_arena_bytes_and_validation(mod):
+    a = mod.arena_bytes([_body(mod)])
+    # five fields; p0, p1, m, g (4 B) + v (8 B) per parameter, plus the composed fields
+    P = sum((16 >> l) * (16 >> l) * (32 >> l) for l in range(3))
+    assert a >= 5 * (24 * P + 4 * 16 * 16 * 32)
+    # measurement cells index the flat (z, y, x) grid and fields 0..4
+    ok = _body(mod, meas_cell=[0, 16 * 16 * 32 - 1], meas_value=[1.0, 2.0], meas_field=[0, 4])
+    assert mod.arena_bytes([ok]) > 0
+    for bad in (dict(meas_cell=[16 * 16 * 32], meas_value=[1.0]),
+                dict(meas_cell=[0], meas_value=[1.0], meas_field=[5])):
+        with pytest.raises(mod.ModilError):
+            mod.arena_bytes([_body(mod, **bad)])
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([_body(mod, shape=(16, 32))])            # 3-D family, ndim 2
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([mod.Desc("ns2d", (8, 8, 8), 2, coef=(100.0, 1.0))])  # 2-D family, ndim 3
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([_body(mod, tile=(8, 32))])
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([mod.Desc("ns3d", (16, 16, 32), 3, coef=(0.0, 0.4, 1.0, 1.0))])
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([_body(mod, shape=(12, 16, 32), L=4)])  # 12 not divisible by 8
