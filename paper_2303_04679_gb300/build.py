@@ -76,11 +76,13 @@ def build(force=False, verbose=False):
 
 
 
-def source_hash():
-    """SHA-256 (first 16 hex digits) of the CUDA sources and the public header."""
+def source_hash(names=None):
+    """SHA-256 (first 16 hex digits) of the CUDA sources and the public header,
+    or of the files of csrc/ listed in names (the sources one kernel is built from)."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(_deps()):
+    files = _deps() if names is None else [os.path.join(CSRC, n) for n in names]
+    for f in sorted(files):
         if os.path.isfile(f):
             h.update(os.path.basename(f).encode())
             h.update(open(f, "rb").read())
