@@ -20,7 +20,8 @@ LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libmodil.so")
 
-SOURCES = ["modil_api.cu", "kernels_st.cu", "kernels_ns2d.cu", "kernels_ns3d.cu", "kernels_common.cu"]
+SOURCES = ["modil_api.cu", "kernels_st.cu", "kernels_ns2d.cu", "kernels_ns3d.cu", "kernels_common.cu",
+           "tc_gemm.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]
@@ -36,6 +37,7 @@ def nvcc():
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     files.append(os.path.join(INCLUDE, "modil.h"))
+    files.append(os.path.join(INCLUDE, "modil_unet.h"))
     return files
 
 

@@ -28,6 +28,18 @@ modil_status fail(modil_status s, const std::string& msg) {
   return s;
 }
 
+}  // namespace
+
+namespace modil {
+// Shared with the other translation units of the library (learned warm start).
+int set_last_error(int status, const std::string& msg) {
+  g_err = msg;
+  return status;
+}
+}  // namespace modil
+
+namespace {
+
 #define CUDA_TRY(expr)                                                              \
   do {                                                                              \
     cudaError_t e_ = (expr);                                                        \

@@ -1,0 +1,848 @@
+// Learned warm start: a 3-D convolutional U-Net trained and evaluated by this
+// library's kernels.  Every convolution is an im2col GEMM on the tensor cores
+// (tc_gemm.cu); the rest (im2col and its transpose, col2im, pooling,
+// upsampling, masks, loss, bias gradients, Adam) are the small streaming
+// kernels below.  Network, arithmetic and layouts: include/modil_unet.h.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "modil.h"
+#include "modil_unet.h"
+#include "tc_gemm.h"
+
+namespace modil {
+int set_last_error(int status, const std::string& msg);
+}
+
+using bf16 = __nv_bfloat16;
+using modil_tc::GemmArgs;
+
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kInPad = 8;    // input channels padded to one 16-byte vector
+constexpr int kHeadPad = 16; // output channels padded to the smallest MMA N
+
+modil_status fail(modil_status s, const std::string& m) { return (modil_status)modil::set_last_error(s, m); }
+
+#define UCUDA(expr)                                                                     \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess) return fail(MODIL_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+inline unsigned blocks(long long n, int nt = kNT) { return (unsigned)((n + nt - 1) / nt); }
+
+// tap t in 0..26 -> offsets (dz, dy, dx) in {-1, 0, 1}, lexicographic
+__device__ __forceinline__ void tap_off(int t, int& dz, int& dy, int& dx) {
+  dz = t / 9 - 1;
+  dy = (t / 3) % 3 - 1;
+  dx = t % 3 - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Streaming kernels
+// ---------------------------------------------------------------------------
+__global__ void k_input_pad(const float* __restrict__ in, int in_ch, long long M, bf16* __restrict__ out) {
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= M) return;
+  __align__(16) bf16 h[kInPad];
+#pragma unroll
+  for (int c = 0; c < kInPad; ++c) h[c] = __float2bfloat16_rn(c < in_ch ? in[v * in_ch + c] : 0.f);
+  reinterpret_cast<uint4*>(out)[v] = *reinterpret_cast<uint4*>(h);
+}
+
+// col[v][t*C + c] = X[v + off_t][c] (zero outside the sample's grid); 8 channels per thread
+__global__ void k_im2col(const bf16* __restrict__ X, int C, int S, long long M, bf16* __restrict__ col) {
+  const int C8 = C >> 3;
+  const long long n = M * 27 * C8;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c8 = (int)(i % C8);
+    const long long r = i / C8;
+    const int t = (int)(r % 27);
+    const long long v = r / 27;
+    const int x = (int)(v % S), y = (int)((v / S) % S), z = (int)((v / ((long long)S * S)) % S);
+    int dz, dy, dx;
+    tap_off(t, dz, dy, dx);
+    const int zz = z + dz, yy = y + dy, xx = x + dx;
+    uint4 val = make_uint4(0, 0, 0, 0);
+    if (zz >= 0 && zz < S && yy >= 0 && yy < S && xx >= 0 && xx < S) {
+      const long long u = v + ((long long)dz * S + dy) * S + dx;
+      val = reinterpret_cast<const uint4*>(X + u * C)[c8];
+    }
+    reinterpret_cast<uint4*>(col + v * (27LL * C) + (long long)t * C)[c8] = val;
+  }
+}
+
+// Y[c][r] = X[r][c] for an R x Cc matrix (32 x 32 tiles); Y rows have pitch ldy >= R
+__global__ void k_transpose(const bf16* __restrict__ X, long long R, int Cc, bf16* __restrict__ Y, long long ldy) {
+  __shared__ bf16 tile[32][33];
+  const long long r0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const long long r = r0 + j;
+    const int c = c0 + threadIdx.x;
+    tile[j][threadIdx.x] = (r < R && c < Cc) ? X[r * Cc + c] : __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int c = c0 + j;
+    const long long r = r0 + threadIdx.x;
+    if (c < Cc && r < R) Y[(long long)c * ldy + r] = tile[threadIdx.x][j];
+  }
+}
+
+// colT[t*C + c][v] = XT[c][v + off_t] (zero outside the grid); rows of pitch ld >= M
+__global__ void k_shift_t(const bf16* __restrict__ XT, int C, int S, long long M, long long ld,
+                          bf16* __restrict__ colT) {
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;  // t * C + c
+  if (v >= M) return;
+  const int t = k / C, c = k - t * C;
+  const int x = (int)(v % S), y = (int)((v / S) % S), z = (int)((v / ((long long)S * S)) % S);
+  int dz, dy, dx;
+  tap_off(t, dz, dy, dx);
+  const int zz = z + dz, yy = y + dy, xx = x + dx;
+  bf16 val = __float2bfloat16_rn(0.f);
+  if (zz >= 0 && zz < S && yy >= 0 && yy < S && xx >= 0 && xx < S)
+    val = XT[(long long)c * ld + v + ((long long)dz * S + dy) * S + dx];
+  colT[(long long)k * ld + v] = val;
+}
+
+// s[v][c] = sum_t dcol[v - off_t][t*C + c]; out: FP32 s, or BF16 of s masked by act > 0
+__global__ void k_col2im(const float* __restrict__ dcol, int C, int S, long long M, float* __restrict__ out_f32,
+                         const bf16* __restrict__ act, bf16* __restrict__ out_bf16) {
+  const long long n = M * C;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long long v = i / C;
+    const int x = (int)(v % S), y = (int)((v / S) % S), z = (int)((v / ((long long)S * S)) % S);
+    float s = 0.f;
+#pragma unroll 1
+    for (int t = 0; t < 27; ++t) {
+      int dz, dy, dx;
+      tap_off(t, dz, dy, dx);
+      const int zz = z - dz, yy = y - dy, xx = x - dx;
+      if (zz >= 0 && zz < S && yy >= 0 && yy < S && xx >= 0 && xx < S) {
+        const long long u = v - (((long long)dz * S + dy) * S + dx);
+        s += dcol[u * (27LL * C) + (long long)t * C + c];
+      }
+    }
+    if (out_f32) out_f32[i] = s;
+    else out_bf16[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.f ? s : 0.f);
+  }
+}
+
+// 2x2x2 average: Y at grid S/2 from X at grid S
+__global__ void k_pool(const bf16* __restrict__ X, int C, int S, long long Mc, bf16* __restrict__ Y) {
+  const int Sc = S / 2;
+  const long long n = Mc * C;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long long w = i / C;
+    const int x = (int)(w % Sc), y = (int)((w / Sc) % Sc), z = (int)((w / ((long long)Sc * Sc)) % Sc);
+    const long long b = w / ((long long)Sc * Sc * Sc);
+    float s = 0.f;
+    for (int k = 0; k < 8; ++k) {
+      const long long u = ((b * S + 2 * z + (k >> 2)) * S + 2 * y + ((k >> 1) & 1)) * S + 2 * x + (k & 1);
+      s += __bfloat162float(X[u * C + c]);
+    }
+    Y[i] = __float2bfloat16_rn(s * 0.125f);
+  }
+}
+
+// U[v] = (up(Dc)[v], E[v]): nearest-neighbour upsampling of the coarse level, then the skip
+__global__ void k_up_concat(const bf16* __restrict__ Dc, int C1, const bf16* __restrict__ E, int C2, int S,
+                            long long M, bf16* __restrict__ U) {
+  const int C = C1 + C2, Sc = S / 2;
+  const long long n = M * C;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long long v = i / C;
+    if (c < C1) {
+      const int x = (int)(v % S), y = (int)((v / S) % S), z = (int)((v / ((long long)S * S)) % S);
+      const long long b = v / ((long long)S * S * S);
+      const long long w = ((b * Sc + z / 2) * Sc + y / 2) * Sc + x / 2;
+      U[i] = Dc[w * C1 + c];
+    } else {
+      U[i] = E[v * C2 + (c - C1)];
+    }
+  }
+}
+
+// out[w][c] = BF16(act[w][c] > 0 ? sum of the 8 fine children gU[child][c] : 0)  (coarse w)
+__global__ void k_up_bwd_mask(const float* __restrict__ gU, int ldu, int C1, int S, long long Mc,
+                              const bf16* __restrict__ act, bf16* __restrict__ out) {
+  const int Sc = S / 2;
+  const long long n = Mc * C1;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C1);
+    const long long w = i / C1;
+    const int x = (int)(w % Sc), y = (int)((w / Sc) % Sc), z = (int)((w / ((long long)Sc * Sc)) % Sc);
+    const long long b = w / ((long long)Sc * Sc * Sc);
+    float s = 0.f;
+    for (int k = 0; k < 8; ++k) {
+      const long long u = ((b * S + 2 * z + (k >> 2)) * S + 2 * y + ((k >> 1) & 1)) * S + 2 * x + (k & 1);
+      s += gU[u * ldu + c];
+    }
+    out[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.f ? s : 0.f);
+  }
+}
+
+// Encoder output gradient: skip part of the decoder's concat gradient plus the
+// pooling adjoint of the next level's input gradient, masked by the ReLU.
+__global__ void k_enc_grad(const float* __restrict__ gU, int ldu, int uoff, const float* __restrict__ gin,
+                           int C, int S, long long M, const bf16* __restrict__ act, bf16* __restrict__ out) {
+  const int Sc = S / 2;
+  const long long n = M * C;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long long v = i / C;
+    float s = gU[v * ldu + uoff + c];
+    if (gin) {
+      const int x = (int)(v % S), y = (int)((v / S) % S), z = (int)((v / ((long long)S * S)) % S);
+      const long long b = v / ((long long)S * S * S);
+      const long long w = ((b * Sc + z / 2) * Sc + y / 2) * Sc + x / 2;
+      s += gin[w * C + c] * 0.125f;
+    }
+    out[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.f ? s : 0.f);
+  }
+}
+
+__global__ void k_mask_f32(const float* __restrict__ a, int lda, int C, long long M, const bf16* __restrict__ act,
+                           bf16* __restrict__ out) {
+  const long long n = M * C;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C);
+    const long long v = i / C;
+    out[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.f ? a[v * lda + c] : 0.f);
+  }
+}
+
+// Head output: copy to the caller, loss partial sums, dL/dout in BF16
+__global__ void k_head_loss(const float* __restrict__ outp, int oc, long long M, const float* __restrict__ target,
+                            float scale, float* __restrict__ user_out, bf16* __restrict__ dout,
+                            double* __restrict__ loss) {
+  const long long n = M * kHeadPad;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int o = (int)(i % kHeadPad);
+    const long long v = i / kHeadPad;
+    float g = 0.f;
+    if (o < oc) {
+      const float y = outp[i];
+      if (user_out) user_out[v * oc + o] = y;
+      if (target) {
+        const float d = y - target[v * oc + o];
+        acc += (double)d * (double)d;
+        g = scale * d;
+      }
+    }
+    if (dout) dout[i] = __float2bfloat16_rn(g);
+  }
+  if (!loss) return;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+}
+
+// db[c] += sum over rows of g[r][c]
+__global__ void k_bias_grad(const bf16* __restrict__ g, long long M, int C, float* __restrict__ db) {
+  const int groups = max(1, kNT / C);
+  const int c = threadIdx.x % C, grp = threadIdx.x / C;
+  if (grp >= groups || threadIdx.x >= groups * C) return;
+  const long long r0 = (long long)blockIdx.x * 1024;
+  const long long r1 = min(M, r0 + 1024);
+  for (int cc = c; cc < C; cc += kNT) {
+    float s = 0.f;
+    for (long long r = r0 + grp; r < r1; r += groups) s += __bfloat162float(g[r * C + cc]);
+    atomicAdd(db + cc, s);
+    if (C <= kNT) break;
+  }
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+}
+
+// BF16 operand copies of a master weight Wm [K][co] (FP32): Wf [co][K] for the
+// forward pass, Wb [K][co] for the input gradient.
+__global__ void k_refresh(const float* __restrict__ Wm, int K, int co, bf16* __restrict__ Wf, bf16* __restrict__ Wb) {
+  const long long n = (long long)K * co;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int o = (int)(i % co);
+  const long long k = i / co;
+  const bf16 h = __float2bfloat16_rn(Wm[i]);
+  Wb[i] = h;
+  Wf[(long long)o * K + k] = h;
+}
+
+// ---------------------------------------------------------------------------
+// Network
+// ---------------------------------------------------------------------------
+struct Conv {
+  int S = 0, cin = 0, cout = 0, taps = 27, K = 0, co = 0;  // co: padded output channels
+  float *Wm = nullptr, *bm = nullptr, *dW = nullptr, *db = nullptr;
+  float *mW = nullptr, *vW = nullptr, *mb = nullptr, *vb = nullptr;
+  bf16 *Wf = nullptr, *Wb = nullptr;
+};
+
+template <class T>
+T* dalloc(std::vector<void*>& pool, size_t n) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+  pool.push_back(p);
+  return static_cast<T*>(p);
+}
+
+}  // namespace
+
+struct modil_unet {
+  modil_unet_desc d{};
+  cudaStream_t s = nullptr;
+  std::vector<void*> pool;
+  int L = 4;
+  std::vector<int> S, c;          // per level
+  std::vector<long long> M;       // voxels per level (batch included)
+  std::vector<Conv> enc_a, enc_b, dec_c, dec_d;  // per level
+  Conv head;
+  // activations
+  bf16* x0 = nullptr;
+  std::vector<bf16*> a, e, p, u, b, dd;  // p[l]: pooled input of level l (l >= 1)
+  float* out = nullptr;                    // [M0][16]
+  bf16* dout = nullptr;
+  // backward
+  std::vector<float*> gU;   // decoder concat gradients (FP32) per level
+  std::vector<float*> gin;  // encoder input gradients (FP32) per level (l >= 1)
+  bf16 *g1 = nullptr, *g2 = nullptr;  // masked pre-activation gradients (BF16), ping-pong
+  float* ghead = nullptr;            // head input gradient (FP32)
+  // scratch
+  bf16 *col = nullptr, *colT = nullptr, *xt = nullptr, *gt = nullptr;
+  float* dcol = nullptr;
+  double* loss = nullptr;
+  int* err = nullptr;
+  long long step = 0;
+  std::vector<Conv*> convs;  // parameter order
+  // profiling
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+};
+
+namespace {
+
+modil_status rec(modil_unet* n) {
+  if (!n->prof) return MODIL_OK;
+  cudaEvent_t e;
+  UCUDA(cudaEventCreate(&e));
+  UCUDA(cudaEventRecord(e, n->s));
+  n->ev.push_back(e);
+  return MODIL_OK;
+}
+
+int pick_bn(int N) {
+  if (N <= 16) return 16;
+  if (N <= 32) return 32;
+  if (N <= 64) return 64;
+  if (N <= 128) return 128;
+  return 256;
+}
+
+modil_status gemm(modil_unet* n, const bf16* A, long long lda, const bf16* B, long long ldb, void* D, long long ldd,
+                  int M, int N, int K, int mode, int relu, const float* bias, bool split) {
+  CUtensorMap ta, tb;
+  const int bn = pick_bn(N);
+  if (modil_tc::make_kmajor_map(&ta, A, M, K, lda, 128) != 0 || modil_tc::make_kmajor_map(&tb, B, N, K, ldb, bn) != 0)
+    return fail(MODIL_ERR_ARG, "tensor map: operand not 16-byte aligned or pitch not a multiple of 8");
+  GemmArgs g{};
+  g.M = M; g.N = N; g.K = K; g.mode = mode; g.relu = relu; g.bias = bias; g.D = D; g.ldd = (int)ldd; g.err = n->err;
+  const int nk = (K + 63) / 64;
+  int splits = 1;
+  if (split) {
+    const long long tiles = (long long)((M + 127) / 128) * ((N + bn - 1) / bn);
+    splits = (int)std::min<long long>(nk, std::max<long long>(1, (2 * 152 + tiles - 1) / tiles));
+  }
+  g.kchunks = (nk + splits - 1) / splits;
+  splits = (nk + g.kchunks - 1) / g.kchunks;
+  UCUDA(modil_tc::launch_gemm(ta, tb, g, bn, splits, n->s));
+  return rec(n);
+}
+
+unsigned gs(long long n) { return (unsigned)std::min<long long>((n + kNT - 1) / kNT, 152LL * 16); }
+
+modil_status conv_fwd(modil_unet* n, Conv& cv, const bf16* X, long long M, bf16* Y) {
+  k_im2col<<<gs(M * 27 * (cv.cin / 8)), kNT, 0, n->s>>>(X, cv.cin, cv.S, M, n->col);
+  UCUDA(cudaGetLastError());
+  modil_status st = rec(n);
+  if (st) return st;
+  return gemm(n, n->col, cv.K, cv.Wf, cv.K, Y, cv.cout, (int)M, cv.cout, cv.K, modil_tc::GEMM_STORE_BF16, 1, cv.bm,
+              false);
+}
+
+// Weight and bias gradients of a 3x3x3 convolution from its input X and the
+// masked pre-activation gradient g; with dx_f32 / (act, dx_bf16) also the
+// input gradient (FP32, or BF16 masked by act > 0).
+modil_status conv_bwd(modil_unet* n, Conv& cv, const bf16* X, long long M, const bf16* g, float* dx_f32,
+                      const bf16* act, bf16* dx_bf16) {
+  modil_status st;
+  k_bias_grad<<<blocks(M, 1024), kNT, 0, n->s>>>(g, M, cv.cout, cv.db);
+  UCUDA(cudaGetLastError());
+  if ((st = rec(n))) return st;
+  // voxel-major operands of the weight gradient; row pitch padded to 8 for TMA
+  const long long Mp = (M + 7) & ~7LL;
+  dim3 tb(32, 8);
+  k_transpose<<<dim3((unsigned)((M + 31) / 32), (cv.cout + 31) / 32), tb, 0, n->s>>>(g, M, cv.cout, n->gt, Mp);
+  UCUDA(cudaGetLastError());
+  k_transpose<<<dim3((unsigned)((M + 31) / 32), (cv.cin + 31) / 32), tb, 0, n->s>>>(X, M, cv.cin, n->xt, Mp);
+  UCUDA(cudaGetLastError());
+  k_shift_t<<<dim3(blocks(M), cv.K), kNT, 0, n->s>>>(n->xt, cv.cin, cv.S, M, Mp, n->colT);
+  UCUDA(cudaGetLastError());
+  if ((st = rec(n))) return st;
+  if ((st = gemm(n, n->colT, Mp, n->gt, Mp, cv.dW, cv.co, cv.K, cv.cout, (int)M, modil_tc::GEMM_ATOMIC_F32, 0,
+                 nullptr, true)))
+    return st;
+  if (!dx_f32 && !dx_bf16) return MODIL_OK;
+  if ((st = gemm(n, g, cv.cout, cv.Wb, cv.co, n->dcol, cv.K, (int)M, cv.K, cv.cout, modil_tc::GEMM_STORE_F32, 0,
+                 nullptr, false)))
+    return st;
+  k_col2im<<<gs(M * cv.cin), kNT, 0, n->s>>>(n->dcol, cv.cin, cv.S, M, dx_f32, act, dx_bf16);
+  UCUDA(cudaGetLastError());
+  return rec(n);
+}
+
+modil_status forward(modil_unet* n, const float* input) {
+  modil_status st;
+  const int L = n->L;
+  k_input_pad<<<blocks(n->M[0]), kNT, 0, n->s>>>(input, n->d.in_ch, n->M[0], n->x0);
+  UCUDA(cudaGetLastError());
+  if ((st = rec(n))) return st;
+  for (int l = 0; l < L; ++l) {
+    const bf16* in = l == 0 ? n->x0 : n->p[l];
+    if (l > 0) {
+      k_pool<<<gs(n->M[l] * n->c[l - 1]), kNT, 0, n->s>>>(n->e[l - 1], n->c[l - 1], n->S[l - 1], n->M[l], n->p[l]);
+      UCUDA(cudaGetLastError());
+      if ((st = rec(n))) return st;
+    }
+    if ((st = conv_fwd(n, n->enc_a[l], in, n->M[l], n->a[l]))) return st;
+    if ((st = conv_fwd(n, n->enc_b[l], n->a[l], n->M[l], n->e[l]))) return st;
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    const bf16* below = (l == L - 2) ? n->e[L - 1] : n->dd[l + 1];
+    k_up_concat<<<gs(n->M[l] * (n->c[l + 1] + n->c[l])), kNT, 0, n->s>>>(below, n->c[l + 1], n->e[l], n->c[l],
+                                                                          n->S[l], n->M[l], n->u[l]);
+    UCUDA(cudaGetLastError());
+    if ((st = rec(n))) return st;
+    if ((st = conv_fwd(n, n->dec_c[l], n->u[l], n->M[l], n->b[l]))) return st;
+    if ((st = conv_fwd(n, n->dec_d[l], n->b[l], n->M[l], n->dd[l]))) return st;
+  }
+  // 1x1x1 head: out[v][0..16) = d0[v] . Wf^T + bias (FP32)
+  return gemm(n, n->dd[0], n->c[0], n->head.Wf, n->c[0], n->out, kHeadPad, (int)n->M[0], kHeadPad, n->c[0],
+              modil_tc::GEMM_STORE_F32, 0, n->head.bm, false);
+}
+
+modil_status backward(modil_unet* n) {
+  modil_status st;
+  const int L = n->L;
+  const long long M0 = n->M[0];
+  // head
+  k_bias_grad<<<blocks(M0, 1024), kNT, 0, n->s>>>(n->dout, M0, kHeadPad, n->head.db);
+  UCUDA(cudaGetLastError());
+  dim3 tb(32, 8);
+  k_transpose<<<dim3((unsigned)((M0 + 31) / 32), 1), tb, 0, n->s>>>(n->dout, M0, kHeadPad, n->gt, M0);
+  UCUDA(cudaGetLastError());
+  k_transpose<<<dim3((unsigned)((M0 + 31) / 32), (n->c[0] + 31) / 32), tb, 0, n->s>>>(n->dd[0], M0, n->c[0], n->xt,
+                                                                                       M0);
+  UCUDA(cudaGetLastError());
+  if ((st = rec(n))) return st;
+  if ((st = gemm(n, n->xt, M0, n->gt, M0, n->head.dW, kHeadPad, n->c[0], kHeadPad, (int)M0, modil_tc::GEMM_ATOMIC_F32,
+                 0, nullptr, true)))
+    return st;
+  if ((st = gemm(n, n->dout, kHeadPad, n->head.Wb, kHeadPad, n->ghead, n->c[0], (int)M0, n->c[0], kHeadPad,
+                 modil_tc::GEMM_STORE_F32, 0, nullptr, false)))
+    return st;
+  k_mask_f32<<<gs(M0 * n->c[0]), kNT, 0, n->s>>>(n->ghead, n->c[0], n->c[0], M0, n->dd[0], n->g1);
+  UCUDA(cudaGetLastError());
+  if ((st = rec(n))) return st;
+  // decoder, level 0 up: g1 holds the masked gradient of d_l
+  for (int l = 0; l <= L - 2; ++l) {
+    Conv& cd = n->dec_d[l];
+    Conv& cc = n->dec_c[l];
+    if ((st = conv_bwd(n, cd, n->b[l], n->M[l], n->g1, nullptr, n->b[l], n->g2))) return st;
+    if ((st = conv_bwd(n, cc, n->u[l], n->M[l], n->g2, n->gU[l], nullptr, nullptr))) return st;
+    // gradient of the level below's output (d_{l+1}, or e_{L-1} at the bottom)
+    const bf16* act = (l == L - 2) ? n->e[L - 1] : n->dd[l + 1];
+    k_up_bwd_mask<<<gs(n->M[l + 1] * n->c[l + 1]), kNT, 0, n->s>>>(n->gU[l], n->c[l + 1] + n->c[l], n->c[l + 1],
+                                                                    n->S[l], n->M[l + 1], act, n->g1);
+    UCUDA(cudaGetLastError());
+    if ((st = rec(n))) return st;
+  }
+  // encoder, bottom up: g1 holds the masked gradient of e_l
+  for (int l = L - 1; l >= 0; --l) {
+    if (l < L - 1) {
+      k_enc_grad<<<gs(n->M[l] * n->c[l]), kNT, 0, n->s>>>(n->gU[l], n->c[l + 1] + n->c[l], n->c[l + 1], n->gin[l + 1],
+                                                          n->c[l], n->S[l], n->M[l], n->e[l], n->g1);
+      UCUDA(cudaGetLastError());
+      if ((st = rec(n))) return st;
+    }
+    Conv& cb = n->enc_b[l];
+    Conv& ca = n->enc_a[l];
+    if ((st = conv_bwd(n, cb, n->a[l], n->M[l], n->g1, nullptr, n->a[l], n->g2))) return st;
+    const bf16* in = l == 0 ? n->x0 : n->p[l];
+    if ((st = conv_bwd(n, ca, in, n->M[l], n->g2, l > 0 ? n->gin[l] : nullptr, nullptr, nullptr))) return st;
+  }
+  return MODIL_OK;
+}
+
+modil_status zero_grads(modil_unet* n) {
+  for (Conv* cv : n->convs) {
+    UCUDA(cudaMemsetAsync(cv->dW, 0, sizeof(float) * (size_t)cv->K * cv->co, n->s));
+    UCUDA(cudaMemsetAsync(cv->db, 0, sizeof(float) * cv->co, n->s));
+  }
+  UCUDA(cudaMemsetAsync(n->loss, 0, sizeof(double), n->s));
+  return MODIL_OK;
+}
+
+modil_status refresh(modil_unet* n, Conv& cv) {
+  const long long e = (long long)cv.K * cv.co;
+  k_refresh<<<blocks(e), kNT, 0, n->s>>>(cv.Wm, cv.K, cv.co, cv.Wf, cv.Wb);
+  UCUDA(cudaGetLastError());
+  return MODIL_OK;
+}
+
+modil_status eval_grad(modil_unet* n, const float* input, const float* target, double* loss) {
+  modil_status st;
+  if ((st = zero_grads(n))) return st;
+  if ((st = forward(n, input))) return st;
+  const long long M0 = n->M[0];
+  const float scale = 2.f / (float)((double)M0 * n->d.out_ch);
+  k_head_loss<<<gs(M0 * kHeadPad), kNT, 0, n->s>>>(n->out, n->d.out_ch, M0, target, scale, nullptr, n->dout, n->loss);
+  UCUDA(cudaGetLastError());
+  if ((st = rec(n))) return st;
+  if ((st = backward(n))) return st;
+  if (loss) {
+    double l = 0;
+    int e = 0;
+    UCUDA(cudaMemcpyAsync(&l, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->s));
+    UCUDA(cudaMemcpyAsync(&e, n->err, sizeof(int), cudaMemcpyDeviceToHost, n->s));
+    UCUDA(cudaStreamSynchronize(n->s));
+    if (e) return fail(MODIL_ERR_CUDA, "tensor-core GEMM wait timed out (code " + std::to_string(e) + ")");
+    *loss = l / ((double)M0 * n->d.out_ch);
+  }
+  return MODIL_OK;
+}
+
+modil_status adam(modil_unet* n) {
+  n->step += 1;
+  const double b1 = n->d.adam_beta1, b2 = n->d.adam_beta2;
+  const float c1 = (float)(1.0 / (1.0 - std::pow(b1, (double)n->step)));
+  const float c2 = (float)(1.0 / (1.0 - std::pow(b2, (double)n->step)));
+  for (Conv* cv : n->convs) {
+    const long long nw = (long long)cv->K * cv->co;
+    k_adam<<<blocks(nw), kNT, 0, n->s>>>(cv->Wm, cv->dW, cv->mW, cv->vW, nw, (float)n->d.adam_lr, (float)b1,
+                                         (float)b2, (float)n->d.adam_eps, c1, c2);
+    k_adam<<<blocks(cv->co), kNT, 0, n->s>>>(cv->bm, cv->db, cv->mb, cv->vb, cv->co, (float)n->d.adam_lr,
+                                             (float)b1, (float)b2, (float)n->d.adam_eps, c1, c2);
+    UCUDA(cudaGetLastError());
+    modil_status st = refresh(n, *cv);
+    if (st) return st;
+  }
+  return rec(n);
+}
+
+Conv make_conv(modil_unet* n, int S, int cin, int cout, int taps, int copad) {
+  Conv cv;
+  cv.S = S; cv.cin = cin; cv.cout = cout; cv.taps = taps; cv.K = taps * cin; cv.co = copad;
+  const size_t nw = (size_t)cv.K * cv.co;
+  cv.Wm = dalloc<float>(n->pool, nw);
+  cv.dW = dalloc<float>(n->pool, nw);
+  cv.mW = dalloc<float>(n->pool, nw);
+  cv.vW = dalloc<float>(n->pool, nw);
+  cv.bm = dalloc<float>(n->pool, cv.co);
+  cv.db = dalloc<float>(n->pool, cv.co);
+  cv.mb = dalloc<float>(n->pool, cv.co);
+  cv.vb = dalloc<float>(n->pool, cv.co);
+  cv.Wf = dalloc<bf16>(n->pool, nw);
+  cv.Wb = dalloc<bf16>(n->pool, nw);
+  return cv;
+}
+
+bool conv_ok(const Conv& c) {
+  return c.Wm && c.dW && c.mW && c.vW && c.bm && c.db && c.mb && c.vb && c.Wf && c.Wb;
+}
+
+modil_status param_check(const modil_unet* n, int i, size_t count, int* kind, Conv** cv) {
+  if (!n) return fail(MODIL_ERR_ARG, "net is NULL");
+  if (i < 0 || i >= 2 * (int)n->convs.size()) return fail(MODIL_ERR_ARG, "parameter index out of range");
+  Conv* c = n->convs[i / 2];
+  *kind = i % 2;
+  *cv = c;
+  const size_t need = *kind ? (size_t)c->cout : (size_t)c->cout * c->taps * c->cin;
+  if (count != need) return fail(MODIL_ERR_ARG, "element count does not match the parameter");
+  return MODIL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+modil_status modil_unet_create(const modil_unet_desc* d, void* stream, modil_unet** out) {
+  if (!d || !out) return fail(MODIL_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (d->levels < 2 || d->levels > 5) return fail(MODIL_ERR_ARG, "levels must be 2..5");
+  if (d->in_ch < 1 || d->in_ch > kInPad) return fail(MODIL_ERR_ARG, "in_ch must be 1..8");
+  if (d->out_ch < 1 || d->out_ch > kHeadPad) return fail(MODIL_ERR_ARG, "out_ch must be 1..16");
+  if (d->base_ch < 8 || d->base_ch > 64 || d->base_ch % 8) return fail(MODIL_ERR_ARG, "base_ch must be 8..64, a multiple of 8");
+  if (d->batch < 1) return fail(MODIL_ERR_ARG, "batch must be >= 1");
+  if (d->side < (1 << (d->levels - 1)) || d->side % (1 << (d->levels - 1)))
+    return fail(MODIL_ERR_ARG, "side must be a multiple of 2^(levels-1)");
+  const long long M0 = (long long)d->batch * d->side * d->side * d->side;
+  if (M0 % 8 || M0 > (1LL << 31) / 64) return fail(MODIL_ERR_ARG, "grid too small or too large");
+  modil_unet* n = new modil_unet();
+  n->d = *d;
+  n->s = static_cast<cudaStream_t>(stream);
+  n->L = d->levels;
+  const int L = n->L;
+  for (int l = 0; l < L; ++l) {
+    n->S.push_back(d->side >> l);
+    n->c.push_back(d->base_ch << l);
+    n->M.push_back((long long)d->batch * (d->side >> l) * (d->side >> l) * (d->side >> l));
+  }
+  auto& P = n->pool;
+  size_t col = 0, dcol = 0, xt = 0, gt = (size_t)M0 * kHeadPad;
+  auto need = [&](const Conv& cv, long long M) {
+    const size_t Mp = (size_t)((M + 7) & ~7LL);
+    col = std::max(col, Mp * cv.K);
+    dcol = std::max(dcol, (size_t)M * cv.K);
+    xt = std::max(xt, Mp * cv.cin);
+    gt = std::max(gt, Mp * cv.cout);
+  };
+  n->enc_a.resize(L); n->enc_b.resize(L); n->dec_c.resize(L); n->dec_d.resize(L);
+  for (int l = 0; l < L; ++l) {
+    const int cin = l == 0 ? kInPad : n->c[l - 1];
+    n->enc_a[l] = make_conv(n, n->S[l], cin, n->c[l], 27, n->c[l]);
+    n->enc_b[l] = make_conv(n, n->S[l], n->c[l], n->c[l], 27, n->c[l]);
+    need(n->enc_a[l], n->M[l]);
+    need(n->enc_b[l], n->M[l]);
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    n->dec_c[l] = make_conv(n, n->S[l], n->c[l + 1] + n->c[l], n->c[l], 27, n->c[l]);
+    n->dec_d[l] = make_conv(n, n->S[l], n->c[l], n->c[l], 27, n->c[l]);
+    need(n->dec_c[l], n->M[l]);
+    need(n->dec_d[l], n->M[l]);
+  }
+  n->head = make_conv(n, d->side, n->c[0], d->out_ch, 1, kHeadPad);
+  xt = std::max(xt, (size_t)M0 * n->c[0]);
+  for (int l = 0; l < L; ++l) n->convs.push_back(&n->enc_a[l]), n->convs.push_back(&n->enc_b[l]);
+  for (int l = L - 2; l >= 0; --l) n->convs.push_back(&n->dec_c[l]), n->convs.push_back(&n->dec_d[l]);
+  n->convs.push_back(&n->head);
+  bool ok = true;
+  for (Conv* cv : n->convs) ok &= conv_ok(*cv);
+  n->x0 = dalloc<bf16>(P, (size_t)M0 * kInPad);
+  n->a.resize(L); n->e.resize(L); n->p.resize(L); n->u.resize(L); n->b.resize(L); n->dd.resize(L);
+  n->gU.resize(L); n->gin.resize(L);
+  size_t gmax = 0;
+  for (int l = 0; l < L; ++l) {
+    const size_t M = (size_t)n->M[l];
+    n->a[l] = dalloc<bf16>(P, M * n->c[l]);
+    n->e[l] = dalloc<bf16>(P, M * n->c[l]);
+    ok &= n->a[l] && n->e[l];
+    if (l > 0) {
+      n->p[l] = dalloc<bf16>(P, M * n->c[l - 1]);
+      n->gin[l] = dalloc<float>(P, M * n->c[l - 1]);
+      ok &= n->p[l] && n->gin[l];
+    }
+    if (l < L - 1) {
+      n->u[l] = dalloc<bf16>(P, M * (n->c[l + 1] + n->c[l]));
+      n->b[l] = dalloc<bf16>(P, M * n->c[l]);
+      n->dd[l] = dalloc<bf16>(P, M * n->c[l]);
+      n->gU[l] = dalloc<float>(P, M * (n->c[l + 1] + n->c[l]));
+      ok &= n->u[l] && n->b[l] && n->dd[l] && n->gU[l];
+    }
+    gmax = std::max(gmax, M * n->c[l]);
+  }
+  n->out = dalloc<float>(P, (size_t)M0 * kHeadPad);
+  n->dout = dalloc<bf16>(P, (size_t)M0 * kHeadPad);
+  n->ghead = dalloc<float>(P, (size_t)M0 * n->c[0]);
+  n->g1 = dalloc<bf16>(P, gmax);
+  n->g2 = dalloc<bf16>(P, gmax);
+  n->col = dalloc<bf16>(P, col);
+  n->colT = dalloc<bf16>(P, col);
+  n->dcol = dalloc<float>(P, dcol);
+  n->xt = dalloc<bf16>(P, xt);
+  n->gt = dalloc<bf16>(P, gt);
+  n->loss = dalloc<double>(P, 1);
+  n->err = dalloc<int>(P, 1);
+  ok &= n->x0 && n->out && n->dout && n->ghead && n->g1 && n->g2 && n->col && n->colT && n->dcol && n->xt && n->gt &&
+        n->loss && n->err;
+  if (!ok) {
+    modil_unet_destroy(n);
+    return fail(MODIL_ERR_OOM, "device allocation of the network failed");
+  }
+  // parameters, optimiser state and gradients start at zero
+  for (Conv* cv : n->convs) {
+    const size_t nw = (size_t)cv->K * cv->co;
+    for (float* q : {cv->Wm, cv->dW, cv->mW, cv->vW}) cudaMemsetAsync(q, 0, nw * sizeof(float), n->s);
+    for (float* q : {cv->bm, cv->db, cv->mb, cv->vb}) cudaMemsetAsync(q, 0, cv->co * sizeof(float), n->s);
+    cudaMemsetAsync(cv->Wf, 0, nw * sizeof(bf16), n->s);
+    cudaMemsetAsync(cv->Wb, 0, nw * sizeof(bf16), n->s);
+  }
+  cudaMemsetAsync(n->err, 0, sizeof(int), n->s);
+  cudaError_t e = cudaStreamSynchronize(n->s);
+  if (e != cudaSuccess) {
+    modil_unet_destroy(n);
+    return fail(MODIL_ERR_CUDA, cudaGetErrorString(e));
+  }
+  *out = n;
+  return MODIL_OK;
+}
+
+void modil_unet_destroy(modil_unet* n) {
+  if (!n) return;
+  cudaStreamSynchronize(n->s);
+  for (void* p : n->pool) cudaFree(p);
+  for (cudaEvent_t e : n->ev) cudaEventDestroy(e);
+  delete n;
+}
+
+modil_status modil_unet_param_count(const modil_unet* n, int* cnt) {
+  if (!n || !cnt) return fail(MODIL_ERR_ARG, "NULL argument");
+  *cnt = 2 * (int)n->convs.size();
+  return MODIL_OK;
+}
+
+modil_status modil_unet_param_shape(const modil_unet* n, int i, int* kind, int dims[3]) {
+  if (!n || !kind || !dims) return fail(MODIL_ERR_ARG, "NULL argument");
+  if (i < 0 || i >= 2 * (int)n->convs.size()) return fail(MODIL_ERR_ARG, "parameter index out of range");
+  const Conv* c = n->convs[i / 2];
+  *kind = i % 2;
+  dims[0] = c->cout;
+  dims[1] = *kind ? 1 : c->taps;
+  dims[2] = *kind ? 1 : c->cin;
+  return MODIL_OK;
+}
+
+// host view [cout][taps][cin] <-> master [taps*cin][co]
+modil_status modil_unet_write_param(modil_unet* n, int i, const float* host, size_t count) {
+  int kind;
+  Conv* c;
+  modil_status st = param_check(n, i, count, &kind, &c);
+  if (st) return st;
+  if (!host) return fail(MODIL_ERR_ARG, "host is NULL");
+  if (kind) {
+    std::vector<float> b(c->co, 0.f);
+    std::copy(host, host + c->cout, b.begin());
+    UCUDA(cudaMemcpyAsync(c->bm, b.data(), sizeof(float) * c->co, cudaMemcpyHostToDevice, n->s));
+  } else {
+    std::vector<float> w((size_t)c->K * c->co, 0.f);
+    for (int o = 0; o < c->cout; ++o)
+      for (int k = 0; k < c->K; ++k) w[(size_t)k * c->co + o] = host[(size_t)o * c->K + k];
+    UCUDA(cudaMemcpyAsync(c->Wm, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, n->s));
+    if ((st = refresh(n, *c))) return st;
+  }
+  UCUDA(cudaStreamSynchronize(n->s));
+  return MODIL_OK;
+}
+
+static modil_status read_param_impl(modil_unet* n, int i, float* host, size_t count, bool grad) {
+  int kind;
+  Conv* c;
+  modil_status st = param_check(n, i, count, &kind, &c);
+  if (st) return st;
+  if (!host) return fail(MODIL_ERR_ARG, "host is NULL");
+  if (kind) {
+    std::vector<float> b(c->co);
+    UCUDA(cudaMemcpyAsync(b.data(), grad ? c->db : c->bm, sizeof(float) * c->co, cudaMemcpyDeviceToHost, n->s));
+    UCUDA(cudaStreamSynchronize(n->s));
+    std::copy(b.begin(), b.begin() + c->cout, host);
+  } else {
+    std::vector<float> w((size_t)c->K * c->co);
+    UCUDA(cudaMemcpyAsync(w.data(), grad ? c->dW : c->Wm, sizeof(float) * w.size(), cudaMemcpyDeviceToHost, n->s));
+    UCUDA(cudaStreamSynchronize(n->s));
+    for (int o = 0; o < c->cout; ++o)
+      for (int k = 0; k < c->K; ++k) host[(size_t)o * c->K + k] = w[(size_t)k * c->co + o];
+  }
+  return MODIL_OK;
+}
+
+modil_status modil_unet_read_param(modil_unet* n, int i, float* host, size_t count) {
+  return read_param_impl(n, i, host, count, false);
+}
+
+modil_status modil_unet_read_grad(modil_unet* n, int i, float* host, size_t count) {
+  return read_param_impl(n, i, host, count, true);
+}
+
+modil_status modil_unet_forward(modil_unet* n, const float* input, float* output) {
+  if (!n || !input || !output) return fail(MODIL_ERR_ARG, "NULL argument");
+  modil_status st = forward(n, input);
+  if (st) return st;
+  const long long M0 = n->M[0];
+  k_head_loss<<<gs(M0 * kHeadPad), kNT, 0, n->s>>>(n->out, n->d.out_ch, M0, nullptr, 0.f, output, nullptr, nullptr);
+  UCUDA(cudaGetLastError());
+  return rec(n);
+}
+
+modil_status modil_unet_eval_grad(modil_unet* n, const float* input, const float* target, double* loss) {
+  if (!n || !input || !target) return fail(MODIL_ERR_ARG, "NULL argument");
+  return eval_grad(n, input, target, loss);
+}
+
+modil_status modil_unet_train_step(modil_unet* n, const float* input, const float* target, double* loss) {
+  if (!n || !input || !target) return fail(MODIL_ERR_ARG, "NULL argument");
+  modil_status st = eval_grad(n, input, target, loss);
+  if (st) return st;
+  return adam(n);
+}
+
+modil_status modil_unet_profile_step(modil_unet* n, const float* input, const float* target, float* ms, int max,
+                                     int* cnt) {
+  if (!n || !input || !target || !ms || !cnt) return fail(MODIL_ERR_ARG, "NULL argument");
+  for (cudaEvent_t e : n->ev) cudaEventDestroy(e);
+  n->ev.clear();
+  n->prof = true;
+  modil_status st = rec(n);
+  if (!st) st = eval_grad(n, input, target, nullptr);
+  n->prof = false;
+  if (st) return st;
+  UCUDA(cudaEventSynchronize(n->ev.back()));
+  const int k = std::min<int>(max, (int)n->ev.size() - 1);
+  for (int j = 0; j < k; ++j) UCUDA(cudaEventElapsedTime(&ms[j], n->ev[j], n->ev[j + 1]));
+  *cnt = k;
+  return MODIL_OK;
+}
+
+modil_status modil_gemm_bf16(const void* A, long long lda, const void* B, long long ldb, void* D, long long ldd,
+                             int M, int N, int K, int mode, int relu, const float* bias, int splits, void* stream) {
+  if (!A || !B || !D) return fail(MODIL_ERR_ARG, "NULL argument");
+  if (M < 1 || N < 1 || K < 1 || mode < 0 || mode > 2 || splits < 1) return fail(MODIL_ERR_ARG, "sizes or mode");
+  if (lda < K || ldb < K || ldd < N) return fail(MODIL_ERR_ARG, "leading dimensions");
+  static int* err = nullptr;
+  if (!err && cudaMalloc(&err, sizeof(int)) != cudaSuccess) return fail(MODIL_ERR_OOM, "error word");
+  CUtensorMap ta, tb;
+  const int bn = pick_bn(N);
+  if (modil_tc::make_kmajor_map(&ta, A, M, K, lda, 128) != 0 || modil_tc::make_kmajor_map(&tb, B, N, K, ldb, bn) != 0)
+    return fail(MODIL_ERR_ARG, "tensor map: operand not 16-byte aligned or pitch not a multiple of 8");
+  GemmArgs g{};
+  g.M = M; g.N = N; g.K = K; g.mode = mode; g.relu = relu; g.bias = bias; g.D = D; g.ldd = (int)ldd; g.err = err;
+  const int nk = (K + 63) / 64;
+  if (mode != modil_tc::GEMM_ATOMIC_F32) splits = 1;
+  g.kchunks = (nk + std::min(splits, nk) - 1) / std::min(splits, nk);
+  const int sp = (nk + g.kchunks - 1) / g.kchunks;
+  UCUDA(modil_tc::launch_gemm(ta, tb, g, bn, sp, static_cast<cudaStream_t>(stream)));
+  return MODIL_OK;
+}
+
+}  // extern "C"

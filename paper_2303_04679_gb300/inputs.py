@@ -305,3 +305,22 @@ def ns3d_workload(n=128, n_levels=8, seed=5):
     return dict(shape=shape, n_levels=n_levels, meas_cell=cells, meas_field=fields,
                 meas_value=vals, centre=centre, axes=axes, coef=dict(NS3D_COEF),
                 w_res=1.0, w_data=1.0, lr=1e-3)
+
+
+# --------------------------------------------------------------------------
+# Learned warm start (3-D U-Net): parameter initialisation
+# --------------------------------------------------------------------------
+
+def unet_params(shapes, seed, bias_scale=0.0):
+    """He-normal weights (std sqrt(2 / fan_in)) for the parameter shapes
+    (weights (c_out, taps, c_in), biases (c_out,)); biases N(0, bias_scale^2).
+    Values are FP32."""
+    rng = make_rng(seed)
+    out = []
+    for s in shapes:
+        if len(s) == 3:
+            std = math.sqrt(2.0 / (s[1] * s[2]))
+            out.append(rng.normal(0.0, std, size=s).astype(np.float32))
+        else:
+            out.append((rng.normal(0.0, bias_scale, size=s) if bias_scale else np.zeros(s)).astype(np.float32))
+    return out
