@@ -378,7 +378,7 @@ def run_body(args):
         loss = float(p.eval_loss()[0, 0])
         prof = np.array([p.profile_step() for _ in range(max(1, min(args.profile_steps, 20)))])
     kern_ms = prof.mean(axis=0)
-    names = (["compose3", "residual_adjoint_adam3"] +
+    names = ([f"prolong3_L{l + 1}" for l in range(L - 2, -1, -1)] + ["residual_adjoint_adam3"] +
              [f"restrict_adam3_L{l + 1}" for l in range(1, L)] + ["finalize"])
     dom = int(np.argmax(kern_ms))
     peak, peak_kind = measured_peak()

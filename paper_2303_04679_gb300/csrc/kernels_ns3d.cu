@@ -13,17 +13,16 @@
 // the inlet, the cell's u at the outlet); walls carry none.
 //
 // Kernels of one pass:
-//   k_compose3  per 3-D tile: stage the tile's pyramid of every level and
-//               field, compose by Horner's scheme (Section 2.2), write the
-//               composed fields (recomputed every pass, no per-level storage);
+//   k_prolong3  one launch per level, coarse to fine: the composed level
+//               w_l = u_l + T w_{l+1} (Horner's scheme, Section 2.2), the finest
+//               into the composed-field buffer;
 //   k_resid3    per 3-D tile: stage the composed fields with a halo of 4,
-//               evaluate the momentum residuals on the tile plus 1 cell and
-//               the continuity residuals on the tile plus 2 cells, each with
-//               its local Jacobian, scatter lambda * dr/du into the tile's
-//               gradient (shared-memory atomics: a stored 3-D Jacobian does
-//               not fit), add the measurements, write dL/du and apply Adam to
-//               level 1;
-// then k_level3 restricts and steps each coarser level.
+//               residuals and their adjoint in gather form (each cell collects
+//               the adjoint of the fluxes through its six faces and of the
+//               neighbouring pressure-gradient and continuity terms; no
+//               atomics), the measurements, dL/du and Adam on level 1;
+//   k_level3    one block per (coarse tile, field): restriction of the level
+//               above (transposed interpolation) and Adam.
 #include <algorithm>
 
 #include "launch.h"
@@ -38,113 +37,70 @@ constexpr int S3Z = C3Z + 2 * H3, S3Y = C3Y + 2 * H3, S3X = C3X + 2 * H3;
 constexpr int NS3 = S3Z * S3Y * S3X;
 constexpr int F3 = 5;
 
-// Region of a level needed to interpolate a fine box [a0, b0] (one axis):
-// unrolled, level l covers [(a0 - k) >> l, (b0 + k) >> l] with k = 2^(l+1) - 2.
-__device__ __forceinline__ void lev_range(int a0, int b0, int l, int n, int& lo, int& cnt) {
-  const int k = (1 << (l + 1)) - 2;
-  lo = max(0, (a0 - k) >> l);
-  cnt = min(n - 1, (b0 + k) >> l) - lo + 1;
-}
-
+// ---------------------------------------------------------------------------
+// Composition, one level per launch (Horner's scheme, Section 2.2):
+// w_l = u_l + T w_{l+1}; the coarsest composed level is u_{L-1} itself (read
+// from the parameters), w_0 goes to the composed-field buffer, the others to
+// the per-level scratch.  One thread per cell, cells of a tile x fastest.
+// ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(MODIL_NT)
-k_compose3(const __grid_constant__ Arena<T> A, int cur) {
-  extern __shared__ __align__(16) unsigned char smem[];
+k_prolong3(const __grid_constant__ Arena<T> A, int l, int cur) {
   __shared__ DevInst D;
-  __shared__ int lo[MODIL_MAXL][3], cnt[MODIL_MAXL][3], poff[MODIL_MAXL + 1];
-  T* pyr = reinterpret_cast<T*>(smem);
-  const int tid = threadIdx.x;
-  const int gt = blockIdx.x;
-  const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[0][gt];
+  const int gt = blockIdx.x, f = blockIdx.y;
+  const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[l][gt];
   load_inst(&D, A, ii);
   __syncthreads();
-  const int L = D.nlev;
-  const int local = gt - D.tile_base[0];
-  const int per_z = D.nt[0][1] * D.nt[0][2];
-  const int tz = local / per_z, tr = local - tz * per_z;
-  const int ty = tr / D.nt[0][2], tx = tr - ty * D.nt[0][2];
-  const int z0 = tz * C3Z, y0 = ty * C3Y, x0 = tx * C3X;
-  if (tid == 0) {
-    int tot = 0;
-    for (int l = 0; l < L; ++l) {
-      lev_range(z0, min(D.n[0][0], z0 + C3Z) - 1, l, D.n[l][0], lo[l][0], cnt[l][0]);
-      lev_range(y0, min(D.n[0][1], y0 + C3Y) - 1, l, D.n[l][1], lo[l][1], cnt[l][1]);
-      lev_range(x0, min(D.n[0][2], x0 + C3X) - 1, l, D.n[l][2], lo[l][2], cnt[l][2]);
-      poff[l] = tot;
-      tot += cnt[l][0] * cnt[l][1] * cnt[l][2];
-    }
-    poff[L] = tot;
-  }
-  __syncthreads();
-  const int PS = poff[L];
   pdl_wait();
   pdl_trigger();
-  const T* __restrict__ P = A.p[cur];
-  for (int f = 0; f < D.nfield; ++f)
-    for (int l = 0; l < L; ++l) {
-      const int cz = cnt[l][0], cy = cnt[l][1], cx = cnt[l][2];
-      const T* src = P + D.off[f][l];
-      for (int i = tid; i < cz * cy * cx; i += MODIL_NT) {
-        const int a = i / (cy * cx), r = i - a * (cy * cx), b = r / cx, c = r - b * cx;
-        const long long g = ((long long)(lo[l][0] + a) * D.n[l][1] + (lo[l][1] + b)) * D.n[l][2] + (lo[l][2] + c);
-        cp_async(pyr + f * PS + poff[l] + i, src + g);
-      }
-    }
-  cp_async_wait_all();
-  __syncthreads();
-  for (int l = L - 2; l >= 0; --l) {
-    for (int f = 0; f < D.nfield; ++f) {
-      const int cz = cnt[l][0], cy = cnt[l][1], cx = cnt[l][2];
-      const int qy = cnt[l + 1][1], qx = cnt[l + 1][2];
-      const T* wc = pyr + f * PS + poff[l + 1];
-      for (int i = tid; i < cz * cy * cx; i += MODIL_NT) {
-        const int a = i / (cy * cx), r = i - a * (cy * cx), b = r / cx, c = r - b * cx;
-        const int z = lo[l][0] + a, y = lo[l][1] + b, x = lo[l][2] + c;
-        int jz0, jz1, jy0, jy1, jx0, jx1;
-        T wz0, wz1, wy0, wy1, wx0, wx1;
-        prolong_taps<T>(z, D.n[l + 1][0], jz0, jz1, wz0, wz1);
-        prolong_taps<T>(y, D.n[l + 1][1], jy0, jy1, wy0, wy1);
-        prolong_taps<T>(x, D.n[l + 1][2], jx0, jx1, wx0, wx1);
-        jz0 -= lo[l + 1][0]; jz1 -= lo[l + 1][0];
-        jy0 -= lo[l + 1][1]; jy1 -= lo[l + 1][1];
-        jx0 -= lo[l + 1][2]; jx1 -= lo[l + 1][2];
-        auto at = [&](int zz, int yy, int xx) { return wc[(zz * qy + yy) * qx + xx]; };
-        const T add =
-            wz0 * (wy0 * (wx0 * at(jz0, jy0, jx0) + wx1 * at(jz0, jy0, jx1)) +
-                   wy1 * (wx0 * at(jz0, jy1, jx0) + wx1 * at(jz0, jy1, jx1))) +
-            wz1 * (wy0 * (wx0 * at(jz1, jy0, jx0) + wx1 * at(jz1, jy0, jx1)) +
-                   wy1 * (wx0 * at(jz1, jy1, jx0) + wx1 * at(jz1, jy1, jx1)));
-        pyr[f * PS + poff[l] + i] += add;
-      }
-    }
-    __syncthreads();
-  }
-  for (int f = 0; f < D.nfield; ++f) {
-    const int cz = cnt[0][0], cy = cnt[0][1], cx = cnt[0][2];
-    T* out = A.ufine + D.fine_off[f];
-    for (int i = tid; i < cz * cy * cx; i += MODIL_NT) {
-      const int a = i / (cy * cx), r = i - a * (cy * cx), b = r / cx, c = r - b * cx;
-      const long long g = ((long long)(lo[0][0] + a) * D.n[0][1] + (lo[0][1] + b)) * D.n[0][2] + (lo[0][2] + c);
-      out[g] = pyr[f * PS + i];
-    }
+  // an instance's coarsest level is read from the parameters directly, except
+  // a single-level instance, whose level 0 is copied to the composed buffer
+  if (f >= D.nfield || l > D.nlev - 1 || (l == D.nlev - 1 && l > 0)) return;
+  const bool copy = (l == D.nlev - 1);
+  const int tz = l == 0 ? C3Z : k3LZ, ty = l == 0 ? C3Y : k3LY, tx = l == 0 ? C3X : k3LX;
+  const int local = gt - D.tile_base[l];
+  const int per_z = D.nt[l][1] * D.nt[l][2];
+  const int bz = local / per_z, br = local - bz * per_z;
+  const int by = br / D.nt[l][2], bx = br - by * D.nt[l][2];
+  const int nz = D.n[l][0], ny = D.n[l][1], nx = D.n[l][2];
+  const int lc = copy ? l : l + 1;
+  const int cz = D.n[lc][0], cy = D.n[lc][1], cx = D.n[lc][2];
+  const T* __restrict__ u = A.p[cur] + D.off[f][l];
+  const T* __restrict__ w = (lc == D.nlev - 1 ? A.p[cur] : A.wl) + D.off[f][lc];
+  T* __restrict__ out = l == 0 ? A.ufine + D.fine_off[f] : A.wl + D.off[f][l];
+  for (int t = threadIdx.x; t < tz * ty * tx; t += MODIL_NT) {
+    const int x = bx * tx + t % tx, y = by * ty + (t / tx) % ty, z = bz * tz + t / (tx * ty);
+    if (x >= nx || y >= ny || z >= nz) continue;
+    int z0, z1, y0, y1, x0, x1;
+    T wz0, wz1, wy0, wy1, wx0, wx1;
+    prolong_taps<T>(z, cz, z0, z1, wz0, wz1);
+    prolong_taps<T>(y, cy, y0, y1, wy0, wy1);
+    prolong_taps<T>(x, cx, x0, x1, wx0, wx1);
+    auto W = [&](int a, int b, int c) { return w[((long long)a * cy + b) * cx + c]; };
+    const T add = wz0 * (wy0 * (wx0 * W(z0, y0, x0) + wx1 * W(z0, y0, x1)) +
+                         wy1 * (wx0 * W(z0, y1, x0) + wx1 * W(z0, y1, x1))) +
+                  wz1 * (wy0 * (wx0 * W(z1, y0, x0) + wx1 * W(z1, y0, x1)) +
+                         wy1 * (wx0 * W(z1, y1, x0) + wx1 * W(z1, y1, x1)));
+    const long long o = ((long long)z * ny + y) * nx + x;
+    out[o] = copy ? u[o] : u[o] + add;
   }
 }
 
-// Ghost coefficient alpha and offset beta of field f beyond face (axis, side)
-// of the domain: ghost = alpha * (value of the adjacent cell) + beta.
+// Ghost coefficient alpha and offset beta of field f (0..3) beyond face
+// (axis, side) of the domain: ghost = alpha * (value of the adjacent cell) + beta.
 template <class T>
 __device__ __forceinline__ void ghost3(int f, int axis, int side, T& alpha, T& beta) {
   beta = T(0);
   if (axis == 2) {           // x
-    if (side == 0) {         // inlet
+    if (side == 0) {         // inlet: u = 2 - u_P (face value 1), v, w odd, p even
       alpha = (f == 3) ? T(1) : T(-1);
       beta = (f == 0) ? T(2) : T(0);
-    } else {                 // outlet
+    } else {                 // outlet: p odd (p = 0 on the face), velocity even
       alpha = (f == 3) ? T(-1) : T(1);
     }
-  } else if (axis == 1) {    // y walls, v normal
+  } else if (axis == 1) {    // y walls: v odd, the rest even
     alpha = (f == 1) ? T(-1) : T(1);
-  } else {                   // z walls, w normal
+  } else {                   // z walls: w odd, the rest even
     alpha = (f == 2) ? T(-1) : T(1);
   }
 }
@@ -155,7 +111,7 @@ struct Ns3Coef {
   T nu, lam, tf;
 };
 
-// Continuity residual from its 22 stencil values (affine in them).
+// Continuity residual from its 22 stencil values.
 // s: u P E W | v P N S | w P T B | p P E W EE WW N S NN SS T B TT BB
 template <class T>
 __device__ __forceinline__ T cont3(const T* s, const bool* in, const Ns3Coef<T>& c) {
@@ -178,6 +134,54 @@ __device__ __forceinline__ T cont3(const T* s, const bool* in, const Ns3Coef<T>&
   return (fe - fw) * c.ih[2] + (fn - fs) * c.ih[1] + (ft - fb) * c.ih[0];
 }
 
+// d(axis part of the continuity residual of cell P)/d(value at P + o e_axis)
+// for the normal velocity (vel = true, |o| <= 1) or the pressure (|o| <= 2).
+// P's position along the axis: i in [0, n); x axis: inflow face at i = 0
+// (flux 1), outflow at n - 1 (flux u_P, odd pressure ghost); y, z: walls
+// (no flux, even pressure ghosts).
+template <class T>
+__device__ __forceinline__ T cont_coef(bool xaxis, int i, int n, int o, bool vel, T tf, T ih) {
+  const bool in0 = i < n - 1, in1 = i > 0, in2 = i < n - 2, in3 = i > 1;
+  const T q = T(0.25) * tf, h = T(0.5);
+  T ce = T(0), cw = T(0);  // partials of the + face flux and of the - face flux
+  if (vel) {
+    if (in0) { if (o == 0 || o == 1) ce = h; }
+    else if (xaxis && o == 0) ce = T(1);   // outflow flux u_P
+    if (in1) { if (o == 0 || o == -1) cw = h; }
+  } else {
+    const T godd = xaxis ? T(-1) : T(1);   // sign of the + end's pressure ghost
+    if (in0) {
+      if (o == 0) ce = tf - q + (in1 ? T(0) : -q);
+      else if (o == 1) ce = -tf + q + (in2 ? T(0) : godd * q);
+      else if (o == -1) ce = in1 ? -q : T(0);
+      else if (o == 2) ce = in2 ? q : T(0);
+    }
+    if (in1) {
+      if (o == 0) cw = -tf + q + (in0 ? T(0) : godd * q);
+      else if (o == -1) cw = tf - q + (in3 ? T(0) : -q);
+      else if (o == -2) cw = in3 ? -q : T(0);
+      else if (o == 1) cw = in0 ? q : T(0);
+    }
+  }
+  return (ce - cw) * ih;
+}
+
+// ---------------------------------------------------------------------------
+// Residuals, adjoint, data term and level-1 Adam for one fine tile.
+//   phase 1  momentum residuals on the tile plus one cell: the adjoint weights
+//            A_c = 2 w dV r_c (1 - chi) of the three components, and for owned
+//            cells the terms of their own residual that do not pass through a
+//            face (penalisation, body fraction); continuity residuals on the
+//            tile plus two cells (weights B = 2 w dV r);
+//   phase 2  each owned cell gathers, per face, the adjoint of the convective
+//            and viscous fluxes through that face, the pressure-gradient terms
+//            of its neighbours and the continuity terms of the cells within two
+//            cells along each axis, adds the data term, writes dL/du and steps
+//            level 1 with Adam.  No atomics: every cell is written by one thread.
+// ---------------------------------------------------------------------------
+constexpr int MZ = C3Z + 2, MY = C3Y + 2, MX = C3X + 2, NM = MZ * MY * MX;    // tile + 1
+constexpr int QZ = C3Z + 4, QY = C3Y + 4, QX = C3X + 4, NQ = QZ * QY * QX;    // tile + 2
+
 template <class T>
 __global__ void __launch_bounds__(MODIL_NT)
 k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
@@ -185,8 +189,11 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
   __shared__ DevInst D;
   __shared__ double red[16];
   __shared__ AdamCoef acS;
-  T* uS = reinterpret_cast<T*>(smem);              // F3 x NS3, staged composed fields
-  T* gS = uS + F3 * NS3;                           // F3 x NC3, tile gradient
+  T* uS = reinterpret_cast<T*>(smem);   // u, v, w, p with a halo of 4: 4 x NS3
+  T* cS = uS + 4 * NS3;                 // chihat on the tile plus one cell: NM
+  T* aS = cS + NM;                      // momentum adjoint weights: 3 x NM
+  T* bS = aS + 3 * NM;                  // continuity adjoint weights: NQ
+  T* gS = bS + NQ;                      // own-residual and data terms: F3 x NC3
   float* redf = reinterpret_cast<float*>(red);
   const int tid = threadIdx.x;
   const int gt = blockIdx.x;
@@ -205,8 +212,7 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
   for (int i = tid; i < F3 * NC3; i += MODIL_NT) gS[i] = T(0);
   pdl_wait();
   pdl_trigger();
-  // stage the composed fields (written by the previous launch) with a halo of 4
-  for (int f = 0; f < F3; ++f) {
+  for (int f = 0; f < 4; ++f) {
     const T* src = A.ufine + D.fine_off[f];
     for (int i = tid; i < NS3; i += MODIL_NT) {
       const int a = i / (S3Y * S3X), r = i - a * (S3Y * S3X), b = r / S3X, c = r - b * S3X;
@@ -215,215 +221,145 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
         cp_async(uS + f * NS3 + i, src + ((long long)z * ny + y) * nx + x);
     }
   }
+  {
+    const T* src = A.ufine + D.fine_off[4];
+    for (int i = tid; i < NM; i += MODIL_NT) {
+      const int a = i / (MY * MX), r = i - a * (MY * MX), b = r / MX, c = r - b * MX;
+      const int z = z0 - 1 + a, y = y0 - 1 + b, x = x0 - 1 + c;
+      if (z >= 0 && z < nz && y >= 0 && y < ny && x >= 0 && x < nx)
+        cp_async(cS + i, src + ((long long)z * ny + y) * nx + x);
+    }
+  }
   cp_async_wait_all();
   __syncthreads();
 
   Ns3Coef<T> cf;
-  const double hh[3] = {D.h[0], D.h[1], D.h[2]};
   for (int a = 0; a < 3; ++a) {
-    cf.ih[a] = (T)(1.0 / hh[a]);
-    cf.ih2[a] = (T)(1.0 / (hh[a] * hh[a]));
-    cf.i2h[a] = (T)(0.5 / hh[a]);
+    const double hh = D.h[a];
+    cf.ih[a] = (T)(1.0 / hh);
+    cf.ih2[a] = (T)(1.0 / (hh * hh));
+    cf.i2h[a] = (T)(0.5 / hh);
   }
   cf.nu = (T)(D.coef[1] / D.coef[0]);  // D / Re
   cf.lam = (T)D.coef[2];
   cf.tf = (T)D.coef[3];
   const int dims[3] = {nz, ny, nx};
-  auto Vs = [&](int f, int z, int y, int x) -> T {
-    return uS[f * NS3 + ((z - z0 + H3) * S3Y + (y - y0 + H3)) * S3X + (x - x0 + H3)];
-  };
+  auto sidx = [&](int z, int y, int x) { return ((z - z0 + H3) * S3Y + (y - y0 + H3)) * S3X + (x - x0 + H3); };
+  auto midx = [&](int z, int y, int x) { return ((z - z0 + 1) * MY + (y - y0 + 1)) * MX + (x - x0 + 1); };
+  auto qidx = [&](int z, int y, int x) { return ((z - z0 + 2) * QY + (y - y0 + 2)) * QX + (x - x0 + 2); };
   auto owned = [&](int z, int y, int x) {
     return z >= z0 && z < z0 + hz && y >= y0 && y < y0 + hy && x >= x0 && x < x0 + hx;
   };
-  auto scatter = [&](int f, int z, int y, int x, T val) {
-    if (owned(z, y, x)) atomicAdd(gS + f * NC3 + ((z - z0) * C3Y + (y - y0)) * C3X + (x - x0), val);
-  };
-  const T lam_scale = T(2) * (T)D.w_res_dV;
+  const T Rs = T(2) * (T)D.w_res_dV;
   const bool adj = (mode != MODE_LOSS);
   float racc = 0.f;
   double raccd = 0.0;
+  auto addsq = [&](T r) {
+    if (sizeof(T) == 4) racc += (float)(r * r);
+    else raccd += (double)(r * r);
+  };
 
-  // ---- momentum on the tile plus one cell ------------------------------------
-  constexpr int MZ = C3Z + 2, MY = C3Y + 2, MX = C3X + 2;
-  for (int i = tid; i < MZ * MY * MX; i += MODIL_NT) {
+  // ---- phase 1a: momentum on the tile plus one cell -------------------------
+  for (int i = tid; i < NM; i += MODIL_NT) {
     const int a = i / (MY * MX), rr = i - a * (MY * MX), b = rr / MX, c = rr - b * MX;
     const int z = z0 - 1 + a, y = y0 - 1 + b, x = x0 - 1 + c;
     if (z < 0 || z >= nz || y < 0 || y >= ny || x < 0 || x >= nx) continue;
     const int P[3] = {z, y, x};
-    // neighbour values along each axis with ghost substitution
-    T nv[F3][3][2], al[F3][3][2];
+    const int sp = sidx(z, y, x);
+    T cen[4], nv[4][3][2];
     bool gh[3][2];
-    T cen[F3];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) cen[f] = Vs(f, z, y, x);
-    cen[4] = Vs(4, z, y, x);
+    for (int f = 0; f < 4; ++f) cen[f] = uS[f * NS3 + sp];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax)
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
-        int q[3] = {P[0], P[1], P[2]};
-        q[ax] += sd ? 1 : -1;
-        const bool inside = q[ax] >= 0 && q[ax] < dims[ax];
+        const int q = P[ax] + (sd ? 1 : -1);
+        const bool inside = q >= 0 && q < dims[ax];
         gh[ax][sd] = !inside;
+        const int stride = ax == 0 ? S3Y * S3X : (ax == 1 ? S3X : 1);
+        const int sq = sp + (sd ? stride : -stride);
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
           if (inside) {
-            nv[f][ax][sd] = Vs(f, q[0], q[1], q[2]);
-            al[f][ax][sd] = T(0);
+            nv[f][ax][sd] = uS[f * NS3 + sq];
           } else {
             T alpha, beta;
             ghost3<T>(f, ax, sd, alpha, beta);
             nv[f][ax][sd] = alpha * cen[f] + beta;
-            al[f][ax][sd] = alpha;
           }
         }
       }
+    const T chat = cS[i];
     // chi and 1 - chi each from its own logistic: 1 - chi is never formed by
     // subtraction, which loses all digits in FP32 where chi is near 1
-    const T chi = T(1) / (T(1) + exp(-(cen[4] + T(5))));
-    const T om = T(1) / (T(1) + exp(cen[4] + T(5)));
-    const bool own = owned(z, y, x);
-    // mass-flux masks: x faces always carry flux, y and z walls none
-    T mk[3][2];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax)
-#pragma unroll
-      for (int sd = 0; sd < 2; ++sd) mk[ax][sd] = (ax == 2 || !gh[ax][sd]) ? T(1) : T(0);
-    // face-normal velocities (axis ax carried by component 2 - ax: z<-w, y<-v, x<-u)
+    const T chi = T(1) / (T(1) + exp(-(chat + T(5))));
+    const T om = T(1) / (T(1) + exp(chat + T(5)));
     T Vf[3][2];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-      const int cmp = 2 - ax;
-      Vf[ax][1] = mk[ax][1] * T(0.5) * (cen[cmp] + nv[cmp][ax][1]);
-      Vf[ax][0] = mk[ax][0] * T(0.5) * (nv[cmp][ax][0] + cen[cmp]);
-    }
+      const int n = 2 - ax;  // velocity component normal to the faces of this axis
 #pragma unroll
-    for (int comp = 0; comp < 3; ++comp) {   // u (x), v (y), w (z)
-      const int cax = 2 - comp;               // axis of this component
+      for (int sd = 0; sd < 2; ++sd) {
+        const T mk = (ax == 2 || !gh[ax][sd]) ? T(1) : T(0);  // mass flux through walls is zero
+        Vf[ax][sd] = mk * T(0.5) * (cen[n] + nv[n][ax][sd]);
+      }
+    }
+    const bool own = owned(z, y, x);
+    T gch = T(0);
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      const int cax = 2 - comp;
       const T phi = cen[comp];
       T conv = T(0), lap = T(0);
-      // raw partials: own field at P and the 6 neighbours, face velocities
-      T Jphi[3][2], JphiP = T(0), Jvel[3][2], JvelP[3];
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) {
-        const T fp = T(0.5) * (phi + nv[comp][ax][1]), fm = T(0.5) * (nv[comp][ax][0] + phi);
-        conv += (Vf[ax][1] * fp - Vf[ax][0] * fm) * cf.ih[ax];
+        conv += (Vf[ax][1] * T(0.5) * (phi + nv[comp][ax][1]) - Vf[ax][0] * T(0.5) * (nv[comp][ax][0] + phi)) *
+                cf.ih[ax];
         lap += (nv[comp][ax][1] - T(2) * phi + nv[comp][ax][0]) * cf.ih2[ax];
-        // d(conv)/d phi
-        JphiP += T(0.5) * (Vf[ax][1] - Vf[ax][0]) * cf.ih[ax];
-        Jphi[ax][1] = T(0.5) * Vf[ax][1] * cf.ih[ax];
-        Jphi[ax][0] = -T(0.5) * Vf[ax][0] * cf.ih[ax];
-        // d(conv)/d face velocity component (component 2 - ax)
-        JvelP[ax] = T(0.5) * (mk[ax][1] * fp - mk[ax][0] * fm) * cf.ih[ax];
-        Jvel[ax][1] = T(0.5) * mk[ax][1] * fp * cf.ih[ax];
-        Jvel[ax][0] = -T(0.5) * mk[ax][0] * fm * cf.ih[ax];
-        // viscous
-        JphiP += T(2) * cf.nu * cf.ih2[ax];
-        Jphi[ax][1] -= cf.nu * cf.ih2[ax];
-        Jphi[ax][0] -= cf.nu * cf.ih2[ax];
       }
-      const T gp = (nv[3][cax][1] - nv[3][cax][0]) * cf.i2h[cax];
-      const T M = conv + gp - cf.nu * lap;
+      const T M = conv + (nv[3][cax][1] - nv[3][cax][0]) * cf.i2h[cax] - cf.nu * lap;
       const T r = om * M + cf.lam * chi * phi;
-      if (own) {
-        if (sizeof(T) == 4) racc += (float)(r * r);
-        else raccd += (double)(r * r);
+      if (own) addsq(r);
+      const T R = Rs * r;
+      aS[comp * NM + i] = R * om;
+      if (own && adj) {
+        gS[comp * NC3 + ((z - z0) * C3Y + (y - y0)) * C3X + (x - x0)] = R * cf.lam * chi;
+        gch += R * chi * om * (cf.lam * phi - M);
       }
-      if (!adj) continue;
-      const T lamr = lam_scale * r;
-      // combine partials per field and slot (the face velocity of axis ax is
-      // component 2 - ax; when it is this component the slots coincide)
-      T jP[4] = {T(0), T(0), T(0), T(0)};
-      T jn[4][3][2];
+    }
+    if (own && adj) gS[4 * NC3 + ((z - z0) * C3Y + (y - y0)) * C3X + (x - x0)] = gch;
+  }
+
+  // ---- phase 1b: continuity on the tile plus two cells ----------------------
+  {
+    const int sf[22] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
+    const int sz[22] = {0, 0, 0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, 2, -2};
+    const int sy[22] = {0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, 2, -2, 0, 0, 0, 0};
+    const int sx[22] = {0, 1, -1, 0, 0, 0, 0, 0, 0, 0, 1, -1, 2, -2, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = tid; i < NQ; i += MODIL_NT) {
+      const int a = i / (QY * QX), rr = i - a * (QY * QX), b = rr / QX, c = rr - b * QX;
+      const int z = z0 - 2 + a, y = y0 - 2 + b, x = x0 - 2 + c;
+      if (z < 0 || z >= nz || y < 0 || y >= ny || x < 0 || x >= nx) continue;
+      bool in[12];
+      in[0] = x < nx - 1; in[1] = x > 0; in[2] = x < nx - 2; in[3] = x > 1;
+      in[4] = y < ny - 1; in[5] = y > 0; in[6] = y < ny - 2; in[7] = y > 1;
+      in[8] = z < nz - 1; in[9] = z > 0; in[10] = z < nz - 2; in[11] = z > 1;
+      T s[22];
+      const int sp = sidx(z, y, x);
 #pragma unroll
-      for (int f = 0; f < 4; ++f)
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) { jn[f][ax][0] = T(0); jn[f][ax][1] = T(0); }
-      jP[comp] += JphiP;
-#pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        jn[comp][ax][0] += Jphi[ax][0];
-        jn[comp][ax][1] += Jphi[ax][1];
-        const int vc = 2 - ax;
-        jP[vc] += JvelP[ax];
-        jn[vc][ax][0] += Jvel[ax][0];
-        jn[vc][ax][1] += Jvel[ax][1];
+      for (int k = 0; k < 22; ++k) {
+        const int zz = z + sz[k], yy = y + sy[k], xx = x + sx[k];
+        const bool ok = zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx;
+        s[k] = ok ? uS[sf[k] * NS3 + sp + (sz[k] * S3Y + sy[k]) * S3X + sx[k]] : T(0);
       }
-      jn[3][cax][1] += cf.i2h[cax];
-      jn[3][cax][0] -= cf.i2h[cax];
-      // fold ghost neighbours into the centre cell
-#pragma unroll
-      for (int f = 0; f < 4; ++f)
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax)
-#pragma unroll
-          for (int sd = 0; sd < 2; ++sd)
-            if (gh[ax][sd]) {
-              jP[f] += al[f][ax][sd] * jn[f][ax][sd];
-              jn[f][ax][sd] = T(0);
-            }
-      // penalisation
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const T extra = (f == comp) ? cf.lam * chi : T(0);
-        scatter(f, z, y, x, lamr * (om * jP[f] + extra));
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax)
-#pragma unroll
-          for (int sd = 0; sd < 2; ++sd) {
-            if (gh[ax][sd] || jn[f][ax][sd] == T(0)) continue;
-            int q[3] = {z, y, x};
-            q[ax] += sd ? 1 : -1;
-            scatter(f, q[0], q[1], q[2], lamr * om * jn[f][ax][sd]);
-          }
-      }
-      scatter(4, z, y, x, lamr * chi * om * (cf.lam * phi - M));
+      const T r = cont3(s, in, cf);
+      if (owned(z, y, x)) addsq(r);
+      bS[i] = Rs * r;
     }
   }
 
-  // ---- continuity on the tile plus two cells ---------------------------------
-  constexpr int QZ = C3Z + 4, QY = C3Y + 4, QX = C3X + 4;
-  // slot -> (field, dz, dy, dx)
-  const int sf[22] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
-  const int sz[22] = {0, 0, 0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, 2, -2};
-  const int sy[22] = {0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, 2, -2, 0, 0, 0, 0};
-  const int sx[22] = {0, 1, -1, 0, 0, 0, 0, 0, 0, 0, 1, -1, 2, -2, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int i = tid; i < QZ * QY * QX; i += MODIL_NT) {
-    const int a = i / (QY * QX), rr = i - a * (QY * QX), b = rr / QX, c = rr - b * QX;
-    const int z = z0 - 2 + a, y = y0 - 2 + b, x = x0 - 2 + c;
-    if (z < 0 || z >= nz || y < 0 || y >= ny || x < 0 || x >= nx) continue;
-    bool in[12];
-    in[0] = x < nx - 1; in[1] = x > 0; in[2] = x < nx - 2; in[3] = x > 1;
-    in[4] = y < ny - 1; in[5] = y > 0; in[6] = y < ny - 2; in[7] = y > 1;
-    in[8] = z < nz - 1; in[9] = z > 0; in[10] = z < nz - 2; in[11] = z > 1;
-    T s[22];
-#pragma unroll
-    for (int k = 0; k < 22; ++k) {
-      const int zz = z + sz[k], yy = y + sy[k], xx = x + sx[k];
-      const bool ok = zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx;
-      s[k] = ok ? Vs(sf[k], zz, yy, xx) : T(0);
-    }
-    const T r = cont3(s, in, cf);
-    if (owned(z, y, x)) {
-      if (sizeof(T) == 4) racc += (float)(r * r);
-      else raccd += (double)(r * r);
-    }
-    if (!adj) continue;
-    const T lamr = lam_scale * r;
-    T e[22];
-#pragma unroll
-    for (int k = 0; k < 22; ++k) e[k] = T(0);
-    const T r0 = cont3(e, in, cf);  // constant part (inlet flux)
-#pragma unroll
-    for (int k = 0; k < 22; ++k) {
-      e[k] = T(1);
-      const T jk = cont3(e, in, cf) - r0;
-      e[k] = T(0);
-      if (jk != T(0)) scatter(sf[k], z + sz[k], y + sy[k], x + sx[k], lamr * jk);
-    }
-  }
-
-  // ---- measurements --------------------------------------------------------------
+  // ---- data term (unique (field, cell) per run) ------------------------------
   float dacc = 0.f;
   double daccd = 0.0;
   const T wd2 = T(2) * (T)D.w_data_n;
@@ -431,7 +367,7 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
   for (int i = rb + tid; i < re; i += MODIL_NT) {
     const int cell = A.run_cell[i], f = A.run_field[i];
     const int z = cell / (ny * nx), rem = cell - z * (ny * nx), y = rem / nx, x = rem - y * nx;
-    const T u = Vs(f, z, y, x);
+    const T u = (f < 4) ? uS[f * NS3 + sidx(z, y, x)] : cS[midx(z, y, x)];
     T sd = T(0), sq = T(0);
     for (int e = A.run_beg[i]; e < A.run_beg[i + 1]; ++e) {
       const T d = u - A.meas_val[e];
@@ -456,21 +392,90 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
   }
   if (!adj) return;
   __syncthreads();
+
+  // ---- phase 2: gather per owned cell -------------------------------------------
   const AdamCoef ac = acS;
-  for (int i = tid; i < F3 * NC3; i += MODIL_NT) {
-    const int f = i / NC3, cidx = i - f * NC3;
-    const int a = cidx / (C3Y * C3X), rr = cidx - a * (C3Y * C3X), b = rr / C3X, c = rr - b * C3X;
+  for (int t = tid; t < NC3; t += MODIL_NT) {
+    const int a = t / (C3Y * C3X), rr = t - a * (C3Y * C3X), b = rr / C3X, c = rr - b * C3X;
     if (a >= hz || b >= hy || c >= hx) continue;
-    const long long o = D.off[f][0] + ((long long)(z0 + a) * ny + (y0 + b)) * nx + (x0 + c);
-    const T g = gS[i] * (T)A.gscale;
-    A.g[o] = g;
-    if (mode == MODE_STEP) {
-      T p = A.p[cur][o], m = A.m[o];
-      double v = A.v[o];
-      adam_update(p, m, v, g, ac);
-      A.p[cur ^ 1][o] = p;
-      A.m[o] = m;
-      A.v[o] = v;
+    const int z = z0 + a, y = y0 + b, x = x0 + c;
+    const int X[3] = {z, y, x};
+    const int sp = sidx(z, y, x), mp = midx(z, y, x), qp = qidx(z, y, x);
+    T g[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) g[f] = gS[f * NC3 + t];
+    T cen[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) cen[f] = uS[f * NS3 + sp];
+    T AX[3];
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) AX[c3] = aS[c3 * NM + mp];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const int n = 2 - ax;
+      const int sstr = ax == 0 ? S3Y * S3X : (ax == 1 ? S3X : 1);
+      const int mstr = ax == 0 ? MY * MX : (ax == 1 ? MX : 1);
+      const int qstr = ax == 0 ? QY * QX : (ax == 1 ? QX : 1);
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int s = sd ? 1 : -1;
+        const bool ghost = (X[ax] + s < 0) || (X[ax] + s >= dims[ax]);
+        T nb[4], al[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          if (ghost) {
+            T alpha, beta;
+            ghost3<T>(f, ax, sd, alpha, beta);
+            nb[f] = alpha * cen[f] + beta;
+            al[f] = alpha;
+          } else {
+            nb[f] = uS[f * NS3 + sp + s * sstr];
+            al[f] = T(0);
+          }
+        }
+        const T mk = (ax == 2 || !ghost) ? T(1) : T(0);
+        const T Vn = mk * T(0.5) * (cen[n] + nb[n]);
+        T tn = T(0);
+#pragma unroll
+        for (int c3 = 0; c3 < 3; ++c3) {
+          const T AY = ghost ? T(0) : aS[c3 * NM + mp + s * mstr];
+          const T Wc = T(s) * (AX[c3] - AY) * cf.ih[ax];
+          tn += Wc * T(0.5) * (cen[c3] + nb[c3]);
+          // convective flux through this face via the transported component
+          g[c3] += T(0.5) * Vn * Wc * (ghost ? (T(1) + al[c3]) : T(1));
+          // viscous flux through this face
+          g[c3] += ghost ? -cf.nu * cf.ih2[ax] * AX[c3] * (al[c3] - T(1)) : cf.nu * cf.ih2[ax] * (AX[c3] - AY);
+        }
+        // convective flux through this face via the normal (transporting) velocity
+        g[n] += T(0.5) * mk * tn * (ghost ? (T(1) + al[n]) : T(1));
+        // pressure gradient of the component normal to this axis
+        if (ghost) g[3] += T(s) * al[3] * AX[n] * cf.i2h[ax];
+        else g[3] -= T(s) * aS[n * NM + mp + s * mstr] * cf.i2h[ax];
+      }
+      // continuity: cells P = X + d e_ax (|d| <= 2) that read X along this axis
+      const bool xaxis = (ax == 2);
+#pragma unroll
+      for (int d = -2; d <= 2; ++d) {
+        const int pi = X[ax] + d;
+        if (pi < 0 || pi >= dims[ax]) continue;
+        const T B = bS[qp + d * qstr];
+        g[3] += B * cont_coef<T>(xaxis, pi, dims[ax], -d, false, cf.tf, cf.ih[ax]);
+        if (d >= -1 && d <= 1) g[n] += B * cont_coef<T>(xaxis, pi, dims[ax], -d, true, cf.tf, cf.ih[ax]);
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      const long long o = D.off[f][0] + ((long long)z * ny + y) * nx + x;
+      const T gg = g[f] * (T)A.gscale;
+      A.g[o] = gg;
+      if (mode == MODE_STEP) {
+        T p = A.p[cur][o], m = A.m[o];
+        double v = A.v[o];
+        adam_update(p, m, v, gg, ac);
+        A.p[cur ^ 1][o] = p;
+        A.m[o] = m;
+        A.v[o] = v;
+      }
     }
   }
 }
@@ -504,7 +509,7 @@ k_level3(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   T* S = reinterpret_cast<T*>(smem);   // staged fine region
   T* Hx = S + L3FZ * L3FY * L3FX;      // after the x pass
   T* Hy = Hx + L3FZ * L3FY * L3X;      // after the y pass
-  const int gt = blockIdx.x;
+  const int gt = blockIdx.x, f = blockIdx.y;
   const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[l][gt];
   load_inst(&D, A, ii);
   __syncthreads();
@@ -528,7 +533,8 @@ k_level3(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   const int fy0 = max(0, 2 * Y0 - 2), fy1 = min(fy, 2 * (Y0 + cy) + 2);
   const int fx0 = max(0, 2 * X0 - 2), fx1 = min(fx, 2 * (X0 + cx) + 2);
   const int dz = fz1 - fz0, dy = fy1 - fy0, dx = fx1 - fx0;
-  for (int f = 0; f < D.nfield; ++f) {
+  if (f >= D.nfield) return;
+  {
     const T* __restrict__ gf = A.g + D.off[f][l - 1];
     for (int i = t; i < dz * dy * dx; i += MODIL_NT) {
       const int a = i / (dy * dx), r = i - a * (dy * dx), b = r / dx, c = r - b * dx;
@@ -595,7 +601,6 @@ k_level3(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
         A.v[o] = vv;
       }
     }
-    __syncthreads();  // S, Hx and Hy are reused by the next field
   }
 }
 
@@ -612,26 +617,24 @@ static cudaLaunchConfig_t cfg3(dim3 grid, size_t smem, cudaStream_t s, cudaLaunc
   return c;
 }
 
-size_t compose3_smem_bytes(size_t pyr_elems, int elem) { return (size_t)elem * F3 * pyr_elems + 64; }
-size_t resid3_smem_bytes(int elem) { return (size_t)elem * (F3 * NS3 + F3 * NC3) + 64; }
+size_t resid3_smem_bytes(int elem) { return (size_t)elem * (4 * NS3 + 4 * NM + NQ + F3 * NC3) + 64; }
 size_t level3_smem_bytes(int elem) {
   return (size_t)elem * (L3FZ * L3FY * L3FX + L3FZ * L3FY * L3X + L3FZ * L3Y * L3X) + 64;
 }
 
 template <class T>
-cudaError_t prepare_ns3d(size_t pyr_elems) {
-  cudaError_t e = raise_smem_limit(k_compose3<T>, compose3_smem_bytes(pyr_elems, sizeof(T)));
-  if (e == cudaSuccess) e = raise_smem_limit(k_resid3<T>, resid3_smem_bytes(sizeof(T)));
+cudaError_t prepare_ns3d(size_t) {
+  cudaError_t e = raise_smem_limit(k_resid3<T>, resid3_smem_bytes(sizeof(T)));
   if (e == cudaSuccess) e = raise_smem_limit(k_level3<T>, level3_smem_bytes(sizeof(T)));
   return e;
 }
 
 template <class T>
-cudaError_t launch_compose3(const Arena<T>& A, int cur, size_t pyr, cudaStream_t s) {
-  if (A.ntiles[0] == 0) return cudaSuccess;
+cudaError_t launch_prolong3(const Arena<T>& A, int level, int nfield, int cur, cudaStream_t s) {
+  if (A.ntiles[level] == 0) return cudaSuccess;
   cudaLaunchAttribute at[1];
-  cudaLaunchConfig_t c = cfg3(dim3(A.ntiles[0]), compose3_smem_bytes(pyr, sizeof(T)), s, at);
-  return cudaLaunchKernelEx(&c, k_compose3<T>, A, cur);
+  cudaLaunchConfig_t c = cfg3(dim3(A.ntiles[level], nfield), 0, s, at);
+  return cudaLaunchKernelEx(&c, k_prolong3<T>, A, level, cur);
 }
 
 template <class T>
@@ -643,20 +646,20 @@ cudaError_t launch_resid3(const Arena<T>& A, int mode, int cur, cudaStream_t s) 
 }
 
 template <class T>
-cudaError_t launch_level3(const Arena<T>& A, int level, int mode, int cur, cudaStream_t s) {
+cudaError_t launch_level3(const Arena<T>& A, int level, int nfield, int mode, int cur, cudaStream_t s) {
   if (A.ntiles[level] == 0) return cudaSuccess;
   cudaLaunchAttribute at[1];
-  cudaLaunchConfig_t c = cfg3(dim3(A.ntiles[level]), level3_smem_bytes(sizeof(T)), s, at);
+  cudaLaunchConfig_t c = cfg3(dim3(A.ntiles[level], nfield), level3_smem_bytes(sizeof(T)), s, at);
   return cudaLaunchKernelEx(&c, k_level3<T>, A, level, mode, cur);
 }
 
 template cudaError_t prepare_ns3d<float>(size_t);
 template cudaError_t prepare_ns3d<double>(size_t);
-template cudaError_t launch_compose3<float>(const Arena<float>&, int, size_t, cudaStream_t);
-template cudaError_t launch_compose3<double>(const Arena<double>&, int, size_t, cudaStream_t);
+template cudaError_t launch_prolong3<float>(const Arena<float>&, int, int, int, cudaStream_t);
+template cudaError_t launch_prolong3<double>(const Arena<double>&, int, int, int, cudaStream_t);
 template cudaError_t launch_resid3<float>(const Arena<float>&, int, int, cudaStream_t);
 template cudaError_t launch_resid3<double>(const Arena<double>&, int, int, cudaStream_t);
-template cudaError_t launch_level3<float>(const Arena<float>&, int, int, int, cudaStream_t);
-template cudaError_t launch_level3<double>(const Arena<double>&, int, int, int, cudaStream_t);
+template cudaError_t launch_level3<float>(const Arena<float>&, int, int, int, int, cudaStream_t);
+template cudaError_t launch_level3<double>(const Arena<double>&, int, int, int, int, cudaStream_t);
 
 }  // namespace modil

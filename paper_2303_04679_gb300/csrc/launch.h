@@ -52,11 +52,11 @@ constexpr int k3LZ = 2, k3LY = 8, k3LX = 16;
 template <class T>
 cudaError_t prepare_ns3d(size_t pyr_elems);
 template <class T>
-cudaError_t launch_compose3(const Arena<T>& A, int cur, size_t pyr_elems, cudaStream_t s);
+cudaError_t launch_prolong3(const Arena<T>& A, int level, int nfield, int cur, cudaStream_t s);
 template <class T>
 cudaError_t launch_resid3(const Arena<T>& A, int mode, int cur, cudaStream_t s);
 template <class T>
-cudaError_t launch_level3(const Arena<T>& A, int level, int mode, int cur, cudaStream_t s);
+cudaError_t launch_level3(const Arena<T>& A, int level, int nfield, int mode, int cur, cudaStream_t s);
 size_t tail_smem_bytes(const TailPlan& tp, int elem_bytes);
 size_t tail_instance_bytes(int L, int ts, const int (*n)[3], int nf, int elem_bytes);
 template <class T>

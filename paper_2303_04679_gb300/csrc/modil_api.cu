@@ -75,7 +75,7 @@ struct Plan {
   std::vector<double> meas_val, run_v0;
   size_t pyr_elems = 0;
   // arena offsets (bytes)
-  size_t o_p0, o_p1, o_m, o_v, o_g, o_uf, o_kq, o_km, o_kv, o_kg, o_aux, o_part, o_rptr, o_rcell,
+  size_t o_p0, o_p1, o_m, o_v, o_g, o_uf, o_wl, o_kq, o_km, o_kv, o_kg, o_aux, o_part, o_rptr, o_rcell,
       o_rfield, o_rbeg, o_mval, o_rv0, o_inst, o_st, o_cnt, o_q, o_ti[MODIL_MAXL], total;
 };
 
@@ -237,25 +237,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
     D.lr = q.adam_lr; D.b1 = q.adam_beta1; D.b2 = q.adam_beta2; D.eps = q.adam_eps;
     // pyramid bound of this instance (unclipped worst case, clipped by level size)
     if (three) {
-      // exact: per axis the largest region over the tile positions; the axes
-      // are independent, so the product of the maxima is the largest box
-      long long tot = 0;
-      const int tdim[3] = {k3TZ, k3TY, k3TX};
-      for (int l = 0; l < L; ++l) {
-        long long box = 1;
-        for (int a = 0; a < 3; ++a) {
-          const int n0 = ip.n[0][a], nl = ip.n[l][a], k = (1 << (l + 1)) - 2;
-          int mx = 0;
-          for (int s0 = 0; s0 < n0; s0 += tdim[a]) {
-            const int lo = std::max(0, (s0 - k) >> l);
-            const int hi = std::min(nl - 1, (std::min(n0, s0 + tdim[a]) - 1 + k) >> l);
-            mx = std::max(mx, hi - lo + 1);
-          }
-          box *= mx;
-        }
-        tot += box;
-      }
-      P.pyr_elems = std::max<size_t>(P.pyr_elems, (size_t)tot);
+      // composition is level by level (no per-tile pyramid)
     } else {
       const int hu = (P.pde == MODIL_PDE_NS2D) ? 4 : 2;  // halo of the composed field
       long long hy = TY + 2 * hu, hx = TX + 2 * hu, tot = 0;
@@ -327,6 +309,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   P.o_v = take(8 * P.n_param);
   P.o_g = take(P.esz * P.n_param);
   P.o_uf = take(P.esz * P.n_fine);
+  P.o_wl = take(P.pde == MODIL_PDE_NS3D ? P.esz * P.n_param : 0);
   P.o_kq = take(P.esz * P.n_k);
   P.o_km = take(P.esz * P.n_k);
   P.o_kv = take(8 * P.n_k);
@@ -375,6 +358,7 @@ void fill_arena(modil_problem* p, Arena<T>& A) {
   A.v = reinterpret_cast<double*>(b + P.o_v);
   A.g = reinterpret_cast<T*>(b + P.o_g);
   A.ufine = reinterpret_cast<T*>(b + P.o_uf);
+  A.wl = reinterpret_cast<T*>(b + P.o_wl);
   A.kq = reinterpret_cast<T*>(b + P.o_kq);
   A.km = reinterpret_cast<T*>(b + P.o_km);
   A.kv = reinterpret_cast<double*>(b + P.o_kv);
@@ -426,12 +410,16 @@ modil_status run_pass_t(modil_problem* p, Arena<T>& A, int mode, int cur, cudaEv
   int k = 0;
   if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
   if (P.pde == MODIL_PDE_NS3D) {
-    CUDA_TRY(launch_compose3<T>(A, cur, P.pyr_elems, p->stream));
+    // compose level by level (coarse to fine), then the fused residual pass
+    for (int l = std::max(0, P.max_lev - 2); l >= 0; --l) {
+      CUDA_TRY(launch_prolong3<T>(A, l, P.nfield, cur, p->stream));
+      if (ev && (l > 0 || mode != MODE_COMPOSE)) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+    }
     if (mode == MODE_COMPOSE) {
+      if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
       if (nev) *nev = k;
       return MODIL_OK;
     }
-    if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
     CUDA_TRY(launch_resid3<T>(A, mode, cur, p->stream));
   } else if (P.pde == MODIL_PDE_NS2D) {
     CUDA_TRY(launch_fine_ns2d<T>(A, P.cfg, mode, cur, P.pyr_elems, p->stream));
@@ -442,7 +430,7 @@ modil_status run_pass_t(modil_problem* p, Arena<T>& A, int mode, int cur, cudaEv
   if (mode == MODE_GRAD || mode == MODE_STEP)
     for (int l = 1; l < P.max_tail; ++l) {
       if (P.pde == MODIL_PDE_NS3D)
-        CUDA_TRY(launch_level3<T>(A, l, mode, cur, p->stream));
+        CUDA_TRY(launch_level3<T>(A, l, P.nfield, mode, cur, p->stream));
       else
         CUDA_TRY(launch_level<T>(A, l, mode, cur, p->stream));
       if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
@@ -462,7 +450,7 @@ modil_status run_pass(modil_problem* p, int mode, cudaEvent_t* ev = nullptr, int
 }
 
 int kernels_per_step(const Plan& P) {
-  return (P.pde == MODIL_PDE_NS3D ? 2 : 1) + (P.max_tail - 1) + 1;
+  return (P.pde == MODIL_PDE_NS3D ? std::max(1, P.max_lev - 1) + 1 : 1) + (P.max_tail - 1) + 1;
 }
 
 modil_status read_terms(modil_problem* p, double* terms) {

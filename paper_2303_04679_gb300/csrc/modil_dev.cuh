@@ -73,7 +73,8 @@ struct Arena {
   T* m;
   double* v;
   T* g;
-  T* ufine;            // composed-field scratch (MODE_COMPOSE)
+  T* ufine;            // composed-field scratch (MODE_COMPOSE; every pass of the 3-D family)
+  T* wl;               // 3-D family: composed coarse levels w_l (l >= 1), same offsets as p
   T* kq;               // conductivity nodes (heat), Adam moments and gradient
   T* km;
   double* kv;
