@@ -23,6 +23,8 @@
 //               atomics), the measurements, dL/du and Adam on level 1;
 //   k_level3    one block per (coarse tile, field): restriction of the level
 //               above (transposed interpolation) and Adam.
+#include <cuda.h>
+
 #include <algorithm>
 
 #include "launch.h"
@@ -41,48 +43,121 @@ constexpr int F3 = 5;
 // Composition, one level per launch (Horner's scheme, Section 2.2):
 // w_l = u_l + T w_{l+1}; the coarsest composed level is u_{L-1} itself (read
 // from the parameters), w_0 goes to the composed-field buffer, the others to
-// the per-level scratch.  One thread per cell, cells of a tile x fastest.
+// the per-level scratch.  One block per (coarse tile of level l+1, field): the
+// coarse tile and a halo of one cell are staged in shared memory, and each
+// thread writes the 8 fine children of its coarse cell (separable weights: per
+// axis the even child takes 1/4, 3/4 of cells j-1, j and the odd child 3/4,
+// 1/4 of cells j, j+1; past the first or last coarse centre the line through
+// the two outermost centres is extended, 5/4 and -1/4; a single coarse cell
+// is copied).
 // ---------------------------------------------------------------------------
+constexpr int PZ = k3LZ + 2, PY = k3LY + 2, PX = k3LX + 2;  // staged coarse region
+
+template <class T>
+__device__ __forceinline__ void child_weights(int j, int nc, T* we, T* wo) {
+  // coefficients of (c[j-1], c[j], c[j+1]) for the even and the odd child of j
+  if (nc == 1) {
+    we[0] = T(0); we[1] = T(1); we[2] = T(0);
+    wo[0] = T(0); wo[1] = T(1); wo[2] = T(0);
+    return;
+  }
+  if (j == 0) { we[0] = T(0); we[1] = T(1.25); we[2] = T(-0.25); }
+  else { we[0] = T(0.25); we[1] = T(0.75); we[2] = T(0); }
+  if (j == nc - 1) { wo[0] = T(-0.25); wo[1] = T(1.25); wo[2] = T(0); }
+  else { wo[0] = T(0); wo[1] = T(0.75); wo[2] = T(0.25); }
+}
+
 template <class T>
 __global__ void __launch_bounds__(MODIL_NT)
 k_prolong3(const __grid_constant__ Arena<T> A, int l, int cur) {
+  static_assert(k3LZ * k3LY * k3LX == MODIL_NT, "one coarse cell per thread");
   __shared__ DevInst D;
+  __shared__ T cS[PZ * PY * PX];
   const int gt = blockIdx.x, f = blockIdx.y;
-  const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[l][gt];
+  const int lc = l + 1;  // the coarse level
+  const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[lc][gt];
   load_inst(&D, A, ii);
   __syncthreads();
   pdl_wait();
   pdl_trigger();
-  // an instance's coarsest level is read from the parameters directly, except
-  // a single-level instance, whose level 0 is copied to the composed buffer
-  if (f >= D.nfield || l > D.nlev - 1 || (l == D.nlev - 1 && l > 0)) return;
-  const bool copy = (l == D.nlev - 1);
-  const int tz = l == 0 ? C3Z : k3LZ, ty = l == 0 ? C3Y : k3LY, tx = l == 0 ? C3X : k3LX;
-  const int local = gt - D.tile_base[l];
-  const int per_z = D.nt[l][1] * D.nt[l][2];
+  if (f >= D.nfield || lc > D.nlev - 1) return;
+  const int local = gt - D.tile_base[lc];
+  const int per_z = D.nt[lc][1] * D.nt[lc][2];
   const int bz = local / per_z, br = local - bz * per_z;
-  const int by = br / D.nt[l][2], bx = br - by * D.nt[l][2];
-  const int nz = D.n[l][0], ny = D.n[l][1], nx = D.n[l][2];
-  const int lc = copy ? l : l + 1;
+  const int by = br / D.nt[lc][2], bx = br - by * D.nt[lc][2];
   const int cz = D.n[lc][0], cy = D.n[lc][1], cx = D.n[lc][2];
-  const T* __restrict__ u = A.p[cur] + D.off[f][l];
+  const int Z0 = bz * k3LZ, Y0 = by * k3LY, X0 = bx * k3LX;
   const T* __restrict__ w = (lc == D.nlev - 1 ? A.p[cur] : A.wl) + D.off[f][lc];
+  // stage the coarse tile with a halo of one cell (clamped at the grid edge;
+  // clamped copies only meet zero weights)
+  for (int i = threadIdx.x; i < PZ * PY * PX; i += MODIL_NT) {
+    const int a = i / (PY * PX), r = i - a * (PY * PX), b = r / PX, c = r - b * PX;
+    const int z = min(max(Z0 - 1 + a, 0), cz - 1), y = min(max(Y0 - 1 + b, 0), cy - 1),
+              x = min(max(X0 - 1 + c, 0), cx - 1);
+    cS[i] = w[((long long)z * cy + y) * cx + x];
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int oz = t / (k3LY * k3LX), oy = (t / k3LX) % k3LY, ox = t % k3LX;
+  const int Z = Z0 + oz, Y = Y0 + oy, Xc = X0 + ox;
+  if (Z >= cz || Y >= cy || Xc >= cx) return;
+  T ez[3], odz[3], ey[3], ody[3], ex[3], odx[3];
+  child_weights<T>(Z, cz, ez, odz);
+  child_weights<T>(Y, cy, ey, ody);
+  child_weights<T>(Xc, cx, ex, odx);
+  // along x: for the 3 x 3 (z, y) rows around the cell, the even and odd x children
+  T hx[2][3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const T* row = cS + ((oz + a) * PY + (oy + b)) * PX + ox;
+      hx[0][a][b] = ex[0] * row[0] + ex[1] * row[1] + ex[2] * row[2];
+      hx[1][a][b] = odx[0] * row[0] + odx[1] * row[1] + odx[2] * row[2];
+    }
+  const int nyf = 2 * cy, nxf = 2 * cx;
+  const T* __restrict__ u = A.p[cur] + D.off[f][l];
   T* __restrict__ out = l == 0 ? A.ufine + D.fine_off[f] : A.wl + D.off[f][l];
-  for (int t = threadIdx.x; t < tz * ty * tx; t += MODIL_NT) {
-    const int x = bx * tx + t % tx, y = by * ty + (t / tx) % ty, z = bz * tz + t / (tx * ty);
-    if (x >= nx || y >= ny || z >= nz) continue;
-    int z0, z1, y0, y1, x0, x1;
-    T wz0, wz1, wy0, wy1, wx0, wx1;
-    prolong_taps<T>(z, cz, z0, z1, wz0, wz1);
-    prolong_taps<T>(y, cy, y0, y1, wy0, wy1);
-    prolong_taps<T>(x, cx, x0, x1, wx0, wx1);
-    auto W = [&](int a, int b, int c) { return w[((long long)a * cy + b) * cx + c]; };
-    const T add = wz0 * (wy0 * (wx0 * W(z0, y0, x0) + wx1 * W(z0, y0, x1)) +
-                         wy1 * (wx0 * W(z0, y1, x0) + wx1 * W(z0, y1, x1))) +
-                  wz1 * (wy0 * (wx0 * W(z1, y0, x0) + wx1 * W(z1, y0, x1)) +
-                         wy1 * (wx0 * W(z1, y1, x0) + wx1 * W(z1, y1, x1)));
+#pragma unroll
+  for (int cz2 = 0; cz2 < 2; ++cz2) {
+    const T* wz = cz2 ? odz : ez;
+#pragma unroll
+    for (int cy2 = 0; cy2 < 2; ++cy2) {
+      const T* wy = cy2 ? ody : ey;
+      const long long rowo = ((long long)(2 * Z + cz2) * nyf + (2 * Y + cy2)) * nxf + 2 * Xc;
+#pragma unroll
+      for (int cx2 = 0; cx2 < 2; ++cx2) {
+        T v = T(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          v += wz[a] * (wy[0] * hx[cx2][a][0] + wy[1] * hx[cx2][a][1] + wy[2] * hx[cx2][a][2]);
+        out[rowo + cx2] = u[rowo + cx2] + v;
+      }
+    }
+  }
+}
+
+// Single-level instances: the composed field is level 0 itself.
+template <class T>
+__global__ void k_copy3(const __grid_constant__ Arena<T> A, int cur) {
+  __shared__ DevInst D;
+  const int gt = blockIdx.x, f = blockIdx.y;
+  const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[0][gt];
+  load_inst(&D, A, ii);
+  __syncthreads();
+  pdl_wait();
+  pdl_trigger();
+  if (f >= D.nfield || D.nlev != 1) return;
+  const int local = gt - D.tile_base[0];
+  const int per_z = D.nt[0][1] * D.nt[0][2];
+  const int bz = local / per_z, br = local - bz * per_z;
+  const int by = br / D.nt[0][2], bx = br - by * D.nt[0][2];
+  const int nz = D.n[0][0], ny = D.n[0][1], nx = D.n[0][2];
+  for (int t = threadIdx.x; t < C3Z * C3Y * C3X; t += blockDim.x) {
+    const int z = bz * C3Z + t / (C3Y * C3X), y = by * C3Y + (t / C3X) % C3Y, x = bx * C3X + t % C3X;
+    if (z >= nz || y >= ny || x >= nx) continue;
     const long long o = ((long long)z * ny + y) * nx + x;
-    out[o] = copy ? u[o] : u[o] + add;
+    A.ufine[D.fine_off[f] + o] = A.p[cur][D.off[f][0] + o];
   }
 }
 
@@ -139,9 +214,9 @@ __device__ __forceinline__ T cont3(const T* s, const bool* in, const Ns3Coef<T>&
 // P's position along the axis: i in [0, n); x axis: inflow face at i = 0
 // (flux 1), outflow at n - 1 (flux u_P, odd pressure ghost); y, z: walls
 // (no flux, even pressure ghosts).
-template <class T>
+template <class T, bool INTR>
 __device__ __forceinline__ T cont_coef(bool xaxis, int i, int n, int o, bool vel, T tf, T ih) {
-  const bool in0 = i < n - 1, in1 = i > 0, in2 = i < n - 2, in3 = i > 1;
+  const bool in0 = INTR || i < n - 1, in1 = INTR || i > 0, in2 = INTR || i < n - 2, in3 = INTR || i > 1;
   const T q = T(0.25) * tf, h = T(0.5);
   T ce = T(0), cw = T(0);  // partials of the + face flux and of the - face flux
   if (vel) {
@@ -182,107 +257,64 @@ __device__ __forceinline__ T cont_coef(bool xaxis, int i, int n, int o, bool vel
 constexpr int MZ = C3Z + 2, MY = C3Y + 2, MX = C3X + 2, NM = MZ * MY * MX;    // tile + 1
 constexpr int QZ = C3Z + 4, QY = C3Y + 4, QX = C3X + 4, NQ = QZ * QY * QX;    // tile + 2
 
-template <class T>
-__global__ void __launch_bounds__(MODIL_NT)
-k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ DevInst D;
-  __shared__ double red[16];
-  __shared__ AdamCoef acS;
-  T* uS = reinterpret_cast<T*>(smem);   // u, v, w, p with a halo of 4: 4 x NS3
-  T* cS = uS + 4 * NS3;                 // chihat on the tile plus one cell: NM
-  T* aS = cS + NM;                      // momentum adjoint weights: 3 x NM
-  T* bS = aS + 3 * NM;                  // continuity adjoint weights: NQ
-  T* gS = bS + NQ;                      // own-residual and data terms: F3 x NC3
-  float* redf = reinterpret_cast<float*>(red);
-  const int tid = threadIdx.x;
-  const int gt = blockIdx.x;
-  const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[0][gt];
-  load_inst(&D, A, ii);
-  const int rb = A.run_ptr[gt], re = A.run_ptr[gt + 1];
-  __syncthreads();
-  const int nz = D.n[0][0], ny = D.n[0][1], nx = D.n[0][2];
-  const int local = gt - D.tile_base[0];
-  const int per_z = D.nt[0][1] * D.nt[0][2];
-  const int tz = local / per_z, tr = local - tz * per_z;
-  const int ty = tr / D.nt[0][2], tx = tr - ty * D.nt[0][2];
-  const int z0 = tz * C3Z, y0 = ty * C3Y, x0 = tx * C3X;
-  const int hz = min(C3Z, nz - z0), hy = min(C3Y, ny - y0), hx = min(C3X, nx - x0);
-  if (tid == 0) acS = adam_coef(D, A.st[ii]);
-  for (int i = tid; i < F3 * NC3; i += MODIL_NT) gS[i] = T(0);
-  pdl_wait();
-  pdl_trigger();
-  for (int f = 0; f < 4; ++f) {
-    const T* src = A.ufine + D.fine_off[f];
-    for (int i = tid; i < NS3; i += MODIL_NT) {
-      const int a = i / (S3Y * S3X), r = i - a * (S3Y * S3X), b = r / S3X, c = r - b * S3X;
-      const int z = z0 - H3 + a, y = y0 - H3 + b, x = x0 - H3 + c;
-      if (z >= 0 && z < nz && y >= 0 && y < ny && x >= 0 && x < nx)
-        cp_async(uS + f * NS3 + i, src + ((long long)z * ny + y) * nx + x);
-    }
-  }
-  {
-    const T* src = A.ufine + D.fine_off[4];
-    for (int i = tid; i < NM; i += MODIL_NT) {
-      const int a = i / (MY * MX), r = i - a * (MY * MX), b = r / MX, c = r - b * MX;
-      const int z = z0 - 1 + a, y = y0 - 1 + b, x = x0 - 1 + c;
-      if (z >= 0 && z < nz && y >= 0 && y < ny && x >= 0 && x < nx)
-        cp_async(cS + i, src + ((long long)z * ny + y) * nx + x);
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
+// chihat is staged on the tile plus one cell in z and y and plus four in x
+// (a TMA box starts on a 16-byte boundary): [CZ3][CY3][CX3], x offset 4.
+constexpr int CZ3 = C3Z + 2, CY3 = C3Y + 2, CX3 = C3X + 8, NC3S = CZ3 * CY3 * CX3;
 
+template <class T>
+struct R3 {  // per-tile context of the residual kernel
+  T *uS, *cS, *aS, *bS, *gS;
+  int z0, y0, x0, hz, hy, hx, nz, ny, nx;
   Ns3Coef<T> cf;
-  for (int a = 0; a < 3; ++a) {
-    const double hh = D.h[a];
-    cf.ih[a] = (T)(1.0 / hh);
-    cf.ih2[a] = (T)(1.0 / (hh * hh));
-    cf.i2h[a] = (T)(0.5 / hh);
+  T Rs;
+  __device__ int sidx(int z, int y, int x) const {
+    return ((z - z0 + H3) * S3Y + (y - y0 + H3)) * S3X + (x - x0 + H3);
   }
-  cf.nu = (T)(D.coef[1] / D.coef[0]);  // D / Re
-  cf.lam = (T)D.coef[2];
-  cf.tf = (T)D.coef[3];
-  const int dims[3] = {nz, ny, nx};
-  auto sidx = [&](int z, int y, int x) { return ((z - z0 + H3) * S3Y + (y - y0 + H3)) * S3X + (x - x0 + H3); };
-  auto midx = [&](int z, int y, int x) { return ((z - z0 + 1) * MY + (y - y0 + 1)) * MX + (x - x0 + 1); };
-  auto qidx = [&](int z, int y, int x) { return ((z - z0 + 2) * QY + (y - y0 + 2)) * QX + (x - x0 + 2); };
-  auto owned = [&](int z, int y, int x) {
+  __device__ int cidx(int z, int y, int x) const {
+    return ((z - z0 + 1) * CY3 + (y - y0 + 1)) * CX3 + (x - x0 + 4);
+  }
+  __device__ int midx(int z, int y, int x) const {
+    return ((z - z0 + 1) * MY + (y - y0 + 1)) * MX + (x - x0 + 1);
+  }
+  __device__ bool owned(int z, int y, int x) const {
     return z >= z0 && z < z0 + hz && y >= y0 && y < y0 + hy && x >= x0 && x < x0 + hx;
-  };
-  const T Rs = T(2) * (T)D.w_res_dV;
-  const bool adj = (mode != MODE_LOSS);
-  float racc = 0.f;
-  double raccd = 0.0;
+  }
+};
+
+// Phase 1: momentum weights on the tile plus one cell, own-residual terms of
+// owned cells, continuity weights on the tile plus two cells.  INTR: the tile
+// and four cells around it lie inside the grid (no ghost, wall or flag logic).
+template <class T, bool INTR>
+__device__ __forceinline__ void r3_phase1(const R3<T>& c, bool adj, float& racc, double& raccd) {
+  const Ns3Coef<T>& cf = c.cf;
+  const int dims[3] = {c.nz, c.ny, c.nx};
   auto addsq = [&](T r) {
     if (sizeof(T) == 4) racc += (float)(r * r);
     else raccd += (double)(r * r);
   };
-
-  // ---- phase 1a: momentum on the tile plus one cell -------------------------
-  for (int i = tid; i < NM; i += MODIL_NT) {
-    const int a = i / (MY * MX), rr = i - a * (MY * MX), b = rr / MX, c = rr - b * MX;
-    const int z = z0 - 1 + a, y = y0 - 1 + b, x = x0 - 1 + c;
-    if (z < 0 || z >= nz || y < 0 || y >= ny || x < 0 || x >= nx) continue;
+  for (int i = threadIdx.x; i < NM; i += MODIL_NT) {
+    const int a = i / (MY * MX), rr = i - a * (MY * MX), b = rr / MX, cc = rr - b * MX;
+    const int z = c.z0 - 1 + a, y = c.y0 - 1 + b, x = c.x0 - 1 + cc;
+    if (!INTR && (z < 0 || z >= c.nz || y < 0 || y >= c.ny || x < 0 || x >= c.nx)) continue;
     const int P[3] = {z, y, x};
-    const int sp = sidx(z, y, x);
+    const int sp = c.sidx(z, y, x);
     T cen[4], nv[4][3][2];
     bool gh[3][2];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) cen[f] = uS[f * NS3 + sp];
+    for (int f = 0; f < 4; ++f) cen[f] = c.uS[f * NS3 + sp];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax)
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
         const int q = P[ax] + (sd ? 1 : -1);
-        const bool inside = q >= 0 && q < dims[ax];
+        const bool inside = INTR || (q >= 0 && q < dims[ax]);
         gh[ax][sd] = !inside;
         const int stride = ax == 0 ? S3Y * S3X : (ax == 1 ? S3X : 1);
         const int sq = sp + (sd ? stride : -stride);
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
           if (inside) {
-            nv[f][ax][sd] = uS[f * NS3 + sq];
+            nv[f][ax][sd] = c.uS[f * NS3 + sq];
           } else {
             T alpha, beta;
             ghost3<T>(f, ax, sd, alpha, beta);
@@ -290,7 +322,7 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
           }
         }
       }
-    const T chat = cS[i];
+    const T chat = c.cS[c.cidx(z, y, x)];
     // chi and 1 - chi each from its own logistic: 1 - chi is never formed by
     // subtraction, which loses all digits in FP32 where chi is near 1
     const T chi = T(1) / (T(1) + exp(-(chat + T(5))));
@@ -305,7 +337,8 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
         Vf[ax][sd] = mk * T(0.5) * (cen[n] + nv[n][ax][sd]);
       }
     }
-    const bool own = owned(z, y, x);
+    const bool own = c.owned(z, y, x);
+    const int ot = ((z - c.z0) * C3Y + (y - c.y0)) * C3X + (x - c.x0);
     T gch = T(0);
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
@@ -321,43 +354,254 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
       const T M = conv + (nv[3][cax][1] - nv[3][cax][0]) * cf.i2h[cax] - cf.nu * lap;
       const T r = om * M + cf.lam * chi * phi;
       if (own) addsq(r);
-      const T R = Rs * r;
-      aS[comp * NM + i] = R * om;
+      const T R = c.Rs * r;
+      c.aS[comp * NM + i] = R * om;
       if (own && adj) {
-        gS[comp * NC3 + ((z - z0) * C3Y + (y - y0)) * C3X + (x - x0)] = R * cf.lam * chi;
+        c.gS[comp * NC3 + ot] = R * cf.lam * chi;
         gch += R * chi * om * (cf.lam * phi - M);
       }
     }
-    if (own && adj) gS[4 * NC3 + ((z - z0) * C3Y + (y - y0)) * C3X + (x - x0)] = gch;
+    if (own && adj) c.gS[4 * NC3 + ot] = gch;
   }
-
-  // ---- phase 1b: continuity on the tile plus two cells ----------------------
-  {
-    const int sf[22] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
-    const int sz[22] = {0, 0, 0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, 2, -2};
-    const int sy[22] = {0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, 2, -2, 0, 0, 0, 0};
-    const int sx[22] = {0, 1, -1, 0, 0, 0, 0, 0, 0, 0, 1, -1, 2, -2, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = tid; i < NQ; i += MODIL_NT) {
-      const int a = i / (QY * QX), rr = i - a * (QY * QX), b = rr / QX, c = rr - b * QX;
-      const int z = z0 - 2 + a, y = y0 - 2 + b, x = x0 - 2 + c;
-      if (z < 0 || z >= nz || y < 0 || y >= ny || x < 0 || x >= nx) continue;
-      bool in[12];
-      in[0] = x < nx - 1; in[1] = x > 0; in[2] = x < nx - 2; in[3] = x > 1;
-      in[4] = y < ny - 1; in[5] = y > 0; in[6] = y < ny - 2; in[7] = y > 1;
-      in[8] = z < nz - 1; in[9] = z > 0; in[10] = z < nz - 2; in[11] = z > 1;
-      T s[22];
-      const int sp = sidx(z, y, x);
+  const int sf[22] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
+  const int sz[22] = {0, 0, 0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, 2, -2};
+  const int sy[22] = {0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, 2, -2, 0, 0, 0, 0};
+  const int sx[22] = {0, 1, -1, 0, 0, 0, 0, 0, 0, 0, 1, -1, 2, -2, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < NQ; i += MODIL_NT) {
+    const int a = i / (QY * QX), rr = i - a * (QY * QX), b = rr / QX, cc = rr - b * QX;
+    const int z = c.z0 - 2 + a, y = c.y0 - 2 + b, x = c.x0 - 2 + cc;
+    if (!INTR && (z < 0 || z >= c.nz || y < 0 || y >= c.ny || x < 0 || x >= c.nx)) continue;
+    bool in[12];
+    in[0] = INTR || x < c.nx - 1; in[1] = INTR || x > 0; in[2] = INTR || x < c.nx - 2; in[3] = INTR || x > 1;
+    in[4] = INTR || y < c.ny - 1; in[5] = INTR || y > 0; in[6] = INTR || y < c.ny - 2; in[7] = INTR || y > 1;
+    in[8] = INTR || z < c.nz - 1; in[9] = INTR || z > 0; in[10] = INTR || z < c.nz - 2; in[11] = INTR || z > 1;
+    T sv[22];
+    const int sp = c.sidx(z, y, x);
+    // every slot lies inside the staged box; slots outside the grid hold
+    // unused values (cont3 takes the ghost instead, by the flags)
 #pragma unroll
-      for (int k = 0; k < 22; ++k) {
-        const int zz = z + sz[k], yy = y + sy[k], xx = x + sx[k];
-        const bool ok = zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx;
-        s[k] = ok ? uS[sf[k] * NS3 + sp + (sz[k] * S3Y + sy[k]) * S3X + sx[k]] : T(0);
+    for (int k = 0; k < 22; ++k) sv[k] = c.uS[sf[k] * NS3 + sp + (sz[k] * S3Y + sy[k]) * S3X + sx[k]];
+    const T r = cont3(sv, in, cf);
+    if (c.owned(z, y, x)) addsq(r);
+    c.bS[i] = c.Rs * r;
+  }
+}
+
+// Phase 2: gather of the adjoint for every owned cell; dL/du and Adam.
+template <class T, bool INTR>
+__device__ __forceinline__ void r3_phase2(const R3<T>& c, const Arena<T>& A, const DevInst& D, int mode, int cur,
+                                          const AdamCoef& ac) {
+  const Ns3Coef<T>& cf = c.cf;
+  const int dims[3] = {c.nz, c.ny, c.nx};
+  for (int t = threadIdx.x; t < NC3; t += MODIL_NT) {
+    const int a = t / (C3Y * C3X), rr = t - a * (C3Y * C3X), b = rr / C3X, cc = rr - b * C3X;
+    if (!INTR && (a >= c.hz || b >= c.hy || cc >= c.hx)) continue;
+    const int z = c.z0 + a, y = c.y0 + b, x = c.x0 + cc;
+    const int X[3] = {z, y, x};
+    const int sp = c.sidx(z, y, x), mp = c.midx(z, y, x);
+    const int qp = ((a + 2) * QY + (b + 2)) * QX + (cc + 2);
+    T g[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) g[f] = c.gS[f * NC3 + t];
+    T cen[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) cen[f] = c.uS[f * NS3 + sp];
+    T AX[3];
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) AX[c3] = c.aS[c3 * NM + mp];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const int n = 2 - ax;
+      const int sstr = ax == 0 ? S3Y * S3X : (ax == 1 ? S3X : 1);
+      const int mstr = ax == 0 ? MY * MX : (ax == 1 ? MX : 1);
+      const int qstr = ax == 0 ? QY * QX : (ax == 1 ? QX : 1);
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int s = sd ? 1 : -1;
+        const bool ghost = !INTR && ((X[ax] + s < 0) || (X[ax] + s >= dims[ax]));
+        T nb[4], al[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          if (ghost) {
+            T alpha, beta;
+            ghost3<T>(f, ax, sd, alpha, beta);
+            nb[f] = alpha * cen[f] + beta;
+            al[f] = alpha;
+          } else {
+            nb[f] = c.uS[f * NS3 + sp + s * sstr];
+            al[f] = T(0);
+          }
+        }
+        const T mk = (ax == 2 || !ghost) ? T(1) : T(0);
+        const T Vn = mk * T(0.5) * (cen[n] + nb[n]);
+        T tn = T(0);
+#pragma unroll
+        for (int c3 = 0; c3 < 3; ++c3) {
+          const T AY = ghost ? T(0) : c.aS[c3 * NM + mp + s * mstr];
+          const T Wc = T(s) * (AX[c3] - AY) * cf.ih[ax];
+          tn += Wc * T(0.5) * (cen[c3] + nb[c3]);
+          // convective flux through this face via the transported component
+          g[c3] += T(0.5) * Vn * Wc * (ghost ? (T(1) + al[c3]) : T(1));
+          // viscous flux through this face
+          g[c3] += ghost ? -cf.nu * cf.ih2[ax] * AX[c3] * (al[c3] - T(1)) : cf.nu * cf.ih2[ax] * (AX[c3] - AY);
+        }
+        // convective flux through this face via the normal (transporting) velocity
+        g[n] += T(0.5) * mk * tn * (ghost ? (T(1) + al[n]) : T(1));
+        // pressure gradient of the component normal to this axis
+        if (ghost) g[3] += T(s) * al[3] * AX[n] * cf.i2h[ax];
+        else g[3] -= T(s) * c.aS[n * NM + mp + s * mstr] * cf.i2h[ax];
       }
-      const T r = cont3(s, in, cf);
-      if (owned(z, y, x)) addsq(r);
-      bS[i] = Rs * r;
+      // continuity: cells P = X + d e_ax (|d| <= 2) that read X along this axis
+      const bool xaxis = (ax == 2);
+#pragma unroll
+      for (int d = -2; d <= 2; ++d) {
+        const int pi = X[ax] + d;
+        if (!INTR && (pi < 0 || pi >= dims[ax])) continue;
+        const T B = c.bS[qp + d * qstr];
+        g[3] += B * cont_coef<T, INTR>(xaxis, pi, dims[ax], -d, false, cf.tf, cf.ih[ax]);
+        if (d >= -1 && d <= 1) g[n] += B * cont_coef<T, INTR>(xaxis, pi, dims[ax], -d, true, cf.tf, cf.ih[ax]);
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      const long long o = D.off[f][0] + ((long long)z * c.ny + y) * c.nx + x;
+      const T gg = g[f] * (T)A.gscale;
+      A.g[o] = gg;
+      if (mode == MODE_STEP) {
+        T p = A.p[cur][o], m = A.m[o];
+        double v = A.v[o];
+        adam_update(p, m, v, gg, ac);
+        A.p[cur ^ 1][o] = p;
+        A.m[o] = m;
+        A.v[o] = v;
+      }
     }
   }
+}
+
+__device__ __forceinline__ uint32_t smem_addr3(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <class T>
+__global__ void __launch_bounds__(MODIL_NT)
+k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur, const __grid_constant__ CUtensorMap tm_u,
+         const __grid_constant__ CUtensorMap tm_c, int use_tma) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ DevInst D;
+  __shared__ double red[16];
+  __shared__ AdamCoef acS;
+  __shared__ Ns3Coef<T> cfS;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int tma_ok;
+  R3<T> c;
+  c.uS = reinterpret_cast<T*>(smem);   // u, v, w, p with a halo of 4: 4 x NS3
+  c.cS = c.uS + 4 * NS3;               // chihat: NC3S
+  c.aS = c.cS + NC3S;                  // momentum adjoint weights: 3 x NM
+  c.bS = c.aS + 3 * NM;                // continuity adjoint weights: NQ
+  c.gS = c.bS + NQ;                    // own-residual and data terms: F3 x NC3
+  float* redf = reinterpret_cast<float*>(red);
+  const int tid = threadIdx.x;
+  const int gt = blockIdx.x;
+  const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[0][gt];
+  load_inst(&D, A, ii);
+  const int rb = A.run_ptr[gt], re = A.run_ptr[gt + 1];
+  __syncthreads();
+  c.nz = D.n[0][0]; c.ny = D.n[0][1]; c.nx = D.n[0][2];
+  const int local = gt - D.tile_base[0];
+  const int per_z = D.nt[0][1] * D.nt[0][2];
+  const int tz = local / per_z, tr = local - tz * per_z;
+  const int ty = tr / D.nt[0][2], tx = tr - ty * D.nt[0][2];
+  c.z0 = tz * C3Z; c.y0 = ty * C3Y; c.x0 = tx * C3X;
+  c.hz = min(C3Z, c.nz - c.z0); c.hy = min(C3Y, c.ny - c.y0); c.hx = min(C3X, c.nx - c.x0);
+  if (tid == 0) {
+    acS = adam_coef(D, A.st[ii]);
+    // stencil coefficients: FP64 divisions by one thread (GB300 runs FP64 at
+    // 1/64 of the FP32 rate; per thread they would cost more than the stencils)
+    for (int a = 0; a < 3; ++a) {
+      const double hh = D.h[a];
+      cfS.ih[a] = (T)(1.0 / hh);
+      cfS.ih2[a] = (T)(1.0 / (hh * hh));
+      cfS.i2h[a] = (T)(0.5 / hh);
+    }
+    cfS.nu = (T)(D.coef[1] / D.coef[0]);  // D / Re
+    cfS.lam = (T)D.coef[2];
+    cfS.tf = (T)D.coef[3];
+    tma_ok = 1;
+    if (use_tma) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr3(&bar)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+  }
+  for (int i = tid; i < F3 * NC3; i += MODIL_NT) c.gS[i] = T(0);
+  __syncthreads();
+  pdl_wait();
+  pdl_trigger();
+  if (use_tma) {
+    // one 4-D box (x, y, z, field 0..3) and one chihat box; reads outside the
+    // grid return zeros (never used: ghosts are formed from the cell values)
+    if (tid == 0) {
+      const uint32_t bytes = (uint32_t)(sizeof(T) * (4 * NS3 + NC3S));
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr3(&bar)), "r"(bytes)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+          " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_addr3(c.uS)),
+          "l"(reinterpret_cast<uint64_t>(&tm_u)), "r"(smem_addr3(&bar)), "r"(c.x0 - H3), "r"(c.y0 - H3),
+          "r"(c.z0 - H3), "r"(0)
+          : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+          " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_addr3(c.cS)),
+          "l"(reinterpret_cast<uint64_t>(&tm_c)), "r"(smem_addr3(&bar)), "r"(c.x0 - 4), "r"(c.y0 - 1),
+          "r"(c.z0 - 1), "r"(4)
+          : "memory");
+    }
+    // bounded wait for the copies
+    bool ok = false;
+    for (long long it = 0; it < (1LL << 24) && !ok; ++it) {
+      uint32_t r;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+          " selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(r)
+          : "r"(smem_addr3(&bar))
+          : "memory");
+      ok = r != 0;
+    }
+    if (!ok) tma_ok = 0;
+  } else {
+    for (int f = 0; f < 4; ++f) {
+      const T* src = A.ufine + D.fine_off[f];
+      for (int i = tid; i < NS3; i += MODIL_NT) {
+        const int a = i / (S3Y * S3X), r = i - a * (S3Y * S3X), b = r / S3X, cc = r - b * S3X;
+        const int z = c.z0 - H3 + a, y = c.y0 - H3 + b, x = c.x0 - H3 + cc;
+        if (z >= 0 && z < c.nz && y >= 0 && y < c.ny && x >= 0 && x < c.nx)
+          cp_async(c.uS + f * NS3 + i, src + ((long long)z * c.ny + y) * c.nx + x);
+      }
+    }
+    const T* src = A.ufine + D.fine_off[4];
+    for (int i = tid; i < NC3S; i += MODIL_NT) {
+      const int a = i / (CY3 * CX3), r = i - a * (CY3 * CX3), b = r / CX3, cc = r - b * CX3;
+      const int z = c.z0 - 1 + a, y = c.y0 - 1 + b, x = c.x0 - 4 + cc;
+      if (z >= 0 && z < c.nz && y >= 0 && y < c.ny && x >= 0 && x < c.nx)
+        cp_async(c.cS + i, src + ((long long)z * c.ny + y) * c.nx + x);
+    }
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  if (!tma_ok) {  // a copy never completed: flag it, skip the tile
+    if (tid == 0) A.st[ii].nonfinite = 2;
+    return;
+  }
+  c.cf = cfS;
+  c.Rs = T(2) * (T)D.w_res_dV;
+  const bool adj = (mode != MODE_LOSS);
+  const bool interior = c.z0 >= 4 && c.z0 + C3Z + 4 <= c.nz && c.y0 >= 4 && c.y0 + C3Y + 4 <= c.ny &&
+                        c.x0 >= 4 && c.x0 + C3X + 4 <= c.nx;
+  float racc = 0.f;
+  double raccd = 0.0;
+  if (interior) r3_phase1<T, true>(c, adj, racc, raccd);
+  else r3_phase1<T, false>(c, adj, racc, raccd);
 
   // ---- data term (unique (field, cell) per run) ------------------------------
   float dacc = 0.f;
@@ -366,8 +610,8 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
   __syncthreads();
   for (int i = rb + tid; i < re; i += MODIL_NT) {
     const int cell = A.run_cell[i], f = A.run_field[i];
-    const int z = cell / (ny * nx), rem = cell - z * (ny * nx), y = rem / nx, x = rem - y * nx;
-    const T u = (f < 4) ? uS[f * NS3 + sidx(z, y, x)] : cS[midx(z, y, x)];
+    const int z = cell / (c.ny * c.nx), rem = cell - z * (c.ny * c.nx), y = rem / c.nx, x = rem - y * c.nx;
+    const T u = (f < 4) ? c.uS[f * NS3 + c.sidx(z, y, x)] : c.cS[c.cidx(z, y, x)];
     T sd = T(0), sq = T(0);
     for (int e = A.run_beg[i]; e < A.run_beg[i + 1]; ++e) {
       const T d = u - A.meas_val[e];
@@ -376,7 +620,7 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
     }
     if (sizeof(T) == 4) dacc += (float)sq;
     else daccd += (double)sq;
-    if (adj) gS[f * NC3 + ((z - z0) * C3Y + (y - y0)) * C3X + (x - x0)] += wd2 * sd;
+    if (adj) c.gS[f * NC3 + ((z - c.z0) * C3Y + (y - c.y0)) * C3X + (x - c.x0)] += wd2 * sd;
   }
   double rsum, dsum;
   if (sizeof(T) == 4) {
@@ -392,92 +636,9 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur) {
   }
   if (!adj) return;
   __syncthreads();
-
-  // ---- phase 2: gather per owned cell -------------------------------------------
   const AdamCoef ac = acS;
-  for (int t = tid; t < NC3; t += MODIL_NT) {
-    const int a = t / (C3Y * C3X), rr = t - a * (C3Y * C3X), b = rr / C3X, c = rr - b * C3X;
-    if (a >= hz || b >= hy || c >= hx) continue;
-    const int z = z0 + a, y = y0 + b, x = x0 + c;
-    const int X[3] = {z, y, x};
-    const int sp = sidx(z, y, x), mp = midx(z, y, x), qp = qidx(z, y, x);
-    T g[5];
-#pragma unroll
-    for (int f = 0; f < 5; ++f) g[f] = gS[f * NC3 + t];
-    T cen[4];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) cen[f] = uS[f * NS3 + sp];
-    T AX[3];
-#pragma unroll
-    for (int c3 = 0; c3 < 3; ++c3) AX[c3] = aS[c3 * NM + mp];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-      const int n = 2 - ax;
-      const int sstr = ax == 0 ? S3Y * S3X : (ax == 1 ? S3X : 1);
-      const int mstr = ax == 0 ? MY * MX : (ax == 1 ? MX : 1);
-      const int qstr = ax == 0 ? QY * QX : (ax == 1 ? QX : 1);
-#pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const int s = sd ? 1 : -1;
-        const bool ghost = (X[ax] + s < 0) || (X[ax] + s >= dims[ax]);
-        T nb[4], al[4];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          if (ghost) {
-            T alpha, beta;
-            ghost3<T>(f, ax, sd, alpha, beta);
-            nb[f] = alpha * cen[f] + beta;
-            al[f] = alpha;
-          } else {
-            nb[f] = uS[f * NS3 + sp + s * sstr];
-            al[f] = T(0);
-          }
-        }
-        const T mk = (ax == 2 || !ghost) ? T(1) : T(0);
-        const T Vn = mk * T(0.5) * (cen[n] + nb[n]);
-        T tn = T(0);
-#pragma unroll
-        for (int c3 = 0; c3 < 3; ++c3) {
-          const T AY = ghost ? T(0) : aS[c3 * NM + mp + s * mstr];
-          const T Wc = T(s) * (AX[c3] - AY) * cf.ih[ax];
-          tn += Wc * T(0.5) * (cen[c3] + nb[c3]);
-          // convective flux through this face via the transported component
-          g[c3] += T(0.5) * Vn * Wc * (ghost ? (T(1) + al[c3]) : T(1));
-          // viscous flux through this face
-          g[c3] += ghost ? -cf.nu * cf.ih2[ax] * AX[c3] * (al[c3] - T(1)) : cf.nu * cf.ih2[ax] * (AX[c3] - AY);
-        }
-        // convective flux through this face via the normal (transporting) velocity
-        g[n] += T(0.5) * mk * tn * (ghost ? (T(1) + al[n]) : T(1));
-        // pressure gradient of the component normal to this axis
-        if (ghost) g[3] += T(s) * al[3] * AX[n] * cf.i2h[ax];
-        else g[3] -= T(s) * aS[n * NM + mp + s * mstr] * cf.i2h[ax];
-      }
-      // continuity: cells P = X + d e_ax (|d| <= 2) that read X along this axis
-      const bool xaxis = (ax == 2);
-#pragma unroll
-      for (int d = -2; d <= 2; ++d) {
-        const int pi = X[ax] + d;
-        if (pi < 0 || pi >= dims[ax]) continue;
-        const T B = bS[qp + d * qstr];
-        g[3] += B * cont_coef<T>(xaxis, pi, dims[ax], -d, false, cf.tf, cf.ih[ax]);
-        if (d >= -1 && d <= 1) g[n] += B * cont_coef<T>(xaxis, pi, dims[ax], -d, true, cf.tf, cf.ih[ax]);
-      }
-    }
-#pragma unroll
-    for (int f = 0; f < 5; ++f) {
-      const long long o = D.off[f][0] + ((long long)z * ny + y) * nx + x;
-      const T gg = g[f] * (T)A.gscale;
-      A.g[o] = gg;
-      if (mode == MODE_STEP) {
-        T p = A.p[cur][o], m = A.m[o];
-        double v = A.v[o];
-        adam_update(p, m, v, gg, ac);
-        A.p[cur ^ 1][o] = p;
-        A.m[o] = m;
-        A.v[o] = v;
-      }
-    }
-  }
+  if (interior) r3_phase2<T, true>(c, A, D, mode, cur, ac);
+  else r3_phase2<T, false>(c, A, D, mode, cur, ac);
 }
 
 // 3-D restriction with Adam for one level: coarse tile 2 x 8 x 16, staged
@@ -536,9 +697,11 @@ k_level3(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   if (f >= D.nfield) return;
   {
     const T* __restrict__ gf = A.g + D.off[f][l - 1];
-    for (int i = t; i < dz * dy * dx; i += MODIL_NT) {
-      const int a = i / (dy * dx), r = i - a * (dy * dx), b = r / dx, c = r - b * dx;
-      cp_async(S + (a * L3FY + b) * L3FX + c, gf + ((long long)(fz0 + a) * fy + (fy0 + b)) * fx + (fx0 + c));
+    // loops run over the constant-size boxes (divisions by constants) with bounds checks
+    for (int i = t; i < L3FZ * L3FY * L3FX; i += MODIL_NT) {
+      const int a = i / (L3FY * L3FX), b = (i / L3FX) % L3FY, c = i % L3FX;
+      if (a < dz && b < dy && c < dx)
+        cp_async(S + i, gf + ((long long)(fz0 + a) * fy + (fy0 + b)) * fx + (fx0 + c));
     }
     // this thread's parameter and moments (plain loads overlap the copies)
     T pv = T(0), mv = T(0);
@@ -552,8 +715,9 @@ k_level3(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
     cp_async_wait_all();
     __syncthreads();
     // x pass: (dz, dy, cx)
-    for (int i = t; i < dz * dy * cx; i += MODIL_NT) {
-      const int a = i / (dy * cx), r = i - a * (dy * cx), b = r / cx, c = r - b * cx;
+    for (int i = t; i < L3FZ * L3FY * L3X; i += MODIL_NT) {
+      const int a = i / (L3FY * L3X), b = (i / L3X) % L3FY, c = i % L3X;
+      if (a >= dz || b >= dy || c >= cx) continue;
       const int X = X0 + c;
       T w[6];
       rwin3<T>(X, nx, w);
@@ -567,8 +731,9 @@ k_level3(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
     }
     __syncthreads();
     // y pass: (dz, cy, cx)
-    for (int i = t; i < dz * cy * cx; i += MODIL_NT) {
-      const int a = i / (cy * cx), r = i - a * (cy * cx), b = r / cx, c = r - b * cx;
+    for (int i = t; i < L3FZ * L3Y * L3X; i += MODIL_NT) {
+      const int a = i / (L3Y * L3X), b = (i / L3X) % L3Y, c = i % L3X;
+      if (a >= dz || b >= cy || c >= cx) continue;
       const int Y = Y0 + b;
       T w[6];
       rwin3<T>(Y, ny, w);
@@ -617,7 +782,7 @@ static cudaLaunchConfig_t cfg3(dim3 grid, size_t smem, cudaStream_t s, cudaLaunc
   return c;
 }
 
-size_t resid3_smem_bytes(int elem) { return (size_t)elem * (4 * NS3 + 4 * NM + NQ + F3 * NC3) + 64; }
+size_t resid3_smem_bytes(int elem) { return (size_t)elem * (4 * NS3 + NC3S + 3 * NM + NQ + F3 * NC3) + 128; }
 size_t level3_smem_bytes(int elem) {
   return (size_t)elem * (L3FZ * L3FY * L3FX + L3FZ * L3FY * L3X + L3FZ * L3Y * L3X) + 64;
 }
@@ -631,18 +796,63 @@ cudaError_t prepare_ns3d(size_t) {
 
 template <class T>
 cudaError_t launch_prolong3(const Arena<T>& A, int level, int nfield, int cur, cudaStream_t s) {
-  if (A.ntiles[level] == 0) return cudaSuccess;
   cudaLaunchAttribute at[1];
-  cudaLaunchConfig_t c = cfg3(dim3(A.ntiles[level], nfield), 0, s, at);
+  if (level < 0) {  // single-level instances: copy level 0
+    if (A.ntiles[0] == 0) return cudaSuccess;
+    cudaLaunchConfig_t c = cfg3(dim3(A.ntiles[0], nfield), 0, s, at);
+    return cudaLaunchKernelEx(&c, k_copy3<T>, A, cur);
+  }
+  if (A.ntiles[level + 1] == 0) return cudaSuccess;
+  cudaLaunchConfig_t c = cfg3(dim3(A.ntiles[level + 1], nfield), 0, s, at);
   return cudaLaunchKernelEx(&c, k_prolong3<T>, A, level, cur);
 }
 
 template <class T>
-cudaError_t launch_resid3(const Arena<T>& A, int mode, int cur, cudaStream_t s) {
+cudaError_t launch_resid3(const Arena<T>& A, int mode, int cur, const Ns3Maps* maps, cudaStream_t s) {
   if (A.ntiles[0] == 0) return cudaSuccess;
   cudaLaunchAttribute at[1];
   cudaLaunchConfig_t c = cfg3(dim3(A.ntiles[0]), resid3_smem_bytes(sizeof(T)), s, at);
-  return cudaLaunchKernelEx(&c, k_resid3<T>, A, mode, cur);
+  static const CUtensorMap zero{};
+  const bool tma = maps && maps->ok;
+  return cudaLaunchKernelEx(&c, k_resid3<T>, A, mode, cur, tma ? maps->u : zero, tma ? maps->c : zero,
+                            tma ? 1 : 0);
+}
+
+// TMA maps of the composed fields of a single-instance 3-D problem: a 4-D view
+// (x, y, z, field) of the buffer, boxes of 24 x 16 x 12 x 4 (u, v, w, p) and
+// 24 x 10 x 6 x 1 (chihat).  ok = false where TMA cannot address the buffer
+// (row pitch not a multiple of 16 bytes): the kernel then stages with cp.async.
+typedef CUresult (*EncodeTiled3)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int make_ns3_maps(Ns3Maps* m, const void* ufine, int nz, int ny, int nx, int elem) {
+  m->ok = false;
+  if (((long long)nx * elem) % 16 || (reinterpret_cast<uintptr_t>(ufine) & 15)) return 0;
+  static EncodeTiled3 enc = nullptr;
+  if (!enc) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess)
+      return -1;
+    enc = reinterpret_cast<EncodeTiled3>(p);
+  }
+  const CUtensorMapDataType dt = elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)F3};
+  cuuint64_t strides[3] = {(cuuint64_t)nx * elem, (cuuint64_t)nx * ny * elem, (cuuint64_t)nx * ny * nz * elem};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  cuuint32_t bu[4] = {S3X, S3Y, S3Z, 4};
+  cuuint32_t bc[4] = {CX3, CY3, CZ3, 1};
+  void* base = const_cast<void*>(ufine);
+  if (enc(&m->u, dt, 4, base, dims, strides, bu, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return -2;
+  if (enc(&m->c, dt, 4, base, dims, strides, bc, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return -2;
+  m->ok = true;
+  return 0;
 }
 
 template <class T>
@@ -657,8 +867,8 @@ template cudaError_t prepare_ns3d<float>(size_t);
 template cudaError_t prepare_ns3d<double>(size_t);
 template cudaError_t launch_prolong3<float>(const Arena<float>&, int, int, int, cudaStream_t);
 template cudaError_t launch_prolong3<double>(const Arena<double>&, int, int, int, cudaStream_t);
-template cudaError_t launch_resid3<float>(const Arena<float>&, int, int, cudaStream_t);
-template cudaError_t launch_resid3<double>(const Arena<double>&, int, int, cudaStream_t);
+template cudaError_t launch_resid3<float>(const Arena<float>&, int, int, const Ns3Maps*, cudaStream_t);
+template cudaError_t launch_resid3<double>(const Arena<double>&, int, int, const Ns3Maps*, cudaStream_t);
 template cudaError_t launch_level3<float>(const Arena<float>&, int, int, int, int, cudaStream_t);
 template cudaError_t launch_level3<double>(const Arena<double>&, int, int, int, int, cudaStream_t);
 

@@ -1,6 +1,7 @@
 // Host-side launch interface between the C ABI layer and the kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -53,8 +54,13 @@ template <class T>
 cudaError_t prepare_ns3d(size_t pyr_elems);
 template <class T>
 cudaError_t launch_prolong3(const Arena<T>& A, int level, int nfield, int cur, cudaStream_t s);
+struct Ns3Maps {
+  CUtensorMap u, c;
+  bool ok = false;
+};
+int make_ns3_maps(Ns3Maps* m, const void* ufine, int nz, int ny, int nx, int elem);
 template <class T>
-cudaError_t launch_resid3(const Arena<T>& A, int mode, int cur, cudaStream_t s);
+cudaError_t launch_resid3(const Arena<T>& A, int mode, int cur, const Ns3Maps* maps, cudaStream_t s);
 template <class T>
 cudaError_t launch_level3(const Arena<T>& A, int level, int nfield, int mode, int cur, cudaStream_t s);
 size_t tail_smem_bytes(const TailPlan& tp, int elem_bytes);

@@ -58,7 +58,7 @@ struct InstPlan {
 
 // Everything derived from the descriptors before any device memory exists.
 struct Plan {
-  int n_inst = 0, pde = 0, dtype = 0, ndim = 2, nfield = 1, cfg = 1, max_lev = 1, nk = 0;
+  int n_inst = 0, pde = 0, dtype = 0, ndim = 2, nfield = 1, cfg = 1, max_lev = 1, min_lev = MODIL_MAXL, nk = 0;
   int max_tail = 1;        // level kernels run for levels 1 .. max_tail-1
   TailPlan tail;
   int npart = 2;
@@ -163,6 +163,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
     ip.nk = P.pde == MODIL_PDE_HEAT ? q.n_knodes : 0;
     P.nk = std::max(P.nk, ip.nk);
     P.max_lev = std::max(P.max_lev, L);
+    P.min_lev = std::min(P.min_lev, L);
     D.nlev = L;
     D.nfield = P.nfield;
     D.nk = ip.nk;
@@ -344,6 +345,7 @@ struct modil_problem {
   cudaGraph_t graph[2] = {nullptr, nullptr};       // one step reading p[0] / p[1]
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   bool use_graph = true;
+  Ns3Maps maps;  // 3-D single instance: TMA maps of the composed fields
 };
 
 namespace {
@@ -411,16 +413,19 @@ modil_status run_pass_t(modil_problem* p, Arena<T>& A, int mode, int cur, cudaEv
   if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
   if (P.pde == MODIL_PDE_NS3D) {
     // compose level by level (coarse to fine), then the fused residual pass
-    for (int l = std::max(0, P.max_lev - 2); l >= 0; --l) {
+    // (level -1: copy of single-level instances, launched only if the batch has one)
+    const int lo = P.min_lev == 1 ? -1 : 0;
+    for (int l = P.max_lev - 2; l >= lo; --l) {
       CUDA_TRY(launch_prolong3<T>(A, l, P.nfield, cur, p->stream));
-      if (ev && (l > 0 || mode != MODE_COMPOSE)) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+      if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
     }
     if (mode == MODE_COMPOSE) {
-      if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
       if (nev) *nev = k;
       return MODIL_OK;
     }
-    CUDA_TRY(launch_resid3<T>(A, mode, cur, p->stream));
+    // the TMA maps address the arena's composed-field buffer (a single instance)
+    const bool own_uf = A.ufine == reinterpret_cast<T*>(static_cast<char*>(p->arena) + P.o_uf);
+    CUDA_TRY(launch_resid3<T>(A, mode, cur, own_uf ? &p->maps : nullptr, p->stream));
   } else if (P.pde == MODIL_PDE_NS2D) {
     CUDA_TRY(launch_fine_ns2d<T>(A, P.cfg, mode, cur, P.pyr_elems, p->stream));
   } else {
@@ -450,7 +455,8 @@ modil_status run_pass(modil_problem* p, int mode, cudaEvent_t* ev = nullptr, int
 }
 
 int kernels_per_step(const Plan& P) {
-  return (P.pde == MODIL_PDE_NS3D ? std::max(1, P.max_lev - 1) + 1 : 1) + (P.max_tail - 1) + 1;
+  const int compose3 = (P.max_lev - 1) + (P.min_lev == 1 ? 1 : 0);
+  return (P.pde == MODIL_PDE_NS3D ? compose3 + 1 : 1) + (P.max_tail - 1) + 1;
 }
 
 modil_status read_terms(modil_problem* p, double* terms) {
@@ -595,6 +601,12 @@ modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t ar
   if (e == cudaSuccess)
     e = P.dtype == MODIL_F64 ? prepare_tail<double>(P.tail) : prepare_tail<float>(P.tail);
   if (e != cudaSuccess) return bail(fail(MODIL_ERR_CUDA, std::string("kernel setup: ") + cudaGetErrorString(e)));
+  if (P.pde == MODIL_PDE_NS3D && P.n_inst == 1) {
+    const InstPlan& ip = P.inst[0];
+    if (make_ns3_maps(&p->maps, static_cast<char*>(p->arena) + P.o_uf, ip.n[0][0], ip.n[0][1], ip.n[0][2],
+                      (int)P.esz) < 0)
+      p->maps.ok = false;  // staged with cp.async instead
+  }
   e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return bail(fail(MODIL_ERR_CUDA, cudaGetErrorString(e)));
   *out = p;
