@@ -49,13 +49,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--workload", default="heat",
-                    choices=["heat", "batched-burgers", "body", "warmstart"],
+                    choices=["heat", "batched-burgers", "body", "warmstart", "unet"],
                     help="heat: the measured workload (default); batched-burgers: 512 uneven "
                          "Burgers instances, batched launch against sequential single runs; "
                          "body: 3-D body-shape inference, 128^3 cells, 8 levels, five fields; "
                          "warmstart: U-Net warm start of the body problem against zero init")
     ap.add_argument("--train", type=int, default=256, help="warmstart: training ellipsoids")
     ap.add_argument("--epochs", type=int, default=20, help="warmstart: U-Net training epochs")
+    ap.add_argument("--side", type=int, default=64, help="unet: grid side of the training step")
     ap.add_argument("--instances", type=int, default=512)
     return ap.parse_args()
 
@@ -437,6 +438,105 @@ def run_body(args):
     print(json.dumps(out), flush=True)
 
 
+def unet_train_flops(side, batch, base, levels, in_pad=8, out_ch=5):
+    """FLOPs of one training step (forward, input and weight gradients) of the
+    U-Net's contractions: 2 M K N per GEMM, three GEMMs per convolution (the
+    first convolution has no input gradient)."""
+    tot = 0
+    first = True
+
+    def conv(S, cin, cout, taps=27):
+        nonlocal tot, first
+        m = batch * S ** 3
+        f = 2 * m * taps * cin * cout
+        tot += f * (2 if first else 3)
+        first = False
+    for l in range(levels):
+        conv(side >> l, in_pad if l == 0 else base << (l - 1), base << l)
+        conv(side >> l, base << l, base << l)
+    for l in range(levels - 2, -1, -1):
+        conv(side >> l, (base << (l + 1)) + (base << l), base << l)
+        conv(side >> l, base << l, base << l)
+    conv(side, base, 16, taps=1)
+    return tot
+
+
+def run_unet(args):
+    """U-Net training throughput on 64^3 (batch 2, 4 levels x 32 channels) and
+    the tensor-core GEMM against the measured BF16 peak."""
+    import torch
+
+    from paper_2303_04679_gb300 import inputs, unet
+    from paper_2303_04679_gb300 import warmstart as W
+    torch.cuda.set_device(0)
+    side, batch, base, levels = args.side, 2, 32, 4
+    net = unet.UNet(side, batch=batch, in_ch=4, out_ch=5, base_ch=base, levels=levels, lr=1e-4)
+    net.write_params(inputs.unet_params(W.param_shapes(levels, base), 0))
+    rng = inputs.make_rng(1)
+    x = torch.from_numpy(rng.normal(size=(batch, side, side, side, 4)).astype(np.float32)).cuda()
+    y = torch.from_numpy(rng.normal(size=(batch, side, side, side, 5)).astype(np.float32)).cuda()
+    for _ in range(max(3, args.warmup)):
+        net.train_step(x, y, read_loss=False)
+    torch.cuda.synchronize()
+    K = max(1, min(args.steps, 200))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.25)
+    a.record(net.stream)
+    for _ in range(K):
+        net.train_step(x, y, read_loss=False)
+    b.record(net.stream)
+    b.synchronize()
+    clocks = sampler.stop()
+    ms = a.elapsed_time(b) / K
+    prof = net.profile_step(x, y)
+    flops = unet_train_flops(side, batch, base, levels)
+    # the GEMMs alone: the largest convolution of the network (decoder level 0,
+    # 96 -> 32 channels: M = 2 side^3, K = 27 x 96, N = 32) and a square 8192^3
+    gem = {}
+    for name, (M, N, Kd) in {"conv_dec0": (batch * side ** 3, 32, 27 * 96), "square_8192": (8192, 8192, 8192)}.items():
+        A = torch.randn(M, Kd, device="cuda").to(torch.bfloat16)
+        B = torch.randn(N, Kd, device="cuda").to(torch.bfloat16)
+        D = torch.empty(M, N, device="cuda", dtype=torch.float32)
+        for _ in range(3):
+            unet.gemm_bf16(A, B, D, mode=1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            unet.gemm_bf16(A, B, D, mode=1)
+        e1.record()
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 10
+        gem[name] = {"M": M, "N": N, "K": Kd, "ms": t, "tflops": 2.0 * M * N * Kd / (t * 1e-3) / 1e12,
+                     "operand_GBps": 2.0 * (M + N) * Kd / (t * 1e-3) / 1e9}
+        del A, B, D
+    net.close()
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak, kind = float(peaks["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        peak, kind = 1900.0, "fallback"
+    sq = gem["square_8192"]
+    out = {
+        "metric": "U-Net training samples/s", "value": batch / (ms * 1e-3), "unit": "samples/s", "n_gpus": 1,
+        "steps": K, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (f32 accumulate)", "data": "synthetic",
+        "config": {"workload": f"3-D U-Net training step, {side}^3, batch 2, 4 levels x 32 channels, Adam",
+                   "flops_per_step": flops},
+        "effective_tflops": flops / (ms * 1e-3) / 1e12,
+        "launches_per_step": int(len(prof)),
+        "gemm": gem,
+        "roofline": {"kernel": "tc_gemm (square 8192^3)", "bound": "tensor", "achieved": sq["tflops"],
+                     "peak": peak, "peak_kind": kind + " (bf16 burst)", "unit": "TFLOP/s",
+                     "frac": sq["tflops"] / peak, "traffic": None},
+        "clocks": clocks,
+        "gpu_launches": int(len(prof)) * K,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def run_warmstart(args):
     """Learned warm start of the 3-D body problem: plain-mODIL forward
     solutions around seeded ellipsoids on 64^3 (training data), the U-Net
@@ -518,6 +618,9 @@ def main():
         return
     if args.workload == "warmstart":
         run_warmstart(args)
+        return
+    if args.workload == "unet":
+        run_unet(args)
         return
     w = inputs.heat_workload()
     if args.impl == "reference":
