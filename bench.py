@@ -61,6 +61,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, world, device="cuda"):
+    """Largest per-rank time (the job's time) of a replicated run; `ms` is this
+    rank's value.  world == 1 returns it unchanged."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(steps_per_rank, world, job_ms):
+    """Whole-job evaluations per second: every rank runs `steps_per_rank`
+    steps of its own replica; the job takes the slowest rank's time."""
+    return world * steps_per_rank / (job_ms * 1e-3)
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -678,10 +695,7 @@ def main():
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(tot_ms, world)
     terms = prob.eval_loss()[0]
 
     # per-kernel device times of a step launched kernel by kernel (cold L2)
@@ -729,7 +743,7 @@ def main():
            len(w["knodes"]) * 4)
     d2h = 32 * e2e_steps + field.nbytes
 
-    value = world * args.steps / (tot_ms * 1e-3)
+    value = job_throughput(args.steps, world, tot_ms)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
