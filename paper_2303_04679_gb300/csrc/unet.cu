@@ -114,6 +114,42 @@ __global__ void k_shift_t(const bf16* __restrict__ XT, int C, int S, long long M
   colT[(long long)k * ld + v] = val;
 }
 
+// The same, 8 consecutive voxels (one 16-byte vector, inside one x row) per
+// thread; grids whose side is a multiple of 8.  Taps shifted by one cell in x
+// take the two neighbouring vectors and a 16-bit funnel shift.
+__global__ void k_shift_t8(const bf16* __restrict__ XT, int C, int S, long long M, long long ld,
+                           bf16* __restrict__ colT) {
+  const long long v0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 8;
+  const int k = blockIdx.y;  // t * C + c
+  if (v0 >= M) return;
+  const int t = k / C, c = k - t * C;
+  const int x0 = (int)(v0 % S), y = (int)((v0 / S) % S), z = (int)((v0 / ((long long)S * S)) % S);
+  int dz, dy, dx;
+  tap_off(t, dz, dy, dx);
+  uint4 out = make_uint4(0, 0, 0, 0);
+  const int zz = z + dz, yy = y + dy;
+  if (zz >= 0 && zz < S && yy >= 0 && yy < S) {
+    const uint4* row = reinterpret_cast<const uint4*>(XT + (long long)c * ld + v0 + ((long long)dz * S + dy) * S);
+    const uint4 A = row[0];
+    if (dx == 0) {
+      out = A;
+    } else if (dx == 1) {  // elements 1..8 of (A, B); x = S is outside
+      const uint4 B = (x0 + 8 < S) ? row[1] : make_uint4(0, 0, 0, 0);
+      out.x = __funnelshift_r(A.x, A.y, 16);
+      out.y = __funnelshift_r(A.y, A.z, 16);
+      out.z = __funnelshift_r(A.z, A.w, 16);
+      out.w = __funnelshift_r(A.w, B.x, 16);
+    } else {  // dx == -1: elements -1..6; x = -1 is outside
+      const uint4 P = (x0 > 0) ? row[-1] : make_uint4(0, 0, 0, 0);
+      out.x = __funnelshift_r(P.w, A.x, 16);
+      out.y = __funnelshift_r(A.x, A.y, 16);
+      out.z = __funnelshift_r(A.y, A.z, 16);
+      out.w = __funnelshift_r(A.z, A.w, 16);
+    }
+  }
+  *reinterpret_cast<uint4*>(colT + (long long)k * ld + v0) = out;
+}
+
 // s[v][c] = sum_t dcol[v - off_t][t*C + c]; out: FP32 s, or BF16 of s masked by act > 0
 __global__ void k_col2im(const float* __restrict__ dcol, int C, int S, long long M, float* __restrict__ out_f32,
                          const bf16* __restrict__ act, bf16* __restrict__ out_bf16) {
@@ -408,7 +444,10 @@ modil_status conv_bwd(modil_unet* n, Conv& cv, const bf16* X, long long M, const
   UCUDA(cudaGetLastError());
   k_transpose<<<dim3((unsigned)((M + 31) / 32), (cv.cin + 31) / 32), tb, 0, n->s>>>(X, M, cv.cin, n->xt, Mp);
   UCUDA(cudaGetLastError());
-  k_shift_t<<<dim3(blocks(M), cv.K), kNT, 0, n->s>>>(n->xt, cv.cin, cv.S, M, Mp, n->colT);
+  if (cv.S % 8 == 0)
+    k_shift_t8<<<dim3(blocks(M / 8), cv.K), kNT, 0, n->s>>>(n->xt, cv.cin, cv.S, M, Mp, n->colT);
+  else
+    k_shift_t<<<dim3(blocks(M), cv.K), kNT, 0, n->s>>>(n->xt, cv.cin, cv.S, M, Mp, n->colT);
   UCUDA(cudaGetLastError());
   if ((st = rec(n))) return st;
   if ((st = gemm(n, n->colT, Mp, n->gt, Mp, cv.dW, cv.co, cv.K, cv.cout, (int)M, modil_tc::GEMM_ATOMIC_F32, 0,
