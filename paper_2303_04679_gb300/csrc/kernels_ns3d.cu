@@ -387,13 +387,24 @@ __device__ __forceinline__ void r3_phase1(const R3<T>& c, bool adj, float& racc,
   }
 }
 
+// Adam state of a thread's two owned cells, loaded at kernel start so that
+// its DRAM latency overlaps the staging and phase 1.
+template <class T>
+struct AdamPre {
+  T p[2][F3], m[2][F3];
+  double v[2][F3];
+};
+
 // Phase 2: gather of the adjoint for every owned cell; dL/du and Adam.
 template <class T, bool INTR>
 __device__ __forceinline__ void r3_phase2(const R3<T>& c, const Arena<T>& A, const DevInst& D, int mode, int cur,
-                                          const AdamCoef& ac) {
+                                          const AdamCoef& ac, const AdamPre<T>& pre) {
+  static_assert(NC3 == 2 * MODIL_NT, "two owned cells per thread");
   const Ns3Coef<T>& cf = c.cf;
   const int dims[3] = {c.nz, c.ny, c.nx};
-  for (int t = threadIdx.x; t < NC3; t += MODIL_NT) {
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const int t = threadIdx.x + kk * MODIL_NT;
     const int a = t / (C3Y * C3X), rr = t - a * (C3Y * C3X), b = rr / C3X, cc = rr - b * C3X;
     if (!INTR && (a >= c.hz || b >= c.hy || cc >= c.hx)) continue;
     const int z = c.z0 + a, y = c.y0 + b, x = c.x0 + cc;
@@ -468,8 +479,8 @@ __device__ __forceinline__ void r3_phase2(const R3<T>& c, const Arena<T>& A, con
       const T gg = g[f] * (T)A.gscale;
       A.g[o] = gg;
       if (mode == MODE_STEP) {
-        T p = A.p[cur][o], m = A.m[o];
-        double v = A.v[o];
+        T p = pre.p[kk][f], m = pre.m[kk][f];
+        double v = pre.v[kk][f];
         adam_update(p, m, v, gg, ac);
         A.p[cur ^ 1][o] = p;
         A.m[o] = m;
@@ -533,6 +544,23 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur, const __grid_con
     }
   }
   for (int i = tid; i < F3 * NC3; i += MODIL_NT) c.gS[i] = T(0);
+  // level-1 parameters and moments were last written one step earlier (many
+  // launches back), so they may be read before the dependency wait
+  AdamPre<T> pre;
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const int t = tid + kk * MODIL_NT;
+    const int a = t / (C3Y * C3X), b = (t / C3X) % C3Y, cc = t % C3X;
+    const bool ok = mode == MODE_STEP && a < c.hz && b < c.hy && cc < c.hx;
+    const long long e = ((long long)(c.z0 + a) * c.ny + (c.y0 + b)) * c.nx + (c.x0 + cc);
+#pragma unroll
+    for (int f = 0; f < F3; ++f) {
+      const long long o = D.off[f][0] + e;
+      pre.p[kk][f] = ok ? A.p[cur][o] : T(0);
+      pre.m[kk][f] = ok ? A.m[o] : T(0);
+      pre.v[kk][f] = ok ? A.v[o] : 0.0;
+    }
+  }
   __syncthreads();
   pdl_wait();
   pdl_trigger();
@@ -637,8 +665,8 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur, const __grid_con
   if (!adj) return;
   __syncthreads();
   const AdamCoef ac = acS;
-  if (interior) r3_phase2<T, true>(c, A, D, mode, cur, ac);
-  else r3_phase2<T, false>(c, A, D, mode, cur, ac);
+  if (interior) r3_phase2<T, true>(c, A, D, mode, cur, ac, pre);
+  else r3_phase2<T, false>(c, A, D, mode, cur, ac, pre);
 }
 
 // 3-D restriction with Adam for one level: coarse tile 2 x 8 x 16, staged
