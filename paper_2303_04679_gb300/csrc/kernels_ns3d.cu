@@ -78,15 +78,35 @@ k_prolong3(const __grid_constant__ Arena<T> A, int l, int cur) {
   const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[lc][gt];
   load_inst(&D, A, ii);
   __syncthreads();
-  pdl_wait();
-  pdl_trigger();
-  if (f >= D.nfield || lc > D.nlev - 1) return;
+  const bool blk = f < D.nfield && lc <= D.nlev - 1;
   const int local = gt - D.tile_base[lc];
   const int per_z = D.nt[lc][1] * D.nt[lc][2];
   const int bz = local / per_z, br = local - bz * per_z;
   const int by = br / D.nt[lc][2], bx = br - by * D.nt[lc][2];
   const int cz = D.n[lc][0], cy = D.n[lc][1], cx = D.n[lc][2];
   const int Z0 = bz * k3LZ, Y0 = by * k3LY, X0 = bx * k3LX;
+  const int t = threadIdx.x;
+  const int oz = t / (k3LY * k3LX), oy = (t / k3LX) % k3LY, ox = t % k3LX;
+  const int Z = Z0 + oz, Y = Y0 + oy, Xc = X0 + ox;
+  const bool mine = blk && Z < cz && Y < cy && Xc < cx;
+  const int nyf = 2 * cy, nxf = 2 * cx;
+  // this level's own values (the 8 children of the thread's coarse cell) were
+  // last written one step earlier: read them before the dependency wait
+  T uo[2][2][2];
+  {
+    const T* __restrict__ u = A.p[cur] + D.off[blk ? f : 0][l];
+#pragma unroll
+    for (int cz2 = 0; cz2 < 2; ++cz2)
+#pragma unroll
+      for (int cy2 = 0; cy2 < 2; ++cy2) {
+        const long long rowo = ((long long)(2 * Z + cz2) * nyf + (2 * Y + cy2)) * nxf + 2 * Xc;
+#pragma unroll
+        for (int cx2 = 0; cx2 < 2; ++cx2) uo[cz2][cy2][cx2] = mine ? u[rowo + cx2] : T(0);
+      }
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (!blk) return;
   const T* __restrict__ w = (lc == D.nlev - 1 ? A.p[cur] : A.wl) + D.off[f][lc];
   // stage the coarse tile with a halo of one cell (clamped at the grid edge;
   // clamped copies only meet zero weights)
@@ -97,10 +117,7 @@ k_prolong3(const __grid_constant__ Arena<T> A, int l, int cur) {
     cS[i] = w[((long long)z * cy + y) * cx + x];
   }
   __syncthreads();
-  const int t = threadIdx.x;
-  const int oz = t / (k3LY * k3LX), oy = (t / k3LX) % k3LY, ox = t % k3LX;
-  const int Z = Z0 + oz, Y = Y0 + oy, Xc = X0 + ox;
-  if (Z >= cz || Y >= cy || Xc >= cx) return;
+  if (!mine) return;
   T ez[3], odz[3], ey[3], ody[3], ex[3], odx[3];
   child_weights<T>(Z, cz, ez, odz);
   child_weights<T>(Y, cy, ey, ody);
@@ -115,8 +132,6 @@ k_prolong3(const __grid_constant__ Arena<T> A, int l, int cur) {
       hx[0][a][b] = ex[0] * row[0] + ex[1] * row[1] + ex[2] * row[2];
       hx[1][a][b] = odx[0] * row[0] + odx[1] * row[1] + odx[2] * row[2];
     }
-  const int nyf = 2 * cy, nxf = 2 * cx;
-  const T* __restrict__ u = A.p[cur] + D.off[f][l];
   T* __restrict__ out = l == 0 ? A.ufine + D.fine_off[f] : A.wl + D.off[f][l];
 #pragma unroll
   for (int cz2 = 0; cz2 < 2; ++cz2) {
@@ -131,7 +146,7 @@ k_prolong3(const __grid_constant__ Arena<T> A, int l, int cur) {
 #pragma unroll
         for (int a = 0; a < 3; ++a)
           v += wz[a] * (wy[0] * hx[cx2][a][0] + wy[1] * hx[cx2][a][1] + wy[2] * hx[cx2][a][2]);
-        out[rowo + cx2] = u[rowo + cx2] + v;
+        out[rowo + cx2] = uo[cz2][cy2][cx2] + v;
       }
     }
   }
@@ -716,6 +731,16 @@ k_level3(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   const long long e = ((long long)(Z0 + oz) * ny + (Y0 + oy)) * nx + (X0 + ox);
   const bool store_g = (mode != MODE_STEP) || (l < D.nlev - 1);
   if (t == 0) acS = adam_coef(D, A.st[ii]);
+  // this thread's parameter and moments: written by this kernel one step
+  // earlier (many launches back), so read before the dependency wait
+  T pv = T(0), mv = T(0);
+  double vv = 0.0;
+  const long long o = D.off[min(f, D.nfield - 1)][l] + e;
+  if (mode == MODE_STEP && mine && f < D.nfield) {
+    pv = A.p[cur][o];
+    mv = A.m[o];
+    vv = A.v[o];
+  }
   pdl_wait();
   pdl_trigger();
   const int fz0 = max(0, 2 * Z0 - 2), fz1 = min(fz, 2 * (Z0 + cz) + 2);
@@ -730,15 +755,6 @@ k_level3(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
       const int a = i / (L3FY * L3FX), b = (i / L3FX) % L3FY, c = i % L3FX;
       if (a < dz && b < dy && c < dx)
         cp_async(S + i, gf + ((long long)(fz0 + a) * fy + (fy0 + b)) * fx + (fx0 + c));
-    }
-    // this thread's parameter and moments (plain loads overlap the copies)
-    T pv = T(0), mv = T(0);
-    double vv = 0.0;
-    const long long o = D.off[f][l] + e;
-    if (mode == MODE_STEP && mine) {
-      pv = A.p[cur][o];
-      mv = A.m[o];
-      vv = A.v[o];
     }
     cp_async_wait_all();
     __syncthreads();
