@@ -85,6 +85,45 @@ __device__ __forceinline__ void restrict_sep(const T* S, int ss, int fy0, int fh
 
 constexpr int kLevFY = 2 * kLevTY + 4, kLevFX = 2 * kLevTX + 4;  // staged fine region
 
+// restrict_sep for the fixed tile of k_level: the loops run over the
+// constant-size boxes (divisions by constants) with bounds checks.
+template <class T, int NT, class Out>
+__device__ __forceinline__ void restrict_box(const T* S, int fy0, int fh, int fx0, int fw, T* H, int Y0, int ch,
+                                             int X0, int cw, int ny, int nx, Out out) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kLevFY * kLevTX; i += NT) {
+    const int r = i / kLevTX, c = i % kLevTX;
+    if (r >= fh || c >= cw) continue;
+    const int X = X0 + c;
+    T w[6];
+    rwin<T>(X, nx, w);
+    const T* row = S + r * kLevFX;
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int f = min(max(2 * X - 2 + k - fx0, 0), fw - 1);
+      acc += w[k] * row[f];
+    }
+    H[r * kLevTX + c] = acc;
+  }
+  __syncthreads();
+  // cells packed as k = Yr * cw + c, so that k == threadIdx.x: each thread
+  // finishes the cell whose Adam state it holds
+  for (int i = tid; i < ch * cw; i += NT) {
+    const int Yr = i / cw, c = i - (i / cw) * cw;
+    const int Y = Y0 + Yr;
+    T w[6];
+    rwin<T>(Y, ny, w);
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int f = min(max(2 * Y - 2 + k - fy0, 0), fh - 1);
+      acc += w[k] * H[f * kLevTX + c];
+    }
+    out(Yr * cw + c, acc);
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(MODIL_NT)
 k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
@@ -133,15 +172,15 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
     if (f >= nf) break;
     // stage field f of the finer level's gradient over the tile's footprint
     const T* __restrict__ gf = A.g + D.off[f][l - 1];
-    for (int i = threadIdx.x; i < fw * fh; i += MODIL_NT) {
-      const int r = i / fw, c = i - r * fw;
-      cp_async(fineS + r * kLevFX + c, gf + (long long)(fy0 + r) * fx + (fx0 + c));
+    for (int i = threadIdx.x; i < kLevFY * kLevFX; i += MODIL_NT) {
+      const int r = i / kLevFX, c = i % kLevFX;
+      if (r < fh && c < fw) cp_async(fineS + i, gf + (long long)(fy0 + r) * fx + (fx0 + c));
     }
     cp_async_wait_all();
     __syncthreads();
     const AdamCoef ac = acS;
     const long long o = D.off[f][l] + e;
-    restrict_sep<T, MODIL_NT>(fineS, kLevFX, fy0, fh, fx0, fw, H, y0, ch, x0, cw, ny, nx,
+    restrict_box<T, MODIL_NT>(fineS, fy0, fh, fx0, fw, H, y0, ch, x0, cw, ny, nx,
                               [&](int k, T g) {
                                 // k == threadIdx.x: each thread finishes its own cell
                                 if (store_g) A.g[o] = g;

@@ -50,7 +50,7 @@ struct StSmem {
   static constexpr size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
   static constexpr size_t o_inst = 0;
   static constexpr size_t o_reg = a16(o_inst + sizeof(DevInst));        // 5 x MAXL ints + misc
-  static constexpr size_t o_red = a16(o_reg + 4 * (5 * MODIL_MAXL + 4));
+  static constexpr size_t o_red = a16(o_reg + 4 * (6 * MODIL_MAXL + 4));
   static constexpr size_t o_sums = a16(o_red + 8 * 16);                 // 2 + MAXK doubles
   static constexpr size_t o_bins = a16(o_sums + 8 * (2 + MODIL_MAXK));  // 8 warps x MAXK
   static constexpr size_t o_u = a16(o_bins + 8 * 8 * MODIL_MAXK);
@@ -106,6 +106,9 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
   int* hgt = reg + 2 * MODIL_MAXL;
   int* wid = reg + 3 * MODIL_MAXL;
   int* poff = reg + 4 * MODIL_MAXL;
+  // 1 / (region width) per level: row = floor((idx + 1/2) / width) in FP32 is
+  // exact for these region sizes (quotients below a few hundred)
+  float* winv = reinterpret_cast<float*>(reg + 5 * MODIL_MAXL + 1);
   double* red = reinterpret_cast<double*>(smem + S::o_red);
   double* bins = reinterpret_cast<double*>(smem + S::o_bins);
   T* uR = reinterpret_cast<T*>(smem + S::o_u);
@@ -165,6 +168,7 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
     }
     region(tid, ly, lx, h, w);
     loy[tid] = ly; lox[tid] = lx; hgt[tid] = h; wid[tid] = w;
+    winv[tid] = 1.0f / (float)w;
     poff[tid] = tot;
   }
   __syncthreads();
@@ -182,7 +186,7 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
     }
     const int nxl = D.n[l][2];
     for (int idx = tid; idx < hgt[l] * wid[l]; idx += MODIL_NT) {
-      const int ry = idx / wid[l], rx = idx - ry * wid[l];
+      const int ry = (int)(((float)idx + 0.5f) * winv[l]), rx = idx - ry * wid[l];
       const int y = loy[l] + ry, x = lox[l] + rx;
       cp_async(pyr + poff[l] + idx, src + (long long)y * nxl + x);
     }
@@ -242,7 +246,7 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
         x = x0 - G::HU + rx;
         if (y < 0 || y >= ny || x < 0 || x >= nx) continue;
       } else {
-        const int ry = idx / wid[l], rx = idx - ry * wid[l];
+        const int ry = (int)(((float)idx + 0.5f) * winv[l]), rx = idx - ry * wid[l];
         y = loy[l] + ry;
         x = lox[l] + rx;
       }
