@@ -56,7 +56,7 @@ struct NsSmem {
   static constexpr size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
   static constexpr size_t o_inst = 0;
   static constexpr size_t o_reg = a16(o_inst + sizeof(DevInst));
-  static constexpr size_t o_red = a16(o_reg + 4 * (5 * MODIL_MAXL + 4));
+  static constexpr size_t o_red = a16(o_reg + 4 * (6 * MODIL_MAXL + 4));
   static constexpr size_t o_u = a16(o_red + 8 * 16);
   static constexpr size_t o_a = a16(o_u + sizeof(T) * F * G::UH * G::UW);
   static constexpr size_t o_g = a16(o_a + sizeof(T) * ns2d::NK * G::RH * G::RW);
@@ -105,6 +105,9 @@ k_fine_ns2d(const __grid_constant__ Arena<T> A, int mode, int cur) {
   int* hgt = reg + 2 * MODIL_MAXL;
   int* wid = reg + 3 * MODIL_MAXL;
   int* poff = reg + 4 * MODIL_MAXL;
+  // 1 / (region width) per level: row = floor((idx + 1/2) / width) in FP32 is
+  // exact for these region sizes (quotients below a few hundred)
+  float* winv = reinterpret_cast<float*>(reg + 5 * MODIL_MAXL + 1);
   double* red = reinterpret_cast<double*>(smem + S::o_red);
   float* redf = reinterpret_cast<float*>(red);
   T* uR = reinterpret_cast<T*>(smem + S::o_u);
@@ -152,6 +155,7 @@ k_fine_ns2d(const __grid_constant__ Arena<T> A, int mode, int cur) {
     }
     region(tid, ly, lx, h, w);
     loy[tid] = ly; lox[tid] = lx; hgt[tid] = h; wid[tid] = w;
+    winv[tid] = 1.0f / (float)w;
     poff[tid] = tot;
     if (tid == L - 1) *pyr_stride = tot + ((L > 1) ? h * w : 0);
   }
@@ -172,7 +176,7 @@ k_fine_ns2d(const __grid_constant__ Arena<T> A, int mode, int cur) {
     }
     const int nxl = D.n[l][2];
     for (int idx = tid; idx < hgt[l] * wid[l]; idx += MODIL_NT) {
-      const int ry = idx / wid[l], rx = idx - ry * wid[l];
+      const int ry = (int)(((float)idx + 0.5f) * winv[l]), rx = idx - ry * wid[l];
       const int y = loy[l] + ry, x = lox[l] + rx;
       cp_async(pyr + f * PS + poff[l] + idx, src + (long long)y * nxl + x);
     }
@@ -222,7 +226,7 @@ k_fine_ns2d(const __grid_constant__ Arena<T> A, int mode, int cur) {
         x = x0 - G::HU + rx;
         if (y < 0 || y >= ny || x < 0 || x >= nx) continue;
       } else {
-        const int ry = idx / wid[l], rx = idx - ry * wid[l];
+        const int ry = (int)(((float)idx + 0.5f) * winv[l]), rx = idx - ry * wid[l];
         y = loy[l] + ry;
         x = lox[l] + rx;
       }
