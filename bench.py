@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--workload", default="heat",
-                    choices=["heat", "batched-burgers", "body", "warmstart", "unet"],
+                    choices=["heat", "batched-burgers", "body", "warmstart", "unet", "burgers", "cavity"],
                     help="heat: the measured workload (default); batched-burgers: 512 uneven "
                          "Burgers instances, batched launch against sequential single runs; "
                          "body: 3-D body-shape inference, 128^3 cells, 8 levels, five fields; "
@@ -456,6 +456,91 @@ def run_body(args):
     print(json.dumps(out), flush=True)
 
 
+def flushed_steps(step, stream, flush, K, W):
+    """Per-step CUDA-event times (ms) of K calls of step(), each after an L2
+    flush (a write of a buffer larger than L2) on the same stream."""
+    import torch
+    for _ in range(max(3, W)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in evs:
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run_small(args):
+    """The two small configurations: Burgers reconstruction on 64 x 64 in FP64
+    (4 levels, 200 measured cells) and the lid-driven cavity on 256^2 in FP32
+    (8 levels, 1000 velocity samples), the latter also through the
+    torch.autograd.Function over the hand-written adjoint with a torch Adam.
+    L2 flushed before every timed step."""
+    import torch
+
+    from paper_2303_04679_gb300 import inputs, modil
+    torch.cuda.set_device(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    K = min(args.steps, 2000)
+    out_extra = {}
+    if args.workload == "burgers":
+        w = inputs.burgers_workload()
+        nt, nx = w["shape"]
+        vals = inputs.burgers_smooth_field(nt, nx, w["amps"], w["nu"]).reshape(-1)[w["meas_cell"]]
+        desc = modil.Desc("burgers", w["shape"], w["n_levels"], "f64", coef=(w["nu"],), meas_cell=w["meas_cell"],
+                          meas_value=vals, lr=w["lr"])
+        name = "Burgers reconstruction 64x64 space-time, 4 levels, FP64, Adam"
+        dtype = "f64"
+    else:
+        w = inputs.cavity_workload()
+        desc = modil.Desc("ns2d", w["shape"], w["n_levels"], "f32", coef=w["coef"], meas_cell=w["meas_cell"],
+                          meas_field=w["meas_field"], meas_value=w["meas_value"], lr=w["lr"])
+        name = "lid-driven cavity 256^2, Re 100, 8 levels, FP32, Adam"
+        dtype = "f32"
+    with modil.Problem(desc) as p:
+        ms = flushed_steps(lambda: p.step(1, read_loss=False), p.stream, flush, K, args.warmup)
+        prof = np.array([p.profile_step() for _ in range(10)]).mean(axis=0)
+        loss = float(p.eval_loss()[0, 0])
+        launches = p.launches_per_step()
+        if args.workload == "cavity":
+            from paper_2303_04679_gb300.autograd import ModilParameters
+            params = ModilParameters(p)
+            opt = torch.optim.Adam(params.parameters(), lr=w["lr"])
+
+            def ag_step():
+                opt.zero_grad()
+                params().backward()
+                opt.step()
+            ms_ag = flushed_steps(ag_step, torch.cuda.current_stream(), flush, min(K, 300), args.warmup)
+            out_extra["autograd"] = {"ms_per_step": float(np.median(ms_ag)), "evals_per_s": 1e3 / float(np.median(ms_ag)),
+                                     "note": "ModilLoss forward + backward (hand-written adjoint) + torch.optim.Adam, "
+                                             "host synchronisations of the autograd call included"}
+    step_ms = float(np.sum(ms) / K)
+    peak, kind = measured_peak()
+    nf = 3 if args.workload == "cavity" else 1
+    fine = int(np.prod(w["shape"]))
+    fine_bytes = nf * fine * ALG_BYTES_PER_PARAM + len(w["meas_cell"]) * ALG_BYTES_PER_MEAS
+    ach = fine_bytes / (prof[0] * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": 1e3 / step_ms, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+        "data": "synthetic", "config": {"workload": name, "l2": "flushed before every timed step (256 MiB write)"},
+        "fine_cells_per_s": fine * 1e3 / step_ms, "loss_final": loss,
+        "kernel_ms": [float(v) for v in prof],
+        "roofline": {"kernel": "fine_tile_fused", "bound": "hbm", "achieved": ach, "peak": peak, "peak_kind": kind,
+                     "unit": "GB/s", "frac": ach / peak, "traffic": None, "alg_bytes_per_launch": fine_bytes},
+        "gpu_launches": launches * K,
+    }
+    out.update(out_extra)
+    print(json.dumps(out), flush=True)
+
+
 def unet_train_flops(side, batch, base, levels, in_pad=8, out_ch=5):
     """FLOPs of one training step (forward, input and weight gradients) of the
     U-Net's contractions: 2 M K N per GEMM, three GEMMs per convolution (the
@@ -639,6 +724,9 @@ def main():
         return
     if args.workload == "unet":
         run_unet(args)
+        return
+    if args.workload in ("burgers", "cavity"):
+        run_small(args)
         return
     w = inputs.heat_workload()
     if args.impl == "reference":

@@ -174,14 +174,21 @@ modil_status modil_profile_step(modil_problem* p, float* ms, int max_kernels, in
  * same as modil_eval_loss / modil_eval_grad (paper Section 2.1 loss, Section
  * 2.2 decomposition) but reads the levels from `levels` (device) instead of
  * the problem's own copy; the heat conductivity nodes come from the problem.
- *   modil_loss_fwd: loss terms (host, n_instances * MODIL_NTERMS, synchronises).
+ *   modil_loss_fwd: loss terms (host, n_instances * MODIL_NTERMS, synchronises);
+ *                   with terms == NULL it only launches the pass (asynchronous)
+ *                   and the terms are read on the device (modil_terms_device).
  *   modil_loss_bwd: grads (device, parameter-vector layout) = grad_out * dL/dlevels;
- *                   asynchronous on the problem's stream. */
+ *                   asynchronous on the problem's stream.
+ *   modil_terms_device: device address of instance 0's MODIL_NTERMS loss terms
+ *                   (doubles, written by every pass) and the distance in doubles
+ *                   between consecutive instances' terms; valid while the
+ *                   problem lives. */
 modil_status modil_param_count(const modil_problem* p, long long* n);
 modil_status modil_level_offset(const modil_problem* p, int instance, int field, int level,
                                 long long* offset);
 modil_status modil_loss_fwd(modil_problem* p, const void* levels, double* terms);
 modil_status modil_loss_bwd(modil_problem* p, const void* levels, double grad_out, void* grads);
+modil_status modil_terms_device(const modil_problem* p, const double** terms, int* stride);
 
 /* Persistent launch of the fine-tile kernel (Burgers, heat): on != 0 launches
  * as many blocks as fit on the GPU at once, each taking tiles of all

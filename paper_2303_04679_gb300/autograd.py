@@ -14,7 +14,12 @@ from . import modil
 
 
 class ModilLoss(torch.autograd.Function):
-    """loss = ModilLoss.apply(levels_flat, problem) -> 0-d float64 tensor."""
+    """loss = ModilLoss.apply(levels_flat, problem) -> 0-d float64 tensor.
+
+    Nothing synchronises the host: the problem's stream waits for torch's
+    current stream on the device, the loss is summed from the library's
+    device-side loss terms, and the incoming gradient scales dL/dlevels on the
+    device.  A non-finite loss shows as NaN in the returned tensor."""
 
     @staticmethod
     def forward(ctx, levels, problem):
@@ -23,19 +28,26 @@ class ModilLoss(torch.autograd.Function):
         dt = torch.float64 if problem.np_dtype.__name__ == "float64" else torch.float32
         if levels.dtype != dt or levels.numel() != problem.param_count():
             raise ValueError("levels must hold param_count() elements of the problem dtype")
-        torch.cuda.current_stream().synchronize()  # levels are ready for the problem's stream
-        terms = problem.loss_fwd(levels)
+        cur = torch.cuda.current_stream()
+        problem.stream.wait_stream(cur)  # levels are ready for the problem's stream
+        problem.loss_fwd_async(levels)
+        cur.wait_stream(problem.stream)
+        if getattr(problem, "_terms_view", None) is None:
+            problem._terms_view = problem.terms_device()
         ctx.save_for_backward(levels)
         ctx.problem = problem
-        return torch.tensor(float(terms[:, 0].sum()), dtype=torch.float64, device=levels.device)
+        return problem._terms_view[:, 0].sum()
 
     @staticmethod
     def backward(ctx, grad_out):
         (levels,) = ctx.saved_tensors
+        problem = ctx.problem
         grads = torch.empty_like(levels)
-        ctx.problem.loss_bwd(levels, float(grad_out), grads)
-        ctx.problem.stream.synchronize()
-        return grads, None
+        cur = torch.cuda.current_stream()
+        problem.stream.wait_stream(cur)
+        problem.loss_bwd(levels, 1.0, grads)
+        cur.wait_stream(problem.stream)
+        return grads.mul_(grad_out.to(grads.dtype)), None
 
 
 class ModilParameters(torch.nn.Module):
@@ -52,7 +64,10 @@ class ModilParameters(torch.nn.Module):
     def level(self, level, field=0, instance=0):
         off = self.problem.level_offset(level, field, instance)
         shape = self.problem.level_shape(level, instance)
-        return self.flat[off:off + shape[0] * shape[1]].view(shape)
+        n = 1
+        for d in shape:  # 2-D (rows, cols) or 3-D (z, y, x)
+            n *= d
+        return self.flat[off:off + n].view(shape)
 
     def forward(self):
         return ModilLoss.apply(self.flat, self.problem)

@@ -805,6 +805,15 @@ modil_status modil_loss_bwd(modil_problem* p, const void* levels, double grad_ou
              : external_pass<float>(p, p->A32, levels, grads, grad_out, MODE_GRAD);
 }
 
+modil_status modil_terms_device(const modil_problem* p, const double** terms, int* stride) {
+  if (!p || !terms || !stride) return fail(MODIL_ERR_ARG, "NULL argument");
+  static_assert(sizeof(InstState) % sizeof(double) == 0, "InstState layout");
+  const InstState* st = reinterpret_cast<const InstState*>(static_cast<const char*>(p->arena) + p->plan.o_st);
+  *terms = st->terms;  // device address (no dereference on the host)
+  *stride = (int)(sizeof(InstState) / sizeof(double));
+  return MODIL_OK;
+}
+
 modil_status modil_set_persistent(modil_problem* p, int on) {
   if (!p) return fail(MODIL_ERR_ARG, "problem is NULL");
   const Plan& P = p->plan;

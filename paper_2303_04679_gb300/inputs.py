@@ -324,3 +324,31 @@ def unet_params(shapes, seed, bias_scale=0.0):
         else:
             out.append((rng.normal(0.0, bias_scale, size=s) if bias_scale else np.zeros(s)).astype(np.float32))
     return out
+
+
+# --------------------------------------------------------------------------
+# Lid-driven cavity (Section 3.3)
+# --------------------------------------------------------------------------
+
+def cavity_velocity(n):
+    """Closed-form recirculating flow on the unit square (cell centres):
+    stream function psi = sin(pi x)^2 sin(pi y)^2, u = dpsi/dy, v = -dpsi/dx
+    (divergence free, zero on the walls).  A synthetic data profile, not a
+    solution of the discrete cavity problem."""
+    c = (np.arange(n) + 0.5) / n
+    y, x = np.meshgrid(c, c, indexing="ij")
+    u = 2.0 * np.pi * np.sin(np.pi * x) ** 2 * np.sin(np.pi * y) * np.cos(np.pi * y)
+    v = -2.0 * np.pi * np.sin(np.pi * y) ** 2 * np.sin(np.pi * x) * np.cos(np.pi * x)
+    return u, v
+
+
+def cavity_workload(n=256, n_levels=8, n_samples=1000, seed=3, Re=100.0):
+    """Cavity at Re = 100 on n^2 cells with 8 levels: 1000 velocity samples
+    (u or v at seeded distinct cells) of the closed-form recirculating flow."""
+    rng = make_rng(seed)
+    cells = measurement_cells(n * n, n_samples, seed)
+    fields = rng.integers(0, 2, size=n_samples).astype(np.int32)
+    u, v = cavity_velocity(n)
+    vals = np.where(fields == 0, u.reshape(-1)[cells], v.reshape(-1)[cells])
+    return dict(shape=(n, n), n_levels=n_levels, meas_cell=cells, meas_field=fields,
+                meas_value=vals, coef=(Re, 1.0), lr=1e-3)

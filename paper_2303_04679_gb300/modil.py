@@ -79,6 +79,7 @@ def _load():
         "modil_level_offset": ([P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_longlong)], C.c_int),
         "modil_loss_fwd": ([P, P, C.POINTER(C.c_double)], C.c_int),
         "modil_loss_bwd": ([P, P, C.c_double, P], C.c_int),
+        "modil_terms_device": ([P, C.POINTER(C.c_void_p), C.POINTER(C.c_int)], C.c_int),
         "modil_eval_grad_noalloc": ([C.POINTER(modil_desc), P, P, C.POINTER(C.c_double),
                                      C.POINTER(C.c_double), P], C.c_int),
         "modil_last_error": ([], C.c_char_p),
@@ -328,6 +329,26 @@ class Problem:
         t = self._terms()
         _check(LIB.modil_loss_fwd(self._h, levels.data_ptr(), _dptr(t, C.c_double)))
         return t.reshape(self.n, NTERMS)
+
+    def loss_fwd_async(self, levels):
+        """Launch the loss pass of caller-owned levels without waiting; the terms
+        are then read on the device (terms_device)."""
+        _check(LIB.modil_loss_fwd(self._h, levels.data_ptr(), None))
+
+    def terms_device(self):
+        """[n_instances, 4] FP64 torch view of the loss terms in device memory
+        (total, residual, data, regulariser), overwritten by every pass."""
+        import torch
+        ptr = C.c_void_p()
+        stride = C.c_int()
+        _check(LIB.modil_terms_device(self._h, C.byref(ptr), C.byref(stride)))
+        n = (self.n - 1) * stride.value + NTERMS
+
+        class _View:  # device memory owned by the problem
+            __cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr.value, False),
+                                        "version": 3, "strides": None}
+        flat = torch.as_tensor(_View(), device="cuda")
+        return flat.as_strided((self.n, NTERMS), (stride.value, 1))
 
     def loss_bwd(self, levels, grad_out, grads):
         """grads <- grad_out * dL/dlevels (device tensors, parameter-vector layout)."""

@@ -165,3 +165,22 @@ def test_ns3d_full_size_sampled(modil):
             fd = (4 * cd(5e-4) - cd(1e-3)) / 3
             gnorm = np.sqrt(sum(float(np.sum(a * a)) for a in gl))
             assert abs(gpu - fd) <= TOL32 * gnorm, (lvl, gpu, fd, gnorm)
+
+
+def test_ns3d_autograd_parameter_views(modil):
+    """The flat torch parameter of a 3-D problem exposes every level as a
+    (z, y, x) view at the library's offsets."""
+    import torch
+    from paper_2303_04679_gb300.autograd import ModilLoss, ModilParameters
+    c = Case("ns3d", (8, 8, 16), 3, "f32", seed=67, n_meas=30)
+    with modil.Problem(c.desc()) as p:
+        params = ModilParameters(p)
+        with torch.no_grad():
+            for f in range(5):
+                for lvl in range(c.L):
+                    v = params.level(lvl, field=f)
+                    assert tuple(v.shape) == tuple(np.asarray(c.levels[f][lvl]).shape)
+                    v.copy_(torch.from_numpy(np.asarray(c.levels[f][lvl], np.float32)))
+        terms, _, _ = c.oracle_eval()
+        loss = ModilLoss.apply(params.flat, p)
+        assert abs(loss.item() - terms["total"]) <= TOL32 * terms["total"]
