@@ -140,3 +140,42 @@ def test_autograd_torch_adam_reduces_loss(modil):
             opt.step()
             first = loss.item() if first is None else first
         assert params().item() < 0.5 * first
+
+
+def test_autograd_step_captured_in_cuda_graph(modil):
+    """The autograd step (ModilLoss forward, backward, torch Adam) captured in
+    a CUDA graph: the library's launches join torch's capture through the
+    stream waits, and replays reproduce the eager steps."""
+    import torch
+    from paper_2303_04679_gb300.autograd import ModilParameters
+    c = Case("ns2d", (32, 32), 4, "f32", seed=48, n_meas=50)
+
+    def run(captured, n=5):
+        with modil.Problem(c.desc()) as p:
+            params = ModilParameters(p)
+            opt = torch.optim.Adam(params.parameters(), lr=1e-2, capturable=captured)
+
+            def step():
+                opt.zero_grad(set_to_none=False)
+                params().backward()
+                opt.step()
+            # the first step also creates the gradient and optimiser buffers
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                step()
+            torch.cuda.current_stream().wait_stream(side)
+            if captured:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    step()
+                for _ in range(n - 1):
+                    g.replay()
+            else:
+                for _ in range(n - 1):
+                    step()
+            torch.cuda.synchronize()
+            return params.flat.detach().cpu().numpy().copy()
+
+    eager, graph = run(False), run(True)
+    assert np.max(np.abs(eager - graph)) <= 1e-6 * max(1.0, np.max(np.abs(eager)))
