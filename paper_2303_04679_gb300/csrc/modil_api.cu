@@ -170,7 +170,8 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
     D.ndim = three ? 3 : 2;
     // first level small enough for the per-instance tail kernel (2-D only: the
     // 3-D levels are all restricted by the level kernel, the tail finalises)
-    const long long tcap = P.dtype == MODIL_F64 ? kTailCellsF64 : kTailCellsF32;
+    // (per field: the tail restricts the fields of a level one after another)
+    const long long tcap = (P.dtype == MODIL_F64 ? kTailCellsF64 : kTailCellsF32) / P.nfield;
     int tail = L;
     if (!three)
       for (int l = 1; l < L; ++l)

@@ -153,7 +153,8 @@ def test_autograd_step_captured_in_cuda_graph(modil):
     def run(captured, n=5):
         with modil.Problem(c.desc()) as p:
             params = ModilParameters(p)
-            opt = torch.optim.Adam(params.parameters(), lr=1e-2, capturable=captured)
+            # the same (capturable) Adam in both runs: only the launch mode differs
+            opt = torch.optim.Adam(params.parameters(), lr=1e-2, capturable=True)
 
             def step():
                 opt.zero_grad(set_to_none=False)
