@@ -83,59 +83,29 @@ __device__ __forceinline__ void restrict_sep(const T* S, int ss, int fy0, int fh
   }
 }
 
-constexpr int kLevFY = 2 * kLevTY + 4, kLevFX = 2 * kLevTX + 4;  // staged fine region
-
-// restrict_sep for the fixed tile of k_level: the loops run over the
-// constant-size boxes (divisions by constants) with bounds checks.
-template <class T, int NT, class Out>
-__device__ __forceinline__ void restrict_box(const T* S, int fy0, int fh, int fx0, int fw, T* H, int Y0, int ch,
-                                             int X0, int cw, int ny, int nx, Out out) {
-  const int tid = threadIdx.x;
-  for (int i = tid; i < kLevFY * kLevTX; i += NT) {
-    const int r = i / kLevTX, c = i % kLevTX;
-    if (r >= fh || c >= cw) continue;
-    const int X = X0 + c;
-    T w[6];
-    rwin<T>(X, nx, w);
-    const T* row = S + r * kLevFX;
-    T acc = T(0);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const int f = min(max(2 * X - 2 + k - fx0, 0), fw - 1);
-      acc += w[k] * row[f];
-    }
-    H[r * kLevTX + c] = acc;
-  }
-  __syncthreads();
-  // cells packed as k = Yr * cw + c, so that k == threadIdx.x: each thread
-  // finishes the cell whose Adam state it holds
-  for (int i = tid; i < ch * cw; i += NT) {
-    const int Yr = i / cw, c = i - (i / cw) * cw;
-    const int Y = Y0 + Yr;
-    T w[6];
-    rwin<T>(Y, ny, w);
-    T acc = T(0);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const int f = min(max(2 * Y - 2 + k - fy0, 0), fh - 1);
-      acc += w[k] * H[f * kLevTX + c];
-    }
-    out(Yr * cw + c, acc);
-  }
+// 16-byte asynchronous copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16_lv(void* dst, const void* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
 }
 
-template <class T>
+// One kLevTY x kLevTX tile of coarse level l (NF fields) over all instances:
+// dL/du_l = T^T dL/du_{l-1} from a staged region of the finer level's
+// gradient, then Adam on the tile.  Each thread finishes one coarse cell:
+// away from the level's ends its weights are the 4 x 4 tensor product of
+// (1/4, 3/4, 3/4, 1/4); within two cells of an end, the 6-tap windows.
+template <class T, int NF>
 __global__ void __launch_bounds__(MODIL_NT)
 k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   static_assert(kLevTY * kLevTX == MODIL_NT, "one coarse cell per thread");
-  __shared__ DevInst D;
-  __shared__ __align__(16) T fineS[kLevFY * kLevFX];
-  __shared__ __align__(16) T H[kLevFY * kLevTX];
+  // staged finer-level rows 2 y0 - 2 .., columns 2 x0 - 4 .. (4-element aligned)
+  constexpr int FH = 2 * kLevTY + 4, FW = 2 * kLevTX + 8;
+  __shared__ __align__(16) T fineS[FH * FW];
+  __shared__ AdamCoef acS;
   const int gt = blockIdx.x;
   const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[l][gt];
-  load_inst(&D, A, ii);
-  __syncthreads();
-  const int nf = D.nfield;
+  // descriptor fields read directly (kernel parameters for one instance)
+  const DevInst& D = (A.n_inst == 1) ? A.inst0 : A.inst[ii];
   const int ny = D.n[l][1], nx = D.n[l][2];
   const int fy = D.n[l - 1][1], fx = D.n[l - 1][2];
   const int local = gt - D.tile_base[l];
@@ -143,55 +113,97 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   const int y0 = ty * kLevTY, x0 = tx * kLevTX;
   const int ch = min(kLevTY, ny - y0), cw = min(kLevTX, nx - x0);
   const bool store_g = (mode != MODE_STEP) || (l < D.nlev - 1);
-  // Prologue: this level's parameters and moments were last written by the
-  // same kernel one step earlier, two or more launches back.
+  // cells packed as k = oy * cw + ox so that a ragged tile keeps the low threads busy
   const int oy = threadIdx.x / cw, ox = threadIdx.x - (threadIdx.x / cw) * cw;
   const bool mine = threadIdx.x < ch * cw;
-  const long long e = (long long)(y0 + oy) * nx + (x0 + ox);
-  T pv[MODIL_MAXF], mv[MODIL_MAXF];
-  double vv[MODIL_MAXF];
+  const int Y = y0 + oy, X = x0 + ox;
+  const long long e = (long long)Y * nx + X;
+  // Prologue: this level's parameters and moments were last written by the
+  // same kernel one step earlier, two or more launches back.
+  T pv[NF], mv[NF];
+  double vv[NF];
 #pragma unroll
-  for (int f = 0; f < MODIL_MAXF; ++f) {
+  for (int f = 0; f < NF; ++f) {
     pv[f] = T(0); mv[f] = T(0); vv[f] = 0.0;
-    if (f < nf && mode == MODE_STEP && mine) {
+    if (mode == MODE_STEP && mine) {
       const long long o = D.off[f][l] + e;
       pv[f] = A.p[cur][o];
       mv[f] = A.m[o];
       vv[f] = A.v[o];
     }
   }
-  __shared__ AdamCoef acS;
   if (threadIdx.x == 0) acS = adam_coef(D, A.st[ii]);  // once per block: no per-thread FP64
   pdl_wait();
   pdl_trigger();
-  const int fy0 = max(0, 2 * y0 - 2), fy1 = min(fy, 2 * (y0 + ch) + 2);
-  const int fx0 = max(0, 2 * x0 - 2), fx1 = min(fx, 2 * (x0 + cw) + 2);
-  const int fw = fx1 - fx0, fh = fy1 - fy0;
+  // rows [ry0, ry1) and columns [rx0, rx1) of the finer level carry weight
+  const int ry0 = max(0, 2 * y0 - 2), ry1 = min(fy, 2 * (y0 + ch) + 2);
+  const int rx0 = max(0, 2 * x0 - 2), rx1 = min(fx, 2 * (x0 + cw) + 2);
+  const int oY = 2 * y0 - 2, oX = 2 * x0 - 4;  // region origin
+  constexpr int CW = FW / 4;
 #pragma unroll
-  for (int f = 0; f < MODIL_MAXF; ++f) {
-    if (f >= nf) break;
-    // stage field f of the finer level's gradient over the tile's footprint
-    const T* __restrict__ gf = A.g + D.off[f][l - 1];
-    for (int i = threadIdx.x; i < kLevFY * kLevFX; i += MODIL_NT) {
-      const int r = i / kLevFX, c = i % kLevFX;
-      if (r < fh && c < fw) cp_async(fineS + i, gf + (long long)(fy0 + r) * fx + (fx0 + c));
+  for (int f = 0; f < NF; ++f) {
+    const long long fo = D.off[f][l - 1];
+    const T* __restrict__ gf = A.g + fo;
+    const bool vec = ((fx & 3) == 0) && ((fo & 3) == 0);
+    for (int k = threadIdx.x; k < FH * CW; k += MODIL_NT) {
+      const int r = k / CW, c = 4 * (k - r * CW);
+      const int yy = oY + r, xx = oX + c;
+      if (yy < ry0 || yy >= ry1) continue;
+      T* dst = fineS + r * FW + c;
+      const T* src = gf + (long long)yy * fx + xx;
+      if (vec) {
+        if (xx + 3 >= rx0 && xx < rx1) {  // whole 4-element chunks inside the level
+          cp_async16_lv(dst, src);
+          if (sizeof(T) == 8) cp_async16_lv(dst + 2, src + 2);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (xx + j >= rx0 && xx + j < rx1) cp_async(dst + j, src + j);
+      }
     }
     cp_async_wait_all();
     __syncthreads();
-    const AdamCoef ac = acS;
-    const long long o = D.off[f][l] + e;
-    restrict_box<T, MODIL_NT>(fineS, fy0, fh, fx0, fw, H, y0, ch, x0, cw, ny, nx,
-                              [&](int k, T g) {
-                                // k == threadIdx.x: each thread finishes its own cell
-                                if (store_g) A.g[o] = g;
-                                if (mode == MODE_STEP) {
-                                  adam_update(pv[f], mv[f], vv[f], g, ac);
-                                  A.p[cur ^ 1][o] = pv[f];
-                                  A.m[o] = mv[f];
-                                  A.v[o] = vv[f];
-                                }
-                              });
-    __syncthreads();  // fineS and H are reused by the next field
+    if (mine) {
+      T g;
+      if (Y >= 2 && Y <= ny - 3 && X >= 2 && X <= nx - 3) {
+        const T* s = fineS + (2 * Y - 1 - oY) * FW + (2 * X - 1 - oX);
+        const T w[4] = {T(0.25), T(0.75), T(0.75), T(0.25)};
+        g = T(0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          T h = T(0);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) h += w[k] * s[i * FW + k];
+          g += w[i] * h;
+        }
+      } else {
+        T wx[6], wy[6];
+        rwin<T>(X, nx, wx);
+        rwin<T>(Y, ny, wy);
+        g = T(0);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          // taps outside the level have zero weight; clamp them into the region
+          const int yy = min(max(2 * Y - 2 + i, ry0), ry1 - 1);
+          const T* row = fineS + (yy - oY) * FW;
+          T h = T(0);
+#pragma unroll
+          for (int k = 0; k < 6; ++k) h += wx[k] * row[min(max(2 * X - 2 + k, rx0), rx1 - 1) - oX];
+          g += wy[i] * h;
+        }
+      }
+      const long long o = D.off[f][l] + e;
+      if (store_g) A.g[o] = g;
+      if (mode == MODE_STEP) {
+        const AdamCoef ac = acS;
+        adam_update(pv[f], mv[f], vv[f], g, ac);
+        A.p[cur ^ 1][o] = pv[f];
+        A.m[o] = mv[f];
+        A.v[o] = vv[f];
+      }
+    }
+    if (f + 1 < NF) __syncthreads();  // fineS is reused by the next field
   }
 }
 
@@ -492,11 +504,13 @@ static cudaLaunchConfig_t pdl_config(dim3 grid, dim3 block, size_t smem, cudaStr
 }
 
 template <class T>
-cudaError_t launch_level(const Arena<T>& A, int level, int mode, int cur, cudaStream_t s) {
+cudaError_t launch_level(const Arena<T>& A, int nf, int level, int mode, int cur, cudaStream_t s) {
   if (A.ntiles[level] == 0) return cudaSuccess;
   cudaLaunchAttribute at[1];
   cudaLaunchConfig_t cfg = pdl_config(dim3(A.ntiles[level]), dim3(MODIL_NT), 0, s, at);
-  return cudaLaunchKernelEx(&cfg, k_level<T>, A, level, mode, cur);
+  if (nf == 1) return cudaLaunchKernelEx(&cfg, k_level<T, 1>, A, level, mode, cur);
+  if (nf == 3) return cudaLaunchKernelEx(&cfg, k_level<T, 3>, A, level, mode, cur);
+  return cudaErrorInvalidValue;
 }
 
 size_t tail_smem_bytes(const TailPlan& tp, int elem) { return tp.smem_bytes; }
@@ -531,8 +545,8 @@ cudaError_t launch_delay(long long ns, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template cudaError_t launch_level<float>(const Arena<float>&, int, int, int, cudaStream_t);
-template cudaError_t launch_level<double>(const Arena<double>&, int, int, int, cudaStream_t);
+template cudaError_t launch_level<float>(const Arena<float>&, int, int, int, int, cudaStream_t);
+template cudaError_t launch_level<double>(const Arena<double>&, int, int, int, int, cudaStream_t);
 template cudaError_t prepare_tail<float>(const TailPlan&);
 template cudaError_t prepare_tail<double>(const TailPlan&);
 template cudaError_t launch_tail<float>(const Arena<float>&, int, int, const TailPlan&, cudaStream_t);

@@ -32,7 +32,7 @@ struct TailPlan {
 // Blocks per instance of the tail kernel (one thread-block cluster).
 constexpr int kTailC = 8;
 
-size_t fine_st_smem_bytes(int cfg, size_t pyr_elems, int elem_bytes);
+size_t fine_st_smem_bytes(int pde, int cfg, size_t pyr_elems, int elem_bytes);
 cudaError_t fine_st_blocks_per_sm(int pde, int cfg, size_t pyr_elems, int elem_bytes, int* n);
 template <class T>
 cudaError_t prepare_fine_st(int pde, int cfg, size_t pyr_elems);
@@ -46,7 +46,7 @@ template <class T>
 cudaError_t launch_fine_ns2d(const Arena<T>& A, int cfg, int mode, int cur, size_t pyr_elems,
                              cudaStream_t s);
 template <class T>
-cudaError_t launch_level(const Arena<T>& A, int level, int mode, int cur, cudaStream_t s);
+cudaError_t launch_level(const Arena<T>& A, int nf, int level, int mode, int cur, cudaStream_t s);
 // 3-D penalised Navier-Stokes: fine tile 4 x 8 x 16 cells, coarse tile 2 x 8 x 16.
 constexpr int k3TZ = 4, k3TY = 8, k3TX = 16;
 constexpr int k3LZ = 2, k3LY = 8, k3LX = 16;

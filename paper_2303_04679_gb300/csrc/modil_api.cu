@@ -438,7 +438,7 @@ modil_status run_pass_t(modil_problem* p, Arena<T>& A, int mode, int cur, cudaEv
       if (P.pde == MODIL_PDE_NS3D)
         CUDA_TRY(launch_level3<T>(A, l, P.nfield, mode, cur, p->stream));
       else
-        CUDA_TRY(launch_level<T>(A, l, mode, cur, p->stream));
+        CUDA_TRY(launch_level<T>(A, P.nfield, l, mode, cur, p->stream));
       if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
     }
   if (mode != MODE_COMPOSE) {
@@ -1007,7 +1007,7 @@ modil_status noalloc_run(const Plan& P, const modil_desc* d, const void* levels,
   CUDA_TRY(prepare_tail<T>(P.tail));
   if (P.pde == MODIL_PDE_NS2D) CUDA_TRY(launch_fine_ns2d<T>(A, P.cfg, MODE_GRAD, 0, P.pyr_elems, s));
   else CUDA_TRY(launch_fine_st<T>(A, P.pde, P.cfg, MODE_GRAD, 0, P.pyr_elems, s));
-  for (int l = 1; l < P.max_tail; ++l) CUDA_TRY(launch_level<T>(A, l, MODE_GRAD, 0, s));
+  for (int l = 1; l < P.max_tail; ++l) CUDA_TRY(launch_level<T>(A, P.nfield, l, MODE_GRAD, 0, s));
   CUDA_TRY(launch_tail<T>(A, MODE_GRAD, 0, P.tail, s));
   InstState out;
   CUDA_TRY(cudaMemcpyAsync(&out, b + o_st, sizeof(out), cudaMemcpyDeviceToHost, s));

@@ -102,6 +102,41 @@ def test_burgers_full_size_64_f64(modil):
 
 
 # ---------------------------------------------------------------------------
+# rows or level starts off 4-element boundaries: the fine kernel's element
+# by element staging and stores instead of 16-byte vectors
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("pde,shape,L", [("burgers", (38, 46), 2), ("heat", (30, 70), 2),
+                                         ("burgers", (37, 45), 1)])
+def test_rows_off_vector_boundaries(modil, pde, shape, L):
+    c = Case(pde, shape, L, "f32", seed=30, n_meas=90, w_reg=0.05 if pde == "heat" else 0.0)
+    with modil.Problem(c.desc()) as p:
+        c.load(p)
+        check_loss_grad(c, p, TOL32)
+
+
+def test_adam_steps_with_unaligned_level_start(modil):
+    """Instance 1 starts at an element offset that is not a multiple of 4
+    (instance 0 holds 38*46 + 19*23 elements), so its fine tiles take the
+    element-by-element Adam path; both FP64 trajectories match the oracle."""
+    cases = [Case("burgers", (38, 46), 2, "f64", seed=31, n_meas=60, lr=5e-3),
+             Case("burgers", (64, 96), 3, "f64", seed=32, n_meas=80, lr=5e-3)]
+    with modil.Problem([c.desc() for c in cases]) as p:
+        for i, c in enumerate(cases):
+            c.load(p, instance=i)
+        assert p.level_offset(0, 0, 1) % 4 != 0
+        refs = [_oracle_steps(c, 3) for c in cases]
+        for k in range(3):
+            t = p.step(1)
+            for i, (_, hist) in enumerate(refs):
+                assert abs(t[i][0] - hist[k]["total"]) <= 1e-11 * hist[k]["total"], (i, k)
+        for i, (c, (st, _)) in enumerate(zip(cases, refs)):
+            for lvl in range(c.L):
+                a = p.read_level(lvl, instance=i)
+                ref = st.levels[lvl]
+                assert np.max(np.abs(a - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref))), (i, lvl)
+
+
+# ---------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------
 def test_no_measurements(modil):
