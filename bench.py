@@ -321,6 +321,7 @@ def run_batched(args):
         "effective_step_GBps": (params * ALG_BYTES_PER_PARAM + nmeas * 8) / (t_batch * 1e-3) / 1e9,
         "sequential_ms_per_step": t_seq, "batched_speedup": t_seq / t_batch,
         "same_final_loss": bool(np.array_equal(final_batch, final_seq)),
+        "final_loss_max_rel_diff": float(np.max(np.abs(final_batch - final_seq) / np.abs(final_seq))),
         "kernel_ms": {"fine_tile_fused": float(prof[0]),
                       "restrict_levels": [float(v) for v in prof[1:-1]], "coarse_tail": float(prof[-1])},
         "roofline": {"kernel": "fine_tile_fused", "bound": "hbm", "achieved": ach, "peak": peak,

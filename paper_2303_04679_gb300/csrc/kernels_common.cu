@@ -208,7 +208,9 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
 }
 
 // ---------------------------------------------------------------------------
-// Tail: one thread-block cluster of kTailC blocks per instance.  The tail
+// Tail: one thread-block cluster of C blocks per instance (C = 1, 2, 4 or 8,
+// chosen at plan time: 8 for small batches, fewer when a batch would need
+// several waves of clusters).  The tail
 // levels are split by rows over the blocks of the cluster; each level is
 // restricted from the rows of the level above, read from global memory (first
 // tail level) or from the owning blocks' shared memory over the cluster's
@@ -232,12 +234,12 @@ struct TailLayout {
   }
 };
 
-__host__ __device__ inline void tail_layout(int L, int ts, const int (*n)[3], int nf, TailLayout& t) {
+__host__ __device__ inline void tail_layout(int L, int ts, const int (*n)[3], int nf, int C, TailLayout& t) {
   int acc = 0, st = 0, h = 0;
   for (int l = 0; l < MODIL_MAXL; ++l) { t.rp[l] = 0; t.own_off[l] = 0; }
   for (int l = ts; l < L; ++l) {
     const int ny = n[l][1], nx = n[l][2];
-    const int rp = (ny + kTailC - 1) / kTailC;
+    const int rp = (ny + C - 1) / C;
     t.rp[l] = rp;
     t.own_off[l] = acc;
     acc += rp * nx;
@@ -252,21 +254,22 @@ __host__ __device__ inline void tail_layout(int L, int ts, const int (*n)[3], in
 }
 
 template <class T>
-__global__ void __cluster_dims__(kTailC, 1, 1) __launch_bounds__(kTailNT)
+__global__ void __launch_bounds__(kTailNT)
 k_tail(const __grid_constant__ Arena<T> A, int mode, int cur) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ DevInst D;
   __shared__ TailLayout TL;
-  __shared__ double psum[2 + MODIL_MAXK];
+  __shared__ double psum[kTailC * (2 + MODIL_MAXK)];  // per slice of the partial sums
   __shared__ double qs[MODIL_MAXK];
-  __shared__ double chunk[kTailNT];
+  __shared__ double chunk[kTailC * kTailNT];  // per slice of the partial sums
   cg::cluster_group cluster = cg::this_cluster();
   const int r = (int)cluster.block_rank();
-  const int ii = blockIdx.x / kTailC;
+  const int C = (int)cluster.num_blocks();
+  const int ii = blockIdx.x / C;
   const int tid = threadIdx.x;
   load_inst(&D, A, ii);
   __syncthreads();
-  if (tid == 0) tail_layout(D.nlev, D.tail, D.n, D.nfield, TL);
+  if (tid == 0) tail_layout(D.nlev, D.tail, D.n, D.nfield, C, TL);
   __syncthreads();
   const int L = D.nlev, ts = D.tail;
   const bool levels = (mode == MODE_GRAD || mode == MODE_STEP) && ts < L;
@@ -301,34 +304,47 @@ k_tail(const __grid_constant__ Arena<T> A, int mode, int cur) {
   pdl_wait();
   pdl_trigger();
 
-  // ---- partial sums: block r adds tiles [r*nt0/C, (r+1)*nt0/C) -------------
+  // ---- partial sums over kTailC slices of the tiles, slice k = tiles
+  // [k*nt0/8, (k+1)*nt0/8), each summed in a fixed order; block r takes
+  // slices r*8/C .. (r+1)*8/C - 1, so the sums do not depend on C -----------
   const int nk = D.nk;
   const int nterm = (mode == MODE_LOSS) ? 2 : 2 + nk;
+  const int per = kTailC / C;
   {
     const int nt0 = D.ntile0, np = A.npart;
-    const int t0 = (int)((long long)r * nt0 / kTailC), t1 = (int)((long long)(r + 1) * nt0 / kTailC);
     const double* part = A.part + (long long)D.tile_base[0] * np;
     const int sub = kTailNT / nterm;  // sub-chunks per term
-    double s = 0.0;
     const int j = tid % nterm, c = tid / nterm;
-    if (c < sub)
-      for (int tb = t0 + c; tb < t1; tb += 8 * sub) {
-        double v[8];  // loads first, then the adds in order
+    // thread (j, c) adds tiles t0 + c, t0 + c + sub, ... of each of the
+    // block's slices in increasing order
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int t = tb + u * sub;
-          v[u] = (t < t1) ? __ldcg(part + (long long)t * np + j) : 0.0;
+    for (int k = 0; k < kTailC; ++k) {
+      if (k >= per) break;
+      double s = 0.0;
+      if (c < sub) {
+        const int vs = r * per + k;
+        const int t0 = (int)((long long)vs * nt0 / kTailC), t1 = (int)((long long)(vs + 1) * nt0 / kTailC);
+        for (int tb = t0 + c; tb < t1; tb += 8 * sub) {
+          double v[8];  // loads first, then the adds in order
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int t = tb + u * sub;
+            v[u] = (t < t1) ? __ldcg(part + (long long)t * np + j) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) s += v[u];
         }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) s += v[u];
       }
-    chunk[tid] = s;
-    __syncthreads();
-    if (tid < nterm) {
-      double a = 0.0;
-      for (int cc = 0; cc < sub; ++cc) a += chunk[cc * nterm + tid];
-      psum[tid] = a;
+      chunk[k * kTailNT + tid] = s;
     }
+    __syncthreads();
+    for (int q = tid; q < per * nterm; q += kTailNT) {
+      const int k = q / nterm, jj = q - k * nterm;
+      double a = 0.0;
+      for (int cc = 0; cc < sub; ++cc) a += chunk[k * kTailNT + cc * nterm + jj];
+      psum[k * (2 + MODIL_MAXK) + jj] = a;
+    }
+    __syncthreads();  // chunk is reused below
   }
 
   // ---- the small levels, distributed by rows over the cluster ---------------
@@ -377,7 +393,8 @@ k_tail(const __grid_constant__ Arena<T> A, int mode, int cur) {
     if (tid < nterm) {
       double v[kTailC];
 #pragma unroll
-      for (int rr = 0; rr < kTailC; ++rr) v[rr] = *cluster.map_shared_rank(psum + tid, rr);
+      for (int rr = 0; rr < kTailC; ++rr)
+        v[rr] = *cluster.map_shared_rank(psum + (rr % per) * (2 + MODIL_MAXK) + tid, rr / per);
       double a = 0.0;
 #pragma unroll
       for (int rr = 0; rr < kTailC; ++rr) a += v[rr];
@@ -516,9 +533,9 @@ cudaError_t launch_level(const Arena<T>& A, int nf, int level, int mode, int cur
 size_t tail_smem_bytes(const TailPlan& tp, int elem) { return tp.smem_bytes; }
 
 // Shared-memory bytes the tail blocks of one instance need.
-size_t tail_instance_bytes(int L, int ts, const int (*n)[3], int nf, int elem) {
+size_t tail_instance_bytes(int L, int ts, const int (*n)[3], int nf, int C, int elem) {
   TailLayout t;
-  tail_layout(L, ts, n, nf, t);
+  tail_layout(L, ts, n, nf, C, t);
   return t.bytes(elem);
 }
 
@@ -529,8 +546,13 @@ cudaError_t prepare_tail(const TailPlan& tp) {
 
 template <class T>
 cudaError_t launch_tail(const Arena<T>& A, int mode, int cur, const TailPlan& tp, cudaStream_t s) {
-  cudaLaunchAttribute at[1];
-  cudaLaunchConfig_t cfg = pdl_config(dim3(A.n_inst * kTailC), dim3(kTailNT), tp.smem_bytes, s, at);
+  cudaLaunchAttribute at[2];
+  cudaLaunchConfig_t cfg = pdl_config(dim3(A.n_inst * tp.cluster), dim3(kTailNT), tp.smem_bytes, s, at);
+  at[1].id = cudaLaunchAttributeClusterDimension;
+  at[1].val.clusterDim.x = tp.cluster;
+  at[1].val.clusterDim.y = 1;
+  at[1].val.clusterDim.z = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_tail<T>, A, mode, cur);
 }
 

@@ -28,8 +28,9 @@ struct TailPlan {
   size_t prev_cells = 0;     // cells of the level just above the tail levels
   size_t tail_cells = 0;     // cells of the tail levels
   size_t smem_bytes = 0;     // dynamic shared memory of a tail block
+  int cluster = 8;           // blocks per instance (one thread-block cluster)
 };
-// Blocks per instance of the tail kernel (one thread-block cluster).
+// Most blocks per instance of the tail kernel.
 constexpr int kTailC = 8;
 
 size_t fine_st_smem_bytes(int pde, int cfg, size_t pyr_elems, int elem_bytes);
@@ -64,7 +65,7 @@ cudaError_t launch_resid3(const Arena<T>& A, int mode, int cur, const Ns3Maps* m
 template <class T>
 cudaError_t launch_level3(const Arena<T>& A, int level, int nfield, int mode, int cur, cudaStream_t s);
 size_t tail_smem_bytes(const TailPlan& tp, int elem_bytes);
-size_t tail_instance_bytes(int L, int ts, const int (*n)[3], int nf, int elem_bytes);
+size_t tail_instance_bytes(int L, int ts, const int (*n)[3], int nf, int C, int elem_bytes);
 template <class T>
 cudaError_t prepare_tail(const TailPlan& tp);
 template <class T>

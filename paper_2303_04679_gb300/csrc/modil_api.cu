@@ -89,6 +89,11 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   if (!d || n < 1) return fail(MODIL_ERR_ARG, "descs is NULL or n < 1");
   P = Plan();
   P.n_inst = n;
+  // Tail kernel: 8 blocks per instance while the batch's clusters fit in one
+  // wave (152 SMs x 4 resident tail blocks), otherwise fewer (and the tail
+  // takes correspondingly smaller levels, so that its blocks stay small)
+  P.tail.cluster = kTailC;
+  while (P.tail.cluster > 1 && (long long)n * P.tail.cluster > 152 * 4) P.tail.cluster /= 2;
   P.pde = d[0].pde;
   P.dtype = d[0].dtype;
   P.ndim = d[0].ndim;
@@ -171,7 +176,8 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
     // first level small enough for the per-instance tail kernel (2-D only: the
     // 3-D levels are all restricted by the level kernel, the tail finalises)
     // (per field: the tail restricts the fields of a level one after another)
-    const long long tcap = (P.dtype == MODIL_F64 ? kTailCellsF64 : kTailCellsF32) / P.nfield;
+    const long long tcap =
+        (P.dtype == MODIL_F64 ? kTailCellsF64 : kTailCellsF32) * P.tail.cluster / (kTailC * P.nfield);
     int tail = L;
     if (!three)
       for (int l = 1; l < L; ++l)
@@ -186,7 +192,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
         P.tail.prev_cells = std::max(P.tail.prev_cells, (size_t)(ny >> (tail - 1)) * (nx >> (tail - 1)));
       int nn[MODIL_MAXL][3] = {};
       for (int l = 0; l < L; ++l) { nn[l][0] = nz >> l; nn[l][1] = ny >> l; nn[l][2] = nx >> l; }
-      P.tail.smem_bytes = std::max(P.tail.smem_bytes, tail_instance_bytes(L, tail, nn, P.nfield, (int)P.esz));
+      P.tail.smem_bytes = std::max(P.tail.smem_bytes, tail_instance_bytes(L, tail, nn, P.nfield, P.tail.cluster, (int)P.esz));
     }
     for (int l = 0; l < L; ++l) {
       ip.n[l][0] = three ? nz >> l : 1;

@@ -152,22 +152,24 @@ struct AdamCoef {
 
 // The second moment is accumulated in FP64 (one FMA per cell: GB300 runs FP64
 // at 1/64 of the FP32 rate); the square of the gradient, the first moment and
-// the update are FP32.
+// the update are FP32.  Where a sum has two products, which one is fused is
+// fixed explicitly, so that every kernel that applies Adam to a level (the
+// restriction kernels, the tail) rounds identically.
 __device__ __forceinline__ void adam_update(float& p, float& m, double& v, float g,
                                             const AdamCoef& c) {
-  m = c.b1f * m + c.omb1f * g;
-  v = fma(c.b2, v, (double)(c.omb2f * (g * g)));
+  m = fmaf(c.b1f, m, __fmul_rn(c.omb1f, g));
+  v = fma(c.b2, v, (double)__fmul_rn(c.omb2f, __fmul_rn(g, g)));
   const float den = sqrtf((float)v * c.c2f) + c.epsf;
-  p = p - c.lrf * ((m * c.c1f) / den);
+  p = fmaf(-c.lrf, __fdiv_rn(__fmul_rn(m, c.c1f), den), p);
 }
 
 __device__ __forceinline__ void adam_update(double& p, double& m, double& v, double g,
                                             const AdamCoef& c) {
-  m = c.b1 * m + (1.0 - c.b1) * g;
-  v = c.b2 * v + (1.0 - c.b2) * (g * g);
+  m = fma(c.b1, m, __dmul_rn(1.0 - c.b1, g));
+  v = fma(c.b2, v, __dmul_rn(1.0 - c.b2, __dmul_rn(g, g)));
   const double mh = m * c.c1;
   const double den = sqrt(v * c.c2) + c.eps;
-  p = p - c.lr * (mh / den);
+  p = fma(-c.lr, mh / den, p);
 }
 
 __device__ __forceinline__ AdamCoef adam_coef(const DevInst& D, const InstState& S) {

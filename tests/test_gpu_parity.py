@@ -174,6 +174,29 @@ def test_batch_of_uneven_instances(modil):
             check_loss_grad(c, p, TOL32, instance=i)
 
 
+@pytest.mark.parametrize("n,shape,L", [(200, (128, 128), 4), (700, (64, 64), 3)])
+def test_large_batches_small_tail_clusters(modil, n, shape, L):
+    """Batches large enough that the tail kernel runs with 4 (200 instances)
+    or 1 (700 instances) blocks per instance and leaves a 64^2 or 32^2 level
+    to the restriction kernel: sampled instances match the oracle, and Adam
+    steps of the batch match the same instances stepped alone."""
+    cases = [Case("burgers", shape, L, "f32", seed=100 + i, n_meas=20, nu=0.01 + 0.002 * (i % 7))
+             for i in range(n)]
+    with modil.Problem([c.desc() for c in cases]) as p:
+        for i, c in enumerate(cases):
+            c.load(p, instance=i)
+        for i in (0, n // 2, n - 1):
+            check_loss_grad(cases[i], p, TOL32, instance=i)
+        p.step(3, read_loss=False)
+        tb = p.eval_loss()
+    for i in (1, n // 3):
+        with modil.Problem(cases[i].desc()) as q:
+            cases[i].load(q)
+            q.step(3, read_loss=False)
+            ts = q.eval_loss()[0]
+        assert abs(tb[i][0] - ts[0]) <= 1e-6 * ts[0], (i, tb[i][0], ts[0])
+
+
 def test_eval_loss_matches_eval_grad(modil):
     c = Case("heat", (64, 96), 3, "f32", seed=11, n_meas=100, w_reg=0.01)
     with modil.Problem(c.desc()) as p:
