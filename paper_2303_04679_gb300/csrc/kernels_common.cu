@@ -42,44 +42,50 @@ __device__ __forceinline__ void rwin(int X, int nc, T* w) {
   w[5] = (X == nc - 2) ? T(-0.25) : T(0);
 }
 
-// Separable restriction of a staged 2-D region of the finer level.
-//   S: fine values, rows fy0 .. fy0+fh-1, cols fx0 .. fx0+fw-1, row stride ss
-//   H: scratch, fh rows x cw cols (row stride cw)
+// Separable restriction of a staged 2-D region of the finer level, nf
+// fields at once (one barrier between the passes for all of them).
+//   S: fine values of field f at S + f * sfs, rows fy0 .. fy0+fh-1, cols
+//      fx0 .. fx0+fw-1, row stride ss
+//   H: scratch, nf x fh rows x cw cols
 //   output coarse rows Y0 .. Y0+ch-1, cols X0 .. X0+cw-1 of a level ny x nx
-//   (finer level nfy x nfx) to out(k, value) for k = (Y-Y0)*cw + (X-X0).
+//   to out(f, k, value) for k = (Y-Y0)*cw + (X-X0).
 // Fine indices outside the level only meet zero weights; they are clamped
 // to stay inside the staged region.
 template <class T, int NT, class Out>
-__device__ __forceinline__ void restrict_sep(const T* S, int ss, int fy0, int fh, int fx0, int fw,
-                                             T* H, int Y0, int ch, int X0, int cw, int ny, int nx,
+__device__ __forceinline__ void restrict_sep(int nf, const T* S, int sfs, int ss, int fy0, int fh, int fx0,
+                                             int fw, T* H, int Y0, int ch, int X0, int cw, int ny, int nx,
                                              Out out) {
   const int tid = threadIdx.x;
-  for (int i = tid; i < fh * cw; i += NT) {
-    const int r = i / cw, X = X0 + (i - (i / cw) * cw);
+  const int nh = fh * cw, no = ch * cw;
+  for (int i = tid; i < nf * nh; i += NT) {
+    const int f = i / nh, j = i - f * nh;
+    const int r = j / cw, X = X0 + (j - r * cw);
     T w[6];
     rwin<T>(X, nx, w);
-    const T* row = S + r * ss;
+    const T* row = S + f * sfs + r * ss;
     T acc = T(0);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      const int f = min(max(2 * X - 2 + k - fx0, 0), fw - 1);
-      acc += w[k] * row[f];
+      const int x = min(max(2 * X - 2 + k - fx0, 0), fw - 1);
+      acc += w[k] * row[x];
     }
     H[i] = acc;
   }
   __syncthreads();
-  for (int i = tid; i < ch * cw; i += NT) {
-    const int Yr = i / cw, c = i - (i / cw) * cw;
+  for (int i = tid; i < nf * no; i += NT) {
+    const int f = i / no, j = i - f * no;
+    const int Yr = j / cw, c = j - Yr * cw;
     const int Y = Y0 + Yr;
     T w[6];
     rwin<T>(Y, ny, w);
+    const T* hf = H + f * nh;
     T acc = T(0);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      const int f = min(max(2 * Y - 2 + k - fy0, 0), fh - 1);
-      acc += w[k] * H[f * cw + c];
+      const int y = min(max(2 * Y - 2 + k - fy0, 0), fh - 1);
+      acc += w[k] * hf[y * cw + c];
     }
-    out(i, acc);
+    out(f, j, acc);
   }
 }
 
@@ -100,7 +106,7 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   static_assert(kLevTY * kLevTX == MODIL_NT, "one coarse cell per thread");
   // staged finer-level rows 2 y0 - 2 .., columns 2 x0 - 4 .. (4-element aligned)
   constexpr int FH = 2 * kLevTY + 4, FW = 2 * kLevTX + 8;
-  __shared__ __align__(16) T fineS[FH * FW];
+  __shared__ __align__(16) T fineS[NF * FH * FW];  // all fields staged at once
   __shared__ AdamCoef acS;
   const int gt = blockIdx.x;
   const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[l][gt];
@@ -144,12 +150,13 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   for (int f = 0; f < NF; ++f) {
     const long long fo = D.off[f][l - 1];
     const T* __restrict__ gf = A.g + fo;
+    T* fs = fineS + f * FH * FW;
     const bool vec = ((fx & 3) == 0) && ((fo & 3) == 0);
     for (int k = threadIdx.x; k < FH * CW; k += MODIL_NT) {
       const int r = k / CW, c = 4 * (k - r * CW);
       const int yy = oY + r, xx = oX + c;
       if (yy < ry0 || yy >= ry1) continue;
-      T* dst = fineS + r * FW + c;
+      T* dst = fs + r * FW + c;
       const T* src = gf + (long long)yy * fx + xx;
       if (vec) {
         if (xx + 3 >= rx0 && xx < rx1) {  // whole 4-element chunks inside the level
@@ -162,12 +169,16 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
           if (xx + j >= rx0 && xx + j < rx1) cp_async(dst + j, src + j);
       }
     }
-    cp_async_wait_all();
-    __syncthreads();
+  }
+  cp_async_wait_all();
+  __syncthreads();
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const T* fs = fineS + f * FH * FW;
     if (mine) {
       T g;
       if (Y >= 2 && Y <= ny - 3 && X >= 2 && X <= nx - 3) {
-        const T* s = fineS + (2 * Y - 1 - oY) * FW + (2 * X - 1 - oX);
+        const T* s = fs + (2 * Y - 1 - oY) * FW + (2 * X - 1 - oX);
         const T w[4] = {T(0.25), T(0.75), T(0.75), T(0.25)};
         g = T(0);
 #pragma unroll
@@ -186,7 +197,7 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
         for (int i = 0; i < 6; ++i) {
           // taps outside the level have zero weight; clamp them into the region
           const int yy = min(max(2 * Y - 2 + i, ry0), ry1 - 1);
-          const T* row = fineS + (yy - oY) * FW;
+          const T* row = fs + (yy - oY) * FW;
           T h = T(0);
 #pragma unroll
           for (int k = 0; k < 6; ++k) h += wx[k] * row[min(max(2 * X - 2 + k, rx0), rx1 - 1) - oX];
@@ -203,7 +214,6 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
         A.v[o] = vv[f];
       }
     }
-    if (f + 1 < NF) __syncthreads();  // fineS is reused by the next field
   }
 }
 
@@ -227,10 +237,10 @@ struct TailLayout {
   int own_off[MODIL_MAXL];  // offset of the block's own rows of each level (one field)
   int own_cells;            // cells of one field owned by one block (upper bound)
   int nf;                   // fields
-  int st_elems, h_elems;    // staging of the level above, separable scratch
+  int st_elems, h_elems;    // staging of the level above, separable scratch (per field)
   size_t bytes(int esz) const {
     const size_t oc = (size_t)own_cells * nf;
-    return 8 * oc + (size_t)esz * (3 * oc + st_elems + h_elems) + 64;
+    return 8 * oc + (size_t)esz * (3 * oc + (size_t)nf * (st_elems + h_elems)) + 64;
   }
 };
 
@@ -280,7 +290,7 @@ k_tail(const __grid_constant__ Arena<T> A, int mode, int cur) {
   T* pS = gO + oc * nf;
   T* mS = pS + oc * nf;
   T* Pst = mS + oc * nf;
-  T* H = Pst + TL.st_elems;
+  T* H = Pst + nf * TL.st_elems;
 
   // Prologue: the tail levels' parameters and moments and the bias-correction
   // powers were last written by this kernel one step earlier.
@@ -355,26 +365,27 @@ k_tail(const __grid_constant__ Arena<T> A, int mode, int cur) {
     if (b > a) {
       const int pa = max(0, 2 * a - 2), pb = min(fy, 2 * b + 2);
       const int prow = pb - pa;
-      for (int f = 0; f < nf; ++f) {
-        if (l == ts) {
+      const int sfs = prow * fx;  // staged elements per field
+      if (l == ts) {
+        for (int f = 0; f < nf; ++f) {
           const T* src = A.g + D.off[f][l - 1] + (long long)pa * fx;
-          for (int i = tid; i < prow * fx; i += kTailNT) cp_async(Pst + i, src + i);
-          cp_async_wait_all();
-        } else {
-          const int rpp = TL.rp[l - 1];
-          for (int i = tid; i < prow * fx; i += kTailNT) {
-            const int y = pa + i / fx, x = i - (i / fx) * fx;
-            const int owner = y / rpp;
-            const T* rem = cluster.map_shared_rank(gO, owner);
-            Pst[i] = rem[f * oc + TL.own_off[l - 1] + (y - owner * rpp) * fx + x];
-          }
+          for (int i = tid; i < sfs; i += kTailNT) cp_async(Pst + f * sfs + i, src + i);
         }
-        __syncthreads();
-        T* dst = gO + f * oc + TL.own_off[l];
-        restrict_sep<T, kTailNT>(Pst, fx, pa, prow, 0, fx, H, a, b - a, 0, nx, ny, nx,
-                                 [&](int k, T g) { dst[k] = g; });
-        __syncthreads();  // Pst and H are reused by the next field
+        cp_async_wait_all();
+      } else {
+        const int rpp = TL.rp[l - 1];
+        for (int i = tid; i < nf * sfs; i += kTailNT) {
+          const int f = i / sfs, j = i - f * sfs;
+          const int y = pa + j / fx, x = j - (j / fx) * fx;
+          const int owner = y / rpp;
+          const T* rem = cluster.map_shared_rank(gO, owner);
+          Pst[i] = rem[f * oc + TL.own_off[l - 1] + (y - owner * rpp) * fx + x];
+        }
       }
+      __syncthreads();
+      restrict_sep<T, kTailNT>(nf, Pst, sfs, fx, pa, prow, 0, fx, H, a, b - a, 0, nx, ny, nx,
+                               [&](int f, int k, T g) { gO[f * oc + TL.own_off[l] + k] = g; });
+      __syncthreads();  // Pst and H are reused by the next level
     }
     cluster.sync();
     // every block has read the bias-correction powers: advance them now (off the
