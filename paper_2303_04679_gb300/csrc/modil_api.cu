@@ -263,7 +263,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   P.n_aux = aoff;
   P.npart = 2 + P.nk;
   P.tail.level_kernels = P.max_tail - 1;
-  if (tail_smem_bytes(P.tail, (int)P.esz) > 220 * 1024)
+  if (tail_smem_bytes(P.tail, (int)P.esz) > 200 * 1024)  // plus about 23 KB of static shared memory
     return fail(MODIL_ERR_UNSUPPORTED, "coarse levels too large for the tail kernel");
 
   // measurements -> runs sorted by (global fine tile, cell)
