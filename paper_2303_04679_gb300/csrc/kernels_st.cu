@@ -243,24 +243,20 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
   auto tile = [&](const int gt, const bool first) {
   // ---- prologue: data no kernel of a step writes -----------------------------
   const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[0][gt];
-  load_inst(&D, A, ii);
   const int rb = A.run_ptr[gt], re = A.run_ptr[gt + 1];
   const int nrun = re - rb;              // runs hold distinct cells of the tile
   const int nst = min(nrun, G::NRUN);    // runs staged in shared memory
-  __syncthreads();
-
-  const int L = D.nlev;
-  const int ny = D.n[0][1], nx = D.n[0][2];
-  const int local = gt - D.tile_base[0];
-  const int ty = local / D.nt[0][2], tx = local - ty * D.nt[0][2];
-  const int y0 = ty * TY, x0 = tx * TX;
-  const int hy = min(TY, ny - y0), hx = min(TX, nx - x0);  // owned extent (ragged edge)
-  const int K = D.nk - 1;
-  // Pyramid regions.  Level 0 covers the tile plus the halo; level l+1 covers
-  // what interpolating level l needs, [lo/2 - 1, hi/2 + 1], clipped to the
-  // level.  Unrolled, level l starts at (lo0 - 2^(l+1) + 2) >> l and ends at
-  // (hi0 + 2^(l+1) - 2) >> l, so thread l computes level l directly.
-  if (tid < 32) {
+  // Pyramid regions, computed by warp 0.  Level 0 covers the tile plus the
+  // halo; level l+1 covers what interpolating level l needs,
+  // [lo/2 - 1, hi/2 + 1], clipped to the level.  Unrolled, level l starts at
+  // (lo0 - 2^(l+1) + 2) >> l and ends at (hi0 + 2^(l+1) - 2) >> l, so lane l
+  // computes level l directly.
+  auto regions = [&]() {
+    const int L = D.nlev;
+    const int ny = D.n[0][1], nx = D.n[0][2];
+    const int local = gt - D.tile_base[0];
+    const int ty = local / D.nt[0][2], tx = local - ty * D.nt[0][2];
+    const int y0 = ty * TY, x0 = tx * TX;
     const int a0 = max(0, y0 - G::HU), b0 = min(ny - 1, y0 + TY - 1 + G::HU);
     const int c0 = max(0, x0 - G::HU), d0 = min(nx - 1, x0 + TX - 1 + G::HU);
     int ly = 0, lx = 0, h = 0, w = 1;
@@ -284,8 +280,22 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
       winv[tid] = 1.0f / (float)w;
       poff[tid] = inc - sz;
     }
-  }
-  if (tid == 32) {  // once per block: no per-thread conversions of FP64 coefficients
+  };
+  load_inst(&D, A, ii);
+  __syncthreads();
+  if (tid < 32) regions();
+  __syncthreads();
+
+  const int L = D.nlev;
+  const int ny = D.n[0][1], nx = D.n[0][2];
+  const int local = gt - D.tile_base[0];
+  const int ty = local / D.nt[0][2], tx = local - ty * D.nt[0][2];
+  const int y0 = ty * TY, x0 = tx * TX;
+  const int hy = min(TY, ny - y0), hx = min(TX, nx - x0);  // owned extent (ragged edge)
+  const int K = D.nk - 1;
+  // once per block (read after the staging barrier): no per-thread
+  // conversions of FP64 coefficients
+  if (tid == 32) {
     StCoef<T> c;
     const T dt = (T)D.h[1], dx = (T)D.h[2];
     c.idt = T(1) / dt;
@@ -297,7 +307,6 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
     c.gscale = (T)A.gscale;
     *cS = c;
   }
-  __syncthreads();
 
   const T* __restrict__ P = A.p[cur];
   const long long o0 = D.off[0][0];
@@ -710,16 +719,19 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
   }
   // persistent launch: take tiles from the queue until it is empty
   __shared__ int s_tile;
+  if (tid == 0) s_tile = atomicAdd(A.queue, 1);
+  __syncthreads();
   bool first = true;
   for (;;) {
-    if (tid == 0) s_tile = atomicAdd(A.queue, 1);
-    __syncthreads();
     const int gt = s_tile;
-    __syncthreads();
     if (gt >= A.ntiles[0]) break;
+    int nxt = 0;
+    if (tid == 0) nxt = atomicAdd(A.queue, 1);  // the next tile, taken while this one runs
     tile(gt, first);
     first = false;
-    __syncthreads();  // shared memory is reused by the next tile
+    // every thread read s_tile before the tile's first barrier
+    if (tid == 0) s_tile = nxt;
+    __syncthreads();  // shared memory is reused by the next tile; s_tile published
   }
   if (first) {  // no tile: still complete the dependency protocol
     pdl_wait();
