@@ -86,8 +86,10 @@ def test_heat_f64_loss_grad(modil):
 
 
 def test_heat_full_size_512(modil):
-    """The measured workload: 512 x 512, 7 levels, 5 % measurements, FP32."""
-    c = Case("heat", (512, 512), 7, "f32", seed=6, n_meas=13107, w_reg=1e-4)
+    """The measured workload: 512 x 512, 7 levels, 5 % measurements, FP32, in
+    the bench's launch configuration (32 x 32 tiles: 256 tiles, 512-thread
+    blocks)."""
+    c = Case("heat", (512, 512), 7, "f32", seed=6, n_meas=13107, w_reg=1e-4, tile=(32, 32))
     with modil.Problem(c.desc()) as p:
         c.load(p)
         check_loss_grad(c, p, TOL32)
