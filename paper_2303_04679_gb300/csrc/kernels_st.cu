@@ -2,19 +2,24 @@
 // heat conduction with unknown conductivity).  One block owns a TY x TX tile
 // of the fine grid (axes t, x) and in one pass:
 //   0. issues every global load it needs at once (cp.async into shared
-//      memory): the tile's region of every level (tile plus a halo of 2 fine
-//      cells, and at each coarser level half that plus one cell), the level-1
-//      parameters and Adam moments of the tile, the conductivity nodes;
+//      memory; 16-byte copies where rows are 4-element aligned): the tile's
+//      region of every level (tile plus a halo of 2 fine cells, and at each
+//      coarser level half that plus one cell), the level-1 Adam moments of
+//      the tile, its measurement runs, the conductivity nodes;
 //   1. composes the field on the tile by Horner's scheme on that pyramid
-//      (w_L = u_L, w_i = u_i + T_i w_{i+1}; paper Section 2.2);
+//      (w_L = u_L, w_i = u_i + T_i w_{i+1}; paper Section 2.2), the fine
+//      level streamed down columns;
 //   2. evaluates every residual that touches the tile (tile plus 1 cell) and
-//      its local Jacobian, dr/du at the 4 stencil points;
-//   3. reduces r^2 over the residuals it owns (FP64 partial per tile);
-//   4. forms dL/du on the tile in gather form: each cell sums
-//      lambda * dr/du over the residuals that read it (lambda = 2 w dV r);
-//   5. adds the data term of the measurements inside the tile;
-//   6. writes the fine gradient, applies Adam to level 1 (step mode), and for
-//      the heat problem reduces dL/dq of the conductivity nodes into a
+//      its local Jacobian, dr/du at the 4 stencil points, streamed down
+//      columns, and keeps lambda * dr/du (lambda = 2 w dV r);
+//   3. adds the data term of the measurements inside the tile to the cell's
+//      own term;
+//   4. reduces r^2 and the data misfit over what it owns (FP64 partials per
+//      tile);
+//   5. forms dL/du in gather form (each cell sums lambda * dr/du over the
+//      residuals that read it), writes it and applies Adam to level 1 (step
+//      mode), 2 or 4 cells of a row per thread;
+//   6. for the heat problem reduces dL/dq of the conductivity nodes into a
 //      per-tile partial (deterministic warp-range binning).
 // The per-tile partials are summed by the per-instance tail kernel.
 // The stencils are the discretisations of the paper's Sections 3.2 and 3.4:
