@@ -547,6 +547,32 @@ def run_small(args):
                                                "loss_after": float(static_loss.item())}
             except Exception as e:  # report, keep the line
                 out_extra["autograd_graph"] = {"error": str(e)[:300]}
+    if args.workload == "burgers":
+        # the configuration's plain Adam run (2000 steps) against L-BFGS with
+        # a history of 50 (the paper's optimiser), both from zero levels
+        with modil.Problem(desc) as pa:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pa.step(2000, read_loss=False)
+            torch.cuda.synchronize()
+            t_adam = time.perf_counter() - t0
+            loss_adam = float(pa.eval_loss()[0, 0])
+
+        def lbfgs_run(iters):
+            with modil.Problem(desc) as pl, modil.LBFGS(pl, history=50) as opt:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                h = opt.run(iters)
+                return h, time.perf_counter() - t0
+        hist, t_lb = lbfgs_run(400)
+        reach = next((k for k, v in enumerate(hist) if v <= loss_adam), None)
+        t_reach = lbfgs_run(reach)[1] if reach else None
+        out_extra["lbfgs"] = {
+            "history": 50, "iterations": len(hist) - 1, "seconds": t_lb,
+            "ms_per_iteration": 1e3 * t_lb / max(len(hist) - 1, 1), "final_loss": float(hist[-1]),
+            "adam_2000_steps": {"seconds": t_adam, "final_loss": loss_adam},
+            "iterations_to_adam_final_loss": reach, "seconds_to_adam_final_loss": t_reach,
+            "note": "host wall time, no L2 flush; L-BFGS line search reads the loss on the host"}
     step_ms = float(np.sum(ms) / K)
     peak, kind = measured_peak()
     nf = 3 if args.workload == "cavity" else 1

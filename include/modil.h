@@ -227,6 +227,34 @@ modil_status modil_reset_optimizer(modil_problem* p);
 modil_status modil_eval_grad_noalloc(const modil_desc* desc, const void* levels, void* grads,
                                      double* terms, double* kgrad, void* stream);
 
+/* Limited-memory BFGS on the levels of a problem: the optimiser the paper
+ * uses for most of its results (SciPy's L-BFGS-B without bounds, Section 2.1;
+ * a history of 50 pairs in Section 3.1).  The paper gives no algorithmic
+ * detail; this is the textbook method: direction -H g by the two-loop
+ * recursion over the newest `history` pairs (s, y) with H0 = (s.y / y.y) I of
+ * the newest pair; the first direction -g with a first trial step of
+ * 1 / ||g||; backtracking on the Armijo condition f(x + t d) <= f(x) +
+ * 1e-4 t g.d, halving t, at most 40 trials (the run stops when none passes
+ * or g.d >= 0); a pair is kept only when s.y > 1e-12 y.y.  Vectors live on
+ * the device in the problem's dtype; dot products are reduced in FP64 in a
+ * fixed order; the loss and gradient are the problem's own kernels.
+ *   modil_lbfgs_create: single-instance problems whose unknowns are their
+ *     levels (Burgers, cavity, body; not heat, whose conductivity nodes are
+ *     unknowns too: MODIL_ERR_UNSUPPORTED).  Allocates (2 history + 6) level
+ *     vectors of device memory.  The optimiser keeps a pointer to p, which
+ *     must outlive it.
+ *   modil_lbfgs_run: continues from the problem's current levels (the pair
+ *     history is kept across calls) for up to `iterations` iterations; writes
+ *     the final levels and their gradient back into the problem (readable
+ *     with modil_read_level / modil_read_grad; Adam's state is untouched).
+ *     loss: host output of iterations + 1 doubles or NULL: the loss at the
+ *     start and after each completed iteration.  done: iterations completed.
+ *     Synchronises the problem's stream (the line search reads the loss). */
+typedef struct modil_lbfgs modil_lbfgs;
+modil_status modil_lbfgs_create(modil_problem* p, int history, modil_lbfgs** out);
+modil_status modil_lbfgs_run(modil_lbfgs* o, int iterations, double* loss, int* done);
+void modil_lbfgs_destroy(modil_lbfgs* o);
+
 /* Last error message of the calling thread ("" if none). */
 const char* modil_last_error(void);
 

@@ -1,0 +1,26 @@
+// Launchers of the limited-memory BFGS vector kernels (lbfgs.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace modil {
+
+// out = (mul ? *mul : 1) * (x . y); part: lb_dot_partials() doubles of scratch.
+template <class T>
+cudaError_t lb_dot(const T* x, const T* y, long long n, double* part, const double* mul, double* out,
+                   cudaStream_t s);
+// y += sign * (*a - (b ? *b : 0)) * x.
+template <class T>
+cudaError_t lb_axpy(T* y, const T* x, const double* a, const double* b, double sign, long long n,
+                    cudaStream_t s);
+// r = (*num / *den) * q.
+template <class T>
+cudaError_t lb_scale(T* r, const T* q, const double* num, const double* den, long long n, cudaStream_t s);
+// z = x + a * y.
+template <class T>
+cudaError_t lb_axpby(T* z, const T* x, const T* y, double a, long long n, cudaStream_t s);
+// z = x - y.
+template <class T>
+cudaError_t lb_sub(T* z, const T* x, const T* y, long long n, cudaStream_t s);
+int lb_dot_partials();
+
+}  // namespace modil

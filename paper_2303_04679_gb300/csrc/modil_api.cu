@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,7 @@
 
 #include "modil.h"
 #include "launch.h"
+#include "lbfgs.h"
 #include "modil_dev.cuh"
 
 using namespace modil;
@@ -878,6 +880,203 @@ modil_status modil_reset_optimizer(modil_problem* p) {
   if (e != cudaSuccess) return fail(MODIL_ERR_CUDA, cudaGetErrorString(e));
   p->steps = 0;
   return MODIL_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Limited-memory BFGS over the level arena of a single-instance problem
+// ---------------------------------------------------------------------------
+struct modil_lbfgs {
+  modil_problem* p = nullptr;
+  int m = 0;                 // pairs kept
+  long long n = 0;           // parameters (all fields and levels)
+  void* vec = nullptr;       // device: S[m], Y[m], then 6 work vectors, problem dtype
+  double* dsc = nullptr;     // device: dot partials, rho[m], alpha[m], sy[m], yy[m], beta, scratch
+  std::vector<int> order;    // slots of the stored pairs, oldest first
+  long long iters = 0;       // iterations completed over the optimiser's life
+};
+
+namespace {
+
+template <class T>
+Arena<T>& arena_of(modil_problem* p);
+template <>
+Arena<float>& arena_of<float>(modil_problem* p) { return p->A32; }
+template <>
+Arena<double>& arena_of<double>(modil_problem* p) { return p->A64; }
+
+template <class T>
+modil_status lbfgs_run_t(modil_lbfgs* o, int iters, double* loss, int* done) {
+  constexpr double kC1 = 1e-4, kCurv = 1e-12;
+  constexpr int kTrials = 40;
+  modil_problem* p = o->p;
+  cudaStream_t s = p->stream;
+  const long long n = o->n;
+  const int m = o->m;
+  const size_t vb = sizeof(T) * (size_t)n;
+  T* base = static_cast<T*>(o->vec);
+  auto Sv = [&](int i) { return base + (size_t)i * n; };
+  auto Yv = [&](int i) { return base + (size_t)(m + i) * n; };
+  T* x = base + (size_t)(2 * m) * n;
+  T* xt = x + n;
+  T* g = xt + n;
+  T* gn = g + n;
+  T* q = gn + n;
+  T* r = q + n;
+  double* part = o->dsc;
+  double* rho = part + lb_dot_partials();
+  double* alpha = rho + m;
+  double* sy = alpha + m;
+  double* yy = sy + m;
+  double* beta = yy + m;
+  double* tmp = beta + 1;
+  Arena<T>& A = arena_of<T>(p);
+  T* pc = A.p[p->steps & 1];  // the problem's current levels
+  double terms[MODIL_NTERMS];
+  // loss (and gradient) at lv; a non-finite loss of a trial point counts as
+  // +inf (the line search backs off) and the problem's latch is cleared
+  auto eval = [&](T* lv, T* gr, double* f) -> modil_status {
+    modil_status st = external_pass<T>(p, A, lv, gr, 1.0, gr ? MODE_GRAD : MODE_LOSS);
+    if (st == MODIL_OK) st = read_terms(p, terms);
+    *f = terms[0];
+    if (st == MODIL_ERR_NONFINITE && !gr) {
+      CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(A.st) + offsetof(InstState, nonfinite), 0, sizeof(int), s));
+      *f = HUGE_VAL;
+      return MODIL_OK;
+    }
+    return st;
+  };
+  auto dot_host = [&](const T* a, const T* b, double* out) -> modil_status {
+    CUDA_TRY(lb_dot<T>(a, b, n, part, nullptr, tmp, s));
+    CUDA_TRY(cudaMemcpyAsync(out, tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return MODIL_OK;
+  };
+  CUDA_TRY(cudaMemcpyAsync(x, pc, vb, cudaMemcpyDeviceToDevice, s));
+  double fx = 0.0;
+  modil_status st = eval(x, g, &fx);
+  if (st != MODIL_OK) return st;
+  if (loss) loss[0] = fx;
+  int k = 0;
+  for (; k < iters; ++k) {
+    // r = H g by the two-loop recursion, newest pair first; d = -r
+    const int np = (int)o->order.size();
+    if (np == 0) {
+      CUDA_TRY(cudaMemcpyAsync(r, g, vb, cudaMemcpyDeviceToDevice, s));
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(q, g, vb, cudaMemcpyDeviceToDevice, s));
+      for (int j = np - 1; j >= 0; --j) {
+        const int i = o->order[j];
+        CUDA_TRY(lb_dot<T>(Sv(i), q, n, part, rho + i, alpha + i, s));   // alpha_i = rho_i s_i.q
+        CUDA_TRY(lb_axpy<T>(q, Yv(i), alpha + i, nullptr, -1.0, n, s));  // q -= alpha_i y_i
+      }
+      const int nw = o->order.back();
+      CUDA_TRY(lb_scale<T>(r, q, sy + nw, yy + nw, n, s));  // r = (s.y / y.y) q
+      for (int j = 0; j < np; ++j) {
+        const int i = o->order[j];
+        CUDA_TRY(lb_dot<T>(Yv(i), r, n, part, rho + i, beta, s));       // beta = rho_i y_i.r
+        CUDA_TRY(lb_axpy<T>(r, Sv(i), alpha + i, beta, 1.0, n, s));    // r += (alpha_i - beta) s_i
+      }
+    }
+    double gr = 0.0;
+    if ((st = dot_host(g, r, &gr)) != MODIL_OK) return st;
+    const double gd = -gr;  // g.d
+    if (!(gd < 0.0)) break;
+    double t = 1.0;
+    if (o->iters == 0) {
+      double gg = 0.0;
+      if ((st = dot_host(g, g, &gg)) != MODIL_OK) return st;
+      t = 1.0 / std::sqrt(gg);
+    }
+    // backtracking on the Armijo condition
+    bool ok = false;
+    double ft = 0.0;
+    for (int trial = 0; trial < kTrials; ++trial) {
+      CUDA_TRY(lb_axpby<T>(xt, x, r, -t, n, s));  // xt = x + t d
+      if ((st = eval(xt, nullptr, &ft)) != MODIL_OK) return st;
+      if (ft <= fx + kC1 * t * gd) { ok = true; break; }
+      t *= 0.5;
+    }
+    if (!ok) break;
+    if ((st = eval(xt, gn, &ft)) != MODIL_OK) return st;
+    // candidate pair in the work vectors q (s) and r (y)
+    CUDA_TRY(lb_sub<T>(q, xt, x, n, s));
+    CUDA_TRY(lb_sub<T>(r, gn, g, n, s));
+    double sy_h = 0.0, yy_h = 0.0;
+    if ((st = dot_host(q, r, &sy_h)) != MODIL_OK) return st;
+    if ((st = dot_host(r, r, &yy_h)) != MODIL_OK) return st;
+    if (sy_h > kCurv * yy_h) {
+      int slot;
+      if ((int)o->order.size() < m) {
+        slot = (int)o->order.size();
+      } else {
+        slot = o->order.front();
+        o->order.erase(o->order.begin());
+      }
+      CUDA_TRY(cudaMemcpyAsync(Sv(slot), q, vb, cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(Yv(slot), r, vb, cudaMemcpyDeviceToDevice, s));
+      const double sc[3] = {sy_h, yy_h, 1.0 / sy_h};
+      CUDA_TRY(cudaMemcpy(sy + slot, &sc[0], sizeof(double), cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(yy + slot, &sc[1], sizeof(double), cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(rho + slot, &sc[2], sizeof(double), cudaMemcpyHostToDevice));
+      o->order.push_back(slot);
+    }
+    std::swap(x, xt);
+    std::swap(g, gn);
+    fx = ft;
+    if (loss) loss[k + 1] = fx;
+    o->iters++;
+  }
+  // the result and its gradient become the problem's levels and gradient
+  CUDA_TRY(cudaMemcpyAsync(pc, x, vb, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(A.g, g, vb, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (done) *done = k;
+  return MODIL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+modil_status modil_lbfgs_create(modil_problem* p, int history, modil_lbfgs** out) {
+  if (!p || !out) return fail(MODIL_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  const Plan& P = p->plan;
+  if (history < 1) return fail(MODIL_ERR_ARG, "history < 1");
+  if (P.n_inst != 1) return fail(MODIL_ERR_UNSUPPORTED, "L-BFGS: single-instance problems only");
+  if (P.pde == MODIL_PDE_HEAT)
+    return fail(MODIL_ERR_UNSUPPORTED, "L-BFGS: the conductivity nodes of the heat problem are not in the level arena");
+  modil_lbfgs* o = new (std::nothrow) modil_lbfgs();
+  if (!o) return fail(MODIL_ERR_ARG, "out of host memory");
+  o->p = p;
+  o->m = history;
+  o->n = P.n_param;
+  cudaError_t e = cudaMalloc(&o->vec, P.esz * (size_t)P.n_param * (2 * (size_t)history + 6));
+  if (e == cudaSuccess)
+    e = cudaMalloc(&o->dsc, sizeof(double) * ((size_t)lb_dot_partials() + 4 * (size_t)history + 2));
+  if (e != cudaSuccess) {
+    modil_lbfgs_destroy(o);
+    return fail(MODIL_ERR_CUDA, std::string("L-BFGS buffers: ") + cudaGetErrorString(e));
+  }
+  *out = o;
+  return MODIL_OK;
+}
+
+modil_status modil_lbfgs_run(modil_lbfgs* o, int iterations, double* loss, int* done) {
+  if (!o) return fail(MODIL_ERR_ARG, "optimiser is NULL");
+  if (iterations < 0) return fail(MODIL_ERR_ARG, "iterations < 0");
+  if (done) *done = 0;
+  return o->p->plan.dtype == MODIL_F64 ? lbfgs_run_t<double>(o, iterations, loss, done)
+                                       : lbfgs_run_t<float>(o, iterations, loss, done);
+}
+
+void modil_lbfgs_destroy(modil_lbfgs* o) {
+  if (!o) return;
+  if (o->vec) cudaFree(o->vec);
+  if (o->dsc) cudaFree(o->dsc);
+  delete o;
 }
 
 const char* modil_last_error(void) { return g_err.c_str(); }

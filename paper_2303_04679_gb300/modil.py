@@ -82,6 +82,9 @@ def _load():
         "modil_terms_device": ([P, C.POINTER(C.c_void_p), C.POINTER(C.c_int)], C.c_int),
         "modil_eval_grad_noalloc": ([C.POINTER(modil_desc), P, P, C.POINTER(C.c_double),
                                      C.POINTER(C.c_double), P], C.c_int),
+        "modil_lbfgs_create": ([P, C.c_int, C.POINTER(P)], C.c_int),
+        "modil_lbfgs_run": ([P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)], C.c_int),
+        "modil_lbfgs_destroy": ([P], None),
         "modil_last_error": ([], C.c_char_p),
         "modil_version": ([], C.c_char_p),
     }
@@ -359,6 +362,40 @@ class Problem:
 
     def reset_optimizer(self):
         _check(LIB.modil_reset_optimizer(self._h))
+
+
+class LBFGS:
+    """Limited-memory BFGS on the levels of a single-instance problem (the
+    library's two-loop recursion and Armijo backtracking on the device; see
+    modil_lbfgs_create).  The problem must outlive the optimiser."""
+
+    def __init__(self, problem, history=50):
+        self.problem = problem
+        h = C.c_void_p()
+        _check(LIB.modil_lbfgs_create(problem._h, int(history), C.byref(h)))
+        self._h = h
+
+    def run(self, iterations):
+        """Up to `iterations` iterations from the problem's current levels;
+        returns the loss at the start and after each completed iteration."""
+        loss = np.zeros(int(iterations) + 1, dtype=np.float64)
+        done = C.c_int()
+        _check(LIB.modil_lbfgs_run(self._h, int(iterations), _dptr(loss, C.c_double), C.byref(done)))
+        return loss[:done.value + 1]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            LIB.modil_lbfgs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def eval_grad_noalloc(desc, levels, grads, stream=None):
