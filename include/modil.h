@@ -65,13 +65,18 @@ enum {
   MODIL_PDE_NS2D = 3,    /* steady incompressible Navier-Stokes, lid-driven cavity on
                             [0,1]^2 (square grid), fields 0 = u, 1 = v, 2 = p; collocated
                             finite volumes with Rhie-Chow continuity; Section 3.3   */
-  MODIL_PDE_NS3D = 4     /* steady Navier-Stokes past a body in 3-D with the body as
+  MODIL_PDE_NS3D = 4,    /* steady Navier-Stokes past a body in 3-D with the body as
                             a penalisation field (Section 3.5, the penalised momentum
                             equation): axes (z, y, x) on [0,1] x [0,1] x [0,2], fields
                             0 = u, 1 = v, 2 = w (velocity along x, y, z), 3 = p,
                             4 = chihat with body fraction chi = 1/(1+exp(-(chihat+5)));
                             inlet x = 0 (u = (1,0,0)), outlet x = 2 (p = 0), free-slip
                             walls in y and z; ndim = 3                               */
+  MODIL_PDE_POISSON = 5  /* Poisson equation lap(u) = f on [0,1]^2, axes (y, x), cell
+                            layout: finite volumes at cell centres, zero Dirichlet
+                            walls by quadratic extrapolation from the wall and the two
+                            nearest centres (ghost = -2 u_0 + u_1 / 3); residual in
+                            every cell; f in aux; both axes >= 2 cells; Section 3.1 */
 };
 
 enum { MODIL_F32 = 0, MODIL_F64 = 1 };
@@ -101,7 +106,9 @@ typedef struct {
   const int32_t* meas_cell;  /* flat fine-grid cell index per measurement       */
   const int32_t* meas_field; /* field index per measurement, or NULL (field 0)  */
   const double* meas_value;  /* measured value                                  */
-  int n_aux;                 /* HEAT: initial temperature, one per x cell       */
+  int n_aux;                 /* HEAT: initial temperature, one per x cell;
+                                POISSON: right-hand side f, one per fine cell
+                                (row-major, n_aux = ny * nx)                   */
   const double* aux;
   int n_knodes;              /* HEAT: conductivity nodes q_0..q_{K}, K+1 <= 64  */
   const double* knodes;      /* initial q (copied)                              */

@@ -31,7 +31,10 @@
 //   heat, rows n >= 1 (row 0: (u^0_i - u_init_i)/dt):
 //     r = (u^n_i - u^{n-1}_i)/dt
 //         - [k_{i+1/2}(u^n_{i+1}-u^n_i) - k_{i-1/2}(u^n_i-u^n_{i-1})]/dx^2,
-//     k_{i+1/2} = k((u^n_i + u^n_{i+1})/2), k piecewise linear in the nodes q.
+//     k_{i+1/2} = k((u^n_i + u^n_{i+1})/2), k piecewise linear in the nodes q;
+//   Poisson (Section 3.1, cell layout on [0,1]^2, axes (y, x)), every cell:
+//     r = (u_E - 2u + u_W)/dx^2 + (u_N - 2u + u_S)/dy^2 - f, a wall's ghost
+//     -2 u_0 + u_1/3 (quadratic extrapolation through the zero wall value).
 #include <algorithm>
 
 #include "launch.h"
@@ -72,7 +75,9 @@ struct StSmem {
   static constexpr size_t o_p0 = a16(o_red + 8 * 16);                   // staged level 0
   static constexpr size_t o_u = a16(o_p0 + sizeof(T) * G::UH * G::SW);  // composed field
   static constexpr size_t o_a = a16(o_u + sizeof(T) * G::UH * G::SW);   // lambda * dr/du
-  static constexpr size_t o_m = a16(o_a + sizeof(T) * 4 * G::NA);
+  // lambda * dr/du per stencil neighbour: W, centre, E, S (and N for Poisson)
+  static constexpr int NJ = (PDE == PDE_POISSON) ? 5 : 4;
+  static constexpr size_t o_m = a16(o_a + sizeof(T) * NJ * G::NA);
   static constexpr size_t o_v = a16(o_m + sizeof(T) * TY * TX);
   static constexpr size_t o_rc = a16(o_v + sizeof(double) * TY * TX);  // runs: cell
   static constexpr size_t o_rb = a16(o_rc + 4 * G::NRUN);              // runs: first value index
@@ -89,7 +94,7 @@ struct StSmem {
 // Coefficients of a tile in the working precision, converted once per block.
 template <class T>
 struct StCoef {
-  T idt, idx1, idx2, nu, lam_scale, wd2, gscale;
+  T idt, idx1, idx2, idy2, nu, lam_scale, wd2, gscale;
 };
 
 // 16-byte asynchronous copies (both addresses 16-byte aligned).
@@ -306,6 +311,7 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
     c.idt = T(1) / dt;
     c.idx1 = T(1) / dx;
     c.idx2 = T(1) / (dx * dx);
+    c.idy2 = T(1) / (dt * dt);
     c.nu = (T)D.coef[0];
     c.lam_scale = T(2) * (T)D.w_res_dV;
     c.wd2 = T(2) * (T)D.w_data_n;
@@ -501,10 +507,29 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
       const T* uq = up + ry * G::SW;
       const T uc = uq[0], uo = uprev;
       uprev = uc;
-      T r = T(0), J0 = T(0), J1 = T(0), J2 = T(0), J3 = T(0), dE = T(0), dW = T(0);
+      T r = T(0), J0 = T(0), J1 = T(0), J2 = T(0), J3 = T(0), J4 = T(0), dE = T(0), dW = T(0);
       bool valid = xin && (y >= 0 && y < ny);
       if (PDE == PDE_BURGERS && y == 0) valid = false;
-      if (valid) {
+      if (valid && PDE == PDE_POISSON) {
+        // 5-point Laplacian minus f; a wall's ghost value is the quadratic
+        // extrapolation -2 u_0 + u_1 / 3 through the zero wall value (both
+        // axes have >= 2 cells, so the inner neighbour exists)
+        const bool hs = (y > 0), hn = (y < ny - 1);
+        const T third = T(1) / T(3);
+        const T uw = uq[-1], ue = uq[1], un = uq[G::SW];
+        const T gw = hw ? uw : T(-2) * uc + ue * third;
+        const T ge = he ? ue : T(-2) * uc + uw * third;
+        const T gs = hs ? uo : T(-2) * uc + un * third;
+        const T gn = hn ? un : T(-2) * uc + uo * third;
+        const T f = A.aux[D.aux_off + (long long)y * nx + x];
+        r = (ge - T(2) * uc + gw) * cf.idx2 + (gn - T(2) * uc + gs) * cf.idy2 - f;
+        J1 = (T(-2) - (hw ? T(0) : T(2)) - (he ? T(0) : T(2))) * cf.idx2 +
+             (T(-2) - (hs ? T(0) : T(2)) - (hn ? T(0) : T(2))) * cf.idy2;
+        J0 = hw ? (T(1) + (he ? T(0) : third)) * cf.idx2 : T(0);  // dr/du at x - 1
+        J2 = he ? (T(1) + (hw ? T(0) : third)) * cf.idx2 : T(0);  // x + 1
+        J3 = hs ? (T(1) + (hn ? T(0) : third)) * cf.idy2 : T(0);  // y - 1
+        J4 = hn ? (T(1) + (hs ? T(0) : third)) * cf.idy2 : T(0);  // y + 1
+      } else if (valid) {
         if (PDE == PDE_HEAT && y == 0) {
           r = (uc - icS[x - x0 + G::SX]) * cf.idt;
           J1 = cf.idt;
@@ -567,6 +592,7 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
         aJ[1 * G::NA + c] = lam * J1;
         aJ[2 * G::NA + c] = lam * J2;
         aJ[3 * G::NA + c] = lam * J3;
+        if (PDE == PDE_POISSON) aJ[4 * G::NA + c] = lam * J4;
         if (PDE == PDE_HEAT && ry >= 1 && ry <= TY && rx >= 1 && rx <= TX) {
           const int o = (ry - 1) * TX + (rx - 1);
           muE[o] = owned ? lam * dE : T(0);
@@ -624,7 +650,8 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
 #pragma unroll
       for (int k = 0; k < VW; ++k)
         g[k] = (aJ[1 * G::NA + c + k] + aJ[0 * G::NA + c + k + 1] + aJ[2 * G::NA + c + k - 1] +
-                aJ[3 * G::NA + c + k + G::RW]) * cf.gscale;
+                aJ[3 * G::NA + c + k + G::RW] + (PDE == PDE_POISSON ? aJ[4 * G::NA + c + k - G::RW] : T(0))) *
+               cf.gscale;
       const long long e = (long long)(y0 + oy) * nx + (x0 + ox);
       const int sp = (oy + G::HU) * G::SW + ox + G::SX, sm = oy * TX + ox;
       if (vec) {  // VW owned cells, aligned
@@ -777,6 +804,7 @@ static cudaError_t launch_cfg(const Arena<T>& A, int pde, int mode, int cur, siz
   if (A.ntiles[0] == 0) return cudaSuccess;
   if (pde == PDE_BURGERS) return launch_one<T, PDE_BURGERS, TY, TX>(A, mode, cur, pyr, s);
   if (pde == PDE_HEAT) return launch_one<T, PDE_HEAT, TY, TX>(A, mode, cur, pyr, s);
+  if (pde == PDE_POISSON) return launch_one<T, PDE_POISSON, TY, TX>(A, mode, cur, pyr, s);
   return cudaErrorInvalidValue;
 }
 
@@ -786,6 +814,8 @@ static cudaError_t prepare_cfg(int pde, size_t pyr) {
     return raise_smem_limit(k_fine_st<T, PDE_BURGERS, TY, TX>, StSmem<T, PDE_BURGERS, TY, TX>::bytes(pyr));
   if (pde == PDE_HEAT)
     return raise_smem_limit(k_fine_st<T, PDE_HEAT, TY, TX>, StSmem<T, PDE_HEAT, TY, TX>::bytes(pyr));
+  if (pde == PDE_POISSON)
+    return raise_smem_limit(k_fine_st<T, PDE_POISSON, TY, TX>, StSmem<T, PDE_POISSON, TY, TX>::bytes(pyr));
   return cudaErrorInvalidValue;
 }
 
@@ -824,6 +854,7 @@ static cudaError_t occ(size_t pyr, int* n) {
 
 template <class T, int TY, int TX>
 static cudaError_t occ_pde(int pde, size_t pyr, int* n) {
+  if (pde == PDE_POISSON) return occ<T, PDE_POISSON, TY, TX>(pyr, n);
   return pde == PDE_HEAT ? occ<T, PDE_HEAT, TY, TX>(pyr, n) : occ<T, PDE_BURGERS, TY, TX>(pyr, n);
 }
 
@@ -854,6 +885,7 @@ static size_t smem_pde(int cfg, size_t pyr, bool d) {
 
 size_t fine_st_smem_bytes(int pde, int cfg, size_t pyr, int elem) {
   const bool d = (elem == 8);
+  if (pde == PDE_POISSON) return smem_pde<PDE_POISSON>(cfg, pyr, d);
   return pde == PDE_HEAT ? smem_pde<PDE_HEAT>(cfg, pyr, d) : smem_pde<PDE_BURGERS>(cfg, pyr, d);
 }
 

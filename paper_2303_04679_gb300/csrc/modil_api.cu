@@ -100,7 +100,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   P.dtype = d[0].dtype;
   P.ndim = d[0].ndim;
   if (P.pde != MODIL_PDE_BURGERS && P.pde != MODIL_PDE_HEAT && P.pde != MODIL_PDE_NS2D &&
-      P.pde != MODIL_PDE_NS3D)
+      P.pde != MODIL_PDE_NS3D && P.pde != MODIL_PDE_POISSON)
     return fail(MODIL_ERR_UNSUPPORTED, "unknown pde " + std::to_string(P.pde));
   if (P.dtype != MODIL_F32 && P.dtype != MODIL_F64) return fail(MODIL_ERR_ARG, "dtype");
   const bool three = P.pde == MODIL_PDE_NS3D;
@@ -151,6 +151,10 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
       if (ny != nx) return fail(MODIL_ERR_ARG, "the cavity grid must be square");
       if (!(q.coef[0] > 0)) return fail(MODIL_ERR_ARG, "NS2D needs coef[0] = Re > 0");
       if (!(q.coef[1] >= 0)) return fail(MODIL_ERR_ARG, "NS2D needs coef[1] = tau factor >= 0");
+    }
+    if (P.pde == MODIL_PDE_POISSON) {
+      if (q.n_aux != ny * nx || !q.aux) return fail(MODIL_ERR_ARG, "Poisson needs aux[ny * nx] (right-hand side)");
+      if (ny < 2 || nx < 2) return fail(MODIL_ERR_ARG, "Poisson needs >= 2 cells per axis");
     }
     if (P.pde == MODIL_PDE_HEAT) {
       if (q.n_aux != nx || !q.aux) return fail(MODIL_ERR_ARG, "heat needs aux[nx] (initial profile)");
@@ -231,7 +235,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
     D.k_off = koff;
     koff += ip.nk;
     D.aux_off = aoff;
-    aoff += (P.pde == MODIL_PDE_HEAT) ? nx : 0;
+    aoff += (P.pde == MODIL_PDE_HEAT) ? nx : (P.pde == MODIL_PDE_POISSON ? (long long)ny * nx : 0);
     if (P.pde == MODIL_PDE_BURGERS) {
       D.h[0] = 1.0; D.h[1] = 1.0 / ny; D.h[2] = 2.0 / nx;
     } else if (three) {
@@ -569,7 +573,8 @@ modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t ar
   std::vector<double> kq, aux;
   for (int i = 0; i < n; ++i) {
     if (P.inst[i].nk) kq.insert(kq.end(), descs[i].knodes, descs[i].knodes + P.inst[i].nk);
-    if (P.pde == MODIL_PDE_HEAT) aux.insert(aux.end(), descs[i].aux, descs[i].aux + descs[i].n_aux);
+    if (P.pde == MODIL_PDE_HEAT || P.pde == MODIL_PDE_POISSON)
+      aux.insert(aux.end(), descs[i].aux, descs[i].aux + descs[i].n_aux);
   }
   modil_status st = MODIL_OK;
   if (P.dtype == MODIL_F64) {

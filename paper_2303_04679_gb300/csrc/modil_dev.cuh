@@ -25,7 +25,7 @@
 namespace modil {
 
 enum Mode { MODE_LOSS = 0, MODE_GRAD = 1, MODE_STEP = 2, MODE_COMPOSE = 3 };
-enum Pde { PDE_BURGERS = 1, PDE_HEAT = 2, PDE_NS2D = 3, PDE_NS3D = 4 };
+enum Pde { PDE_BURGERS = 1, PDE_HEAT = 2, PDE_NS2D = 3, PDE_NS3D = 4, PDE_POISSON = 5 };
 
 // Per-instance description (read-only on the device).
 struct DevInst {

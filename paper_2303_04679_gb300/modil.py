@@ -19,6 +19,7 @@ PDE_BURGERS = 1
 PDE_HEAT = 2
 PDE_NS2D = 3
 PDE_NS3D = 4
+PDE_POISSON = 5
 F32 = 0
 F64 = 1
 NTERMS = 4
@@ -118,7 +119,7 @@ class Desc:
                            meas_value=meas_value, meas_field=meas_field, aux=aux, knodes=knodes,
                            lr=lr, beta1=beta1, beta2=beta2, eps=eps, tile=tile)
         self.pde = {"burgers": PDE_BURGERS, "heat": PDE_HEAT, "ns2d": PDE_NS2D,
-                    "ns3d": PDE_NS3D}.get(pde, pde)
+                    "ns3d": PDE_NS3D, "poisson": PDE_POISSON}.get(pde, pde)
         self.dtype = {"f32": F32, "f64": F64}.get(dtype, dtype)
         self.shape = tuple(int(s) for s in shape)
         self.n_levels = int(n_levels)
