@@ -54,7 +54,8 @@ def _oracle_run(c, m, iters):
 
 
 @pytest.mark.parametrize("pde,shape,L,kw", [("burgers", (64, 64), 4, dict(n_meas=200, nu=0.01)),
-                                            ("ns2d", (16, 16), 3, dict(n_meas=40, Re=100.0))])
+                                            ("ns2d", (16, 16), 3, dict(n_meas=40, Re=100.0)),
+                                            ("ns3d", (8, 8, 16), 3, dict(n_meas=50, Re=60.0))])
 def test_lbfgs_matches_oracle_f64(modil, pde, shape, L, kw):
     c = Case(pde, shape, L, "f64", seed=40, **kw)
     m, iters = 4, 10
