@@ -377,3 +377,12 @@ def poisson_workload(n=32):
     grad2 = (dphx * phy) ** 2 + (phx * dphy) ** 2
     lapv = -10.0 * phy - 10.0 * phx
     return dict(shape=(n, n), u_ref=g, f=g2 * grad2 + g1 * lapv)
+
+
+def uniform_noise(values, amplitude=0.05, seed=0):
+    """Measured values with additive noise drawn from U[0, amplitude] (the
+    noisy variant of the Burgers reconstruction in Section 3.2 uses
+    U[0, 0.05])."""
+    rng = make_rng(seed)
+    v = np.asarray(values, dtype=np.float64)
+    return v + rng.uniform(0.0, amplitude, size=v.shape)

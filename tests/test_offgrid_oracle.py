@@ -1,0 +1,60 @@
+"""Pins of the off-grid measurement oracle (CPU): exact at cell centres,
+exact for fields linear along every axis between the outermost centres,
+clamped beyond them, weights forming a partition of unity, and a gradient
+that matches finite differences of the data term."""
+import numpy as np
+
+from oracle import offgrid_oracle as og
+
+
+def _centres(n, length):
+    return (np.arange(n) + 0.5) * length / n
+
+
+def test_cell_centres_return_cell_values():
+    rng = np.random.default_rng(7)
+    shape, lengths = (6, 9), (1.0, 2.0)
+    u = rng.standard_normal(shape)
+    yc, xc = _centres(6, 1.0), _centres(9, 2.0)
+    pts = np.array([(y, x) for y in yc for x in xc])
+    idx, w = og.sample_weights(pts, shape, lengths)
+    assert np.allclose(og.sample(u, idx, w), u.reshape(-1), rtol=0, atol=1e-14)
+
+
+def test_linear_fields_are_reproduced_inside_the_centres():
+    rng = np.random.default_rng(8)
+    for shape, lengths in (((7, 5), (1.0, 1.0)), ((4, 6, 8), (1.0, 1.0, 2.0))):
+        d = len(shape)
+        coef = rng.standard_normal(d + 1)
+        grids = np.meshgrid(*[_centres(n, L) for n, L in zip(shape, lengths)], indexing="ij")
+        u = coef[0] + sum(c * g for c, g in zip(coef[1:], grids))
+        lo = np.array([L / n / 2 for n, L in zip(shape, lengths)])
+        hi = np.array([L - L / n / 2 for n, L in zip(shape, lengths)])
+        pts = lo + rng.uniform(0, 1, (200, d)) * (hi - lo)
+        idx, w = og.sample_weights(pts, shape, lengths)
+        exact = coef[0] + pts @ coef[1:]
+        assert np.allclose(og.sample(u, idx, w), exact, rtol=0, atol=1e-12)
+        assert np.all(w >= 0) and np.allclose(w.sum(axis=1), 1.0)
+
+
+def test_points_beyond_the_outermost_centres_are_clamped():
+    shape, lengths = (4, 4), (1.0, 1.0)
+    u = np.arange(16.0).reshape(shape)
+    idx, w = og.sample_weights([(0.0, 0.0), (1.0, 1.0), (0.05, 0.5)], shape, lengths)
+    s = og.sample(u, idx, w)
+    assert s[0] == u[0, 0] and s[1] == u[3, 3]
+    assert np.isclose(s[2], 0.5 * (u[0, 1] + u[0, 2]))  # y clamped to row 0, x halfway
+
+
+def test_gradient_matches_finite_differences():
+    rng = np.random.default_rng(9)
+    shape, lengths = (5, 7), (1.0, 2.0)
+    u = rng.standard_normal(shape)
+    pts = rng.uniform([0, 0], [1, 2], (30, 2))
+    vals = rng.standard_normal(30)
+    idx, w = og.sample_weights(pts, shape, lengths)
+    _, g = og.data_term(u, idx, w, vals, w_data=1.7)
+    d = rng.standard_normal(shape)
+    eps = 1e-6
+    fd = (og.data_term(u + eps * d, idx, w, vals, 1.7)[0] - og.data_term(u - eps * d, idx, w, vals, 1.7)[0]) / (2 * eps)
+    assert abs(fd - float(np.sum(g * d))) <= 1e-8 * max(1.0, abs(fd))
