@@ -246,7 +246,7 @@ modil_status modil_eval_grad_noalloc(const modil_desc* desc, const void* levels,
  * the device in the problem's dtype; dot products are reduced in FP64 in a
  * fixed order; the loss and gradient are the problem's own kernels.
  *   modil_lbfgs_create: single-instance problems whose unknowns are their
- *     levels (Burgers, cavity, body; not heat, whose conductivity nodes are
+ *     levels (Burgers, cavity, body, Poisson; not heat, whose conductivity nodes are
  *     unknowns too: MODIL_ERR_UNSUPPORTED).  Allocates (2 history + 6) level
  *     vectors of device memory.  The optimiser keeps a pointer to p, which
  *     must outlive it.
