@@ -196,10 +196,22 @@ class Problem:
     meas_field: np.ndarray = None
     meas_value: np.ndarray = None
     aux: np.ndarray = None
+    # off-grid measurements (single-field 2-D problems): physical (y, x) points
+    # and values, sampled d-linearly (oracle/offgrid_oracle.py)
+    meas_points: np.ndarray = None
+    point_value: np.ndarray = None
 
     @property
     def n_fields(self):
         return {"ns2d": 3, "ns3d": 5}.get(self.pde, 1)
+
+    def domain(self):
+        """Lower corner and length per axis (same order as shape)."""
+        if self.pde == "burgers":       # t in [0,1], x in [-1,1]
+            return (0.0, -1.0), (1.0, 2.0)
+        if self.pde in ("heat", "poisson", "ns2d"):
+            return tuple(0.0 for _ in self.shape), tuple(1.0 for _ in self.shape)
+        raise ValueError(self.pde)
 
     def spacing(self):
         """Grid spacings per axis (same order as shape)."""
@@ -708,8 +720,14 @@ def ns3d_fine_grad_colours(p, u, colours):
 # ---------------------------------------------------------------------------
 
 def _data_term(p, u):
-    """Data term of one field u, or of a list of fields (meas_field selects)."""
+    """Data term of one field u, or of a list of fields (meas_field selects).
+
+    With off-grid points (single-field problems) the misfits of the cells and
+    of the points share one normalisation, w_data / (n_cells + n_points)."""
+    n_pts = 0 if p.meas_points is None else len(p.meas_points)
     if isinstance(u, (list, tuple)):
+        if n_pts:
+            raise ValueError("off-grid points: single-field problems only")
         if p.meas_cell is None or len(p.meas_cell) == 0:
             return 0.0, [np.zeros_like(x) for x in u]
         mf = np.zeros(len(p.meas_cell), int) if p.meas_field is None else np.asarray(p.meas_field)
@@ -725,14 +743,25 @@ def _data_term(p, u):
             total += float(w * np.sum(diff * diff))
             gs.append(g.reshape(x.shape))
         return total, gs
-    if p.meas_cell is None or len(p.meas_cell) == 0:
+    n_cells = 0 if p.meas_cell is None else len(p.meas_cell)
+    if n_cells + n_pts == 0:
         return 0.0, np.zeros_like(u)
-    flat = u.reshape(-1)
-    diff = flat[p.meas_cell] - p.meas_value
-    w = p.w_data / len(p.meas_cell)
-    g = np.zeros_like(flat)
-    np.add.at(g, p.meas_cell, 2.0 * w * diff)
-    return float(w * np.sum(diff * diff)), g.reshape(u.shape)
+    w = p.w_data / (n_cells + n_pts)
+    total = 0.0
+    g = np.zeros(u.size)
+    if n_cells:
+        flat = u.reshape(-1)
+        diff = flat[p.meas_cell] - p.meas_value
+        np.add.at(g, p.meas_cell, 2.0 * w * diff)
+        total += float(w * np.sum(diff * diff))
+    if n_pts:
+        from .offgrid_oracle import data_term, sample_weights
+        origin, lengths = p.domain()
+        idx, wt = sample_weights(p.meas_points, u.shape, lengths, origin)
+        t, gp = data_term(u, idx, wt, p.point_value, w_data=w * n_pts)
+        total += t
+        g += gp.reshape(-1)
+    return total, g.reshape(u.shape)
 
 
 def loss_terms(p, u, q=None):

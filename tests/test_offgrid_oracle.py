@@ -58,3 +58,45 @@ def test_gradient_matches_finite_differences():
     eps = 1e-6
     fd = (og.data_term(u + eps * d, idx, w, vals, 1.7)[0] - og.data_term(u - eps * d, idx, w, vals, 1.7)[0]) / (2 * eps)
     assert abs(fd - float(np.sum(g * d))) <= 1e-8 * max(1.0, abs(fd))
+
+
+def test_point_at_a_cell_centre_is_an_on_grid_measurement():
+    """One data term over cells and points: a point at the centre of cell c
+    contributes exactly what a measurement of cell c does."""
+    import oracle as o
+    from paper_2303_04679_gb300 import inputs
+    shape, L = (16, 32), 3
+    rng = np.random.default_rng(10)
+    levels = inputs.random_levels(shape, L, 1, 10, -1.0, 1.0, 0.5)[0]
+    cells = np.array([5, 77, 300, 511], dtype=np.int32)
+    vals = rng.uniform(-0.5, 0.5, 4)
+    y, x = cells // 32, cells % 32
+    pts = np.stack([(y + 0.5) / 16, -1.0 + (x + 0.5) * 2.0 / 32], axis=1)  # Burgers: x in [-1, 1]
+    on = o.Problem("burgers", shape, L, coef={"nu": 0.02}, meas_cell=cells, meas_value=vals)
+    off = o.Problem("burgers", shape, L, coef={"nu": 0.02}, meas_points=pts, point_value=vals)
+    t1, g1, _ = o.loss_grad_levels(on, levels)
+    t2, g2, _ = o.loss_grad_levels(off, levels)
+    assert np.isclose(t1["data"], t2["data"], rtol=1e-13)
+    for a, b in zip(g1, g2):
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-14)
+
+
+def test_offgrid_level_gradient_matches_finite_differences():
+    import oracle as o
+    from paper_2303_04679_gb300 import inputs
+    shape, L = (16, 16), 3
+    rng = np.random.default_rng(11)
+    levels = inputs.random_levels(shape, L, 1, 11, -1.0, 1.0, 0.5)[0]
+    f = rng.standard_normal(shape)
+    pts = rng.uniform(0, 1, (25, 2))
+    p = o.Problem("poisson", shape, L, coef={"f": f}, meas_cell=np.array([3, 40], np.int32),
+                  meas_value=np.array([0.1, -0.2]), meas_points=pts, point_value=rng.uniform(-1, 1, 25))
+    _, grads, _ = o.loss_grad_levels(p, levels)
+    d = [rng.standard_normal(a.shape) for a in levels]
+    eps = 1e-6
+
+    def loss(s):
+        return o.loss_terms(p, o.compose([a + s * b for a, b in zip(levels, d)]))["total"]
+    fd = (loss(eps) - loss(-eps)) / (2 * eps)
+    an = sum(float(np.sum(g * b)) for g, b in zip(grads, d))
+    assert abs(fd - an) <= 1e-7 * max(1.0, abs(an))
