@@ -113,6 +113,15 @@ typedef struct {
   int n_knodes;              /* HEAT: conductivity nodes q_0..q_{K}, K+1 <= 64  */
   const double* knodes;      /* initial q (copied)                              */
   double adam_lr, adam_beta1, adam_beta2, adam_eps;
+  int n_points;               /* off-grid measurements (Burgers, heat, Poisson):  */
+  const double* point_coord;  /* n_points x (y, x) physical coordinates: Burgers
+                                 t in [0,1], x in [-1,1]; heat, Poisson [0,1]^2;
+                                 the field there is interpolated linearly along
+                                 each axis between the two nearest cell centres
+                                 (clamped between a wall and the outermost
+                                 centre); cells and points share one data weight
+                                 w_data / (n_meas + n_points)                   */
+  const double* point_value;
   int tile[2];               /* fine tile (rows, cols); 0 = library default.
                                 Burgers/heat: 16x32 16x64 8x64 32x32 8x128;
                                 NS2D: 8x32 16x32.  NS3D: 0 only (4x8x16 cells)  */

@@ -601,12 +601,33 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
       }
     }
   }
-  __syncthreads();  // aJ / muE complete
+  // ---- 3b. off-grid points whose corner cells the tile owns: the sampled
+  // value minus the measurement per record (the tile of a point's lower
+  // corner counts its misfit) --------------------------------------------------
+  float dacc_f = 0.f;
+  double dacc_d = 0.0;
+  if (A.pt_ptr) {
+    const int p1 = A.pt_ptr[gt + 1];
+    for (int j = A.pt_ptr[gt] + tid; j < p1; j += MODIL_NT) {
+      T smp = T(0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int cell = A.pt_cell[4 * (long long)j + k];
+        const int yy = cell / nx, xx = cell - (cell / nx) * nx;
+        smp += A.pt_w[4 * (long long)j + k] * U(yy, xx);
+      }
+      const T dd = smp - A.pt_val[j];
+      A.pt_diff[j] = dd;
+      if (A.pt_own[j]) {
+        if (sizeof(T) == 4) dacc_f += (float)(dd * dd);
+        else dacc_d += (double)(dd * dd);
+      }
+    }
+  }
+  __syncthreads();  // aJ / muE complete; point misfits written
 
   // ---- 4. data term: runs of equal cells inside the tile; its gradient joins
   // the cell's own residual term ----------------------------------------------
-  float dacc_f = 0.f;
-  double dacc_d = 0.0;
   for (int i = tid; i < nrun; i += MODIL_NT) {
     int cell, e0, e1;
     T v0;
@@ -635,6 +656,20 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
   if (tid == 0) {
     A.part[(long long)gt * A.npart + 0] = rsum;
     A.part[(long long)gt * A.npart + 1] = dsum;
+  }
+
+  // the points' gradient: each owned corner cell sums weight * misfit over
+  // the records that reach it (fixed order)
+  if (adj && A.pc_ptr && A.pc_ptr[gt + 1] > A.pc_ptr[gt]) {
+    const int c1 = A.pc_ptr[gt + 1];
+    for (int rr = A.pc_ptr[gt] + tid; rr < c1; rr += MODIL_NT) {
+      const int cell = A.pc_cell[rr];
+      const int yy = cell / nx, xx = cell - (cell / nx) * nx;
+      T acc = T(0);
+      for (int e = A.pc_beg[rr]; e < A.pc_beg[rr + 1]; ++e) acc += A.pe_w[e] * A.pt_diff[A.pe_rec[e]];
+      aJ[1 * G::NA + (yy - y0 + 1) * G::RW + (xx - x0 + 1)] += cf.wd2 * acc;
+    }
+    __syncthreads();
   }
 
   if (adj) {

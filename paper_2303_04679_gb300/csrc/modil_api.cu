@@ -75,10 +75,15 @@ struct Plan {
   // measurements, grouped into runs of equal (tile, cell)
   std::vector<int> run_ptr, run_cell, run_field, run_beg;
   std::vector<double> meas_val, run_v0;
+  // off-grid points: records per tile and runs of corner contributions
+  long long n_points = 0;
+  std::vector<int> pt_ptr, pt_cell, pt_own, pc_ptr, pc_cell, pc_beg, pe_rec;
+  std::vector<double> pt_w, pt_val, pe_w;
   size_t pyr_elems = 0;
   // arena offsets (bytes)
   size_t o_p0, o_p1, o_m, o_v, o_g, o_uf, o_wl, o_kq, o_km, o_kv, o_kg, o_aux, o_part, o_rptr, o_rcell,
       o_rfield, o_rbeg, o_mval, o_rv0, o_inst, o_st, o_cnt, o_q, o_ti[MODIL_MAXL], total;
+  size_t o_pptr, o_pcell, o_pw, o_pval, o_pown, o_pdiff, o_cptr, o_ccell, o_cbeg, o_erec, o_ew;
 };
 
 int find_cfg(int ty, int tx) {
@@ -163,6 +168,10 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
     }
     if (q.n_meas < 0 || (q.n_meas > 0 && (!q.meas_cell || !q.meas_value)))
       return fail(MODIL_ERR_ARG, "measurement arrays");
+    if (q.n_points < 0 || (q.n_points > 0 && (!q.point_coord || !q.point_value)))
+      return fail(MODIL_ERR_ARG, "point arrays");
+    if (q.n_points > 0 && P.pde != MODIL_PDE_BURGERS && P.pde != MODIL_PDE_HEAT && P.pde != MODIL_PDE_POISSON)
+      return fail(MODIL_ERR_UNSUPPORTED, "off-grid points: Burgers, heat and Poisson only");
     if (!(q.adam_lr >= 0) || !(q.adam_beta1 >= 0 && q.adam_beta1 < 1) ||
         !(q.adam_beta2 >= 0 && q.adam_beta2 < 1) || !(q.adam_eps >= 0))
       return fail(MODIL_ERR_ARG, "Adam parameters");
@@ -246,7 +255,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
     const double dV = D.h[0] * D.h[1] * D.h[2];
     for (int c = 0; c < 4; ++c) D.coef[c] = q.coef[c];
     D.w_res_dV = q.w_res * dV;
-    D.w_data_n = q.n_meas > 0 ? q.w_data / q.n_meas : 0.0;
+    D.w_data_n = (q.n_meas + q.n_points) > 0 ? q.w_data / (q.n_meas + q.n_points) : 0.0;
     D.w_reg = q.w_reg;
     D.lr = q.adam_lr; D.b1 = q.adam_beta1; D.b2 = q.adam_beta2; D.eps = q.adam_eps;
     // pyramid bound of this instance (unclipped worst case, clipped by level size)
@@ -314,6 +323,108 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   P.run_beg.push_back((int)all.size());
   for (int t = 0; t < nft; ++t) P.run_ptr[t + 1] += P.run_ptr[t];
 
+  // off-grid points -> records of every tile owning one of a point's four
+  // corner cells (the tile of the lower corner counts the misfit), and per
+  // tile runs of (record, weight) entries sorted by target cell
+  {
+    struct R { int tile; int cell[4]; double w[4]; double val; int own; };
+    std::vector<R> recs;
+    for (int i = 0; i < n; ++i) {
+      const modil_desc& q = d[i];
+      if (q.n_points <= 0) continue;
+      const InstPlan& ip = P.inst[i];
+      const int ny = ip.n[0][1], nx = ip.n[0][2];
+      const double oy = 0.0, ly = 1.0;
+      const double ox = (P.pde == MODIL_PDE_BURGERS) ? -1.0 : 0.0, lx = (P.pde == MODIL_PDE_BURGERS) ? 2.0 : 1.0;
+      // position along one axis in units of cell centres, clamped to the
+      // outermost centres; lower centre i0 and fraction t towards i0 + 1
+      auto axis = [](double pos, double o, double len, int nn, int& i0, double& t) {
+        double sc = (pos - o) / (len / nn) - 0.5;
+        sc = std::min(std::max(sc, 0.0), (double)(nn - 1));
+        if (nn == 1) { i0 = 0; t = 0.0; return; }
+        i0 = std::min((int)std::floor(sc), nn - 2);
+        t = sc - i0;
+      };
+      auto tile_of = [&](int y, int x) {
+        return P.dev[i].tile_base[0] + (y / TY) * ip.nt[0][2] + (x / TX);
+      };
+      for (int k = 0; k < q.n_points; ++k) {
+        const double py = q.point_coord[2 * k], px = q.point_coord[2 * k + 1], v = q.point_value[k];
+        if (!std::isfinite(py) || !std::isfinite(px) || !std::isfinite(v))
+          return fail(MODIL_ERR_ARG, "point coordinate or value not finite");
+        int iy, ix;
+        double ty_, tx_;
+        axis(py, oy, ly, ny, iy, ty_);
+        axis(px, ox, lx, nx, ix, tx_);
+        R r;
+        r.val = v;
+        const int cy[2] = {iy, std::min(iy + 1, ny - 1)}, cx[2] = {ix, std::min(ix + 1, nx - 1)};
+        const double wy[2] = {1.0 - ty_, ty_}, wx[2] = {1.0 - tx_, tx_};
+        int tiles[4];
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) {
+            r.cell[2 * a + b] = cy[a] * nx + cx[b];
+            r.w[2 * a + b] = wy[a] * wx[b];
+            tiles[2 * a + b] = tile_of(cy[a], cx[b]);
+          }
+        for (int c = 0; c < 4; ++c) {
+          bool seen = false;
+          for (int e = 0; e < c; ++e) seen |= tiles[e] == tiles[c];
+          if (seen) continue;
+          r.tile = tiles[c];
+          r.own = (tiles[c] == tiles[0]) ? 1 : 0;
+          recs.push_back(r);
+        }
+        P.n_points++;
+      }
+    }
+    if (!recs.empty()) {
+      std::stable_sort(recs.begin(), recs.end(), [](const R& a, const R& b) { return a.tile < b.tile; });
+      P.pt_ptr.assign(nft + 1, 0);
+      struct E { int tile, cell, rec; double w; };
+      std::vector<E> ents;
+      for (size_t j = 0; j < recs.size(); ++j) {
+        const R& r = recs[j];
+        P.pt_ptr[r.tile + 1]++;
+        for (int c = 0; c < 4; ++c) {
+          P.pt_cell.push_back(r.cell[c]);
+          P.pt_w.push_back(r.w[c]);
+        }
+        P.pt_val.push_back(r.val);
+        P.pt_own.push_back(r.own);
+      }
+      for (int t = 0; t < nft; ++t) P.pt_ptr[t + 1] += P.pt_ptr[t];
+      // entries: the corners each record's tile owns
+      for (size_t j = 0; j < recs.size(); ++j) {
+        const R& r = recs[j];
+        const int ii = P.tile_inst[0][r.tile];
+        const int nx = P.inst[ii].n[0][2];
+        for (int c = 0; c < 4; ++c) {
+          const int y = r.cell[c] / nx, x = r.cell[c] % nx;
+          const int t = P.dev[ii].tile_base[0] + (y / TY) * P.inst[ii].nt[0][2] + (x / TX);
+          if (t == r.tile) ents.push_back({t, r.cell[c], (int)j, r.w[c]});
+        }
+      }
+      std::stable_sort(ents.begin(), ents.end(), [](const E& a, const E& b) {
+        if (a.tile != b.tile) return a.tile < b.tile;
+        if (a.cell != b.cell) return a.cell < b.cell;
+        return a.rec < b.rec;
+      });
+      P.pc_ptr.assign(nft + 1, 0);
+      for (size_t k = 0; k < ents.size(); ++k) {
+        if (k == 0 || ents[k].tile != ents[k - 1].tile || ents[k].cell != ents[k - 1].cell) {
+          P.pc_cell.push_back(ents[k].cell);
+          P.pc_beg.push_back((int)k);
+          P.pc_ptr[ents[k].tile + 1]++;
+        }
+        P.pe_rec.push_back(ents[k].rec);
+        P.pe_w.push_back(ents[k].w);
+      }
+      P.pc_beg.push_back((int)ents.size());
+      for (int t = 0; t < nft; ++t) P.pc_ptr[t + 1] += P.pc_ptr[t];
+    }
+  }
+
   // arena layout
   size_t o = 0;
   auto take = [&](size_t bytes) { const size_t r = o; o = align256(o + std::max<size_t>(bytes, 1)); return r; };
@@ -336,6 +447,17 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   P.o_rbeg = take(4 * P.run_beg.size());
   P.o_mval = take(P.esz * P.meas_val.size());
   P.o_rv0 = take(P.esz * P.run_v0.size());
+  P.o_pptr = take(4 * P.pt_ptr.size());
+  P.o_pcell = take(4 * P.pt_cell.size());
+  P.o_pw = take(P.esz * P.pt_w.size());
+  P.o_pval = take(P.esz * P.pt_val.size());
+  P.o_pown = take(4 * P.pt_own.size());
+  P.o_pdiff = take(P.esz * P.pt_val.size());
+  P.o_cptr = take(4 * P.pc_ptr.size());
+  P.o_ccell = take(4 * P.pc_cell.size());
+  P.o_cbeg = take(4 * P.pc_beg.size());
+  P.o_erec = take(4 * P.pe_rec.size());
+  P.o_ew = take(P.esz * P.pe_w.size());
   P.o_inst = take(sizeof(DevInst) * n);
   P.o_st = take(sizeof(InstState) * n);
   P.o_cnt = take(sizeof(int) * n);
@@ -386,6 +508,18 @@ void fill_arena(modil_problem* p, Arena<T>& A) {
   A.run_beg = reinterpret_cast<const int*>(b + P.o_rbeg);
   A.meas_val = reinterpret_cast<const T*>(b + P.o_mval);
   A.run_v0 = reinterpret_cast<const T*>(b + P.o_rv0);
+  const bool pts = !P.pt_ptr.empty();
+  A.pt_ptr = pts ? reinterpret_cast<const int*>(b + P.o_pptr) : nullptr;
+  A.pt_cell = reinterpret_cast<const int*>(b + P.o_pcell);
+  A.pt_w = reinterpret_cast<const T*>(b + P.o_pw);
+  A.pt_val = reinterpret_cast<const T*>(b + P.o_pval);
+  A.pt_own = reinterpret_cast<const int*>(b + P.o_pown);
+  A.pt_diff = reinterpret_cast<T*>(b + P.o_pdiff);
+  A.pc_ptr = pts ? reinterpret_cast<const int*>(b + P.o_cptr) : nullptr;
+  A.pc_cell = reinterpret_cast<const int*>(b + P.o_ccell);
+  A.pc_beg = reinterpret_cast<const int*>(b + P.o_cbeg);
+  A.pe_rec = reinterpret_cast<const int*>(b + P.o_erec);
+  A.pe_w = reinterpret_cast<const T*>(b + P.o_ew);
   A.inst = reinterpret_cast<const DevInst*>(b + P.o_inst);
   A.st = reinterpret_cast<InstState*>(b + P.o_st);
   A.counter = reinterpret_cast<int*>(b + P.o_cnt);
@@ -582,6 +716,9 @@ modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t ar
     if (st == MODIL_OK) st = upload(p, P.o_aux, aux.data(), 8 * aux.size());
     if (st == MODIL_OK) st = upload(p, P.o_mval, P.meas_val.data(), 8 * P.meas_val.size());
     if (st == MODIL_OK) st = upload(p, P.o_rv0, P.run_v0.data(), 8 * P.run_v0.size());
+    if (st == MODIL_OK) st = upload(p, P.o_pw, P.pt_w.data(), 8 * P.pt_w.size());
+    if (st == MODIL_OK) st = upload(p, P.o_pval, P.pt_val.data(), 8 * P.pt_val.size());
+    if (st == MODIL_OK) st = upload(p, P.o_ew, P.pe_w.data(), 8 * P.pe_w.size());
   } else {
     auto kq32 = convert<float>(kq), aux32 = convert<float>(aux), mv32 = convert<float>(P.meas_val);
     auto rv32 = convert<float>(P.run_v0);
@@ -589,12 +726,23 @@ modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t ar
     if (st == MODIL_OK) st = upload(p, P.o_aux, aux32.data(), 4 * aux32.size());
     if (st == MODIL_OK) st = upload(p, P.o_mval, mv32.data(), 4 * mv32.size());
     if (st == MODIL_OK) st = upload(p, P.o_rv0, rv32.data(), 4 * rv32.size());
+    auto pw32 = convert<float>(P.pt_w), pv32 = convert<float>(P.pt_val), ew32 = convert<float>(P.pe_w);
+    if (st == MODIL_OK) st = upload(p, P.o_pw, pw32.data(), 4 * pw32.size());
+    if (st == MODIL_OK) st = upload(p, P.o_pval, pv32.data(), 4 * pv32.size());
+    if (st == MODIL_OK) st = upload(p, P.o_ew, ew32.data(), 4 * ew32.size());
     if (st == MODIL_OK) {
       e = cudaStreamSynchronize(p->stream);
       if (e != cudaSuccess) st = fail(MODIL_ERR_CUDA, cudaGetErrorString(e));
     }
   }
   if (st == MODIL_OK) st = upload(p, P.o_rptr, P.run_ptr.data(), 4 * P.run_ptr.size());
+  if (st == MODIL_OK) st = upload(p, P.o_pptr, P.pt_ptr.data(), 4 * P.pt_ptr.size());
+  if (st == MODIL_OK) st = upload(p, P.o_pcell, P.pt_cell.data(), 4 * P.pt_cell.size());
+  if (st == MODIL_OK) st = upload(p, P.o_pown, P.pt_own.data(), 4 * P.pt_own.size());
+  if (st == MODIL_OK) st = upload(p, P.o_cptr, P.pc_ptr.data(), 4 * P.pc_ptr.size());
+  if (st == MODIL_OK) st = upload(p, P.o_ccell, P.pc_cell.data(), 4 * P.pc_cell.size());
+  if (st == MODIL_OK) st = upload(p, P.o_cbeg, P.pc_beg.data(), 4 * P.pc_beg.size());
+  if (st == MODIL_OK) st = upload(p, P.o_erec, P.pe_rec.data(), 4 * P.pe_rec.size());
   if (st == MODIL_OK) st = upload(p, P.o_rcell, P.run_cell.data(), 4 * P.run_cell.size());
   if (st == MODIL_OK) st = upload(p, P.o_rfield, P.run_field.data(), 4 * P.run_field.size());
   if (st == MODIL_OK) st = upload(p, P.o_rbeg, P.run_beg.data(), 4 * P.run_beg.size());
@@ -1242,6 +1390,8 @@ extern "C" modil_status modil_eval_grad_noalloc(const modil_desc* desc, const vo
   if (s != MODIL_OK) return s;
   if (P.pde == MODIL_PDE_NS3D)
     return fail(MODIL_ERR_UNSUPPORTED, "the allocation-free entry point takes the 2-D families");
+  if (P.n_points > 0)
+    return fail(MODIL_ERR_UNSUPPORTED, "the allocation-free entry point takes no off-grid points");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   return P.dtype == MODIL_F64 ? noalloc_run<double>(P, desc, levels, grads, terms, kgrad, st)
                               : noalloc_run<float>(P, desc, levels, grads, terms, kgrad, st);

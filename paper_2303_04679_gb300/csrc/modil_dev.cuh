@@ -87,6 +87,20 @@ struct Arena {
   const int* run_beg;  // first value of each run; run r spans [run_beg[r], run_beg[r+1])
   const T* meas_val;
   const T* run_v0;     // first value of each run (meas_val[run_beg[r]])
+  // off-grid points (NULL when a batch has none): per global fine tile the
+  // records of the points one of whose four corner cells it owns, and the
+  // runs of (record, weight) entries adding to each owned corner cell
+  const int* pt_ptr;   // per tile: first record
+  const int* pt_cell;  // 4 corner cells per record (flat, within the instance)
+  const T* pt_w;       // 4 weights per record
+  const T* pt_val;     // measured value per record
+  const int* pt_own;   // 1 where this record's tile counts the point's misfit
+  T* pt_diff;          // scratch: sample - value per record
+  const int* pc_ptr;   // per tile: first run of corner contributions
+  const int* pc_cell;  // target cell of each run
+  const int* pc_beg;   // first entry of each run (one past the last after it)
+  const int* pe_rec;   // record of each entry
+  const T* pe_w;       // weight of each entry
   const DevInst* inst;
   DevInst inst0;       // copy of instance 0 in the kernel parameters (read when n_inst == 1)
   InstState* st;

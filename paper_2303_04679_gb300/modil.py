@@ -46,6 +46,8 @@ class modil_desc(C.Structure):
         ("aux", C.POINTER(C.c_double)), ("n_knodes", C.c_int),
         ("knodes", C.POINTER(C.c_double)), ("adam_lr", C.c_double),
         ("adam_beta1", C.c_double), ("adam_beta2", C.c_double), ("adam_eps", C.c_double),
+        ("n_points", C.c_int), ("point_coord", C.POINTER(C.c_double)),
+        ("point_value", C.POINTER(C.c_double)),
         ("tile", C.c_int * 2),
     ]
 
@@ -113,11 +115,13 @@ class Desc:
 
     def __init__(self, pde, shape, n_levels, dtype="f32", coef=(), w_res=1.0, w_data=1.0,
                  w_reg=0.0, meas_cell=None, meas_value=None, meas_field=None, aux=None,
-                 knodes=None, lr=5e-3, beta1=0.9, beta2=0.999, eps=1e-8, tile=(0, 0)):
+                 knodes=None, lr=5e-3, beta1=0.9, beta2=0.999, eps=1e-8, tile=(0, 0),
+                 points=None, point_value=None):
         self.kwargs = dict(pde=pde, shape=shape, n_levels=n_levels, dtype=dtype, coef=coef,
                            w_res=w_res, w_data=w_data, w_reg=w_reg, meas_cell=meas_cell,
                            meas_value=meas_value, meas_field=meas_field, aux=aux, knodes=knodes,
-                           lr=lr, beta1=beta1, beta2=beta2, eps=eps, tile=tile)
+                           lr=lr, beta1=beta1, beta2=beta2, eps=eps, tile=tile, points=points,
+                           point_value=point_value)
         self.pde = {"burgers": PDE_BURGERS, "heat": PDE_HEAT, "ns2d": PDE_NS2D,
                     "ns3d": PDE_NS3D, "poisson": PDE_POISSON}.get(pde, pde)
         self.dtype = {"f32": F32, "f64": F64}.get(dtype, dtype)
@@ -128,6 +132,8 @@ class Desc:
         self._field = None if meas_field is None else np.ascontiguousarray(meas_field, np.int32)
         self._aux = None if aux is None else np.ascontiguousarray(aux, np.float64)
         self._knodes = None if knodes is None else np.ascontiguousarray(knodes, np.float64)
+        self._pts = None if points is None else np.ascontiguousarray(np.reshape(points, (-1, 2)), np.float64)
+        self._pval = None if point_value is None else np.ascontiguousarray(point_value, np.float64)
         d = modil_desc()
         d.pde, d.dtype, d.ndim = self.pde, self.dtype, len(self.shape)
         for i, s in enumerate(self.shape):
@@ -145,6 +151,9 @@ class Desc:
         d.n_knodes = 0 if self._knodes is None else len(self._knodes)
         d.knodes = _dptr(self._knodes, C.c_double)
         d.adam_lr, d.adam_beta1, d.adam_beta2, d.adam_eps = lr, beta1, beta2, eps
+        d.n_points = 0 if self._pts is None else len(self._pts)
+        d.point_coord = _dptr(self._pts, C.c_double)
+        d.point_value = _dptr(self._pval, C.c_double)
         d.tile[0], d.tile[1] = int(tile[0]), int(tile[1])
         self.c = d
 

@@ -107,3 +107,28 @@ def test_ns3d_arena_bytes_and_validation(mod):
         mod.arena_bytes([mod.Desc("ns3d", (16, 16, 32), 3, coef=(0.0, 0.4, 1.0, 1.0))])
     with pytest.raises(mod.ModilError):
         mod.arena_bytes([_body(mod, shape=(12, 16, 32), L=4)])  # 12 not divisible by 8
+
+
+def test_offgrid_points_in_the_plan(mod):
+    """Off-grid points enlarge the arena (their per-tile records), non-finite
+    coordinates and unsupported families are rejected (host only)."""
+    import ctypes as C
+    rng = np.random.default_rng(0)
+    pts = np.column_stack([rng.uniform(0, 1, 300), rng.uniform(-1, 1, 300)])
+
+    def nbytes(d):
+        b = C.c_size_t()
+        return mod.LIB.modil_arena_bytes(C.byref(d.c), 1, C.byref(b)), b.value
+
+    base = mod.Desc("burgers", (48, 96), 3, "f32", coef=(0.02,), tile=(16, 32))
+    with_pts = mod.Desc("burgers", (48, 96), 3, "f32", coef=(0.02,), points=pts,
+                        point_value=np.zeros(300), tile=(16, 32))
+    r0, b0 = nbytes(base)
+    r1, b1 = nbytes(with_pts)
+    assert r0 == 0 and r1 == 0 and b1 > b0
+    bad = mod.Desc("burgers", (48, 96), 3, "f32", coef=(0.02,), points=[[np.nan, 0.0]],
+                   point_value=np.zeros(1))
+    assert nbytes(bad)[0] != 0
+    ns2d = mod.Desc("ns2d", (16, 16), 2, "f32", coef=(100.0, 1.0), points=[[0.5, 0.5]],
+                    point_value=np.zeros(1))
+    assert nbytes(ns2d)[0] != 0

@@ -1,0 +1,103 @@
+"""Off-grid measurement points (d-linear sampling of the composed field) on the
+GPU against the FP64 oracle: loss terms and every level gradient with points
+near walls and on tile borders, mixed with on-grid cells, in a batch, in the
+persistent launch, and Adam trajectories in FP64."""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2303_04679_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def modil():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_04679_gb300 import build
+    build.build()
+    from paper_2303_04679_gb300 import modil as m
+    return m
+
+
+def _case(modil, pde, shape, L, dtype, seed, n_cells=30, n_pts=40, tile=(0, 0)):
+    rng = np.random.default_rng(seed)
+    npd = np.float64 if dtype == "f64" else np.float32
+    rnd = lambda a: np.asarray(a, np.float64).astype(npd).astype(np.float64)  # noqa: E731
+    levels = [rnd(a) for a in inputs.random_levels(shape, L, 1, seed, -1.0, 1.0, 0.5)[0]]
+    n = int(np.prod(shape))
+    cells = inputs.measurement_cells(n, n_cells, seed) if n_cells else None
+    cval = rnd(rng.uniform(-0.5, 0.5, n_cells)) if n_cells else None
+    lo, ln = ((0.0, -1.0), (1.0, 2.0)) if pde == "burgers" else ((0.0, 0.0), (1.0, 1.0))
+    u01 = rng.uniform(0, 1, (n_pts, 2))
+    # a few points at the walls, at the outermost centres and on tile borders
+    u01[:4] = [[0.0, 0.0], [1.0, 1.0], [0.5 / shape[0], 1.0 - 0.5 / shape[1]], [16.0 / shape[0], 32.0 / shape[1]]]
+    pts = np.array(lo) + u01 * np.array(ln)
+    pval = rnd(rng.uniform(-0.5, 0.5, n_pts))
+    kw = dict(meas_cell=cells, meas_value=cval, meas_points=pts, point_value=pval)
+    if pde == "burgers":
+        orc = o.Problem("burgers", shape, L, coef={"nu": 0.02}, **kw)
+        desc = modil.Desc("burgers", shape, L, dtype, coef=(0.02,), meas_cell=cells, meas_value=cval,
+                          points=pts, point_value=pval, lr=5e-3, tile=tile)
+    else:
+        f = rnd(rng.standard_normal(shape) * 10.0)
+        orc = o.Problem("poisson", shape, L, coef={"f": f}, **kw)
+        desc = modil.Desc("poisson", shape, L, dtype, aux=f.ravel(), meas_cell=cells, meas_value=cval,
+                          points=pts, point_value=pval, lr=5e-3, tile=tile)
+    return orc, desc, levels
+
+
+def _check(p, orc, levels, tol, instance=0):
+    terms, grads, _ = o.loss_grad_levels(orc, levels)
+    t = p.eval_grad()[instance]
+    for j, name in enumerate(("total", "res", "data")):
+        assert abs(t[j] - terms[name]) <= tol * abs(terms[name]), (name, t[j], terms[name])
+    for lvl, gr in enumerate(grads):
+        g = p.read_grad(lvl, instance=instance).astype(np.float64)
+        assert np.linalg.norm(g - gr) <= tol * np.linalg.norm(gr), lvl
+
+
+@pytest.mark.parametrize("pde,shape,L,dtype,tile", [("burgers", (48, 96), 3, "f32", (16, 32)),
+                                                    ("burgers", (64, 64), 4, "f64", (32, 32)),
+                                                    ("poisson", (32, 64), 3, "f32", (16, 64)),
+                                                    ("poisson", (40, 72), 3, "f64", (8, 64))])
+def test_points_loss_grad(modil, pde, shape, L, dtype, tile):
+    orc, desc, levels = _case(modil, pde, shape, L, dtype, seed=60, tile=tile)
+    with modil.Problem(desc) as p:
+        p.write_levels(levels)
+        _check(p, orc, levels, 1e-5 if dtype == "f32" else 1e-11)
+
+
+def test_points_only_and_persistent_batch(modil):
+    cases = [_case(modil, "burgers", s, L, "f32", seed=61 + i, n_cells=0, n_pts=50, tile=(16, 32))
+             for i, (s, L) in enumerate([((32, 64), 3), ((64, 32), 3)])]
+    with modil.Problem([c[1] for c in cases]) as p:
+        for i, (_, _, lv) in enumerate(cases):
+            p.write_levels(lv, instance=i)
+        for persistent in (False, True):
+            p.set_persistent(persistent)
+            for i, (orc, _, lv) in enumerate(cases):
+                _check(p, orc, lv, 1e-5, instance=i)
+
+
+def test_points_adam_steps_f64(modil):
+    orc, desc, levels = _case(modil, "burgers", (32, 64), 3, "f64", seed=63)
+    st = o.OracleState.zeros_like_levels(levels)
+    hist = [o.oracle_step(orc, st, 5e-3) for _ in range(3)]
+    with modil.Problem(desc) as p:
+        p.write_levels(levels)
+        for k in range(3):
+            t = p.step(1)[0]
+            assert abs(t[0] - hist[k]["total"]) <= 1e-11 * hist[k]["total"]
+        for lvl in range(3):
+            ref = st.levels[lvl]
+            assert np.max(np.abs(p.read_level(lvl) - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_points_rejected_where_unsupported(modil):
+    pts = np.array([[0.5, 0.5]])
+    with pytest.raises(modil.ModilError):
+        modil.Problem(modil.Desc("ns2d", (16, 16), 2, "f32", coef=(100.0, 1.0), points=pts,
+                                 point_value=np.zeros(1)))
