@@ -178,7 +178,7 @@ def test_batch_of_uneven_instances(modil):
 
 @pytest.mark.parametrize("n,shape,L", [(200, (128, 128), 4), (700, (64, 64), 3)])
 def test_large_batches_small_tail_clusters(modil, n, shape, L):
-    """Batches large enough that the tail kernel runs with 4 (200 instances)
+    """Batches large enough that the tail kernel runs with 2 (200 instances)
     or 1 (700 instances) blocks per instance and leaves a 64^2 or 32^2 level
     to the restriction kernel: sampled instances match the oracle, and Adam
     steps of the batch match the same instances stepped alone."""
