@@ -13,7 +13,9 @@
 //      its local Jacobian, dr/du at the 4 stencil points, streamed down
 //      columns, and keeps lambda * dr/du (lambda = 2 w dV r);
 //   3. adds the data term of the measurements inside the tile to the cell's
-//      own term;
+//      own term, and that of the off-grid points whose corner cells the tile
+//      owns (d-linear samples of the composed field; per owned corner cell a
+//      fixed-order sum over the points reaching it);
 //   4. reduces r^2 and the data misfit over what it owns (FP64 partials per
 //      tile);
 //   5. forms dL/du in gather form (each cell sums lambda * dr/du over the
