@@ -1,17 +1,21 @@
 #!/usr/bin/env python
 """Throughput of one mODIL optimiser step on the GPU (and of the CPU oracle).
 
-Workload: conductivity inference in 1-D transient heat conduction
-(u_t = (k(u) u_x)_x, paper Section 3.4) on a 512 (x) by 512 (t) grid in FP32,
-7 multigrid levels, the temperature plus 32 conductivity nodes as unknowns,
-5 % of the cells measured with Gaussian noise sigma = 1e-3, a second-difference
-regulariser on the nodes, Adam.  A step is one loss+gradient evaluation of
-every level followed by the Adam update of every level and of the nodes.
+Default workload (the largest configuration on one GPU): 512 viscous Burgers
+instances of uneven size (paper Section 3.2 discretisation; N_x, N_t drawn
+from {64, 128, 256, 512}, nu log-uniform in [1e-3, 1e-1], 0.5 % of the cells
+measured), all stepped together: one persistent launch per phase of the step
+(fused fine tile kernel, restriction + Adam of the coarse levels, per-instance
+tail), replayed as one CUDA graph.  A step is one loss+gradient evaluation of
+every instance followed by the Adam update of every level of every instance;
+the metric is instance evaluations per second.  The ~1.3 GB working set is
+larger than L2, so no flush is needed.
 
-Timing: W untimed warm-up steps, then K steps each timed with CUDA events on
-the problem's stream; before every timed step a 256 MiB buffer is written so
-the step starts with a cold L2 (the working set, 11 MB, would otherwise stay
-resident).  One JSON line is printed by rank 0.
+Timing: W untimed warm-up steps, then K steps between two CUDA events on the
+problem's stream, bracketed by a barrier and a device synchronisation, the
+maximum over ranks (replicas under torchrun); SM clocks sampled meanwhile.
+One JSON line is printed by rank 0.  Other workloads: --workload heat | body |
+cavity | burgers | poisson | unet | warmstart.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl modil|reference]
 """
@@ -41,18 +45,19 @@ ALG_BYTES_PER_MEAS = 8       # cell index + value
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="modil", choices=["modil", "reference"])
     ap.add_argument("--tile", default="32x32")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=50)
-    ap.add_argument("--workload", default="heat",
+    ap.add_argument("--workload", default="batched-burgers",
                     choices=["heat", "batched-burgers", "body", "warmstart", "unet", "burgers", "cavity",
                              "poisson"],
-                    help="heat: the measured workload (default); batched-burgers: 512 uneven "
-                         "Burgers instances, batched launch against sequential single runs; "
+                    help="batched-burgers (default): 512 uneven Burgers instances in one "
+                         "persistent graph-captured launch per phase, against sequential single "
+                         "runs; heat: conductivity inference on 512x512; "
                          "body: 3-D body-shape inference, 128^3 cells, 8 levels, five fields; "
                          "warmstart: U-Net warm start of the body problem against zero init")
     ap.add_argument("--train", type=int, default=256, help="warmstart: training ellipsoids")
@@ -82,6 +87,14 @@ def job_throughput(steps_per_rank, world, job_ms):
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def heat_config(args, w):
+    """The `config` of the heat line, identical in both arms."""
+    params, _ = workload_sizes(w)
+    return {"workload": WORKLOAD, "grid": list(w["shape"]), "levels": w["n_levels"],
+            "params": params, "measurements": len(w["meas_cell"]), "tile": args.tile,
+            "l2": "flushed before every timed step (256 MiB write)", "parallelism": "replicas"}
 
 
 def workload_sizes(w):
@@ -164,7 +177,7 @@ def run_reference(args, w):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "config": heat_config(args, w),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{n} full oracle Adam steps of the workload ({cpu_model()})"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -245,14 +258,126 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+BATCH_METRIC_UNIT = "instance " + UNIT
+
+
+def batched_config(args, tile, pers, fine, params, nmeas):
+    """The `config` of the batched line, identical in both arms."""
+    return {"workload": f"batched Burgers x{args.instances}: N_x, N_t uniform in {{64,128,256,512}}, "
+                        "nu log-uniform in [1e-3, 1e-1], 0.5 % measured cells, "
+                        "L = log2(min(N_x, N_t)/8) + 1, FP32, Adam, one persistent launch per phase "
+                        "in one CUDA graph",
+            "instances": args.instances, "tile": list(tile), "persistent": pers,
+            "fine_cells": fine, "params": params, "measurements": nmeas,
+            "l2": "working set (about 1.3 GB) larger than L2 (no flush)",
+            "parallelism": "replicas"}
+
+
+def batch_sizes(batch):
+    fine = sum(d["shape"][0] * d["shape"][1] for d in batch)
+    params = sum(sum((d["shape"][0] >> l) * (d["shape"][1] >> l) for l in range(d["n_levels"]))
+                 for d in batch)
+    nmeas = sum(len(d["meas_cell"]) for d in batch)
+    return fine, params, nmeas
+
+
+def oracle_burgers(d):
+    import oracle as o
+    from paper_2303_04679_gb300 import inputs
+    f32 = lambda a: np.asarray(a, np.float64).astype(np.float32).astype(np.float64)  # noqa: E731
+    prob = o.Problem("burgers", d["shape"], d["n_levels"], coef={"nu": d["nu"]},
+                     meas_cell=d["meas_cell"], meas_value=f32(d["meas_value"]))
+    st = o.OracleState.zeros_like_levels([np.zeros(s) for s in inputs.level_shapes(d["shape"], d["n_levels"])])
+    return o, prob, st
+
+
+def time_batch_oracle(batch, seconds, per_step=None):
+    """Oracle Adam steps on the batch's instances in order (cycling), each
+    instance set up outside the clock; returns (instance steps, seconds)."""
+    n, el, i = 0, 0.0, 0
+    while el < seconds and (per_step is None or n < per_step):
+        o, prob, st = oracle_burgers(batch[i % len(batch)])
+        t0 = time.perf_counter()
+        o.oracle_step(prob, st, 5e-3)
+        el += time.perf_counter() - t0
+        n += 1
+        i += 1
+    return n, el
+
+
+def traffic_record(name, sources_ok=True):
+    """A kernel's DRAM bytes from profiles/traffic.json, if its sources still
+    hash to the recorded value (otherwise the counters are stale: None)."""
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        from paper_2303_04679_gb300 import build as bld
+        tj = json.load(open(tfile))[name]
+        if tj.get("source_hash") == bld.source_hash(tj["sources"]):
+            return tj
+    except Exception:
+        pass
+    return None
+
+
+def run_reference_batched(args):
+    """The reference arm of the batched line: the FP64 CPU oracle as it
+    stands, on the host cores; each step is a bounded sample of the same
+    batch (16 consecutive instances, cycling through the 512), one oracle Adam
+    step each; rank 0 only."""
+    from paper_2303_04679_gb300 import inputs
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    batch = inputs.burgers_batch(args.instances)
+    fine, params, nmeas = batch_sizes(batch)
+    tile = tuple(int(v) for v in args.tile.split("x")) if args.tile != "auto" else (32, 32)
+    per = 16
+    for w in range(max(args.warmup, 0)):
+        o, prob, st = oracle_burgers(batch[w % len(batch)])
+        o.oracle_step(prob, st, 5e-3)
+    n, el, i = 0, 0.0, 0
+    for _ in range(args.steps):
+        for _ in range(per):
+            o, prob, st = oracle_burgers(batch[i % len(batch)])
+            t0 = time.perf_counter()
+            o.oracle_step(prob, st, 5e-3)
+            el += time.perf_counter() - t0
+            n += 1
+            i += 1
+    value = n / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": BATCH_METRIC_UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": batched_config(args, tile, True, fine, params, nmeas),
+        "cpu_baseline": {"value": value, "unit": BATCH_METRIC_UNIT, "cores": blas_threads(),
+                         "kind": "oracle",
+                         "sample": f"{per} instances of the batch per step (cycling, {n} in all), one "
+                                   f"oracle Adam step each ({cpu_model()}, {os.cpu_count()} host cores)"},
+        "e2e": {"value": value, "unit": BATCH_METRIC_UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args):
-    """512 uneven Burgers instances: one batched (graph-captured, optionally
-    persistent) launch per phase against the same instances stepped one
-    problem after another; same kernels, same per-instance arithmetic."""
+    """512 uneven Burgers instances (the largest configuration): one batched,
+    persistent, graph-captured launch per phase.  Device time of K steps with
+    CUDA events; the same instances stepped one problem after another with
+    the same kernels as the comparison; the fine kernel's roofline; the
+    public-API end-to-end rate from pinned host buffers; the CPU oracle on a
+    bounded sample."""
     import torch
 
     from paper_2303_04679_gb300 import autotune, inputs, modil
-    torch.cuda.set_device(0)
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
     batch = inputs.burgers_batch(args.instances)
 
     def descs(tile):
@@ -260,77 +385,127 @@ def run_batched(args):
                            meas_cell=d["meas_cell"], meas_value=d["meas_value"], lr=5e-3,
                            tile=tile) for d in batch]
 
-    base = descs((16, 32))
     if args.tile == "auto":
         tile, pers, _ = autotune.autotune(
-            base, measure=lambda d, t, q: autotune.time_steps(d, t, q, steps=10, warmup=3))
+            descs((16, 32)), measure=lambda d, t, q: autotune.time_steps(d, t, q, steps=10, warmup=3))
     else:
         tile, pers = tuple(int(v) for v in args.tile.split("x")), True
     ds = descs(tile)
-    fine = sum(d["shape"][0] * d["shape"][1] for d in batch)
-    params = sum(sum((d["shape"][0] >> l) * (d["shape"][1] >> l) for l in range(d["n_levels"]))
-                 for d in batch)
-    nmeas = sum(len(d["meas_cell"]) for d in batch)
+    fine, params, nmeas = batch_sizes(batch)
     K = args.steps
     with modil.Problem(ds) as p:
         if pers:
             p.set_persistent(True)
         p.step(max(3, args.warmup), read_loss=False)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(local)
+        if world > 1:
+            torch.distributed.barrier()
         torch.cuda.synchronize()
+        sampler.start()
+        time.sleep(0.25)
         a.record(p.stream)
         p.step(K, read_loss=False)
         b.record(p.stream)
         b.synchronize()
-        t_batch = a.elapsed_time(b) / K
+        clocks = sampler.stop()
+        if world > 1:
+            torch.distributed.barrier()
+        job_ms = max_over_ranks(a.elapsed_time(b), world)
+        t_batch = job_ms / K
         final_batch = p.eval_loss()[:, 0].copy()
         prof = np.array([p.profile_step() for _ in range(5)]).mean(axis=0)
         launches = p.launches_per_step()
     # the same instances as separate problems, stepped one after another
-    probs = [modil.Problem(d, stream=torch.cuda.Stream()) for d in ds]
-    s0 = torch.cuda.current_stream()
-    for q in probs:
-        q.step(max(3, args.warmup), read_loss=False)
+    t_seq, same, maxrel = None, None, None
+    if rank == 0 and world == 1:
+        probs = [modil.Problem(d, stream=torch.cuda.Stream()) for d in ds]
+        s0 = torch.cuda.current_stream()
+        for q in probs:
+            q.step(max(3, args.warmup), read_loss=False)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s0)
+        prev = a
+        for q in probs:  # each problem starts when the previous one has finished
+            q.stream.wait_event(prev)
+            q.step(K, read_loss=False)
+            prev = torch.cuda.Event()
+            prev.record(q.stream)
+        s0.wait_event(prev)
+        b.record(s0)
+        b.synchronize()
+        t_seq = a.elapsed_time(b) / K
+        final_seq = np.array([q.eval_loss()[0, 0] for q in probs])
+        for q in probs:
+            q.close()
+        same = bool(np.array_equal(final_batch, final_seq))
+        maxrel = float(np.max(np.abs(final_batch - final_seq) / np.abs(final_seq)))
+
+    # end to end through the public C ABI: create from host descriptors, write
+    # every level from pinned host memory, K steps each reading the loss terms
+    # back, read the composed fields; copies inside the timed region
+    lv_host = [[torch.zeros(s, dtype=torch.float32).pin_memory()
+                for s in inputs.level_shapes(d["shape"], d["n_levels"])] for d in batch]
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(s0)
-    prev = a
-    for q in probs:  # each problem starts when the previous one has finished
-        q.stream.wait_event(prev)
-        q.step(K, read_loss=False)
-        prev = torch.cuda.Event()
-        prev.record(q.stream)
-    s0.wait_event(prev)
-    b.record(s0)
-    b.synchronize()
-    t_seq = a.elapsed_time(b) / K
-    final_seq = np.array([q.eval_loss()[0, 0] for q in probs])
-    for q in probs:
-        q.close()
+    t0 = time.perf_counter()
+    with modil.Problem(ds) as pe:
+        if pers:
+            pe.set_persistent(True)
+        for i, lv in enumerate(lv_host):
+            for lvl, t in enumerate(lv):
+                modil._check(modil.LIB.modil_write_level(pe._h, i, 0, lvl, t.data_ptr(), t.numel() * 4, 0))
+        for _ in range(K):
+            pe.step(1, read_loss=True)
+        fields = [pe.read_field(instance=i) for i in range(len(batch))]
+    e2e_s = time.perf_counter() - t0
+    h2d = (sum(t.numel() * 4 for lv in lv_host for t in lv) + nmeas * 8)
+    d2h = K * len(batch) * 4 * 8 + sum(f.nbytes for f in fields)
+    e2e_ms = max_over_ranks(1e3 * e2e_s, world)
+
     peak, peak_kind = measured_peak()
     fine_bytes = fine * ALG_BYTES_PER_PARAM + nmeas * ALG_BYTES_PER_MEAS
     ach = fine_bytes / (prof[0] * 1e-3) / 1e9
+    tr = traffic_record("batched_fine")
+    traffic = None
+    if tr is not None and tr.get("tile") == list(tile):
+        traffic = tr["bytes_per_fine_cell"] * fine
     out = {
-        "metric": METRIC, "value": args.instances / (t_batch * 1e-3), "unit": "instance " + UNIT,
-        "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": t_batch,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": f"batched Burgers x{args.instances}, N_x,N_t in {{64..512}}, FP32",
-                   "tile": list(tile), "persistent": pers, "fine_cells": fine, "params": params,
-                   "l2": "working set larger than L2 (no flush)"},
-        "fine_cells_per_s": fine / (t_batch * 1e-3),
+        "metric": METRIC, "value": job_throughput(args.instances * K, world, job_ms),
+        "unit": BATCH_METRIC_UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": batched_config(args, tile, pers, fine, params, nmeas),
+        "fine_cells_per_s": world * fine / (t_batch * 1e-3),
         "effective_step_GBps": (params * ALG_BYTES_PER_PARAM + nmeas * 8) / (t_batch * 1e-3) / 1e9,
-        "sequential_ms_per_step": t_seq, "batched_speedup": t_seq / t_batch,
-        "same_final_loss": bool(np.array_equal(final_batch, final_seq)),
-        "final_loss_max_rel_diff": float(np.max(np.abs(final_batch - final_seq) / np.abs(final_seq))),
+        "hbm_frac_step": (params * ALG_BYTES_PER_PARAM + nmeas * 8) / (t_batch * 1e-3) / 1e9 / peak,
+        "sequential_ms_per_step": t_seq, "batched_speedup": (t_seq / t_batch) if t_seq else None,
+        "same_final_loss": same, "final_loss_max_rel_diff": maxrel,
         "kernel_ms": {"fine_tile_fused": float(prof[0]),
                       "restrict_levels": [float(v) for v in prof[1:-1]], "coarse_tail": float(prof[-1])},
         "roofline": {"kernel": "fine_tile_fused", "bound": "hbm", "achieved": ach, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
-                     "alg_bytes_per_launch": fine_bytes},
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
+                     "alg_bytes_per_launch": fine_bytes,
+                     "note": "algorithmic bytes: 32 B per fine cell (p, m FP32 and v FP64 read and "
+                             "written) + 8 B per measurement; fine kernel's CUDA-event time on the "
+                             "problem's stream; peak = measured burst copy"},
+        "clocks": clocks,
         "gpu_launches": launches * K,
+        "e2e": {"value": world * args.instances * K / (e2e_ms * 1e-3), "unit": BATCH_METRIC_UNIT,
+                "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K, "steps": K,
+                "note": "create + level upload from pinned host memory + K steps with the loss "
+                        "terms read back every step + composed fields read"},
     }
-    print(json.dumps(out), flush=True)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, el = time_batch_oracle(batch, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": n / el, "unit": BATCH_METRIC_UNIT, "cores": blas_threads(),
+                               "kind": "oracle",
+                               "sample": f"{n} oracle Adam steps of single instances, cycling through the "
+                                         f"batch in order, {el:.1f} s ({cpu_model()}, {os.cpu_count()} host cores)"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def body_levels(w):
@@ -782,7 +957,7 @@ def run_warmstart(args):
         hz, histz = W.steps_to_losses(desc, W.zero_levels((big,) * 3, Lb), thresholds, args.steps)
         hw, histw = W.steps_to_losses(desc, W.warm_levels((big,) * 3, Lb, 1, pred), thresholds, args.steps)
         chi_ref = inputs.ns3d_body_fraction((side,) * 3, c, a)
-        chi_pred = 1.0 / (1.0 + np.exp(-(pred[4] + 5.0)))
+        chi_pred = 1.0 / (1.0 + np.exp(-(pred[4] - 5.0)))
         results.append({
             "seed": seed, "forward_loss": float(tb[0][0]), "inference_s": t_inf,
             "chi_mean_abs_err_prediction": float(np.mean(np.abs(chi_pred - chi_ref))),
@@ -813,7 +988,10 @@ def main():
     args = parse()
     from paper_2303_04679_gb300 import inputs
     if args.workload == "batched-burgers":
-        run_batched(args)
+        if args.impl == "reference":
+            run_reference_batched(args)
+        else:
+            run_batched(args)
         return
     if args.workload == "body":
         run_body(args)
@@ -938,10 +1116,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": list(w["shape"]), "levels": w["n_levels"],
-                   "params": params, "measurements": n_meas, "tile": args.tile,
-                   "l2": "flushed before every timed step (256 MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": heat_config(args, w),
         "fine_cells_per_s": value * fine,
         "effective_step_GBps": step_alg_bytes * value / world / 1e9,
         "hbm_frac_step": step_alg_bytes * value / world / 1e9 / peak,

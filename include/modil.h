@@ -53,7 +53,10 @@ typedef enum {
   MODIL_ERR_CUDA = -3,        /* a CUDA runtime call failed                */
   MODIL_ERR_UNSUPPORTED = -4, /* valid request this build does not handle  */
   MODIL_ERR_NONFINITE = -5,   /* loss became NaN or Inf                     */
-  MODIL_ERR_STATE = -6        /* call not valid in the problem's state      */
+  MODIL_ERR_STATE = -6,       /* call not valid in the problem's state      */
+  MODIL_ERR_TIMEOUT = -7      /* a bounded wait inside a kernel ran out: the
+                                 pass skipped the affected tiles, so its
+                                 results are incomplete; reported once       */
 } modil_status;
 
 /* PDE families (paper Section 3). */
@@ -69,7 +72,7 @@ enum {
                             a penalisation field (Section 3.5, the penalised momentum
                             equation): axes (z, y, x) on [0,1] x [0,1] x [0,2], fields
                             0 = u, 1 = v, 2 = w (velocity along x, y, z), 3 = p,
-                            4 = chihat with body fraction chi = 1/(1+exp(-(chihat+5)));
+                            4 = chihat with body fraction chi = 1/(1+exp(-(chihat-5)));
                             inlet x = 0 (u = (1,0,0)), outlet x = 2 (p = 0), free-slip
                             walls in y and z; ndim = 3                               */
   MODIL_PDE_POISSON = 5  /* Poisson equation lap(u) = f on [0,1]^2, axes (y, x), cell
@@ -215,6 +218,22 @@ modil_status modil_set_persistent(modil_problem* p, int on);
 /* Steps taken so far (the Adam step counter t). */
 modil_status modil_step_count(const modil_problem* p, long long* t);
 
+/* Checkpoint and resume (the paper has no counterpart; its runs take up to
+ * two hours).  modil_save synchronises the problem's stream and writes, to a
+ * file at `path`, a header (format version, PDE, dtype, fields, instances,
+ * parameter counts, a hash of every instance's level shapes, the step count)
+ * followed by the current levels, the Adam moments m and v, the conductivity
+ * nodes with their moments, and the per-instance step state.  modil_load
+ * reads such a file into a problem created from the same descriptors (same
+ * PDE, dtype and level shapes; otherwise MODIL_ERR_ARG and the problem is
+ * unchanged) and continues from it: the steps that follow are bit for bit
+ * those of the run that wrote it, since every reduction of a step has a
+ * fixed order.  Measurements, weights and coefficients come from the
+ * problem's own descriptors, not from the file.  Both return MODIL_ERR_ARG
+ * when the file cannot be opened, written or read in full. */
+modil_status modil_save(modil_problem* p, const char* path);
+modil_status modil_load(modil_problem* p, const char* path);
+
 /* Zero the Adam moments and the step counter of every instance. */
 modil_status modil_reset_optimizer(modil_problem* p);
 
@@ -226,15 +245,22 @@ modil_status modil_reset_optimizer(modil_problem* p);
  * buffers it was given.  The working memory (per-tile partial sums, problem
  * tables, measurement runs) lives in one file-scope __device__ array of 8 MiB
  * that every GPU loading the library keeps until the process exits.
- *   desc:   one problem, as for modil_create (read on the host).
- *   levels: device, all levels of field 0 back to back (level 0 first, each
- *           row-major), dtype of desc.  Conductivity nodes come from desc.
- *   grads:  device output, dL/du of every level, same layout as levels.
+ *   desc:   one problem, as for modil_create (read on the host): Burgers,
+ *           heat, Poisson or the cavity.
+ *   levels: device, every field's levels back to back, field-major (field 0's
+ *           levels, then field 1's, ...; within a field level 0 first, each
+ *           row-major), dtype of desc; one field except the cavity (u, v, p).
+ *           Conductivity nodes come from desc.  Must start on a 16-byte
+ *           boundary (the kernels use 16-byte vector accesses).
+ *   grads:  device output, dL/du of every level, same layout and alignment
+ *           as levels.
  *   terms:  host output, MODIL_NTERMS doubles.  kgrad: host output of n_knodes
  *           doubles (heat) or NULL.
  *   stream: cudaStream_t; the call synchronises it before returning.
  * Returns MODIL_ERR_ARG if the problem needs more than the 8 MiB of working
- * memory.  The first call on a device looks up the array's device address
+ * memory or a pointer is misaligned, MODIL_ERR_UNSUPPORTED for the 3-D body
+ * problem (it needs a composed-field buffer) and for off-grid points, before
+ * anything runs on the GPU.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the one array, which keeps the last call's contents (every
  * value a call reads is written by that call first), so calls that overlap on
@@ -270,6 +296,15 @@ typedef struct modil_lbfgs modil_lbfgs;
 modil_status modil_lbfgs_create(modil_problem* p, int history, modil_lbfgs** out);
 modil_status modil_lbfgs_run(modil_lbfgs* o, int iterations, double* loss, int* done);
 void modil_lbfgs_destroy(modil_lbfgs* o);
+
+/* Fault injection for tests (the paper has no counterpart): the number of
+ * polls after which the 3-D body kernel's bounded wait for its tile copies
+ * gives up (polls < 0 restores the default of 2^24; 0 gives up at once).  A
+ * block whose wait runs out flags MODIL_ERR_TIMEOUT, waits (with the default
+ * bound) for the copies still in flight, skips its tile and returns; the next
+ * call that returns numbers reports the status once.  Affects every problem
+ * on the current device; nothing hangs or faults. */
+modil_status modil_test_set_spin_limit(long long polls);
 
 /* Last error message of the calling thread ("" if none). */
 const char* modil_last_error(void);

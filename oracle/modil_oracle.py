@@ -572,7 +572,13 @@ def ns2d_fields_residual_jacobian_grad(u, v, p, lam_u, lam_v, lam_c, Re, h, tau_
 # Penalised steady Navier-Stokes in 3-D, body shape (Section 3.5, eq_nschi3)
 # ---------------------------------------------------------------------------
 # Reading.  Fields u, v, w, p, chihat on (z, y, x) cells of [0,1] x [0,1] x
-# [0,2], flow along x.  chi = 1 / (1 + exp(-(chihat + 5))).  Residuals follow
+# [0,2], flow along x.  chi = 1 / (1 + exp(-(chihat - 5))), so that the
+# initial guess chihat = 0 is chi = 1 / (1 + e^5), almost no body.  Section
+# 3.5 prints the transform with chihat + 5 but states in the same paragraph
+# that chihat = 0 corresponds to chi = 1 / (1 + e^5); the two statements
+# disagree, and only the shift by -5 makes the stated initial guess (uniform
+# inflow, no pressure, no body) consistent, so that reading is taken.
+# Residuals follow
 # the cavity discretisation (Section 3.3 reading) in 3-D with the spacings of
 # each axis:
 #   momentum:  r = (1 - chi) (conv + grad p - (D/Re) lap) + lambda chi u_c
@@ -586,7 +592,8 @@ def ns2d_fields_residual_jacobian_grad(u, v, p, lam_u, lam_v, lam_c, Re, h, tau_
 # analytic in chihat, so complex input is accepted.
 
 def ns3d_chi(ch):
-    return 1.0 / (1.0 + np.exp(-(ch + 5.0)))
+    """Body fraction from its transform: chi = 1/(1 + exp(-(chihat - 5)))."""
+    return 1.0 / (1.0 + np.exp(-(ch - 5.0)))
 
 
 def _ns3d_pad(f, kind):

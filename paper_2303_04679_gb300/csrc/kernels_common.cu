@@ -436,7 +436,7 @@ k_tail(const __grid_constant__ Arena<T> A, int mode, int cur) {
       S.terms[1] = res;
       S.terms[2] = dat;
       S.terms[3] = rg;
-      if (!isfinite(tot)) S.nonfinite = 1;
+      if (!isfinite(tot)) S.nonfinite |= kStatusNonfinite;
     }
     if (mode != MODE_LOSS)
       for (int j = tid; j < nk; j += kTailNT) {

@@ -1,6 +1,7 @@
 // Penalised steady Navier-Stokes in 3-D (body shape, paper Section 3.5,
 // equation eq_nschi3): fields u, v, w, p, chihat on (z, y, x) cells of
-// [0,1] x [0,1] x [0,2], chi = 1/(1 + exp(-(chihat + 5))).
+// [0,1] x [0,1] x [0,2], chi = 1/(1 + exp(-(chihat - 5))) (the initial guess
+// chihat = 0 is chi = 1/(1 + e^5), almost no body, as Section 3.5 states).
 //
 //   momentum   r = (1 - chi)(conv + grad p - (D/Re) lap) + lambda chi u_c
 //   continuity r = sum over axes of Rhie-Chow face fluxes (tau = tau_factor h)
@@ -31,6 +32,16 @@
 #include "modil_dev.cuh"
 
 namespace modil {
+
+// Polls of one bounded mbarrier wait before the block gives up; a test can
+// lower it (set_spin_limit) to make a wait run out on purpose.
+constexpr long long kSpinPolls = 1LL << 24;
+__device__ long long g_spin_limit = kSpinPolls;
+
+cudaError_t set_spin_limit(long long polls) {
+  if (polls < 0) polls = kSpinPolls;
+  return cudaMemcpyToSymbol(g_spin_limit, &polls, sizeof(polls));
+}
 
 constexpr int C3Z = k3TZ, C3Y = k3TY, C3X = k3TX;  // fine tile (owned cells)
 constexpr int NC3 = C3Z * C3Y * C3X;
@@ -340,8 +351,8 @@ __device__ __forceinline__ void r3_phase1(const R3<T>& c, bool adj, float& racc,
     const T chat = c.cS[c.cidx(z, y, x)];
     // chi and 1 - chi each from its own logistic: 1 - chi is never formed by
     // subtraction, which loses all digits in FP32 where chi is near 1
-    const T chi = T(1) / (T(1) + exp(-(chat + T(5))));
-    const T om = T(1) / (T(1) + exp(chat + T(5)));
+    const T chi = T(1) / (T(1) + exp(-(chat - T(5))));
+    const T om = T(1) / (T(1) + exp(chat - T(5)));
     T Vf[3][2];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
@@ -599,19 +610,27 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur, const __grid_con
           "r"(c.z0 - 1), "r"(4)
           : "memory");
     }
-    // bounded wait for the copies
-    bool ok = false;
-    for (long long it = 0; it < (1LL << 24) && !ok; ++it) {
-      uint32_t r;
-      asm volatile(
-          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
-          " selp.u32 %0, 1, 0, p;\n}\n"
-          : "=r"(r)
-          : "r"(smem_addr3(&bar))
-          : "memory");
-      ok = r != 0;
+    // bounded wait for the copies; on timeout the block flags it, then waits
+    // (bounded again) for the copies still in flight into its shared memory
+    // before it skips the tile and returns
+    auto wait_copies = [&](long long polls) {
+      bool done = false;
+      for (long long it = 0; it < polls && !done; ++it) {
+        uint32_t r;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(r)
+            : "r"(smem_addr3(&bar))
+            : "memory");
+        done = r != 0;
+      }
+      return done;
+    };
+    if (!wait_copies(g_spin_limit)) {
+      tma_ok = 0;
+      wait_copies(kSpinPolls);
     }
-    if (!ok) tma_ok = 0;
   } else {
     for (int f = 0; f < 4; ++f) {
       const T* src = A.ufine + D.fine_off[f];
@@ -632,8 +651,8 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur, const __grid_con
     cp_async_wait_all();
   }
   __syncthreads();
-  if (!tma_ok) {  // a copy never completed: flag it, skip the tile
-    if (tid == 0) A.st[ii].nonfinite = 2;
+  if (!tma_ok) {  // the wait for a copy ran out: flag it, skip the tile
+    if (tid == 0) atomicOr(&A.st[ii].nonfinite, kStatusTimeout);
     return;
   }
   c.cf = cfS;

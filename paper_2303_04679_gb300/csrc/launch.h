@@ -53,6 +53,9 @@ constexpr int k3TZ = 4, k3TY = 8, k3TX = 16;
 constexpr int k3LZ = 2, k3LY = 8, k3LX = 16;
 template <class T>
 cudaError_t prepare_ns3d(size_t pyr_elems);
+// Polls of the 3-D kernel's bounded copy wait (negative: the default); for
+// tests that make a wait run out.
+cudaError_t set_spin_limit(long long polls);
 template <class T>
 cudaError_t launch_prolong3(const Arena<T>& A, int level, int nfield, int cur, cudaStream_t s);
 struct Ns3Maps {

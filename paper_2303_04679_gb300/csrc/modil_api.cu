@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstddef>
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -612,11 +613,24 @@ modil_status read_terms(modil_problem* p, double* terms) {
   std::vector<InstState> st(P.n_inst);
   CUDA_TRY(cudaMemcpy(st.data(), static_cast<char*>(p->arena) + P.o_st,
                       sizeof(InstState) * P.n_inst, cudaMemcpyDeviceToHost));
-  bool bad = false;
+  bool bad = false, late = false;
   for (int i = 0; i < P.n_inst; ++i) {
     if (terms)
       for (int j = 0; j < MODIL_NTERMS; ++j) terms[i * MODIL_NTERMS + j] = st[i].terms[j];
-    bad |= st[i].nonfinite != 0;
+    bad |= (st[i].nonfinite & kStatusNonfinite) != 0;
+    late |= (st[i].nonfinite & kStatusTimeout) != 0;
+  }
+  if (late) {
+    // reported once: clear the timeout bits, keep the non-finite latch
+    for (int i = 0; i < P.n_inst; ++i) {
+      if (!(st[i].nonfinite & kStatusTimeout)) continue;
+      const int v = st[i].nonfinite & ~kStatusTimeout;
+      CUDA_TRY(cudaMemcpy(static_cast<char*>(p->arena) + P.o_st + sizeof(InstState) * i +
+                              offsetof(InstState, nonfinite),
+                          &v, sizeof(int), cudaMemcpyHostToDevice));
+    }
+    return fail(MODIL_ERR_TIMEOUT, "a bounded wait inside a kernel ran out; the pass skipped the "
+                "affected tiles, so its loss, gradient and step are incomplete");
   }
   if (bad) return fail(MODIL_ERR_NONFINITE, "loss became non-finite");
   return MODIL_OK;
@@ -663,6 +677,47 @@ modil_status external_pass(modil_problem* p, Arena<T> A, const void* levels, voi
   if (grads) A.g = static_cast<T*>(grads);
   A.gscale = (float)scale;
   return run_pass_t<T>(p, A, mode, 0, nullptr, nullptr);
+}
+
+}  // namespace
+
+namespace {
+
+// Checkpoint file: a fixed header, then the optimiser state in arena order.
+struct CkptHeader {
+  char magic[8];           // "MODILCK1"
+  int32_t version, n_inst, pde, dtype, nfield, pad;
+  int64_t n_param, n_k, steps;
+  uint64_t shape_hash;     // FNV-1a over every instance's level shapes
+};
+
+uint64_t shape_hash(const Plan& P) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](long long v) {
+    for (int k = 0; k < 8; ++k) {
+      h ^= (uint64_t)((v >> (8 * k)) & 0xff);
+      h *= 1099511628211ull;
+    }
+  };
+  for (const DevInst& D : P.dev) {
+    mix(D.nlev);
+    for (int l = 0; l < D.nlev; ++l)
+      for (int a = 0; a < 3; ++a) mix(D.n[l][a]);
+  }
+  return h;
+}
+
+// The regions a checkpoint holds: current levels, Adam moments, conductivity
+// nodes and their moments, per-instance step state.
+struct CkptRegion { size_t off, bytes; };
+
+std::vector<CkptRegion> ckpt_regions(const modil_problem* p) {
+  const Plan& P = p->plan;
+  const size_t cur = (p->steps & 1) ? P.o_p1 : P.o_p0;
+  return {{cur, P.esz * P.n_param},      {P.o_m, P.esz * P.n_param},
+          {P.o_v, 8 * (size_t)P.n_param}, {P.o_kq, P.esz * P.n_k},
+          {P.o_km, P.esz * P.n_k},        {P.o_kv, 8 * (size_t)P.n_k},
+          {P.o_st, sizeof(InstState) * P.n_inst}};
 }
 
 }  // namespace
@@ -1016,6 +1071,68 @@ modil_status modil_level_offset(const modil_problem* p, int instance, int field,
 modil_status modil_step_count(const modil_problem* p, long long* t) {
   if (!p || !t) return fail(MODIL_ERR_ARG, "NULL argument");
   *t = p->steps;
+  return MODIL_OK;
+}
+
+modil_status modil_save(modil_problem* p, const char* path) {
+  if (!p || !path) return fail(MODIL_ERR_ARG, "NULL argument");
+  const Plan& P = p->plan;
+  CUDA_TRY(cudaStreamSynchronize(p->stream));
+  CkptHeader h{};
+  std::memcpy(h.magic, "MODILCK1", 8);
+  h.version = 1;
+  h.n_inst = P.n_inst; h.pde = P.pde; h.dtype = P.dtype; h.nfield = P.nfield;
+  h.n_param = P.n_param; h.n_k = P.n_k; h.steps = p->steps;
+  h.shape_hash = shape_hash(P);
+  std::FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(MODIL_ERR_ARG, std::string("cannot open ") + path + " for writing");
+  bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+  std::vector<char> buf;
+  for (const CkptRegion& r : ckpt_regions(p)) {
+    if (!ok || r.bytes == 0) continue;
+    buf.resize(r.bytes);
+    cudaError_t e = cudaMemcpy(buf.data(), static_cast<char*>(p->arena) + r.off, r.bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      std::fclose(f);
+      return fail(MODIL_ERR_CUDA, cudaGetErrorString(e));
+    }
+    ok = std::fwrite(buf.data(), 1, r.bytes, f) == r.bytes;
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(MODIL_ERR_ARG, std::string("writing ") + path + " failed");
+  return MODIL_OK;
+}
+
+modil_status modil_load(modil_problem* p, const char* path) {
+  if (!p || !path) return fail(MODIL_ERR_ARG, "NULL argument");
+  const Plan& P = p->plan;
+  std::FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(MODIL_ERR_ARG, std::string("cannot open ") + path);
+  CkptHeader h{};
+  if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "MODILCK1", 8) != 0 || h.version != 1) {
+    std::fclose(f);
+    return fail(MODIL_ERR_ARG, std::string(path) + " is not a checkpoint of this library");
+  }
+  if (h.n_inst != P.n_inst || h.pde != P.pde || h.dtype != P.dtype || h.nfield != P.nfield ||
+      h.n_param != P.n_param || h.n_k != P.n_k || h.shape_hash != shape_hash(P) || h.steps < 0) {
+    std::fclose(f);
+    return fail(MODIL_ERR_ARG, "the checkpoint was written by a problem of another shape");
+  }
+  CUDA_TRY(cudaStreamSynchronize(p->stream));
+  const long long old = p->steps;
+  p->steps = h.steps;  // selects the level buffer the next step reads
+  std::vector<char> buf;
+  for (const CkptRegion& r : ckpt_regions(p)) {
+    if (r.bytes == 0) continue;
+    buf.resize(r.bytes);
+    if (std::fread(buf.data(), 1, r.bytes, f) != r.bytes) {
+      std::fclose(f);
+      p->steps = old;
+      return fail(MODIL_ERR_ARG, std::string(path) + " is truncated");
+    }
+    CUDA_TRY(cudaMemcpy(static_cast<char*>(p->arena) + r.off, buf.data(), r.bytes, cudaMemcpyHostToDevice));
+  }
+  std::fclose(f);
   return MODIL_OK;
 }
 
@@ -1375,16 +1492,26 @@ modil_status noalloc_run(const Plan& P, const modil_desc* d, const void* levels,
   for (int j = 0; j < MODIL_NTERMS; ++j) terms[j] = out.terms[j];
   if (kgrad)
     for (int j = 0; j < P.nk; ++j) kgrad[j] = (double)kg[j];
+  if (out.nonfinite & kStatusTimeout)
+    return fail(MODIL_ERR_TIMEOUT, "a bounded wait inside a kernel ran out");
   if (out.nonfinite) return fail(MODIL_ERR_NONFINITE, "loss became non-finite");
   return MODIL_OK;
 }
 
 }  // namespace
 
+extern "C" modil_status modil_test_set_spin_limit(long long polls) {
+  CUDA_TRY(set_spin_limit(polls));
+  return MODIL_OK;
+}
+
 extern "C" modil_status modil_eval_grad_noalloc(const modil_desc* desc, const void* levels,
                                                 void* grads, double* terms, double* kgrad,
                                                 void* stream) {
   if (!desc || !levels || !grads || !terms) return fail(MODIL_ERR_ARG, "NULL argument");
+  // the kernels move aligned runs of 4 elements with 16-byte accesses
+  if ((reinterpret_cast<uintptr_t>(levels) | reinterpret_cast<uintptr_t>(grads)) & 15)
+    return fail(MODIL_ERR_ARG, "levels and grads must start on 16-byte boundaries");
   Plan P;
   modil_status s = make_plan(desc, 1, P);
   if (s != MODIL_OK) return s;

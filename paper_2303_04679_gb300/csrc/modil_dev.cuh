@@ -47,13 +47,18 @@ struct DevInst {
   double lr, b1, b2, eps;      // Adam
 };
 
+// Bits of InstState::nonfinite.
+constexpr int kStatusNonfinite = 1;
+constexpr int kStatusTimeout = 2;
+
 // Per-instance mutable state.
 struct InstState {
   long long t;        // completed Adam steps
   double b1t, b2t;    // beta1^t, beta2^t
   double c1, c2;      // bias corrections of step t+1: 1/(1-beta1^(t+1)), 1/(1-beta2^(t+1))
   double terms[4];    // total, residual, data, regulariser of the last evaluation
-  int nonfinite;      // latched when a loss is NaN/Inf
+  int nonfinite;      // status bits: kStatusNonfinite (a loss was NaN/Inf, latched),
+                      // kStatusTimeout (a bounded wait ran out; cleared when reported)
   int pad;
 };
 

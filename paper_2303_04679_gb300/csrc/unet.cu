@@ -577,7 +577,7 @@ modil_status eval_grad(modil_unet* n, const float* input, const float* target, d
     UCUDA(cudaMemcpyAsync(&l, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->s));
     UCUDA(cudaMemcpyAsync(&e, n->err, sizeof(int), cudaMemcpyDeviceToHost, n->s));
     UCUDA(cudaStreamSynchronize(n->s));
-    if (e) return fail(MODIL_ERR_CUDA, "tensor-core GEMM wait timed out (code " + std::to_string(e) + ")");
+    if (e) return fail(MODIL_ERR_TIMEOUT, "tensor-core GEMM wait timed out (code " + std::to_string(e) + ")");
     *loss = l / ((double)M0 * n->d.out_ch);
   }
   return MODIL_OK;

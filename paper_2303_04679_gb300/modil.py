@@ -27,11 +27,13 @@ TERM_NAMES = ("total", "res", "data", "reg")
 MAX_LEVELS = 10
 
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_UNSUPPORTED",
-          -5: "ERR_NONFINITE", -6: "ERR_STATE"}
+          -5: "ERR_NONFINITE", -6: "ERR_STATE", -7: "ERR_TIMEOUT"}
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED, ERR_NONFINITE, ERR_STATE, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6, -7
 
 
 class ModilError(RuntimeError):
     def __init__(self, code, msg):
+        self.code = code
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
         self.code = code
 
@@ -134,6 +136,15 @@ class Desc:
         self._knodes = None if knodes is None else np.ascontiguousarray(knodes, np.float64)
         self._pts = None if points is None else np.ascontiguousarray(np.reshape(points, (-1, 2)), np.float64)
         self._pval = None if point_value is None else np.ascontiguousarray(point_value, np.float64)
+        # the C planner reads these arrays up to n_meas / n_points entries
+        n_cells = 0 if self._cell is None else len(self._cell)
+        if n_cells and (self._val is None or len(self._val) != n_cells):
+            raise ValueError("meas_value needs one value per measurement cell")
+        if self._field is not None and len(self._field) != n_cells:
+            raise ValueError("meas_field needs one field index per measurement cell")
+        n_pts = 0 if self._pts is None else len(self._pts)
+        if n_pts and (self._pval is None or len(self._pval) != n_pts):
+            raise ValueError("point_value needs one value per off-grid point")
         d = modil_desc()
         d.pde, d.dtype, d.ndim = self.pde, self.dtype, len(self.shape)
         for i, s in enumerate(self.shape):
@@ -164,6 +175,17 @@ class Desc:
     @property
     def n_fields(self):
         return {PDE_NS2D: 3, PDE_NS3D: 5}.get(self.pde, 1)
+
+    def param_count(self):
+        """Unknowns of the levels: fields x sum over levels of the cells of each
+        level (every axis halved per level)."""
+        per_field = 0
+        for lvl in range(self.n_levels):
+            n = 1
+            for s in self.shape:
+                n *= s >> lvl
+            per_field += n
+        return self.n_fields * per_field
 
 
 def _desc_array(descs):
@@ -367,6 +389,14 @@ class Problem:
         """grads <- grad_out * dL/dlevels (device tensors, parameter-vector layout)."""
         _check(LIB.modil_loss_bwd(self._h, levels.data_ptr(), float(grad_out), grads.data_ptr()))
 
+    def save(self, path):
+        """Write the optimiser state (levels, Adam moments, step count) to a file."""
+        _check(LIB.modil_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        """Continue from a file written by save() of a problem with the same descriptors."""
+        _check(LIB.modil_load(self._h, os.fsencode(path)))
+
     def set_persistent(self, on=True):
         _check(LIB.modil_set_persistent(self._h, 1 if on else 0))
 
@@ -411,11 +441,21 @@ class LBFGS:
 def eval_grad_noalloc(desc, levels, grads, stream=None):
     """Loss and gradient of one problem with no device allocation.
 
-    ``levels`` and ``grads`` are device tensors holding all levels back to back
-    (level 0 first); returns (terms, kgrad).  The library keeps its working
-    memory in a fixed 8 MiB device array, for callers that cannot allocate.
+    ``levels`` and ``grads`` are contiguous device tensors of the problem's
+    dtype holding every field's levels back to back (field-major; within a
+    field level 0 first, each row-major), 16-byte aligned; returns (terms,
+    kgrad).  The library keeps its working memory in a fixed 8 MiB device
+    array, for callers that cannot allocate.
     """
     import torch
+    want = torch.float64 if desc.dtype == F64 else torch.float32
+    n = desc.param_count()
+    for name, t in (("levels", levels), ("grads", grads)):
+        if not t.is_cuda or not t.is_contiguous() or t.dtype != want or t.numel() != n:
+            raise ValueError(f"{name}: need a contiguous CUDA tensor of {want} with {n} elements, "
+                             f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+        if t.data_ptr() % 16:
+            raise ValueError(f"{name}: must start on a 16-byte boundary")
     s = stream if stream is not None else torch.cuda.current_stream()
     terms = np.zeros(NTERMS, dtype=np.float64)
     nk = 0 if desc._knodes is None else len(desc._knodes)

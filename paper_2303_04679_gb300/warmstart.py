@@ -25,9 +25,9 @@ FIELDS = 5  # u, v, w, p, chihat
 
 
 def chihat_from_fraction(chi, clip=1e-3):
-    """chihat with 1 / (1 + exp(-(chihat + 5))) = chi, chi clipped to [clip, 1 - clip]."""
+    """chihat with 1 / (1 + exp(-(chihat - 5))) = chi, chi clipped to [clip, 1 - clip]."""
     c = np.clip(chi, clip, 1.0 - clip)
-    return np.log(c / (1.0 - c)) - 5.0
+    return np.log(c / (1.0 - c)) + 5.0
 
 
 def zero_levels(shape, n_levels, inflow_level=0):

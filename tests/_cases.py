@@ -18,7 +18,7 @@ class Case:
     def __init__(self, pde, shape, L, dtype="f32", seed=0, n_meas=50, nu=0.01, w_res=1.0,
                  w_data=1.0, w_reg=0.0, lr=5e-3, tile=(0, 0), duplicate=0, n_knodes=32,
                  fine_lo=None, fine_hi=None, coarse_scale=None, Re=100.0, tau=1.0, D=0.4,
-                 lam=1.0, chi_shift=-5.0):
+                 lam=1.0, chi_shift=5.0):
         self.pde, self.shape, self.L, self.dtype = pde, tuple(shape), L, dtype
         self.npd = np.float64 if dtype == "f64" else np.float32
         nx = shape[-1]
@@ -53,7 +53,7 @@ class Case:
             cs = cs if coarse_scale is None else coarse_scale
             self.levels = inputs.random_levels(shape, L, self.nf, seed, lo, hi, cs, dtype=self.npd)
             if pde == "ns3d":
-                # body-fraction logits around chihat = -5 (chi near 1/2) so that
+                # body-fraction logits around chihat = 5 (chi near 1/2) so that
                 # both the flow and the penalisation terms are exercised
                 self.levels[4][0] = rnd(self.levels[4][0] * 8.0 + chi_shift, self.npd)
         else:
@@ -109,31 +109,52 @@ def abs_chain(g_fine, n_levels):
     return out
 
 
+# (field, level) pairs of the criterion's floor, per PDE: the cavity's
+# pressure on the coarse levels, whose constant mode only the single gauge
+# residual sees, so their gradients are sums of terms that cancel to far
+# below the terms' size (reading R14).  Everywhere else the error is measured
+# against ||g_ref|| alone.
+FLOOR_PAIRS = {"ns2d": lambda f, lvl: f == 2 and lvl >= 1}
+
+# what the last check_loss_grad call compared: (field, level, branch, ratio),
+# branch "ref" (against ||g_ref||) or "terms" (against 0.1 ||A||)
+LAST_CRITERIA = []
+
+
 def check_loss_grad(case, prob, tol, instance=0, levels=None, q=None, check_max=True):
     """Compare loss terms, every level gradient and dL/dq with the oracle.
 
-    Gradient criterion per (field, level): ||g - g_ref|| <= tol * max(||g_ref||,
-    0.1 ||A||), A = the absolute-value restriction of |dL/du_fine| to that
-    level.  Where the terms of a coarse-level gradient cancel to much less than
-    their size (the pressure levels of the cavity, whose constant mode only
-    the gauge term sees), the error is measured against the terms."""
+    Gradient criterion per (field, level): ||g - g_ref|| <= tol ||g_ref||.
+    Only for the pairs FLOOR_PAIRS names (the cavity's coarse pressure levels)
+    is the scale max(||g_ref||, 0.1 ||A||), A = the absolute-value restriction
+    of |dL/du_fine| to that level: there the terms of the gradient cancel to
+    much less than their size, and FP32 cannot resolve the sum below the size
+    of its terms.  LAST_CRITERIA records which scale each comparison used."""
     terms_ref, grads_ref, gq_ref = case.oracle_eval(levels, q)
     t = prob.eval_grad()[instance]
     for j, name in enumerate(("total", "res", "data", "reg")):
         ref = terms_ref[name]
         assert abs(t[j] - ref) <= tol * max(abs(ref), 1e-300), (name, t[j], ref)
     per_field = grads_ref if case.nf > 1 else [grads_ref]
+    floor = FLOOR_PAIRS.get(case.pde, lambda f, lvl: False)
+    LAST_CRITERIA.clear()
     for f, grads_f in enumerate(per_field):
         absl = abs_chain(grads_f[0], len(grads_f))
         for lvl, gr in enumerate(grads_f):
             g = prob.read_grad(lvl, field=f, instance=instance).astype(np.float64)
-            scale = max(np.linalg.norm(gr), 0.1 * np.linalg.norm(absl[lvl]))
+            nref = np.linalg.norm(gr)
+            use_floor = floor(f, lvl) and 0.1 * np.linalg.norm(absl[lvl]) > nref
+            scale = 0.1 * np.linalg.norm(absl[lvl]) if use_floor else nref
             r = np.linalg.norm(g - gr) / (scale if scale > 0 else 1.0)
-            assert r <= tol, ("field", f, "level", lvl, r)
+            branch = "terms" if use_floor else "ref"
+            LAST_CRITERIA.append((f, lvl, branch, r))
+            assert r <= tol, ("field", f, "level", lvl, branch, r)
             if check_max:
                 err = np.max(np.abs(g - gr))
-                mscale = max(np.max(np.abs(gr)), 0.1 * np.max(absl[lvl]))
-                assert err <= 10 * tol * mscale, ("level max", f, lvl, err, mscale)
+                mscale = np.max(np.abs(gr))
+                if floor(f, lvl):
+                    mscale = max(mscale, 0.1 * np.max(absl[lvl]))
+                assert err <= 10 * tol * mscale, ("level max", f, lvl, branch, err, mscale)
     if case.pde == "heat":
         gq = prob.read_kgrad(instance)
         assert rel(gq, gq_ref) <= tol, ("kgrad", rel(gq, gq_ref))

@@ -274,6 +274,26 @@ def test_heat_implicit_solve_zeroes_residual():
     assert u.max() <= init.max() + 1e-12 and u.min() >= -1e-12
 
 
+def test_heat_regulariser_closed_forms():
+    """Second difference of the conductivity nodes (Section 3.4 reading R7):
+    zero for nodes on a line; for q_j = j^2 every second difference is 2, so
+    the regulariser is 4 per interior node, 4 (K - 1) for K + 1 = 32 nodes,
+    and its gradient 2 sum_i d2_i d(d2_i)/dq_j is (4, -4, 0, ..., 0, -4, 4).
+    A first difference, a q[2:] - q[:-2] stencil or a dropped factor fails."""
+    n = 32
+    p = o.Problem("heat", (4, 8), 1, w_res=0.0, w_data=0.0, w_reg=0.25,
+                  aux=np.zeros(8))
+    u = np.zeros((4, 8))
+    lin = 0.013 + 0.002 * np.arange(n)
+    assert o.loss_terms(p, u, lin)["reg"] == pytest.approx(0.0, abs=1e-30)
+    q = np.arange(n, dtype=float) ** 2
+    assert o.loss_terms(p, u, q)["reg"] == 0.25 * 4.0 * (n - 2)
+    gq = o.loss_grad_fine(p, u, q)[2]
+    want = np.zeros(n)
+    want[[0, 1, -2, -1]] = [4.0, -4.0, -4.0, 4.0]
+    np.testing.assert_array_equal(gq, 0.25 * want)
+
+
 # --------------------------------------------------------------------------
 # Poisson (Section 3.1): exact discrete solution and second-order convergence
 # --------------------------------------------------------------------------
@@ -284,23 +304,33 @@ def _u_ref(x):
 
 
 @pytest.mark.parametrize("layout", ["cell", "node"])
-def test_poisson_paper_reference_is_exact_discrete_solution(layout):
-    n = 32
+def test_poisson_laplacian_exact_on_biquadratics(layout):
+    """u = x(1-x) y(1-y) vanishes on the walls of [0,1]^2 and is quadratic in
+    each axis, so the three-point difference is exact along each axis, and
+    so (cell layout) is the quadratic extrapolation through the zero wall value
+    (Section 3.1) that supplies the ghost: the residual against
+    f = -2 y(1-y) - 2 x(1-x) is zero to rounding in every cell, the wall rows
+    included.  A linear ghost (-u_0) or a wrong extrapolation weight leaves
+    O(1) residuals in the wall rows."""
+    n = 16
     h = (1.0 / n, 1.0 / n)
-    if layout == "cell":
-        c = (np.arange(n) + 0.5) / n
-    else:
-        c = np.arange(n + 1) / n
-    X = np.meshgrid(c, c, indexing="ij")
-    u = _u_ref(X)
-    z = np.zeros_like(u)
-    f = o.poisson_residual(u, z, h, layout)
-    if layout == "node":
-        full = np.zeros_like(u)
-        full[1:-1, 1:-1] = f
-        f = full
+    c = (np.arange(n) + 0.5) / n if layout == "cell" else np.arange(n + 1) / n
+    Y, X = np.meshgrid(c, c, indexing="ij")
+    u = X * (1 - X) * Y * (1 - Y)
+    f = -2.0 * Y * (1 - Y) - 2.0 * X * (1 - X)
+    r = o.poisson_residual(u, f, h, layout)
+    np.testing.assert_allclose(r, 0.0, atol=1e-11)
     p = o.Problem("poisson", (n, n), 1, layout=layout, coef={"f": f})
-    assert o.loss_terms(p, u)["total"] < 1e-24
+    assert o.loss_terms(p, u)["total"] < 1e-22
+    # a field that does not vanish on the walls: u = 1 in every cell.  Its
+    # quadratic-extrapolation ghost is -2 + 1/3 = -5/3, so a wall cell's
+    # residual has (-5/3 - 2 + 1)/h^2 = -8/(3 h^2) per wall it touches.
+    if layout == "cell":
+        one = np.ones((n, n))
+        r1 = o.poisson_residual(one, np.zeros((n, n)), h, layout)
+        walls = (np.arange(n) == 0)[:, None].astype(int) + (np.arange(n) == n - 1)[:, None]
+        walls = walls + walls.T
+        np.testing.assert_allclose(r1, -8.0 / 3.0 * walls * n * n, rtol=1e-13, atol=1e-9)
 
 
 def _quadratic_minimiser(p, shape):
@@ -435,6 +465,26 @@ def test_ns2d_fluid_at_rest_closed_form():
     assert rg == c
 
 
+def test_ns2d_checkerboard_pressure_rhie_chow_closed_form():
+    """Fluid at rest with a checkerboard pressure p = c (-1)^(i+j).  The
+    central pressure gradient cannot see it (interior r_u = r_v = 0), which is
+    why the continuity residual of Section 3.3 uses Rhie-Chow face velocities:
+    at an interior face U = -tau (p_E - p_P)/h (the cell gradients vanish), so
+    each axis contributes 4 tau p / h^2 and r_c = 8 tau_f p / h with
+    tau = tau_f h.  A flipped sign or another coefficient of the correction
+    fails here, though both are invisible to the consistency orders."""
+    n, Re, c, tf = 10, 100.0, 0.3, 0.7
+    h = 1.0 / n
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    p = c * (-1.0) ** (ii + jj)
+    z = np.zeros((n, n))
+    ru, rv, rc, _ = o.ns2d_residuals(z, z, p, Re, h, tau_factor=tf, lid=0.0)
+    inner = (slice(2, -2), slice(2, -2))
+    np.testing.assert_allclose(ru[inner], 0.0, atol=1e-12)
+    np.testing.assert_allclose(rv[inner], 0.0, atol=1e-12)
+    np.testing.assert_allclose(rc[inner], (8.0 * tf * p / h)[inner], rtol=1e-12)
+
+
 def test_ns2d_interior_consistency_second_order():
     """Smooth fields: interior residuals -> (u^2)_x + (uv)_y + p_x - nu lap u,
     (uv)_x + (v^2)_y + p_y - nu lap v and u_x + v_y at second order."""
@@ -509,6 +559,47 @@ def test_ns3d_inside_the_body_only_penalisation_remains():
     np.testing.assert_allclose(ru, 0.7 * u, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(rv, 0.7 * v, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(rw, 0.7 * w, rtol=1e-12, atol=1e-12)
+
+
+def test_ns3d_chi_shift_of_the_initial_guess():
+    """Section 3.5 states that the initial guess chihat = 0 is the body
+    fraction chi = 1/(1 + e^5) (almost no body), which fixes the transform as
+    chi = 1/(1 + exp(-(chihat - 5))); so chihat = 5 is chi = 1/2.  Uniform
+    inflow u = (1, 0, 0), p = 0 solves the flow part exactly (inlet ghost
+    2 - 1 = 1), so the x-momentum residual is the penalisation lambda chi u
+    alone: lambda/(1 + e^5) at chihat = 0 and lambda/2 at chihat = 5.  A
+    dropped or negated shift fails."""
+    assert o.ns3d_chi(np.array(0.0)) == pytest.approx(1.0 / (1.0 + math.exp(5.0)), rel=1e-15)
+    assert o.ns3d_chi(np.array(5.0)) == 0.5
+    sh = (4, 5, 8)
+    one, z = np.ones(sh), np.zeros(sh)
+    lam = 0.7
+    for chihat, chi in ((0.0, 1.0 / (1.0 + math.exp(5.0))), (5.0, 0.5)):
+        ru, rv, rw, rc = o.ns3d_residuals(one, z, z, z, np.full(sh, chihat), 60.0, 0.4, lam,
+                                          _ns3d_h(sh))
+        np.testing.assert_allclose(ru, lam * chi, rtol=1e-12)
+        for r in (rv, rw, rc):
+            np.testing.assert_allclose(r, 0.0, atol=1e-10)
+
+
+def test_ns3d_checkerboard_pressure_rhie_chow_closed_form():
+    """Fluid at rest, checkerboard p = c (-1)^(i+j+k), no body: the central
+    pressure gradient vanishes in the interior and the Rhie-Chow face
+    velocity along axis a is -tau_f (p_+ - p_P), so r_c = 4 tau_f p sum_a 1/h_a
+    (the 3-D form of the cavity's correction, Section 3.5 following 3.3)."""
+    sh = (8, 8, 12)
+    hz, hy, hx = _ns3d_h(sh)
+    c, tf = 0.4, 0.6
+    kk, jj, ii = np.meshgrid(*(np.arange(s) for s in sh), indexing="ij")
+    p = c * (-1.0) ** (ii + jj + kk)
+    z = np.zeros(sh)
+    ru, rv, rw, rc = o.ns3d_residuals(z, z, z, p, np.full(sh, -40.0), 60.0, 0.4, 1.0,
+                                      (hz, hy, hx), tau_factor=tf)
+    inner = (slice(2, -2),) * 3
+    for r in (ru, rv, rw):
+        np.testing.assert_allclose(r[inner], 0.0, atol=1e-10)
+    want = 4.0 * tf * p * (1.0 / hx + 1.0 / hy + 1.0 / hz)
+    np.testing.assert_allclose(rc[inner], want[inner], rtol=1e-12)
 
 
 def test_ns3d_mass_balance():
