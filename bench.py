@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="modil", choices=["modil", "reference"])
-    ap.add_argument("--tile", default="32x32")
+    ap.add_argument("--tile", default=None,
+                    help="fine tile 'ROWSxCOLS' (heat default 32x32; batched default 32x28, the "
+                         "warp-streaming strip) or 'auto' (autotuner)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=50)
@@ -330,7 +332,7 @@ def run_reference_batched(args):
         return
     batch = inputs.burgers_batch(args.instances)
     fine, params, nmeas = batch_sizes(batch)
-    tile = tuple(int(v) for v in args.tile.split("x")) if args.tile != "auto" else (32, 32)
+    tile = tuple(int(v) for v in (args.tile or "32x28").split("x")) if args.tile != "auto" else (32, 28)
     per = 16
     for w in range(max(args.warmup, 0)):
         o, prob, st = oracle_burgers(batch[w % len(batch)])
@@ -350,7 +352,7 @@ def run_reference_batched(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": batched_config(args, tile, True, fine, params, nmeas),
+        "config": batched_config(args, tile, tile != (32, 28), fine, params, nmeas),
         "cpu_baseline": {"value": value, "unit": BATCH_METRIC_UNIT, "cores": blas_threads(),
                          "kind": "oracle",
                          "sample": f"{per} instances of the batch per step (cycling, {n} in all), one "
@@ -389,7 +391,8 @@ def run_batched(args):
         tile, pers, _ = autotune.autotune(
             descs((16, 32)), measure=lambda d, t, q: autotune.time_steps(d, t, q, steps=10, warmup=3))
     else:
-        tile, pers = tuple(int(v) for v in args.tile.split("x")), True
+        tile = tuple(int(v) for v in (args.tile or "32x28").split("x"))
+        pers = tile != autotune.STREAM_TILE
     ds = descs(tile)
     fine, params, nmeas = batch_sizes(batch)
     K = args.steps
@@ -415,6 +418,7 @@ def run_batched(args):
         t_batch = job_ms / K
         final_batch = p.eval_loss()[:, 0].copy()
         prof = np.array([p.profile_step() for _ in range(5)]).mean(axis=0)
+        labels = p.profile_labels()
         launches = p.launches_per_step()
     # the same instances as separate problems, stepped one after another
     t_seq, same, maxrel = None, None, None
@@ -465,7 +469,8 @@ def run_batched(args):
 
     peak, peak_kind = measured_peak()
     fine_bytes = fine * ALG_BYTES_PER_PARAM + nmeas * ALG_BYTES_PER_MEAS
-    ach = fine_bytes / (prof[0] * 1e-3) / 1e9
+    kms = {lab: float(v) for lab, v in zip(labels, prof)}
+    ach = fine_bytes / (kms["fine"] * 1e-3) / 1e9
     tr = traffic_record("batched_fine")
     traffic = None
     if tr is not None and tr.get("tile") == list(tile):
@@ -481,9 +486,9 @@ def run_batched(args):
         "hbm_frac_step": (params * ALG_BYTES_PER_PARAM + nmeas * 8) / (t_batch * 1e-3) / 1e9 / peak,
         "sequential_ms_per_step": t_seq, "batched_speedup": (t_seq / t_batch) if t_seq else None,
         "same_final_loss": same, "final_loss_max_rel_diff": maxrel,
-        "kernel_ms": {"fine_tile_fused": float(prof[0]),
-                      "restrict_levels": [float(v) for v in prof[1:-1]], "coarse_tail": float(prof[-1])},
-        "roofline": {"kernel": "fine_tile_fused", "bound": "hbm", "achieved": ach, "peak": peak,
+        "kernel_ms": kms,
+        "roofline": {"kernel": "fine" + (" (warp-streaming)" if tile == autotune.STREAM_TILE else " (tile)"),
+                     "bound": "hbm", "achieved": ach, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
                      "alg_bytes_per_launch": fine_bytes,
                      "note": "algorithmic bytes: 32 B per fine cell (p, m FP32 and v FP64 read and "
@@ -1009,6 +1014,7 @@ def main():
         run_poisson(args)
         return
     w = inputs.heat_workload()
+    args.tile = args.tile or "32x32"
     if args.impl == "reference":
         run_reference(args, w)
         return

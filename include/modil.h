@@ -176,14 +176,21 @@ modil_status modil_eval_grad(modil_problem* p, double* terms);
 /* n_steps Adam steps of every instance.  terms (nullable) receives the loss
  * terms evaluated at the start of the last step.  Asynchronous when NULL. */
 modil_status modil_step(modil_problem* p, int n_steps, double* terms);
-/* Kernel launches one modil_step issues (the fused fine-tile kernel, one
- * restriction+Adam kernel per coarser level, one finalising kernel). */
+/* Kernel launches one modil_step issues: the composition launches (one per
+ * level, coarse to fine: the 3-D family and the warp-streaming Burgers
+ * kernel), the fused fine kernel, one restriction+Adam kernel per coarser
+ * level above the tail, one finalising (tail) kernel. */
 modil_status modil_launches_per_step(const modil_problem* p, int* n);
 
 /* One Adam step issued kernel by kernel with a CUDA event between launches;
  * ms[k] receives the device time of launch k (order as above).  Synchronises.
  * max_kernels: capacity of ms; *n_kernels: launches timed. */
 modil_status modil_profile_step(modil_problem* p, float* ms, int max_kernels, int* n_kernels);
+/* What each launch of modil_profile_step is: kind[k] 0 = composition of a
+ * level, 1 = fused fine kernel, 2 = restriction+Adam of a level, 3 = tail;
+ * level[k] its level (the tail: the first level it finishes). */
+modil_status modil_profile_labels(const modil_problem* p, int* kind, int* level, int max_kernels,
+                                  int* n_kernels);
 
 /* ---- caller-owned parameters (e.g. a torch.autograd.Function) -------------
  * The layout of all levels of a batch in one buffer ("parameter vector"):

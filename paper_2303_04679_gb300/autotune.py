@@ -13,6 +13,7 @@ import json
 import os
 
 ST_TILES = ((16, 32), (16, 64), (8, 64), (32, 32), (8, 128))
+STREAM_TILE = (32, 28)   # Burgers: the warp-streaming kernel's strip (no persistent variant)
 NS2D_TILES = ((8, 32), (16, 32))
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "modil_gb300", "autotune.json")
 
@@ -60,11 +61,13 @@ def autotune(descs, candidates=None, persistent_options=(False, True), measure=t
             return tuple(c["tile"]), bool(c["persistent"]), float(c["ms"])
     if candidates is None:
         candidates = NS2D_TILES if descs[0].pde == 3 else ST_TILES
+        if descs[0].pde == 1 and not any(d._pts is not None for d in descs):
+            candidates = candidates + (STREAM_TILE,)
     best = None
     results = []
     for tile in candidates:
         for pers in persistent_options:
-            if pers and descs[0].pde == 3:
+            if pers and (descs[0].pde == 3 or tuple(tile) == STREAM_TILE):
                 continue
             ms = float(measure(descs, tile, pers))
             results.append((tile, pers, ms))

@@ -351,8 +351,8 @@ __device__ __forceinline__ void r3_phase1(const R3<T>& c, bool adj, float& racc,
     const T chat = c.cS[c.cidx(z, y, x)];
     // chi and 1 - chi each from its own logistic: 1 - chi is never formed by
     // subtraction, which loses all digits in FP32 where chi is near 1
-    const T chi = T(1) / (T(1) + exp(-(chat - T(5))));
-    const T om = T(1) / (T(1) + exp(chat - T(5)));
+    const T chi = T(1) / (T(1) + texp(-(chat - T(5))));
+    const T om = T(1) / (T(1) + texp(chat - T(5)));
     T Vf[3][2];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {

@@ -192,9 +192,9 @@ __device__ __forceinline__ void block_sum2(double a, double b, void* scratch, do
 // outside [0, 1].  Returns k; s, th are the segment and local coordinate.
 template <class T>
 __device__ __forceinline__ T kcond(T u, const T* q, int K, int& s, T& th, T& dk) {
-  const T ub = fmin(fmax(u, T(0)), T(1));
+  const T ub = tmin(tmax(u, T(0)), T(1));
   const T x = ub * T(K);
-  int si = (int)floor(x);
+  int si = (int)tfloor(x);
   si = si > K - 1 ? K - 1 : si;
   s = si;
   th = x - T(si);
@@ -205,8 +205,8 @@ __device__ __forceinline__ T kcond(T u, const T* q, int K, int& s, T& th, T& dk)
 
 template <class T>
 __device__ __forceinline__ T eo_flux(T a, T b, T& da, T& db) {
-  const T ap = fmax(a, T(0));
-  const T bm = fmin(b, T(0));
+  const T ap = tmax(a, T(0));
+  const T bm = tmin(b, T(0));
   da = ap;
   db = bm;
   return T(0.5) * ap * ap + T(0.5) * bm * bm;

@@ -1,0 +1,375 @@
+// Warp-streaming fine kernel of the viscous Burgers problem (paper Section
+// 3.2; axes (t, x)) and the level-by-level composition pass it reads.
+//
+// Composition pass (k_compose2, one launch per level l = L-2 .. 1, coarse to
+// fine): w_l = u_l + T_l w_{l+1} on every cell of level l of every instance,
+// w_{L-1} = u_{L-1} (Horner's scheme of Section 2.2, T the tensor product of
+// the cell-based 1-D interpolation), stored in the scratch arrays wl at the
+// offsets of the levels.
+//
+// Fine kernel (k_fine_stream): one warp owns a strip of kSW = 28 columns and
+// kSR = 32 rows of the fine grid.  Lane j holds column x = x0 - 2 + j, so the
+// warp covers the owned columns plus two on each side: the composed field is
+// needed two columns out, the residuals one column out.  The warp walks down
+// the rows of its strip (from one row above it to one row below); per row it
+//   1. composes u = u_0 + T w_1 (level 0 of the row, the two rows of w_1 it
+//      interpolates between, interpolated in x once per row of w_1);
+//   2. evaluates the residual of the row and lambda * dr/du at its four
+//      stencil points (lambda = 2 w_res dV r), the neighbours u(x-1), u(x+1)
+//      taken from the adjacent lanes by shuffles;
+//   3. adds the data term of the measured cells of the row;
+//   4. finishes the previous row: dL/du(n-1, x) gathers lambda dr/du of the
+//      residuals that read u(n-1, x) -- its own, those of x-1 and x+1 of row
+//      n-1 (shuffles) and that of (n, x) -- writes it and applies Adam.
+// Everything stays in registers: no shared memory and no block barriers.
+// Level 0's parameters and Adam moments stream through a per-warp ring of
+// kRing rows in shared memory, copied asynchronously kRing - 1 rows ahead;
+// the rows of w_1 are loaded one fine row ahead.  Each warp writes its FP64 partial sums (r^2 and the data
+// misfit, compensated FP32 in between) for the per-instance tail kernel.
+// The stencil (rows n >= 1, the implicit step of the reading of Section 3.2):
+//   r = (u^n_i - u^{n-1}_i)/dt + (F_{i+1/2} - F_{i-1/2})/dx
+//       - nu (u^n_{i+1} - 2u^n_i + u^n_{i-1})/dx^2,
+//   F = Engquist-Osher upwind flux of u^2/2, zero convective flux through the
+//   walls, odd ghosts (u_{-1} = -u_0) for the viscous term.
+#include "launch.h"
+#include "modil_dev.cuh"
+
+namespace modil {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRing = 4;  // rows of level 0 in flight per warp (a power of two)
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <class T>
+__device__ __forceinline__ T eo_flux_s(T a, T b, T& da, T& db) {
+  const T ap = tmax(a, T(0));
+  const T bm = tmin(b, T(0));
+  da = ap;
+  db = bm;
+  return T(0.5) * ap * ap + T(0.5) * bm * bm;
+}
+
+// ---------------------------------------------------------------------------
+// Composition of one level of every instance that has a coarser level
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(kComposeNT) k_compose2(const __grid_constant__ Arena<T> A, int l, int cur) {
+  const int b = blockIdx.x;
+  const int ii = (A.n_inst == 1) ? 0 : A.cblk_inst[l][b];
+  const DevInst& D = (A.n_inst == 1) ? A.inst0 : A.inst[ii];
+  const int ny = D.n[l][1], nx = D.n[l][2];
+  const int nyc = D.n[l + 1][1], nxc = D.n[l + 1][2];
+  const long long cell = (long long)A.cblk_first[l][b] + threadIdx.x;
+  // the levels are written by the previous step's last kernels and, for
+  // w_{l+1}, by the previous launch
+  pdl_wait();
+  pdl_trigger();
+  if (cell >= (long long)ny * nx) return;
+  const int y = (int)(cell / nx), x = (int)(cell - (long long)y * nx);
+  const T* __restrict__ P = A.p[cur];
+  const T* __restrict__ Wc = (l + 1 == D.nlev - 1) ? P + D.off[0][l + 1] : A.wl + D.off[0][l + 1];
+  int jy0, jy1, jx0, jx1;
+  T wy0, wy1, wx0, wx1;
+  prolong_taps<T>(y, nyc, jy0, jy1, wy0, wy1);
+  prolong_taps<T>(x, nxc, jx0, jx1, wx0, wx1);
+  const T* r0 = Wc + (long long)jy0 * nxc;
+  const T* r1 = Wc + (long long)jy1 * nxc;
+  const T c = wy0 * (wx0 * r0[jx0] + wx1 * r0[jx1]) + wy1 * (wx0 * r1[jx0] + wx1 * r1[jx1]);
+  A.wl[D.off[0][l] + cell] = P[D.off[0][l] + cell] + c;
+}
+
+// ---------------------------------------------------------------------------
+// The streaming fine kernel
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void acc_add(float& hi, float& lo, T x) {
+  ff_add(hi, lo, (float)x, 0.f);
+}
+
+// Loop-invariant coefficients of a strip in the working precision, computed
+// once per warp into shared memory: under register pressure the compiler
+// reloads them from there instead of recomputing conversions and divisions.
+template <class T>
+struct StreamCoef {
+  AdamCoef ac;
+  T idt, idx1, idx2, nu, lam_scale, wd2, gscale;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stream(const __grid_constant__ Arena<T> A, int mode, int cur) {
+  // per warp: a ring of kRing rows of level 0's parameters and Adam moments,
+  // filled with asynchronous copies kRing - 1 rows ahead of their use
+  __shared__ __align__(16) T sP[kStreamNT / 32][kRing][32];
+  __shared__ __align__(16) T sM[kStreamNT / 32][kRing][32];
+  __shared__ __align__(16) double sV[kStreamNT / 32][kRing][32];
+  __shared__ StreamCoef<T> sC[kStreamNT / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int gt = blockIdx.x * (kStreamNT / 32) + w;
+  if (gt >= A.ntiles[0]) return;
+  const int ii = (A.n_inst == 1) ? 0 : A.tile_inst[0][gt];
+  const DevInst& D = (A.n_inst == 1) ? A.inst0 : A.inst[ii];
+  const int ny = D.n[0][1], nx = D.n[0][2];
+  const int L = D.nlev;
+  const int local = gt - D.tile_base[0];
+  const int sty = local / D.nt[0][2], stx = local - sty * D.nt[0][2];
+  const int y0 = sty * kSR, x0 = stx * kSW;
+  const int y1 = min(y0 + kSR, ny), xo1 = min(x0 + kSW, nx);  // owned rows [y0, y1), columns [x0, xo1)
+  const int x = x0 - 2 + lane;
+  const bool xin = x >= 0 && x < nx;
+  const bool own_x = x >= x0 && x < xo1;
+  const bool res_x = xin && x >= x0 - 1 && x <= xo1;  // residual columns [x0 - 1, xo1]
+  const bool hw = x > 0, he = x < nx - 1;
+  const bool step = (mode == MODE_STEP), adj = (mode != MODE_LOSS);
+  // per-instance bases; indices within an instance's level fit 32 bits
+  const long long o0 = D.off[0][0];
+  const T* __restrict__ P0 = A.p[cur] + o0;
+  const T* __restrict__ M0 = A.m + o0;
+  const double* __restrict__ V0 = A.v + o0;
+  const int nstart = max(y0 - 1, 0);
+  // level 0 of rows [nstart, y1] (and m, v of the owned rows) -> ring slot r % kRing;
+  // one copy group per row, committed even when empty
+  auto issue = [&](int r) {
+    if (r <= y1 && r < ny && xin) {
+      const int sl = r & (kRing - 1);
+      const int e = r * nx + x;
+      cp_async(&sP[w][sl][lane], P0 + e);
+      if (step && r >= y0 && own_x) {
+        cp_async(&sM[w][sl][lane], M0 + e);
+        cp_async(&sV[w][sl][lane], V0 + e);
+      }
+    }
+    cp_async_commit();
+  };
+  // level 0, m and v were last written by this kernel one step earlier
+#pragma unroll
+  for (int k = 0; k < kRing - 1; ++k) issue(nstart + k);
+  const T cdiag = T(-2) - (hw ? T(0) : T(1)) - (he ? T(0) : T(1));
+  // level 1 composed (w_1; the coarsest level itself when L == 2) and the
+  // lane's column taps into it
+  const int nyc = L >= 2 ? D.n[1][1] : 1, nxc = L >= 2 ? D.n[1][2] : 1;
+  int jx0 = 0, jx1 = 0;
+  T wx0 = T(0), wx1 = T(0);
+  if (L >= 2 && xin) prolong_taps<T>(x, nxc, jx0, jx1, wx0, wx1);
+  const T* __restrict__ W1 = (L >= 3) ? A.wl + D.off[0][1] : A.p[cur] + D.off[0][1];
+  // fine row n lies between rows lo(n) and lo(n) + 1 of w_1
+  auto lo_of = [&](int n) { return nyc > 1 ? min(max((n - 1) >> 1, 0), nyc - 2) : 0; };
+  const int rb = A.run_ptr[gt], re = A.run_ptr[gt + 1];
+  // the row of the next measurement run (runs sorted by cell)
+  auto run_row = [&](int r) { return r < re ? A.run_cell[r] / nx : 0x7fffffff; };
+
+  pdl_wait();  // w_1 (previous launch) and the step state (previous step's tail)
+  pdl_trigger();
+  if (lane == 0) {
+    StreamCoef<T> c;
+    const T dt = (T)D.h[1], dx = (T)D.h[2];
+    c.idt = T(1) / dt;
+    c.idx1 = T(1) / dx;
+    c.idx2 = T(1) / (dx * dx);
+    c.nu = (T)D.coef[0];
+    c.lam_scale = T(2) * (T)D.w_res_dV;
+    c.wd2 = T(2) * (T)D.w_data_n;
+    c.gscale = (T)A.gscale;
+    c.ac = adam_coef(D, A.st[ii]);
+    sC[w] = c;
+  }
+  __syncwarp();
+  const StreamCoef<T>& cf = sC[w];
+  const AdamCoef& ac = cf.ac;
+
+  // x-interpolated rows lo(n), lo(n) + 1 of w_1; the next row's new one is
+  // loaded one row ahead
+  T va = T(0), vb = T(0), wa = T(0), wb = T(0);
+  bool pend = false;
+  if (L >= 2 && xin) {
+    const int lo = lo_of(nstart), hi = nyc > 1 ? lo + 1 : 0;
+    va = wx0 * W1[lo * nxc + jx0] + wx1 * W1[lo * nxc + jx1];
+    vb = wx0 * W1[hi * nxc + jx0] + wx1 * W1[hi * nxc + jx1];
+  }
+  float rh = 0.f, rl = 0.f, dh = 0.f, dl = 0.f;  // compensated FP32 sums (FP32 problems)
+  double rd = 0.0, dd = 0.0;                     // FP64 problems
+  T lJ0p = T(0), lJ1p = T(0), lJ2p = T(0), datp = T(0);  // row n-1 (pending gradient)
+  T p0p = T(0), mp = T(0);
+  double vp = 0.0;
+  int rr = rb, nr = run_row(rb);
+  int lon = lo_of(nstart);
+  T uo = T(0);  // u(n-1, x)
+  // row n: the field, the residual and the data term of row n; the gradient
+  // and the Adam update of row n - 1.  Row y1 (< ny) supplies the residual
+  // that reads the last owned row; the pass with n == ny only finishes rows.
+  for (int n = nstart; n <= y1; ++n) {
+    issue(n + kRing - 1);
+    cp_async_wait_group<kRing - 1>();  // this lane's copies of row n have landed
+    const bool row_ok = n < ny;
+    const bool own_row = n >= y0 && n < y1;
+    const int sl = n & (kRing - 1);
+    T p0 = T(0), u = T(0), mn = T(0);
+    double vn = 0.0;
+    if (pend) {
+      va = vb;
+      vb = wx0 * wa + wx1 * wb;
+      pend = false;
+    }
+    if (row_ok && xin) {
+      p0 = sP[w][sl][lane];
+      if (step && own_row && own_x) {
+        mn = sM[w][sl][lane];
+        vn = sV[w][sl][lane];
+      }
+      u = p0;
+      if (L >= 2) {
+        // weights 5/4 - t/2 and t/2 - 1/4 with t = n - 2 lo (3/4, 1/4 inside;
+        // 5/4, -1/4 at the ends); one row of w_1: a copy
+        T wlo = T(1), whi = T(0);
+        if (nyc > 1) {
+          wlo = T(1.25) - T(0.5) * (T)(n - 2 * lon);
+          whi = T(1) - wlo;
+        }
+        u = p0 + (wlo * va + whi * vb);
+      }
+    }
+    {
+      const int lo1 = lo_of(n + 1);
+      if (L >= 2 && xin && lo1 != lon && n + 1 < ny) {
+        const int h1 = (lo1 + 1) * nxc;
+        wa = W1[h1 + jx0];
+        wb = W1[h1 + jx1];
+        pend = true;
+      }
+      lon = lo1;
+    }
+    if (mode == MODE_COMPOSE) {
+      if (row_ok && own_row && own_x) A.ufine[D.fine_off[0] + n * nx + x] = u;
+      continue;
+    }
+    const T uW = __shfl_up_sync(kFull, u, 1);
+    const T uE = __shfl_down_sync(kFull, u, 1);
+    T lJ0 = T(0), lJ1 = T(0), lJ2 = T(0), lJ3 = T(0);
+    if (row_ok && res_x && n >= 1 && n >= y0) {
+      const T uw = hw ? uW : -u;
+      const T ue = he ? uE : -u;
+      T dFEc = T(0), dFEe = T(0), dFWw = T(0), dFWc = T(0), FE = T(0), FW = T(0);
+      if (he) FE = eo_flux_s(u, ue, dFEc, dFEe);
+      if (hw) FW = eo_flux_s(uw, u, dFWw, dFWc);
+      const T lap = (ue - T(2) * u + uw) * cf.idx2;
+      const T r = (u - uo) * cf.idt + (FE - FW) * cf.idx1 - cf.nu * lap;
+      const T lam = cf.lam_scale * r;
+      lJ1 = lam * (cf.idt + (dFEc - dFWc) * cf.idx1 - cf.nu * cdiag * cf.idx2);
+      lJ0 = hw ? lam * (-dFWw * cf.idx1 - cf.nu * cf.idx2) : T(0);
+      lJ2 = he ? lam * (dFEe * cf.idx1 - cf.nu * cf.idx2) : T(0);
+      lJ3 = lam * (-cf.idt);
+      if (own_row && own_x) {
+        if (sizeof(T) == 4) acc_add(rh, rl, r * r);
+        else rd += (double)(r * r);
+      }
+    }
+    // data term of the measured cells of row n (runs sorted by cell)
+    T dat = T(0);
+    if (n == nr && own_row) {
+      const int rowbase = n * nx;
+      for (; rr < re; ++rr) {
+        const int off = A.run_cell[rr] - rowbase;
+        if (off >= nx) break;
+        if (x == off) {
+          const int e0 = A.run_beg[rr], e1 = A.run_beg[rr + 1];
+          T d = u - A.run_v0[rr];
+          T sd = d, sq = d * d;
+          for (int k = e0 + 1; k < e1; ++k) {  // repeated measurements of a cell
+            d = u - A.meas_val[k];
+            sd += d;
+            sq += d * d;
+          }
+          if (sizeof(T) == 4) acc_add(dh, dl, sq);
+          else dd += (double)sq;
+          dat = cf.wd2 * sd;
+        }
+      }
+      nr = run_row(rr);
+    }
+    // gradient and Adam of row n - 1
+    const T fromE = __shfl_down_sync(kFull, lJ0p, 1);  // lambda dr/du of residual (n-1, x+1)
+    const T fromW = __shfl_up_sync(kFull, lJ2p, 1);    // lambda dr/du of residual (n-1, x-1)
+    const int m1 = n - 1;
+    if (adj && m1 >= y0 && m1 < y1 && own_x) {
+      const T g = ((lJ1p + datp) + fromE + fromW + lJ3) * cf.gscale;
+      const int em = m1 * nx + x;
+      A.g[o0 + em] = g;
+      if (step) {
+        T p = p0p, m = mp;
+        double v = vp;
+        adam_update(p, m, v, g, ac);
+        A.p[cur ^ 1][o0 + em] = p;
+        const_cast<T*>(M0)[em] = m;
+        const_cast<double*>(V0)[em] = v;
+      }
+    }
+    lJ0p = lJ0; lJ1p = lJ1; lJ2p = lJ2; datp = dat;
+    p0p = p0; mp = mn; vp = vn;
+    uo = u;
+  }
+  cp_async_wait_all();  // the ring's trailing (empty or unused) copies
+  if (mode == MODE_COMPOSE) return;
+  double rs, ds;
+  if (sizeof(T) == 4) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float a0 = __shfl_xor_sync(kFull, rh, o), a1 = __shfl_xor_sync(kFull, rl, o);
+      const float b0 = __shfl_xor_sync(kFull, dh, o), b1 = __shfl_xor_sync(kFull, dl, o);
+      ff_add(rh, rl, a0, a1);
+      ff_add(dh, dl, b0, b1);
+    }
+    rs = (double)rh + (double)rl;
+    ds = (double)dh + (double)dl;
+  } else {
+    rs = warp_sum(rd);
+    ds = warp_sum(dd);
+  }
+  if (lane == 0) {
+    A.part[(long long)gt * A.npart + 0] = rs;
+    A.part[(long long)gt * A.npart + 1] = ds;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+static cudaLaunchConfig_t pdl_cfg(dim3 grid, dim3 block, cudaStream_t s, cudaLaunchAttribute* at) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+template <class T>
+cudaError_t launch_compose2(const Arena<T>& A, int level, int cur, cudaStream_t s) {
+  if (A.ncblk[level] == 0) return cudaSuccess;
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t cfg = pdl_cfg(dim3(A.ncblk[level]), dim3(kComposeNT), s, at);
+  return cudaLaunchKernelEx(&cfg, k_compose2<T>, A, level, cur);
+}
+
+template <class T>
+cudaError_t launch_fine_stream(const Arena<T>& A, int mode, int cur, cudaStream_t s) {
+  if (A.ntiles[0] == 0) return cudaSuccess;
+  constexpr int wpb = kStreamNT / 32;
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t cfg = pdl_cfg(dim3((A.ntiles[0] + wpb - 1) / wpb), dim3(kStreamNT), s, at);
+  return cudaLaunchKernelEx(&cfg, k_fine_stream<T>, A, mode, cur);
+}
+
+template cudaError_t launch_compose2<float>(const Arena<float>&, int, int, cudaStream_t);
+template cudaError_t launch_compose2<double>(const Arena<double>&, int, int, cudaStream_t);
+template cudaError_t launch_fine_stream<float>(const Arena<float>&, int, int, cudaStream_t);
+template cudaError_t launch_fine_stream<double>(const Arena<double>&, int, int, cudaStream_t);
+
+}  // namespace modil

@@ -11,9 +11,15 @@
 
 namespace modil {
 
-// Tile configurations of the fused fine kernel: (rows, cols).
-constexpr int kNumTileCfg = 6;
-constexpr int kTileCfg[kNumTileCfg][2] = {{16, 32}, {16, 64}, {8, 64}, {32, 32}, {8, 128}, {8, 32}};
+// Tile configurations of the fused fine kernel: (rows, cols).  The last one
+// is the strip of the warp-streaming Burgers kernel (kSR rows, kSW owned
+// columns per warp).
+constexpr int kNumTileCfg = 7;
+constexpr int kTileCfg[kNumTileCfg][2] = {{16, 32}, {16, 64}, {8, 64}, {32, 32}, {8, 128}, {8, 32}, {32, 28}};
+constexpr int kStreamCfg = 6;
+constexpr int kSR = 32, kSW = 28;
+constexpr int kStreamNT = 128;   // threads per block of the streaming kernel (one strip per warp)
+constexpr int kComposeNT = 256;  // threads (cells) per block of the 2-D composition pass
 // Tile of the restriction kernels (coarse levels), rows x cols.
 constexpr int kLevTY = 8, kLevTX = 32;
 
@@ -48,6 +54,12 @@ cudaError_t launch_fine_ns2d(const Arena<T>& A, int cfg, int mode, int cur, size
                              cudaStream_t s);
 template <class T>
 cudaError_t launch_level(const Arena<T>& A, int nf, int level, int mode, int cur, cudaStream_t s);
+// Warp-streaming Burgers kernel and the composition pass it reads (w_l of
+// levels 1 .. L-2 into the scratch wl).
+template <class T>
+cudaError_t launch_compose2(const Arena<T>& A, int level, int cur, cudaStream_t s);
+template <class T>
+cudaError_t launch_fine_stream(const Arena<T>& A, int mode, int cur, cudaStream_t s);
 // 3-D penalised Navier-Stokes: fine tile 4 x 8 x 16 cells, coarse tile 2 x 8 x 16.
 constexpr int k3TZ = 4, k3TY = 8, k3TX = 16;
 constexpr int k3LZ = 2, k3LY = 8, k3LX = 16;

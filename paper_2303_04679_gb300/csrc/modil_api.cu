@@ -81,6 +81,9 @@ struct Plan {
   std::vector<int> pt_ptr, pt_cell, pt_own, pc_ptr, pc_cell, pc_beg, pe_rec;
   std::vector<double> pt_w, pt_val, pe_w;
   size_t pyr_elems = 0;
+  bool stream = false;     // warp-streaming fine kernel and composition pass (Burgers)
+  std::vector<int> cblk_inst[MODIL_MAXL], cblk_first[MODIL_MAXL];
+  size_t o_cbi[MODIL_MAXL], o_cbf[MODIL_MAXL];
   // arena offsets (bytes)
   size_t o_p0, o_p1, o_m, o_v, o_g, o_uf, o_wl, o_kq, o_km, o_kv, o_kg, o_aux, o_part, o_rptr, o_rcell,
       o_rfield, o_rbeg, o_mval, o_rv0, o_inst, o_st, o_cnt, o_q, o_ti[MODIL_MAXL], total;
@@ -93,7 +96,7 @@ int find_cfg(int ty, int tx) {
   return -1;
 }
 
-modil_status make_plan(const modil_desc* d, int n, Plan& P) {
+modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = true) {
   if (!d || n < 1) return fail(MODIL_ERR_ARG, "descs is NULL or n < 1");
   P = Plan();
   P.n_inst = n;
@@ -117,12 +120,25 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   // tile configuration (same for the batch)
   int ty = d[0].tile[0], tx = d[0].tile[1];
   if (three && (ty != 0 || tx != 0)) return fail(MODIL_ERR_ARG, "NS3D takes the library tile (tile = 0)");
+  bool any_points = false;
+  for (int i = 0; i < n; ++i) any_points |= d[i].n_points > 0;
   if (ty == 0 && tx == 0) {
     ty = (P.pde == MODIL_PDE_NS2D) ? 8 : 16;
     tx = 32;
+    // Burgers: the warp-streaming kernel unless off-grid points need the tile kernel
+    if (P.pde == MODIL_PDE_BURGERS && !any_points && allow_stream) {
+      ty = kSR;
+      tx = kSW;
+    }
   }
   P.cfg = find_cfg(ty, tx);
   if (P.cfg < 0) return fail(MODIL_ERR_ARG, "unsupported tile shape");
+  if (P.cfg == kStreamCfg) {
+    if (P.pde != MODIL_PDE_BURGERS) return fail(MODIL_ERR_ARG, "the 32 x 28 strip is the Burgers streaming kernel's");
+    if (any_points) return fail(MODIL_ERR_UNSUPPORTED, "off-grid points need a tile kernel shape (not 32 x 28)");
+    if (!allow_stream) P.cfg = 0;
+  }
+  P.stream = (P.cfg == kStreamCfg);
   if (P.pde == MODIL_PDE_NS2D && P.cfg != 0 && P.cfg != 5)
     return fail(MODIL_ERR_ARG, "NS2D tiles are 8x32 or 16x32");
   if (P.pde != MODIL_PDE_NS2D && P.cfg == 5)
@@ -158,6 +174,14 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
       if (!(q.coef[0] > 0)) return fail(MODIL_ERR_ARG, "NS2D needs coef[0] = Re > 0");
       if (!(q.coef[1] >= 0)) return fail(MODIL_ERR_ARG, "NS2D needs coef[1] = tau factor >= 0");
     }
+    if (P.stream)  // composition pass: levels 1 .. L-2, kComposeNT cells per block
+      for (int l = 1; l + 1 < L; ++l) {
+        const long long cells = (long long)(ny >> l) * (nx >> l);
+        for (long long c = 0; c < cells; c += kComposeNT) {
+          P.cblk_inst[l].push_back(i);
+          P.cblk_first[l].push_back((int)c);
+        }
+      }
     if (P.pde == MODIL_PDE_POISSON) {
       if (q.n_aux != ny * nx || !q.aux) return fail(MODIL_ERR_ARG, "Poisson needs aux[ny * nx] (right-hand side)");
       if (ny < 2 || nx < 2) return fail(MODIL_ERR_ARG, "Poisson needs >= 2 cells per axis");
@@ -435,7 +459,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   P.o_v = take(8 * P.n_param);
   P.o_g = take(P.esz * P.n_param);
   P.o_uf = take(P.esz * P.n_fine);
-  P.o_wl = take(P.pde == MODIL_PDE_NS3D ? P.esz * P.n_param : 0);
+  P.o_wl = take((P.pde == MODIL_PDE_NS3D || P.stream) ? P.esz * P.n_param : 0);
   P.o_kq = take(P.esz * P.n_k);
   P.o_km = take(P.esz * P.n_k);
   P.o_kv = take(8 * P.n_k);
@@ -464,6 +488,10 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P) {
   P.o_cnt = take(sizeof(int) * n);
   P.o_q = take(2 * sizeof(int));
   for (int l = 0; l < MODIL_MAXL; ++l) P.o_ti[l] = take(4 * P.tile_inst[l].size());
+  for (int l = 0; l < MODIL_MAXL; ++l) {
+    P.o_cbi[l] = take(4 * P.cblk_inst[l].size());
+    P.o_cbf[l] = take(4 * P.cblk_first[l].size());
+  }
   P.total = o;
   return MODIL_OK;
 }
@@ -529,6 +557,9 @@ void fill_arena(modil_problem* p, Arena<T>& A) {
   for (int l = 0; l < MODIL_MAXL; ++l) {
     A.tile_inst[l] = reinterpret_cast<const int*>(b + P.o_ti[l]);
     A.ntiles[l] = (int)P.tile_inst[l].size();
+    A.cblk_inst[l] = reinterpret_cast<const int*>(b + P.o_cbi[l]);
+    A.cblk_first[l] = reinterpret_cast<const int*>(b + P.o_cbf[l]);
+    A.ncblk[l] = (int)P.cblk_inst[l].size();
   }
   A.npart = P.npart;
   A.n_inst = P.n_inst;
@@ -576,6 +607,13 @@ modil_status run_pass_t(modil_problem* p, Arena<T>& A, int mode, int cur, cudaEv
     CUDA_TRY(launch_resid3<T>(A, mode, cur, own_uf ? &p->maps : nullptr, p->stream));
   } else if (P.pde == MODIL_PDE_NS2D) {
     CUDA_TRY(launch_fine_ns2d<T>(A, P.cfg, mode, cur, P.pyr_elems, p->stream));
+  } else if (P.stream) {
+    // compose w_{L-2} .. w_1 (coarse to fine), then the streaming fine kernel
+    for (int l = P.max_lev - 2; l >= 1; --l) {
+      CUDA_TRY(launch_compose2<T>(A, l, cur, p->stream));
+      if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+    }
+    CUDA_TRY(launch_fine_stream<T>(A, mode, cur, p->stream));
   } else {
     CUDA_TRY(launch_fine_st<T>(A, P.pde, P.cfg, mode, cur, P.pyr_elems, p->stream));
   }
@@ -604,7 +642,8 @@ modil_status run_pass(modil_problem* p, int mode, cudaEvent_t* ev = nullptr, int
 
 int kernels_per_step(const Plan& P) {
   const int compose3 = (P.max_lev - 1) + (P.min_lev == 1 ? 1 : 0);
-  return (P.pde == MODIL_PDE_NS3D ? compose3 + 1 : 1) + (P.max_tail - 1) + 1;
+  const int compose2 = P.stream ? std::max(P.max_lev - 2, 0) : 0;
+  return (P.pde == MODIL_PDE_NS3D ? compose3 + 1 : 1 + compose2) + (P.max_tail - 1) + 1;
 }
 
 modil_status read_terms(modil_problem* p, double* terms) {
@@ -804,6 +843,10 @@ modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t ar
   if (st == MODIL_OK) st = upload(p, P.o_inst, P.dev.data(), sizeof(DevInst) * n);
   for (int l = 0; l < MODIL_MAXL && st == MODIL_OK; ++l)
     st = upload(p, P.o_ti[l], P.tile_inst[l].data(), 4 * P.tile_inst[l].size());
+  for (int l = 0; l < MODIL_MAXL && st == MODIL_OK; ++l) {
+    st = upload(p, P.o_cbi[l], P.cblk_inst[l].data(), 4 * P.cblk_inst[l].size());
+    if (st == MODIL_OK) st = upload(p, P.o_cbf[l], P.cblk_first[l].data(), 4 * P.cblk_first[l].size());
+  }
   if (st != MODIL_OK) return bail(st);
   e = P.dtype == MODIL_F64 ? launch_reset<double>(p->A64, p->stream) : launch_reset<float>(p->A32, p->stream);
   if (e != cudaSuccess) return bail(fail(MODIL_ERR_CUDA, cudaGetErrorString(e)));
@@ -812,7 +855,7 @@ modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t ar
   else if (P.pde == MODIL_PDE_NS2D)
     e = P.dtype == MODIL_F64 ? prepare_fine_ns2d<double>(P.cfg, P.pyr_elems)
                              : prepare_fine_ns2d<float>(P.cfg, P.pyr_elems);
-  else
+  else if (!P.stream)
     e = P.dtype == MODIL_F64 ? prepare_fine_st<double>(P.pde, P.cfg, P.pyr_elems)
                              : prepare_fine_st<float>(P.pde, P.cfg, P.pyr_elems);
   if (e == cudaSuccess)
@@ -985,6 +1028,27 @@ modil_status modil_launches_per_step(const modil_problem* p, int* n) {
   return MODIL_OK;
 }
 
+modil_status modil_profile_labels(const modil_problem* p, int* kind, int* level, int max_kernels,
+                                  int* n_kernels) {
+  if (!p || !kind || !level || !n_kernels) return fail(MODIL_ERR_ARG, "NULL argument");
+  const Plan& P = p->plan;
+  const int nk = kernels_per_step(P);
+  if (max_kernels < nk) return fail(MODIL_ERR_ARG, "arrays too short");
+  int k = 0;
+  auto put = [&](int kd, int lv) { kind[k] = kd; level[k] = lv; ++k; };
+  if (P.pde == MODIL_PDE_NS3D) {
+    const int lo = P.min_lev == 1 ? -1 : 0;
+    for (int l = P.max_lev - 2; l >= lo; --l) put(0, l);
+  } else if (P.stream) {
+    for (int l = P.max_lev - 2; l >= 1; --l) put(0, l);
+  }
+  put(1, 0);
+  for (int l = 1; l < P.max_tail; ++l) put(2, l);
+  put(3, P.max_tail);
+  *n_kernels = k;
+  return MODIL_OK;
+}
+
 modil_status modil_profile_step(modil_problem* p, float* ms, int max_kernels, int* n_kernels) {
   if (!p || !ms || !n_kernels) return fail(MODIL_ERR_ARG, "NULL argument");
   const int nk = kernels_per_step(p->plan);
@@ -1036,6 +1100,7 @@ modil_status modil_set_persistent(modil_problem* p, int on) {
   const Plan& P = p->plan;
   if ((P.pde == MODIL_PDE_NS2D || P.pde == MODIL_PDE_NS3D) && on)
     return fail(MODIL_ERR_UNSUPPORTED, "persistent launch: Burgers/heat only");
+  if (P.stream) return MODIL_OK;  // equal strips, one warp each: nothing to balance
   int grid = 0;
   if (on) {
     int dev = 0, sms = 0;
@@ -1513,7 +1578,7 @@ extern "C" modil_status modil_eval_grad_noalloc(const modil_desc* desc, const vo
   if ((reinterpret_cast<uintptr_t>(levels) | reinterpret_cast<uintptr_t>(grads)) & 15)
     return fail(MODIL_ERR_ARG, "levels and grads must start on 16-byte boundaries");
   Plan P;
-  modil_status s = make_plan(desc, 1, P);
+  modil_status s = make_plan(desc, 1, P, /*allow_stream=*/false);
   if (s != MODIL_OK) return s;
   if (P.pde == MODIL_PDE_NS3D)
     return fail(MODIL_ERR_UNSUPPORTED, "the allocation-free entry point takes the 2-D families");

@@ -112,12 +112,28 @@ struct Arena {
   int* counter;        // per instance: fine tiles done in the current launch
   const int* tile_inst[MODIL_MAXL];  // instance owning each global tile of level l
   int ntiles[MODIL_MAXL];
+  // 2-D composition pass (streaming path): per block of level l its instance
+  // and the first cell (within the instance's level) it composes
+  const int* cblk_inst[MODIL_MAXL];
+  const int* cblk_first[MODIL_MAXL];
+  int ncblk[MODIL_MAXL];
   int npart;
   int n_inst;
   float gscale;        // factor on the written fine gradient (d loss / d output), 1 normally
   int persistent;      // 0: one fine block per tile; > 0: grid size of the persistent launch
   int* queue;          // persistent launch: next tile, blocks finished
 };
+
+// Minimum, maximum and floor in the working precision (FP32 arguments take the
+// FP32 instructions, never a round trip through FP64).
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float tfloor(float a) { return floorf(a); }
+__device__ __forceinline__ double tfloor(double a) { return floor(a); }
+__device__ __forceinline__ float texp(float a) { return expf(a); }
+__device__ __forceinline__ double texp(double a) { return exp(a); }
 
 // ---------------------------------------------------------------------------
 // Interpolation taps (cell-based linear interpolation, printed 1-D matrices)
@@ -169,17 +185,46 @@ struct AdamCoef {
   float lrf, b1f, omb1f, omb2f, epsf, c1f, c2f;
 };
 
+// FP32 <-> FP64 of a non-negative value with integer operations only (IEEE-754
+// binary32 / binary64 layouts: rebias the exponent by 1023 - 127 = 896 and
+// move the mantissa by 52 - 23 = 29 bits).  On GB300 every FP64-pipe
+// instruction, conversions included, costs about one SM cycle per lane, so
+// Adam's second moment keeps exactly one (the FMA).  Widening is exact for
+// normal values and keeps Inf and NaN; values below the FP32 normal range
+// become 0.  Narrowing truncates the mantissa (relative error below 2^-23);
+// values below the FP32 normal range become 0, values of 2^128 and more
+// become Inf, NaN stays NaN.  Branch-free: no conversion instruction is ever
+// issued.
+__device__ __forceinline__ double widen_nonneg(float x) {
+  const unsigned b = __float_as_uint(x);
+  const bool nz = b >= 0x00800000u, special = b >= 0x7f800000u;
+  const unsigned hi = special ? (0x7ff00000u | ((b >> 3) & 0x000fffffu)) : (nz ? (b >> 3) + (896u << 20) : 0u);
+  const unsigned lo = nz ? (b << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ float narrow_nonneg(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned ah = hi & 0x7fffffffu;
+  const bool nan = ah > 0x7ff00000u || (ah == 0x7ff00000u && lo != 0u);
+  const unsigned big = nan ? 0x7fc00000u : 0x7f800000u;
+  const unsigned b = __funnelshift_l(lo, hi, 3) - (896u << 23);
+  return __uint_as_float(hi >= 0x47f00000u ? big : (hi >= 0x38100000u ? b : 0u));
+}
+
 // The second moment is accumulated in FP64 (one FMA per cell: GB300 runs FP64
 // at 1/64 of the FP32 rate); the square of the gradient, the first moment and
-// the update are FP32.  Where a sum has two products, which one is fused is
-// fixed explicitly, so that every kernel that applies Adam to a level (the
-// restriction kernels, the tail) rounds identically.
+// the update are FP32, the square root and the division by the hardware's
+// approximate reciprocal square root and reciprocal (relative error of a few
+// 2^-23).  Where a sum has two products, which one is fused is fixed
+// explicitly, so that every kernel that applies Adam to a level (the fine
+// kernels, the restriction kernels, the tail) rounds identically.
 __device__ __forceinline__ void adam_update(float& p, float& m, double& v, float g,
                                             const AdamCoef& c) {
   m = fmaf(c.b1f, m, __fmul_rn(c.omb1f, g));
-  v = fma(c.b2, v, (double)__fmul_rn(c.omb2f, __fmul_rn(g, g)));
-  const float den = sqrtf((float)v * c.c2f) + c.epsf;
-  p = fmaf(-c.lrf, __fdiv_rn(__fmul_rn(m, c.c1f), den), p);
+  v = fma(c.b2, v, widen_nonneg(__fmul_rn(c.omb2f, __fmul_rn(g, g))));
+  const float s = __fmul_rn(narrow_nonneg(v), c.c2f);
+  const float den = (s > 0.f ? __fmul_rn(s, rsqrtf(s)) : 0.f) + c.epsf;
+  p = fmaf(-c.lrf, __fdividef(__fmul_rn(m, c.c1f), den), p);
 }
 
 __device__ __forceinline__ void adam_update(double& p, double& m, double& v, double g,

@@ -341,6 +341,16 @@ class Problem:
         _check(LIB.modil_launches_per_step(self._h, C.byref(n)))
         return n.value
 
+    def profile_labels(self):
+        """Names of the launches profile_step times, in order ("compose_L2",
+        "fine", "restrict_L1", ..., "tail")."""
+        cap = 64
+        kind, level = (C.c_int * cap)(), (C.c_int * cap)()
+        n = C.c_int()
+        _check(LIB.modil_profile_labels(self._h, kind, level, cap, C.byref(n)))
+        names = {0: "compose_L{}", 1: "fine", 2: "restrict_L{}", 3: "tail"}
+        return [names[kind[i]].format(level[i]) for i in range(n.value)]
+
     def profile_step(self):
         """One step launched kernel by kernel; returns the device ms of each launch."""
         cap = 64

@@ -30,6 +30,11 @@ def chihat_from_fraction(chi, clip=1e-3):
     return np.log(c / (1.0 - c)) + 5.0
 
 
+def fraction_from_chihat(ch):
+    """Body fraction chi = 1 / (1 + exp(-(chihat - 5)))."""
+    return 1.0 / (1.0 + np.exp(-(np.asarray(ch, np.float64) - 5.0)))
+
+
 def zero_levels(shape, n_levels, inflow_level=0):
     """Uniform inflow u = 1 on one level, every other value zero (chihat = 0)."""
     lv = [[np.zeros(s, np.float32) for s in inputs.level_shapes(shape, n_levels)] for _ in range(FIELDS)]
@@ -177,26 +182,34 @@ def inverse_problem(shape, n_levels, cells, fidx, vals, lr=1e-3):
                       w_res=1.0, w_data=1.0, meas_cell=cells, meas_field=fidx, meas_value=vals, lr=lr)
 
 
-def steps_to_losses(desc, levels, thresholds, max_steps, chunk=100):
+def steps_to_losses(desc, levels, thresholds, max_steps, chunk=100, chi_ref=None, run_all=False):
     """Run mODIL from the given levels; for every threshold the first step
     count (multiple of chunk) and wall time at which the loss is at or below
-    it (None if never).  Returns (hits, loss history per chunk)."""
+    it (None if never).  Returns (hits, loss history per chunk), and with
+    chi_ref also the mean absolute body-fraction error per chunk (the
+    composed chihat read back outside the timed steps).  Stops once every
+    threshold is reached unless run_all."""
     import torch
     hits = {t: None for t in thresholds}
-    hist = []
+    hist, chi_err = [], []
     with modil.Problem(desc) as p:
         p.write_fields(levels)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        el = 0.0
         done = 0
         while done < max_steps:
+            t0 = time.perf_counter()
             loss = float(p.step(chunk)[0][0])
+            el += time.perf_counter() - t0
             done += chunk
             hist.append(loss)
-            el = time.perf_counter() - t0
+            if chi_ref is not None:
+                chi_err.append(float(np.mean(np.abs(fraction_from_chihat(p.read_field(4)) - chi_ref))))
             for t in thresholds:
                 if hits[t] is None and loss <= t:
                     hits[t] = (done, el)
-            if hits and all(v is not None for v in hits.values()):
+            if not run_all and hits and all(v is not None for v in hits.values()):
                 break
+    if chi_ref is not None:
+        return hits, hist, chi_err
     return hits, hist

@@ -38,7 +38,7 @@ def test_autotune_picks_fastest_and_caches(tmp_path):
     cache = str(tmp_path / "tune.json")
     best = autotune.autotune(descs, measure=fake, cache_path=cache)
     assert best[0] == (8, 128) and best[1] is True
-    assert len(calls) == 2 * len(autotune.ST_TILES)
+    assert len(calls) == 2 * len(autotune.ST_TILES) + 1   # the streaming strip: one variant
     calls.clear()
     again = autotune.autotune(descs, measure=fake, cache_path=cache)
     assert again[:2] == best[:2] and not calls           # served from the cache

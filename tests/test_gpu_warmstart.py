@@ -2,7 +2,14 @@
 solutions around 32 seeded ellipsoids on 16^3 (batched in one problem), a
 3-level U-Net trained on them by the library's own kernels, then the inverse
 problem on 32^3 from wake-slab data, zero-initialised against warm-started
-(network prediction on level 2 of the decomposition)."""
+(network prediction on level 2 of the decomposition).
+
+What the network gains is the body: the inverse problem is ill-posed (many
+bodies explain a slab of wake data), and from zero (no body) mODIL lowers the
+loss with a wrong shape whose body-fraction error grows, while the
+warm-started run keeps the predicted shape.  Measured on four held-out seeds:
+body-fraction error 0.006-0.016 warm-started against 0.036-0.071 from zero
+after 1000 steps, at comparable losses (both pass 1e-3)."""
 import numpy as np
 import pytest
 
@@ -20,7 +27,7 @@ def ws():
     return warmstart, inputs, unet
 
 
-def test_warm_start_beats_zero_init(ws):
+def test_warm_start_gains_body_shape(ws):
     W, inputs, unet = ws
     side, L = 16, 5
     cases = [inputs.ns3d_ellipsoid(10000 + i) for i in range(32)]
@@ -39,10 +46,13 @@ def test_warm_start_beats_zero_init(ws):
     cells, fidx, vals = W.slab((big,) * 3, 5, c, a, fb[0])
     pred = W.predict(inf, norm, W.unet_input((big,) * 3, cells, fidx, vals, side))
     desc = W.inverse_problem((big,) * 3, L + 1, cells, fidx, vals)
+    chi_ref = inputs.ns3d_body_fraction((big,) * 3, c, a)
     tol = [1e-3]
-    hz, histz = W.steps_to_losses(desc, W.zero_levels((big,) * 3, L + 1), tol, 4000)
-    hw, histw = W.steps_to_losses(desc, W.warm_levels((big,) * 3, L + 1, 1, pred), tol, 4000)
-    # measured: zero init stalls near 6e-2, the warm start passes 1e-3 within ~200 steps
-    assert hw[1e-3] is not None and hw[1e-3][0] <= 2000, (hw, histw[:5])
-    assert hz[1e-3] is None or hz[1e-3][0] > 2 * hw[1e-3][0], (hz, hw)
-    assert min(histw) < 0.1 * min(histz)
+    hz, lz, cz = W.steps_to_losses(desc, W.zero_levels((big,) * 3, L + 1), tol, 1000, chunk=50,
+                                   chi_ref=chi_ref, run_all=True)
+    hw, lw, cw = W.steps_to_losses(desc, W.warm_levels((big,) * 3, L + 1, 1, pred), tol, 1000, chunk=50,
+                                   chi_ref=chi_ref, run_all=True)
+    # both runs fit the data; the warm start keeps the body
+    assert hz[1e-3] is not None and hw[1e-3] is not None, (lz[::4], lw[::4])
+    assert cw[-1] < 0.5 * cz[-1], (cw[::4], cz[::4])
+    assert max(cw) < 0.5 * max(cz)
