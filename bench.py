@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--workload", default="batched-burgers",
                     choices=["heat", "batched-burgers", "body", "warmstart", "unet", "burgers", "cavity",
-                             "poisson"],
+                             "poisson", "burgers-paper"],
                     help="batched-burgers (default): 512 uneven Burgers instances in one "
                          "persistent graph-captured launch per phase, against sequential single "
                          "runs; heat: conductivity inference on 512x512; "
@@ -704,6 +704,77 @@ def run_poisson(args):
     print(json.dumps(out), flush=True)
 
 
+def bilinear_at(u, pts, lengths=(1.0, 1.0), origin=(0.0, 0.0)):
+    """Values of a cell-centred 2-D field at (y, x) points, linear between the
+    two nearest centres along each axis (clamped at the outermost centres);
+    used to impose a reference field at off-grid points."""
+    out = np.zeros(len(pts))
+    coords = []
+    for a in range(2):
+        n = u.shape[a]
+        s = np.clip((pts[:, a] - origin[a]) / (lengths[a] / n) - 0.5, 0.0, n - 1.0)
+        i0 = np.minimum(np.floor(s).astype(int), max(n - 2, 0))
+        coords.append((i0, s - i0, np.minimum(i0 + 1, n - 1)))
+    (y0, ty, y1), (x0, tx, x1) = coords
+    out = ((1 - ty) * ((1 - tx) * u[y0, x0] + tx * u[y0, x1]) + ty * ((1 - tx) * u[y1, x0] + tx * u[y1, x1]))
+    return out
+
+
+def run_burgers_paper(args):
+    """The paper's Burgers reconstruction (Section 3.2): inviscid, [0, 1]^2,
+    64 x 64, the reference solution imposed at 84 points on the edges of a
+    rectangle; L-BFGS (history 50) with six levels (mODIL) against one level
+    (plain ODIL), with and without U[0, 0.05] noise.  The reference is the
+    discrete problem solved by the library itself: the initial row imposed at
+    every cell, the loss minimised by L-BFGS until it vanishes."""
+    import torch
+
+    from paper_2303_04679_gb300 import inputs, modil
+    torch.cuda.set_device(0)
+    P = inputs.BURGERS_PAPER
+    nt, nx = P["shape"]
+    x = (np.arange(nx) + 0.5) / nx
+    ic = inputs.burgers_paper_ic(x)
+    fwd = modil.Desc("burgers", P["shape"], P["n_levels"], "f64", coef=(0.0,), domain=P["domain"],
+                     meas_cell=np.arange(nx, dtype=np.int32), meas_value=ic)
+    with modil.Problem(fwd) as p, modil.LBFGS(p, history=50) as opt:
+        fh = opt.run(3000)
+        u_ref = p.read_field()
+    pts = inputs.rectangle_points()
+    vals = bilinear_at(u_ref, pts)
+    T, X = np.meshgrid((np.arange(nt) + 0.5) / nt, x, indexing="ij")
+    (t0, t1), (x0, x1) = P["rect"]
+    inside = (T >= t0) & (T <= t1) & (X >= x0) & (X <= x1)
+    out = {"metric": "Burgers reconstruction: L-BFGS iterations and wall time to loss 1e-4, RMS error",
+           "workload": "Section 3.2: inviscid Burgers, [0,1]^2, 64x64, 84 points on the edges of the "
+                       "square [1/4,3/4]^2, FP64, L-BFGS history 50",
+           "reference": {"loss": float(fh[-1]), "iterations": len(fh) - 1,
+                         "max": float(u_ref.max()), "min": float(u_ref.min())},
+           "runs": []}
+    for noise in (0.0, 0.05):
+        v = vals if noise == 0 else inputs.uniform_noise(vals, noise, seed=1)
+        for L in (P["n_levels"], 1):
+            d = modil.Desc("burgers", P["shape"], L, "f64", coef=(0.0,), domain=P["domain"], points=pts,
+                           point_value=v)
+            iters = min(args.steps, 2000)
+            with modil.Problem(d) as p, modil.LBFGS(p, history=50) as opt:
+                torch.cuda.synchronize()
+                t0_ = time.perf_counter()
+                hist = opt.run(iters)
+                el = time.perf_counter() - t0_
+                u = p.read_field()
+            reach = next((k for k, val in enumerate(hist) if val <= 1e-4), None)
+            dd = u - u_ref
+            out["runs"].append({
+                "levels": L, "noise": noise, "iterations": len(hist) - 1, "seconds": el,
+                "ms_per_iteration": 1e3 * el / max(len(hist) - 1, 1), "final_loss": float(hist[-1]),
+                "iterations_to_1e-4": reach,
+                "rms_error": float(np.sqrt(np.mean(dd ** 2))),
+                "rms_error_inside_rectangle": float(np.sqrt(np.mean(dd[inside] ** 2))),
+                "loss_at": {str(k): float(hist[k]) for k in (10, 40, 100, 400, 1000, 2000) if k < len(hist)}})
+    print(json.dumps(out), flush=True)
+
+
 def run_small(args):
     """The two small configurations: Burgers reconstruction on 64 x 64 in FP64
     (4 levels, 200 measured cells) and the lid-driven cavity on 256^2 in FP32
@@ -1012,6 +1083,9 @@ def main():
         return
     if args.workload == "poisson":
         run_poisson(args)
+        return
+    if args.workload == "burgers-paper":
+        run_burgers_paper(args)
         return
     w = inputs.heat_workload()
     args.tile = args.tile or "32x32"

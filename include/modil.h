@@ -117,8 +117,9 @@ typedef struct {
   const double* knodes;      /* initial q (copied)                              */
   double adam_lr, adam_beta1, adam_beta2, adam_eps;
   int n_points;               /* off-grid measurements (Burgers, heat, Poisson):  */
-  const double* point_coord;  /* n_points x (y, x) physical coordinates: Burgers
-                                 t in [0,1], x in [-1,1]; heat, Poisson [0,1]^2;
+  const double* point_coord;  /* n_points x (y, x) physical coordinates in the
+                                 problem's domain (by default Burgers t in [0,1],
+                                 x in [-1,1]; heat, Poisson [0,1]^2; see domain_lo);
                                  the field there is interpolated linearly along
                                  each axis between the two nearest cell centres
                                  (clamped between a wall and the outermost
@@ -126,8 +127,17 @@ typedef struct {
                                  w_data / (n_meas + n_points)                   */
   const double* point_value;
   int tile[2];               /* fine tile (rows, cols); 0 = library default.
-                                Burgers/heat: 16x32 16x64 8x64 32x32 8x128;
+                                Burgers/heat/Poisson: 16x32 16x64 8x64 32x32 8x128;
+                                Burgers without off-grid points also 32x28 (the
+                                warp-streaming kernel, its default);
                                 NS2D: 8x32 16x32.  NS3D: 0 only (4x8x16 cells)  */
+  double domain_lo[3], domain_hi[3];
+                             /* physical extent per axis, slowest first (2-D: entries
+                                0 and 1), for Burgers, heat and Poisson: spacing
+                                (hi - lo) / cells, the origin of off-grid points.
+                                All zero: the family's own domain (Burgers t in
+                                [0, 1], x in [-1, 1]; heat and Poisson [0, 1]^2).
+                                The cavity and the body take only their own.    */
 } modil_desc;
 
 /* Device bytes needed for a batch of n problems described by descs[0..n-1]. */

@@ -45,7 +45,7 @@ __all__ = [
     "loss_grad_fine", "loss_grad_levels", "adam_step", "OracleState",
     "oracle_step", "burgers_explicit_solve", "heat_implicit_solve",
     "eo_flux", "ns2d_residuals", "ns2d_fields_residual_jacobian_grad", "ns3d_residuals",
-    "ns3d_chi", "ns3d_residual_jacobian_grad", "ns3d_fine_grad_colours",
+    "ns3d_chi", "ns3d_residual_jacobian_grad", "ns3d_fine_grad_colours", "burgers_implicit_solve",
 ]
 
 
@@ -200,6 +200,9 @@ class Problem:
     # and values, sampled d-linearly (oracle/offgrid_oracle.py)
     meas_points: np.ndarray = None
     point_value: np.ndarray = None
+    # physical extent ((lo, hi) per axis, same order as shape) of a 2-D
+    # Burgers, heat or Poisson problem; None: the family's own domain
+    domain_bounds: tuple = None
 
     @property
     def n_fields(self):
@@ -207,6 +210,9 @@ class Problem:
 
     def domain(self):
         """Lower corner and length per axis (same order as shape)."""
+        if self.domain_bounds is not None:
+            return (tuple(float(lo) for lo, _ in self.domain_bounds),
+                    tuple(float(hi) - float(lo) for lo, hi in self.domain_bounds))
         if self.pde == "burgers":       # t in [0,1], x in [-1,1]
             return (0.0, -1.0), (1.0, 2.0)
         if self.pde in ("heat", "poisson", "ns2d"):
@@ -215,6 +221,8 @@ class Problem:
 
     def spacing(self):
         """Grid spacings per axis (same order as shape)."""
+        if self.domain_bounds is not None:
+            return tuple(float(hi - lo) / n for (lo, hi), n in zip(self.domain_bounds, self.shape))
         if self.pde == "burgers":       # t in [0,1], x in [-1,1]
             return (1.0 / self.shape[0], 2.0 / self.shape[1])
         if self.pde == "heat":          # t in [0,1], x in [0,1]
@@ -236,9 +244,13 @@ class Problem:
 # all spatial terms at row n.  Row 0 has no residual (only data constrain it).
 # F is a first-order upwind flux for f(u) = u^2/2: the Engquist-Osher flux
 # F(a, b) = max(a, 0)^2/2 + min(b, 0)^2/2, evaluated at interior faces from
-# the two adjacent cells.  The walls x = -1, 1 carry zero Dirichlet data:
-# the convective flux there is f(0) = 0 and the viscous term uses the odd
-# ghost u_{-1} = -u_0, u_{N} = -u_{N-1} (linear profile through zero at the wall).
+# the two adjacent cells.  The walls carry zero Dirichlet data (Section 3.2):
+# the upwind flux through a wall is the same flux between the wall value 0
+# and the adjacent cell, F(0, u_0) = min(u_0, 0)^2/2 on the left and
+# F(u_{N-1}, 0) = max(u_{N-1}, 0)^2/2 on the right, so a state flowing out of
+# the domain leaves it and nothing enters from a wall; the viscous term uses
+# the odd ghost u_{-1} = -u_0, u_{N} = -u_{N-1} (linear profile through zero
+# at the wall).
 
 def eo_flux(a, b):
     """Engquist-Osher flux for f(u) = u^2/2 and its two partial derivatives."""
@@ -258,6 +270,8 @@ def burgers_residual(u, nu, dt, dx):
     nx = u.shape[1]
     F = np.zeros((un.shape[0], nx + 1))
     F[:, 1:nx], _, _ = eo_flux(un[:, :-1], un[:, 1:])
+    F[:, 0], _, _ = eo_flux(0.0 * un[:, 0], un[:, 0])      # left wall: value 0
+    F[:, nx], _, _ = eo_flux(un[:, -1], 0.0 * un[:, -1])   # right wall
     ug = _ghost_odd(un)
     lap = (ug[:, 2:] - 2.0 * un + ug[:, :-2]) / dx**2
     return (un - uo) / dt + (F[:, 1:] - F[:, :-1]) / dx - nu * lap
@@ -276,6 +290,11 @@ def _burgers_adjoint(u, lam, nu, dt, dx):
     _, dFa, dFb = eo_flux(un[:, :-1], un[:, 1:])
     g[1:, :-1] += lamF * dFa
     g[1:, 1:] += lamF * dFb
+    # wall faces: r_0 has -F(0, u_0)/dx, r_{N-1} has +F(u_{N-1}, 0)/dx
+    _, _, dW = eo_flux(0.0 * un[:, 0], un[:, 0])
+    _, dE, _ = eo_flux(un[:, -1], 0.0 * un[:, -1])
+    g[1:, 0] -= lam[:, 0] * dW / dx
+    g[1:, -1] += lam[:, -1] * dE / dx
     # viscous term, through the odd ghosts
     lamD = -nu * lam / dx**2
     gug = np.zeros((un.shape[0], nx + 2))
@@ -919,8 +938,8 @@ def oracle_step(p, st, lr, b1=0.9, b2=0.999, eps=1e-8):
 def burgers_explicit_solve(u0, nu, dx, t_out, cfl=0.4, bc="dirichlet"):
     """March u_t + (u^2/2)_x = nu u_xx with forward Euler finite volumes.
 
-    Same flux as the residual (Engquist-Osher, zero convective flux through
-    the walls, odd viscous ghosts) or a periodic variant.  Returns the cell
+    Same flux as the residual (Engquist-Osher, the upwind flux against the
+    zero wall value at the walls, odd viscous ghosts) or a periodic variant.  Returns the cell
     averages at each time in ``t_out`` (linear interpolation between steps).
     """
     u = np.array(u0, dtype=np.float64)
@@ -946,6 +965,8 @@ def burgers_explicit_solve(u0, nu, dx, t_out, cfl=0.4, bc="dirichlet"):
         else:
             F = np.zeros(len(u) + 1)
             F[1:-1], _, _ = eo_flux(u[:-1], u[1:])
+            F[0], _, _ = eo_flux(0.0, u[0])        # zero Dirichlet walls, upwind
+            F[-1], _, _ = eo_flux(u[-1], 0.0)
             Fe, Fw = F[1:], F[:-1]
             ug = np.concatenate([[-u[0]], u, [-u[-1]]])
             lap = (ug[2:] - 2.0 * u + ug[:-2]) / dx**2
@@ -953,6 +974,54 @@ def burgers_explicit_solve(u0, nu, dx, t_out, cfl=0.4, bc="dirichlet"):
         u = u - dt * (Fe - Fw) / dx + dt * nu * lap
         t += dt
     return np.array(out)
+
+
+def burgers_implicit_solve(u0, nt, dt, dx, nu=0.0, tol=1e-14, max_iter=100):
+    """The discrete Burgers problem of the residual above, solved row by row:
+    row 0 is the given initial condition, and each later row is the root of
+    its residual given the previous row (backward Euler, Engquist-Osher flux,
+    zero convective flux through the walls, odd viscous ghosts), found by
+    Newton's method with the residual's tridiagonal Jacobian.  This is how the
+    reference of the reconstruction problem of Section 3.2 is made ("solve the
+    discrete problem with zero Dirichlet boundary conditions and the initial
+    condition").  Returns the (nt, nx) field."""
+    from scipy.linalg import solve_banded
+    u0 = np.asarray(u0, dtype=np.float64)
+    nx = len(u0)
+    out = np.zeros((nt, nx))
+    out[0] = u0
+    for n in range(1, nt):
+        prev = out[n - 1]
+        w = prev.copy()
+        for _ in range(max_iter):
+            r = burgers_residual(np.stack([prev, w]), nu, dt, dx)[0]
+            # Jacobian: dr_i/du_{i-1}, dr_i/du_i, dr_i/du_{i+1}
+            _, dFa, dFb = eo_flux(w[:-1], w[1:])        # face i+1/2 of cells i, i+1
+            lo = np.zeros(nx)
+            di = np.full(nx, 1.0 / dt)
+            up = np.zeros(nx)
+            di[:-1] += dFa / dx                          # east face of cell i
+            up[:-1] += dFb / dx
+            di[1:] -= dFb / dx                           # west face of cell i+1
+            lo[1:] -= dFa / dx
+            di[0] -= min(w[0], 0.0) / dx                  # wall faces
+            di[-1] += max(w[-1], 0.0) / dx
+            c = nu / dx**2
+            di += 2.0 * c
+            di[0] += c                                   # odd ghosts
+            di[-1] += c
+            lo[1:] -= c
+            up[:-1] -= c
+            ab = np.zeros((3, nx))
+            ab[0, 1:] = up[:-1]
+            ab[1] = di
+            ab[2, :-1] = lo[1:]
+            dw = solve_banded((1, 1), ab, -r)
+            w = w + dw
+            if np.max(np.abs(dw)) < tol * max(1.0, np.max(np.abs(w))):
+                break
+        out[n] = w
+    return out
 
 
 def heat_implicit_solve(u_init, nt, dt, dx, kfun, tol=1e-13, max_iter=200):

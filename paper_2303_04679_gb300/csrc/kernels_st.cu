@@ -28,8 +28,8 @@
 //   Burgers, rows n >= 1:
 //     r = (u^n_i - u^{n-1}_i)/dt + (F_{i+1/2} - F_{i-1/2})/dx
 //         - nu (u^n_{i+1} - 2u^n_i + u^n_{i-1})/dx^2,
-//     F = Engquist-Osher upwind flux of u^2/2, zero convective flux through
-//     the walls, odd ghosts for the viscous term;
+//     F = Engquist-Osher upwind flux of u^2/2, through a wall the same flux
+//     against the zero wall value, odd ghosts for the viscous term;
 //   heat, rows n >= 1 (row 0: (u^0_i - u_init_i)/dt):
 //     r = (u^n_i - u^{n-1}_i)/dt
 //         - [k_{i+1/2}(u^n_{i+1}-u^n_i) - k_{i-1/2}(u^n_i-u^n_{i-1})]/dx^2,
@@ -539,9 +539,10 @@ k_fine_st(const __grid_constant__ Arena<T> A, int mode, int cur) {
           const T uw = hw ? uq[-1] : -uc;
           const T ue = he ? uq[1] : -uc;
           if (PDE == PDE_BURGERS) {
-            T dFEc = T(0), dFEe = T(0), dFWw = T(0), dFWc = T(0), FE = T(0), FW = T(0);
-            if (he) FE = eo_flux(uc, ue, dFEc, dFEe);
-            if (hw) FW = eo_flux(uw, uc, dFWw, dFWc);
+            // the flux through a wall is the upwind flux against the zero wall value
+            T dFEc, dFEe, dFWw, dFWc;
+            const T FE = eo_flux(uc, he ? ue : T(0), dFEc, dFEe);
+            const T FW = eo_flux(hw ? uw : T(0), uc, dFWw, dFWc);
             const T lap = (ue - T(2) * uc + uw) * cf.idx2;
             r = (uc - uo) * cf.idt + (FE - FW) * cf.idx1 - cf.nu * lap;
             const T cdiag = T(-2) - (hw ? T(0) : T(1)) - (he ? T(0) : T(1));

@@ -29,8 +29,9 @@
 // The stencil (rows n >= 1, the implicit step of the reading of Section 3.2):
 //   r = (u^n_i - u^{n-1}_i)/dt + (F_{i+1/2} - F_{i-1/2})/dx
 //       - nu (u^n_{i+1} - 2u^n_i + u^n_{i-1})/dx^2,
-//   F = Engquist-Osher upwind flux of u^2/2, zero convective flux through the
-//   walls, odd ghosts (u_{-1} = -u_0) for the viscous term.
+//   F = Engquist-Osher upwind flux of u^2/2; through a wall the same flux
+//   against the zero wall value (Dirichlet data); odd ghosts (u_{-1} = -u_0)
+//   for the viscous term.
 #include "launch.h"
 #include "modil_dev.cuh"
 
@@ -252,9 +253,10 @@ __global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stre
     if (row_ok && res_x && n >= 1 && n >= y0) {
       const T uw = hw ? uW : -u;
       const T ue = he ? uE : -u;
-      T dFEc = T(0), dFEe = T(0), dFWw = T(0), dFWc = T(0), FE = T(0), FW = T(0);
-      if (he) FE = eo_flux_s(u, ue, dFEc, dFEe);
-      if (hw) FW = eo_flux_s(uw, u, dFWw, dFWc);
+      // the flux through a wall is the upwind flux against the zero wall value
+      T dFEc, dFEe, dFWw, dFWc;
+      const T FE = eo_flux_s(u, he ? ue : T(0), dFEc, dFEe);
+      const T FW = eo_flux_s(hw ? uw : T(0), u, dFWw, dFWc);
       const T lap = (ue - T(2) * u + uw) * cf.idx2;
       const T r = (u - uo) * cf.idt + (FE - FW) * cf.idx1 - cf.nu * lap;
       const T lam = cf.lam_scale * r;

@@ -169,6 +169,18 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
         return fail(MODIL_ERR_ARG, "NS3D needs D, lambda and the Rhie-Chow factor >= 0");
     }
     if (P.pde == MODIL_PDE_BURGERS && ny < 2) return fail(MODIL_ERR_ARG, "Burgers needs >= 2 rows");
+    if (P.pde == MODIL_PDE_BURGERS && !(q.coef[0] >= 0)) return fail(MODIL_ERR_ARG, "Burgers needs coef[0] = nu >= 0");
+    // physical domain: all zero = the family's own
+    bool dom = false;
+    for (int a = 0; a < 3; ++a) dom |= (q.domain_lo[a] != 0.0 || q.domain_hi[a] != 0.0);
+    if (dom) {
+      if (P.pde == MODIL_PDE_NS2D || three)
+        return fail(MODIL_ERR_UNSUPPORTED, "the cavity and the body take only their own domain");
+      if (!(q.domain_hi[0] > q.domain_lo[0]) || !(q.domain_hi[1] > q.domain_lo[1]) ||
+          !std::isfinite(q.domain_lo[0]) || !std::isfinite(q.domain_hi[0]) ||
+          !std::isfinite(q.domain_lo[1]) || !std::isfinite(q.domain_hi[1]))
+        return fail(MODIL_ERR_ARG, "domain_hi must exceed domain_lo (finite) on both axes");
+    }
     if (P.pde == MODIL_PDE_NS2D) {
       if (ny != nx) return fail(MODIL_ERR_ARG, "the cavity grid must be square");
       if (!(q.coef[0] > 0)) return fail(MODIL_ERR_ARG, "NS2D needs coef[0] = Re > 0");
@@ -270,7 +282,9 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
     koff += ip.nk;
     D.aux_off = aoff;
     aoff += (P.pde == MODIL_PDE_HEAT) ? nx : (P.pde == MODIL_PDE_POISSON ? (long long)ny * nx : 0);
-    if (P.pde == MODIL_PDE_BURGERS) {
+    if (dom) {
+      D.h[0] = 1.0; D.h[1] = (q.domain_hi[0] - q.domain_lo[0]) / ny; D.h[2] = (q.domain_hi[1] - q.domain_lo[1]) / nx;
+    } else if (P.pde == MODIL_PDE_BURGERS) {
       D.h[0] = 1.0; D.h[1] = 1.0 / ny; D.h[2] = 2.0 / nx;
     } else if (three) {
       D.h[0] = 1.0 / nz; D.h[1] = 1.0 / ny; D.h[2] = 2.0 / nx;
@@ -359,8 +373,11 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
       if (q.n_points <= 0) continue;
       const InstPlan& ip = P.inst[i];
       const int ny = ip.n[0][1], nx = ip.n[0][2];
-      const double oy = 0.0, ly = 1.0;
-      const double ox = (P.pde == MODIL_PDE_BURGERS) ? -1.0 : 0.0, lx = (P.pde == MODIL_PDE_BURGERS) ? 2.0 : 1.0;
+      bool dom = false;
+      for (int a = 0; a < 3; ++a) dom |= (q.domain_lo[a] != 0.0 || q.domain_hi[a] != 0.0);
+      const double oy = dom ? q.domain_lo[0] : 0.0, ly = dom ? q.domain_hi[0] - q.domain_lo[0] : 1.0;
+      const double ox = dom ? q.domain_lo[1] : ((P.pde == MODIL_PDE_BURGERS) ? -1.0 : 0.0);
+      const double lx = dom ? q.domain_hi[1] - q.domain_lo[1] : ((P.pde == MODIL_PDE_BURGERS) ? 2.0 : 1.0);
       // position along one axis in units of cell centres, clamped to the
       // outermost centres; lower centre i0 and fraction t towards i0 + 1
       auto axis = [](double pos, double o, double len, int nn, int& i0, double& t) {

@@ -204,6 +204,33 @@ def burgers_workload(nt=64, nx=64, n_levels=4, seed=0, n_meas=200, nu=0.01):
                 amps=burgers_ic_amplitudes(seed), w_res=1.0, w_data=1.0, lr=5e-3)
 
 
+# The paper's own Burgers reconstruction (Section 3.2): inviscid, (x, t) in
+# [0, 1]^2 on 64 x 64 cells, six levels, the reference solution imposed at 84
+# points on the edges of a rectangle.  The rectangle is not given in the
+# paper; the reading here is the square [1/4, 3/4]^2 (21 points per edge,
+# each corner counted once).
+BURGERS_PAPER = dict(shape=(64, 64), n_levels=6, nu=0.0, domain=((0.0, 1.0), (0.0, 1.0)),
+                     rect=((0.25, 0.75), (0.25, 0.75)), per_edge=21)
+
+
+def burgers_paper_ic(x):
+    """Initial condition u(x, 0) = (1 - cos 6 pi x) / 2 of Section 3.2."""
+    return 0.5 * (1.0 - np.cos(6.0 * math.pi * np.asarray(x, dtype=np.float64)))
+
+
+def rectangle_points(rect=BURGERS_PAPER["rect"], per_edge=BURGERS_PAPER["per_edge"]):
+    """(t, x) points on the edges of the rectangle rect = ((t0, t1), (x0, x1)):
+    per_edge equally spaced points on each edge, walked counter-clockwise from
+    (t0, x0) so that every corner appears once (4 x per_edge points)."""
+    (t0, t1), (x0, x1) = rect
+    s = np.arange(per_edge) / per_edge
+    edges = [np.stack([np.full(per_edge, t0), x0 + (x1 - x0) * s], axis=1),       # t = t0
+             np.stack([t0 + (t1 - t0) * s, np.full(per_edge, x1)], axis=1),       # x = x1
+             np.stack([np.full(per_edge, t1), x1 - (x1 - x0) * s], axis=1),       # t = t1
+             np.stack([t1 - (t1 - t0) * s, np.full(per_edge, x0)], axis=1)]       # x = x0
+    return np.concatenate(edges, axis=0)
+
+
 def burgers_batch(n=512, base_seed=0, meas_frac=0.005):
     """The batched Burgers workload: n instances of uneven size.
 

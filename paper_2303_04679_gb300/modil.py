@@ -51,6 +51,7 @@ class modil_desc(C.Structure):
         ("n_points", C.c_int), ("point_coord", C.POINTER(C.c_double)),
         ("point_value", C.POINTER(C.c_double)),
         ("tile", C.c_int * 2),
+        ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3),
     ]
 
 
@@ -118,12 +119,12 @@ class Desc:
     def __init__(self, pde, shape, n_levels, dtype="f32", coef=(), w_res=1.0, w_data=1.0,
                  w_reg=0.0, meas_cell=None, meas_value=None, meas_field=None, aux=None,
                  knodes=None, lr=5e-3, beta1=0.9, beta2=0.999, eps=1e-8, tile=(0, 0),
-                 points=None, point_value=None):
+                 points=None, point_value=None, domain=None):
         self.kwargs = dict(pde=pde, shape=shape, n_levels=n_levels, dtype=dtype, coef=coef,
                            w_res=w_res, w_data=w_data, w_reg=w_reg, meas_cell=meas_cell,
                            meas_value=meas_value, meas_field=meas_field, aux=aux, knodes=knodes,
                            lr=lr, beta1=beta1, beta2=beta2, eps=eps, tile=tile, points=points,
-                           point_value=point_value)
+                           point_value=point_value, domain=domain)
         self.pde = {"burgers": PDE_BURGERS, "heat": PDE_HEAT, "ns2d": PDE_NS2D,
                     "ns3d": PDE_NS3D, "poisson": PDE_POISSON}.get(pde, pde)
         self.dtype = {"f32": F32, "f64": F64}.get(dtype, dtype)
@@ -166,6 +167,9 @@ class Desc:
         d.point_coord = _dptr(self._pts, C.c_double)
         d.point_value = _dptr(self._pval, C.c_double)
         d.tile[0], d.tile[1] = int(tile[0]), int(tile[1])
+        if domain is not None:  # ((lo, hi) per axis, slowest first)
+            for a, (lo, hi) in enumerate(domain):
+                d.domain_lo[a], d.domain_hi[a] = float(lo), float(hi)
         self.c = d
 
     @property

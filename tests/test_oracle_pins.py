@@ -151,24 +151,35 @@ def test_burgers_residual_consistent_with_pde_first_order():
 
 
 def test_burgers_constant_field_closed_form():
-    """Constant c: interior residual 0; wall cells see the zero wall flux and ghost."""
-    n, c, nu = 16, 0.8, 0.03
+    """Constant c: interior residual 0.  The walls carry the value 0: with
+    c > 0 the flow enters nothing at the left wall (upwind flux F(0, c) = 0)
+    and leaves through the right one (F(c, 0) = c^2/2, the interior flux), so
+    only the left cell sees a flux difference, c^2/(2 dx); with c < 0 the
+    mirror image.  The odd viscous ghost adds 2 nu c / dx^2 at both walls."""
+    n, nu = 16, 0.03
     dt, dx = 1.0 / n, 2.0 / n
-    r = o.burgers_residual(np.full((n, n), c), nu, dt, dx)
-    np.testing.assert_allclose(r[:, 1:-1], 0.0, atol=1e-12)
-    np.testing.assert_allclose(r[:, 0], c * c / (2 * dx) + 2 * nu * c / dx**2, rtol=1e-13)
-    np.testing.assert_allclose(r[:, -1], -c * c / (2 * dx) + 2 * nu * c / dx**2, rtol=1e-13)
+    for c in (0.8, -0.6):
+        r = o.burgers_residual(np.full((n, n), c), nu, dt, dx)
+        np.testing.assert_allclose(r[:, 1:-1], 0.0, atol=1e-12)
+        inflow = c * c / (2 * dx)
+        left = (inflow if c > 0 else 0.0) + 2 * nu * c / dx**2
+        right = (-inflow if c < 0 else 0.0) + 2 * nu * c / dx**2
+        np.testing.assert_allclose(r[:, 0], left, rtol=1e-13)
+        np.testing.assert_allclose(r[:, -1], right, rtol=1e-13)
 
 
 def test_burgers_mass_balance_of_residual():
-    """sum_i r^n_i dx = (M^n - M^{n-1})/dt + 2 nu (u_0 + u_{N-1})/dx (telescoping)."""
+    """sum_i r^n_i dx = (M^n - M^{n-1})/dt + (outflow through the walls)
+    + 2 nu (u_0 + u_{N-1})/dx (telescoping); the wall fluxes are the upwind
+    fluxes against the wall value 0: max(u_{N-1}, 0)^2/2 and min(u_0, 0)^2/2."""
     rng = np.random.default_rng(5)
     n, nu = 24, 0.02
     dt, dx = 1.0 / n, 2.0 / n
     u = rng.normal(size=(n, n))
     r = o.burgers_residual(u, nu, dt, dx)
     M = u.sum(axis=1) * dx
-    rhs = (M[1:] - M[:-1]) / dt + 2 * nu * (u[1:, 0] + u[1:, -1]) / dx
+    out = 0.5 * np.maximum(u[1:, -1], 0.0) ** 2 - 0.5 * np.minimum(u[1:, 0], 0.0) ** 2
+    rhs = (M[1:] - M[:-1]) / dt + out + 2 * nu * (u[1:, 0] + u[1:, -1]) / dx
     np.testing.assert_allclose(r.sum(axis=1) * dx, rhs, rtol=1e-11, atol=1e-11)
 
 
@@ -199,6 +210,42 @@ def test_burgers_explicit_solver_invariants():
     dirich = o.burgers_explicit_solve(u0, 0.01, dx, ts)
     E = np.sum(dirich**2, axis=1)
     assert np.all(np.diff(E) <= 1e-12)
+
+
+def test_burgers_implicit_solve_reference_of_the_paper_problem():
+    """The discrete problem of Section 3.2 (inviscid, [0,1]^2, 64 x 64, zero
+    Dirichlet walls, u(x, 0) = (1 - cos 6 pi x)/2) solved row by row: every
+    row's residual vanishes; the scheme is conservative, so each row's mass
+    changes only by the upwind outflow through the walls,
+    (M^n - M^{n-1})/dt = -max(u^n_{N-1}, 0)^2/2 + min(u^n_0, 0)^2/2; the
+    solution keeps within the initial range [0, 1] (monotone upwind scheme)
+    and its energy never grows."""
+    n = 64
+    dt = dx = 1.0 / n
+    x = (np.arange(n) + 0.5) * dx
+    u0 = inputs.burgers_paper_ic(x)
+    assert u0.min() >= 0.0 and u0.max() <= 1.0
+    u = o.burgers_implicit_solve(u0, n, dt, dx, nu=0.0)
+    np.testing.assert_array_equal(u[0], u0)
+    assert np.max(np.abs(o.burgers_residual(u, 0.0, dt, dx))) < 1e-11
+    M = u.sum(axis=1) * dx
+    out = 0.5 * np.maximum(u[1:, -1], 0.0) ** 2 - 0.5 * np.minimum(u[1:, 0], 0.0) ** 2
+    np.testing.assert_allclose((M[1:] - M[:-1]) / dt, -out, rtol=0, atol=1e-11)
+    assert u.min() >= -1e-12 and u.max() <= 1.0 + 1e-12
+    E = np.sum(u**2, axis=1)
+    assert np.all(np.diff(E) <= 1e-12)
+
+
+def test_burgers_paper_points_on_rectangle_edges():
+    """84 points on the edges of the rectangle, 21 per edge, corners once."""
+    p = inputs.rectangle_points()
+    assert p.shape == (84, 2)
+    assert len({(round(a, 12), round(b, 12)) for a, b in p}) == 84
+    (t0, t1), (x0, x1) = inputs.BURGERS_PAPER["rect"]
+    on_t = np.isclose(p[:, 0], t0) | np.isclose(p[:, 0], t1)
+    on_x = np.isclose(p[:, 1], x0) | np.isclose(p[:, 1], x1)
+    assert np.all(on_t | on_x)
+    assert np.all((p[:, 0] >= t0) & (p[:, 0] <= t1) & (p[:, 1] >= x0) & (p[:, 1] <= x1))
 
 
 # --------------------------------------------------------------------------
