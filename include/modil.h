@@ -116,12 +116,15 @@ typedef struct {
   int n_knodes;              /* HEAT: conductivity nodes q_0..q_{K}, K+1 <= 64  */
   const double* knodes;      /* initial q (copied)                              */
   double adam_lr, adam_beta1, adam_beta2, adam_eps;
-  int n_points;               /* off-grid measurements (Burgers, heat, Poisson):  */
-  const double* point_coord;  /* n_points x (y, x) physical coordinates in the
-                                 problem's domain (by default Burgers t in [0,1],
-                                 x in [-1,1]; heat, Poisson [0,1]^2; see domain_lo);
+  int n_points;               /* off-grid measurements (every family):            */
+  const double* point_coord;  /* n_points x ndim physical coordinates, slowest
+                                 axis first, in the problem's domain (by default
+                                 Burgers t in [0,1], x in [-1,1]; heat, Poisson,
+                                 cavity [0,1]^2; the body (z, y, x) in [0,1] x
+                                 [0,1] x [0,2]; see domain_lo);
                                  the field there is interpolated linearly along
-                                 each axis between the two nearest cell centres
+                                 each axis (bilinear, trilinear) between the
+                                 two nearest cell centres
                                  (clamped between a wall and the outermost
                                  centre); cells and points share one data weight
                                  w_data / (n_meas + n_points)                   */
@@ -138,6 +141,9 @@ typedef struct {
                                 All zero: the family's own domain (Burgers t in
                                 [0, 1], x in [-1, 1]; heat and Poisson [0, 1]^2).
                                 The cavity and the body take only their own.    */
+  const int32_t* point_field; /* field sampled at each off-grid point, or NULL
+                                 (field 0): the cavity's u, v or p, the body's
+                                 u, v, w, p or chihat                           */
 } modil_desc;
 
 /* Device bytes needed for a batch of n problems described by descs[0..n-1]. */

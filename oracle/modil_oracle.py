@@ -203,6 +203,8 @@ class Problem:
     # physical extent ((lo, hi) per axis, same order as shape) of a 2-D
     # Burgers, heat or Poisson problem; None: the family's own domain
     domain_bounds: tuple = None
+    # field sampled at each off-grid point (multi-field problems; None: 0)
+    point_field: np.ndarray = None
 
     @property
     def n_fields(self):
@@ -217,6 +219,8 @@ class Problem:
             return (0.0, -1.0), (1.0, 2.0)
         if self.pde in ("heat", "poisson", "ns2d"):
             return tuple(0.0 for _ in self.shape), tuple(1.0 for _ in self.shape)
+        if self.pde == "ns3d":              # [0,1] (z) x [0,1] (y) x [0,2] (x)
+            return (0.0, 0.0, 0.0), (1.0, 1.0, 2.0)
         raise ValueError(self.pde)
 
     def spacing(self):
@@ -746,27 +750,40 @@ def ns3d_fine_grad_colours(p, u, colours):
 # ---------------------------------------------------------------------------
 
 def _data_term(p, u):
-    """Data term of one field u, or of a list of fields (meas_field selects).
+    """Data term of one field u, or of a list of fields (meas_field and
+    point_field select the field of each cell and point).
 
-    With off-grid points (single-field problems) the misfits of the cells and
-    of the points share one normalisation, w_data / (n_cells + n_points)."""
+    With off-grid points the misfits of the cells and of the points share one
+    normalisation, w_data / (n_cells + n_points); a point's value is the
+    d-linear sample of its field (oracle/offgrid_oracle.py)."""
     n_pts = 0 if p.meas_points is None else len(p.meas_points)
     if isinstance(u, (list, tuple)):
-        if n_pts:
-            raise ValueError("off-grid points: single-field problems only")
-        if p.meas_cell is None or len(p.meas_cell) == 0:
+        n_cells = 0 if p.meas_cell is None else len(p.meas_cell)
+        if n_cells + n_pts == 0:
             return 0.0, [np.zeros_like(x) for x in u]
-        mf = np.zeros(len(p.meas_cell), int) if p.meas_field is None else np.asarray(p.meas_field)
-        w = p.w_data / len(p.meas_cell)
+        mf = np.zeros(n_cells, int) if p.meas_field is None else np.asarray(p.meas_field)
+        pf = np.zeros(n_pts, int) if p.point_field is None else np.asarray(p.point_field)
+        w = p.w_data / (n_cells + n_pts)
         total = 0.0
         gs = []
+        if n_pts:
+            from .offgrid_oracle import data_term, sample_weights
+            origin, lengths = p.domain()
+            idx, wt = sample_weights(p.meas_points, u[0].shape, lengths, origin)
         for f, x in enumerate(u):
-            sel = mf == f
             flat = x.reshape(-1)
-            diff = flat[p.meas_cell[sel]] - p.meas_value[sel]
             g = np.zeros_like(flat)
-            np.add.at(g, p.meas_cell[sel], 2.0 * w * diff)
-            total += float(w * np.sum(diff * diff))
+            if n_cells:
+                sel = mf == f
+                diff = flat[p.meas_cell[sel]] - p.meas_value[sel]
+                np.add.at(g, p.meas_cell[sel], 2.0 * w * diff)
+                total += float(w * np.sum(diff * diff))
+            if n_pts and np.any(pf == f):
+                sel = pf == f
+                t, gp = data_term(x, idx[sel], wt[sel], np.asarray(p.point_value)[sel],
+                                  w_data=w * int(sel.sum()))
+                total += t
+                g += gp.reshape(-1)
             gs.append(g.reshape(x.shape))
         return total, gs
     n_cells = 0 if p.meas_cell is None else len(p.meas_cell)

@@ -407,6 +407,28 @@ k_fine_ns2d(const __grid_constant__ Arena<T> A, int mode, int cur) {
     else dacc_d += (double)sq;
     if (adj) gS[f * TY * TX + (y - y0) * TX + (x - x0)] += wd2 * sd;
   }
+  // off-grid points whose corner cells the tile owns: the sampled value of
+  // the record's field (its four corners lie in the composed region) minus
+  // the measurement; the tile of a point's lower corner counts its misfit
+  if (A.pt_ptr) {
+    const int p1 = A.pt_ptr[gt + 1];
+    for (int j = A.pt_ptr[gt] + tid; j < p1; j += MODIL_NT) {
+      const int f = A.pt_field[j];
+      T smp = T(0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int cell = A.pt_cell[4 * (long long)j + k];
+        const int yy = cell / nx, xx = cell - yy * nx;
+        smp += A.pt_w[4 * (long long)j + k] * V(f, yy, xx);
+      }
+      const T dd = smp - A.pt_val[j];
+      A.pt_diff[j] = dd;
+      if (A.pt_own[j]) {
+        if (sizeof(T) == 4) dacc_f += (float)(dd * dd);
+        else dacc_d += (double)(dd * dd);
+      }
+    }
+  }
   double rsum, dsum;
   if (sizeof(T) == 4) {
     rsum = block_sum_ff<MODIL_NT>(racc_f, redf);
@@ -420,6 +442,19 @@ k_fine_ns2d(const __grid_constant__ Arena<T> A, int mode, int cur) {
     A.part[(long long)gt * A.npart + 1] = dsum;
   }
   if (!adj) return;
+  // the points' gradient: each owned (field, corner cell) sums weight x
+  // misfit over the records reaching it, in a fixed order (the block sums'
+  // barriers above published the misfits)
+  if (A.pc_ptr) {
+    const int c1 = A.pc_ptr[gt + 1];
+    for (int rr = A.pc_ptr[gt] + tid; rr < c1; rr += MODIL_NT) {
+      const int cell = A.pc_cell[rr], f = A.pc_field[rr];
+      const int yy = cell / nx, xx = cell - yy * nx;
+      T acc = T(0);
+      for (int e = A.pc_beg[rr]; e < A.pc_beg[rr + 1]; ++e) acc += A.pe_w[e] * A.pt_diff[A.pe_rec[e]];
+      gS[f * TY * TX + (yy - y0) * TX + (xx - x0)] += wd2 * acc;
+    }
+  }
   __syncthreads();
   const AdamCoef ac = *acS;
   for (int idx = tid; idx < F * TY * TX; idx += MODIL_NT) {

@@ -684,6 +684,24 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur, const __grid_con
     else daccd += (double)sq;
     if (adj) c.gS[f * NC3 + ((z - c.z0) * C3Y + (y - c.y0)) * C3X + (x - c.x0)] += wd2 * sd;
   }
+  // off-grid points whose corner cells the tile owns: trilinear sample of the
+  // record's field from the composed fields (eight corners) minus the
+  // measurement; the tile of a point's lower corner counts its misfit
+  if (A.pt_ptr) {
+    const int p1 = A.pt_ptr[gt + 1];
+    for (int j = A.pt_ptr[gt] + tid; j < p1; j += MODIL_NT) {
+      const T* uf = A.ufine + D.fine_off[A.pt_field[j]];
+      T smp = T(0);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) smp += A.pt_w[8 * (long long)j + k] * uf[A.pt_cell[8 * (long long)j + k]];
+      const T dd = smp - A.pt_val[j];
+      A.pt_diff[j] = dd;
+      if (A.pt_own[j]) {
+        if (sizeof(T) == 4) dacc += (float)(dd * dd);
+        else daccd += (double)(dd * dd);
+      }
+    }
+  }
   double rsum, dsum;
   if (sizeof(T) == 4) {
     rsum = block_sum_ff<MODIL_NT>(racc, redf);
@@ -697,6 +715,19 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur, const __grid_con
     A.part[(long long)gt * A.npart + 1] = dsum;
   }
   if (!adj) return;
+  // the points' gradient: each owned (field, corner cell) sums weight x
+  // misfit over the records reaching it, in a fixed order (the block sums'
+  // barriers above published the misfits)
+  if (A.pc_ptr) {
+    const int c1 = A.pc_ptr[gt + 1];
+    for (int rr = A.pc_ptr[gt] + tid; rr < c1; rr += MODIL_NT) {
+      const int cell = A.pc_cell[rr], f = A.pc_field[rr];
+      const int z = cell / (c.ny * c.nx), rem = cell - z * (c.ny * c.nx), y = rem / c.nx, x = rem - y * c.nx;
+      T acc = T(0);
+      for (int e = A.pc_beg[rr]; e < A.pc_beg[rr + 1]; ++e) acc += A.pe_w[e] * A.pt_diff[A.pe_rec[e]];
+      c.gS[f * NC3 + ((z - c.z0) * C3Y + (y - c.y0)) * C3X + (x - c.x0)] += wd2 * acc;
+    }
+  }
   __syncthreads();
   const AdamCoef ac = acS;
   if (interior) r3_phase2<T, true>(c, A, D, mode, cur, ac, pre);

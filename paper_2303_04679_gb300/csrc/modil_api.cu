@@ -78,7 +78,8 @@ struct Plan {
   std::vector<double> meas_val, run_v0;
   // off-grid points: records per tile and runs of corner contributions
   long long n_points = 0;
-  std::vector<int> pt_ptr, pt_cell, pt_own, pc_ptr, pc_cell, pc_beg, pe_rec;
+  std::vector<int> pt_ptr, pt_cell, pt_own, pt_field, pc_ptr, pc_cell, pc_field, pc_beg, pe_rec;
+  int pt_nc = 4;           // corner cells per record (2^d)
   std::vector<double> pt_w, pt_val, pe_w;
   size_t pyr_elems = 0;
   bool stream = false;     // warp-streaming fine kernel and composition pass (Burgers)
@@ -87,7 +88,7 @@ struct Plan {
   // arena offsets (bytes)
   size_t o_p0, o_p1, o_m, o_v, o_g, o_uf, o_wl, o_kq, o_km, o_kv, o_kg, o_aux, o_part, o_rptr, o_rcell,
       o_rfield, o_rbeg, o_mval, o_rv0, o_inst, o_st, o_cnt, o_q, o_ti[MODIL_MAXL], total;
-  size_t o_pptr, o_pcell, o_pw, o_pval, o_pown, o_pdiff, o_cptr, o_ccell, o_cbeg, o_erec, o_ew;
+  size_t o_pptr, o_pcell, o_pw, o_pval, o_pown, o_pdiff, o_cptr, o_ccell, o_cbeg, o_erec, o_ew, o_pfield, o_cfield;
 };
 
 int find_cfg(int ty, int tx) {
@@ -207,8 +208,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
       return fail(MODIL_ERR_ARG, "measurement arrays");
     if (q.n_points < 0 || (q.n_points > 0 && (!q.point_coord || !q.point_value)))
       return fail(MODIL_ERR_ARG, "point arrays");
-    if (q.n_points > 0 && P.pde != MODIL_PDE_BURGERS && P.pde != MODIL_PDE_HEAT && P.pde != MODIL_PDE_POISSON)
-      return fail(MODIL_ERR_UNSUPPORTED, "off-grid points: Burgers, heat and Poisson only");
+
     if (!(q.adam_lr >= 0) || !(q.adam_beta1 >= 0 && q.adam_beta1 < 1) ||
         !(q.adam_beta2 >= 0 && q.adam_beta2 < 1) || !(q.adam_eps >= 0))
       return fail(MODIL_ERR_ARG, "Adam parameters");
@@ -362,54 +362,78 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
   P.run_beg.push_back((int)all.size());
   for (int t = 0; t < nft; ++t) P.run_ptr[t + 1] += P.run_ptr[t];
 
-  // off-grid points -> records of every tile owning one of a point's four
+  // off-grid points -> records of every tile owning one of a point's 2^d
   // corner cells (the tile of the lower corner counts the misfit), and per
-  // tile runs of (record, weight) entries sorted by target cell
+  // tile runs of (record, weight) entries sorted by (field, target cell)
   {
-    struct R { int tile; int cell[4]; double w[4]; double val; int own; };
+    const int nd = three ? 3 : 2, nc = 1 << nd;
+    P.pt_nc = nc;
+    struct R { int tile, field; int cell[8]; double w[8]; double val; int own; };
     std::vector<R> recs;
     for (int i = 0; i < n; ++i) {
       const modil_desc& q = d[i];
       if (q.n_points <= 0) continue;
       const InstPlan& ip = P.inst[i];
-      const int ny = ip.n[0][1], nx = ip.n[0][2];
+      const int nn[3] = {ip.n[0][0], ip.n[0][1], ip.n[0][2]};  // (1, ny, nx) in 2-D
       bool dom = false;
       for (int a = 0; a < 3; ++a) dom |= (q.domain_lo[a] != 0.0 || q.domain_hi[a] != 0.0);
-      const double oy = dom ? q.domain_lo[0] : 0.0, ly = dom ? q.domain_hi[0] - q.domain_lo[0] : 1.0;
-      const double ox = dom ? q.domain_lo[1] : ((P.pde == MODIL_PDE_BURGERS) ? -1.0 : 0.0);
-      const double lx = dom ? q.domain_hi[1] - q.domain_lo[1] : ((P.pde == MODIL_PDE_BURGERS) ? 2.0 : 1.0);
+      // origin and length of the axes (z,) y, x
+      double org[3] = {0.0, 0.0, 0.0}, len[3] = {1.0, 1.0, 1.0};
+      if (three) {
+        len[2] = 2.0;  // the body: [0,1] x [0,1] x [0,2]
+      } else if (dom) {
+        org[1] = q.domain_lo[0]; len[1] = q.domain_hi[0] - q.domain_lo[0];
+        org[2] = q.domain_lo[1]; len[2] = q.domain_hi[1] - q.domain_lo[1];
+      } else if (P.pde == MODIL_PDE_BURGERS) {
+        org[2] = -1.0; len[2] = 2.0;
+      }
       // position along one axis in units of cell centres, clamped to the
       // outermost centres; lower centre i0 and fraction t towards i0 + 1
-      auto axis = [](double pos, double o, double len, int nn, int& i0, double& t) {
-        double sc = (pos - o) / (len / nn) - 0.5;
-        sc = std::min(std::max(sc, 0.0), (double)(nn - 1));
-        if (nn == 1) { i0 = 0; t = 0.0; return; }
-        i0 = std::min((int)std::floor(sc), nn - 2);
+      auto axis = [](double pos, double o, double l, int m, int& i0, double& t) {
+        double sc = (pos - o) / (l / m) - 0.5;
+        sc = std::min(std::max(sc, 0.0), (double)(m - 1));
+        if (m == 1) { i0 = 0; t = 0.0; return; }
+        i0 = std::min((int)std::floor(sc), m - 2);
         t = sc - i0;
       };
-      auto tile_of = [&](int y, int x) {
-        return P.dev[i].tile_base[0] + (y / TY) * ip.nt[0][2] + (x / TX);
+      const int tz = three ? k3TZ : 1, ty = three ? k3TY : TY, tx = three ? k3TX : TX;
+      auto tile_of = [&](int z, int y, int x) {
+        return P.dev[i].tile_base[0] + ((z / tz) * ip.nt[0][1] + (y / ty)) * ip.nt[0][2] + (x / tx);
       };
       for (int k = 0; k < q.n_points; ++k) {
-        const double py = q.point_coord[2 * k], px = q.point_coord[2 * k + 1], v = q.point_value[k];
-        if (!std::isfinite(py) || !std::isfinite(px) || !std::isfinite(v))
-          return fail(MODIL_ERR_ARG, "point coordinate or value not finite");
-        int iy, ix;
-        double ty_, tx_;
-        axis(py, oy, ly, ny, iy, ty_);
-        axis(px, ox, lx, nx, ix, tx_);
+        double pc[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < nd; ++a) pc[3 - nd + a] = q.point_coord[nd * k + a];
+        const double v = q.point_value[k];
+        const int f = q.point_field ? q.point_field[k] : 0;
+        bool fin = std::isfinite(v);
+        for (int a = 0; a < 3; ++a) fin = fin && std::isfinite(pc[a]);
+        if (!fin) return fail(MODIL_ERR_ARG, "point coordinate or value not finite");
+        if (f < 0 || f >= P.nfield) return fail(MODIL_ERR_ARG, "point field out of range");
+        int i0[3];
+        double t[3];
+        for (int a = 0; a < 3; ++a) {
+          if (a < 3 - nd) { i0[a] = 0; t[a] = 0.0; continue; }
+          axis(pc[a], org[a], len[a], nn[a], i0[a], t[a]);
+        }
         R r;
         r.val = v;
-        const int cy[2] = {iy, std::min(iy + 1, ny - 1)}, cx[2] = {ix, std::min(ix + 1, nx - 1)};
-        const double wy[2] = {1.0 - ty_, ty_}, wx[2] = {1.0 - tx_, tx_};
-        int tiles[4];
-        for (int a = 0; a < 2; ++a)
-          for (int b = 0; b < 2; ++b) {
-            r.cell[2 * a + b] = cy[a] * nx + cx[b];
-            r.w[2 * a + b] = wy[a] * wx[b];
-            tiles[2 * a + b] = tile_of(cy[a], cx[b]);
+        r.field = f;
+        int tiles[8];
+        for (int c = 0; c < nc; ++c) {
+          // corner c: bit 0 -> x, bit 1 -> y, bit 2 -> z (upper neighbour when set)
+          int cc[3];
+          double w = 1.0;
+          for (int a = 0; a < 3; ++a) {
+            const int bit = (a == 2) ? (c & 1) : (a == 1 ? (c >> 1) & 1 : (c >> 2) & 1);
+            if (a < 3 - nd) { cc[a] = 0; continue; }
+            cc[a] = bit ? std::min(i0[a] + 1, nn[a] - 1) : i0[a];
+            w *= bit ? t[a] : 1.0 - t[a];
           }
-        for (int c = 0; c < 4; ++c) {
+          r.cell[c] = (cc[0] * nn[1] + cc[1]) * nn[2] + cc[2];
+          r.w[c] = w;
+          tiles[c] = tile_of(cc[0], cc[1], cc[2]);
+        }
+        for (int c = 0; c < nc; ++c) {
           bool seen = false;
           for (int e = 0; e < c; ++e) seen |= tiles[e] == tiles[c];
           if (seen) continue;
@@ -423,39 +447,45 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
     if (!recs.empty()) {
       std::stable_sort(recs.begin(), recs.end(), [](const R& a, const R& b) { return a.tile < b.tile; });
       P.pt_ptr.assign(nft + 1, 0);
-      struct E { int tile, cell, rec; double w; };
+      struct E { int tile, field, cell, rec; double w; };
       std::vector<E> ents;
       for (size_t j = 0; j < recs.size(); ++j) {
         const R& r = recs[j];
         P.pt_ptr[r.tile + 1]++;
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < nc; ++c) {
           P.pt_cell.push_back(r.cell[c]);
           P.pt_w.push_back(r.w[c]);
         }
         P.pt_val.push_back(r.val);
         P.pt_own.push_back(r.own);
+        P.pt_field.push_back(r.field);
       }
       for (int t = 0; t < nft; ++t) P.pt_ptr[t + 1] += P.pt_ptr[t];
       // entries: the corners each record's tile owns
       for (size_t j = 0; j < recs.size(); ++j) {
         const R& r = recs[j];
         const int ii = P.tile_inst[0][r.tile];
-        const int nx = P.inst[ii].n[0][2];
-        for (int c = 0; c < 4; ++c) {
-          const int y = r.cell[c] / nx, x = r.cell[c] % nx;
-          const int t = P.dev[ii].tile_base[0] + (y / TY) * P.inst[ii].nt[0][2] + (x / TX);
-          if (t == r.tile) ents.push_back({t, r.cell[c], (int)j, r.w[c]});
+        const InstPlan& ip = P.inst[ii];
+        const int ny = ip.n[0][1], nx = ip.n[0][2];
+        const int tz = three ? k3TZ : 1, ty = three ? k3TY : TY, tx = three ? k3TX : TX;
+        for (int c = 0; c < nc; ++c) {
+          const int z = r.cell[c] / (ny * nx), y = (r.cell[c] / nx) % ny, x = r.cell[c] % nx;
+          const int t = P.dev[ii].tile_base[0] + ((z / tz) * ip.nt[0][1] + (y / ty)) * ip.nt[0][2] + (x / tx);
+          if (t == r.tile) ents.push_back({t, r.field, r.cell[c], (int)j, r.w[c]});
         }
       }
       std::stable_sort(ents.begin(), ents.end(), [](const E& a, const E& b) {
         if (a.tile != b.tile) return a.tile < b.tile;
+        if (a.field != b.field) return a.field < b.field;
         if (a.cell != b.cell) return a.cell < b.cell;
         return a.rec < b.rec;
       });
       P.pc_ptr.assign(nft + 1, 0);
       for (size_t k = 0; k < ents.size(); ++k) {
-        if (k == 0 || ents[k].tile != ents[k - 1].tile || ents[k].cell != ents[k - 1].cell) {
+        if (k == 0 || ents[k].tile != ents[k - 1].tile || ents[k].cell != ents[k - 1].cell ||
+            ents[k].field != ents[k - 1].field) {
           P.pc_cell.push_back(ents[k].cell);
+          P.pc_field.push_back(ents[k].field);
           P.pc_beg.push_back((int)k);
           P.pc_ptr[ents[k].tile + 1]++;
         }
@@ -494,6 +524,8 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
   P.o_pw = take(P.esz * P.pt_w.size());
   P.o_pval = take(P.esz * P.pt_val.size());
   P.o_pown = take(4 * P.pt_own.size());
+  P.o_pfield = take(4 * P.pt_field.size());
+  P.o_cfield = take(4 * P.pc_field.size());
   P.o_pdiff = take(P.esz * P.pt_val.size());
   P.o_cptr = take(4 * P.pc_ptr.size());
   P.o_ccell = take(4 * P.pc_cell.size());
@@ -560,6 +592,8 @@ void fill_arena(modil_problem* p, Arena<T>& A) {
   A.pt_w = reinterpret_cast<const T*>(b + P.o_pw);
   A.pt_val = reinterpret_cast<const T*>(b + P.o_pval);
   A.pt_own = reinterpret_cast<const int*>(b + P.o_pown);
+  A.pt_field = reinterpret_cast<const int*>(b + P.o_pfield);
+  A.pc_field = reinterpret_cast<const int*>(b + P.o_cfield);
   A.pt_diff = reinterpret_cast<T*>(b + P.o_pdiff);
   A.pc_ptr = pts ? reinterpret_cast<const int*>(b + P.o_cptr) : nullptr;
   A.pc_cell = reinterpret_cast<const int*>(b + P.o_ccell);
@@ -850,6 +884,8 @@ modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t ar
   if (st == MODIL_OK) st = upload(p, P.o_pptr, P.pt_ptr.data(), 4 * P.pt_ptr.size());
   if (st == MODIL_OK) st = upload(p, P.o_pcell, P.pt_cell.data(), 4 * P.pt_cell.size());
   if (st == MODIL_OK) st = upload(p, P.o_pown, P.pt_own.data(), 4 * P.pt_own.size());
+  if (st == MODIL_OK) st = upload(p, P.o_pfield, P.pt_field.data(), 4 * P.pt_field.size());
+  if (st == MODIL_OK) st = upload(p, P.o_cfield, P.pc_field.data(), 4 * P.pc_field.size());
   if (st == MODIL_OK) st = upload(p, P.o_cptr, P.pc_ptr.data(), 4 * P.pc_ptr.size());
   if (st == MODIL_OK) st = upload(p, P.o_ccell, P.pc_cell.data(), 4 * P.pc_cell.size());
   if (st == MODIL_OK) st = upload(p, P.o_cbeg, P.pc_beg.data(), 4 * P.pc_beg.size());

@@ -96,10 +96,12 @@ struct Arena {
   // records of the points one of whose four corner cells it owns, and the
   // runs of (record, weight) entries adding to each owned corner cell
   const int* pt_ptr;   // per tile: first record
-  const int* pt_cell;  // 4 corner cells per record (flat, within the instance)
-  const T* pt_w;       // 4 weights per record
+  const int* pt_cell;  // 4 (2-D) or 8 (3-D) corner cells per record (flat, within the instance)
+  const T* pt_w;       // as many weights per record
   const T* pt_val;     // measured value per record
   const int* pt_own;   // 1 where this record's tile counts the point's misfit
+  const int* pt_field; // field each record samples
+  const int* pc_field; // field of each run's target cell
   T* pt_diff;          // scratch: sample - value per record
   const int* pc_ptr;   // per tile: first run of corner contributions
   const int* pc_cell;  // target cell of each run

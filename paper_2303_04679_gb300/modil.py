@@ -52,6 +52,7 @@ class modil_desc(C.Structure):
         ("point_value", C.POINTER(C.c_double)),
         ("tile", C.c_int * 2),
         ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3),
+        ("point_field", C.POINTER(C.c_int32)),
     ]
 
 
@@ -119,12 +120,12 @@ class Desc:
     def __init__(self, pde, shape, n_levels, dtype="f32", coef=(), w_res=1.0, w_data=1.0,
                  w_reg=0.0, meas_cell=None, meas_value=None, meas_field=None, aux=None,
                  knodes=None, lr=5e-3, beta1=0.9, beta2=0.999, eps=1e-8, tile=(0, 0),
-                 points=None, point_value=None, domain=None):
+                 points=None, point_value=None, domain=None, point_field=None):
         self.kwargs = dict(pde=pde, shape=shape, n_levels=n_levels, dtype=dtype, coef=coef,
                            w_res=w_res, w_data=w_data, w_reg=w_reg, meas_cell=meas_cell,
                            meas_value=meas_value, meas_field=meas_field, aux=aux, knodes=knodes,
                            lr=lr, beta1=beta1, beta2=beta2, eps=eps, tile=tile, points=points,
-                           point_value=point_value, domain=domain)
+                           point_value=point_value, domain=domain, point_field=point_field)
         self.pde = {"burgers": PDE_BURGERS, "heat": PDE_HEAT, "ns2d": PDE_NS2D,
                     "ns3d": PDE_NS3D, "poisson": PDE_POISSON}.get(pde, pde)
         self.dtype = {"f32": F32, "f64": F64}.get(dtype, dtype)
@@ -135,7 +136,9 @@ class Desc:
         self._field = None if meas_field is None else np.ascontiguousarray(meas_field, np.int32)
         self._aux = None if aux is None else np.ascontiguousarray(aux, np.float64)
         self._knodes = None if knodes is None else np.ascontiguousarray(knodes, np.float64)
-        self._pts = None if points is None else np.ascontiguousarray(np.reshape(points, (-1, 2)), np.float64)
+        nd = 3 if self.pde == PDE_NS3D else 2
+        self._pts = None if points is None else np.ascontiguousarray(np.reshape(points, (-1, nd)), np.float64)
+        self._pfield = None if point_field is None else np.ascontiguousarray(point_field, np.int32)
         self._pval = None if point_value is None else np.ascontiguousarray(point_value, np.float64)
         # the C planner reads these arrays up to n_meas / n_points entries
         n_cells = 0 if self._cell is None else len(self._cell)
@@ -146,6 +149,8 @@ class Desc:
         n_pts = 0 if self._pts is None else len(self._pts)
         if n_pts and (self._pval is None or len(self._pval) != n_pts):
             raise ValueError("point_value needs one value per off-grid point")
+        if self._pfield is not None and len(self._pfield) != n_pts:
+            raise ValueError("point_field needs one field index per off-grid point")
         d = modil_desc()
         d.pde, d.dtype, d.ndim = self.pde, self.dtype, len(self.shape)
         for i, s in enumerate(self.shape):
@@ -166,6 +171,7 @@ class Desc:
         d.n_points = 0 if self._pts is None else len(self._pts)
         d.point_coord = _dptr(self._pts, C.c_double)
         d.point_value = _dptr(self._pval, C.c_double)
+        d.point_field = _dptr(self._pfield, C.c_int32)
         d.tile[0], d.tile[1] = int(tile[0]), int(tile[1])
         if domain is not None:  # ((lo, hi) per axis, slowest first)
             for a, (lo, hi) in enumerate(domain):

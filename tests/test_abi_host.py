@@ -111,7 +111,7 @@ def test_ns3d_arena_bytes_and_validation(mod):
 
 def test_offgrid_points_in_the_plan(mod):
     """Off-grid points enlarge the arena (their per-tile records), non-finite
-    coordinates and unsupported families are rejected (host only)."""
+    coordinates and out-of-range fields are rejected (host only)."""
     import ctypes as C
     rng = np.random.default_rng(0)
     pts = np.column_stack([rng.uniform(0, 1, 300), rng.uniform(-1, 1, 300)])
@@ -129,6 +129,13 @@ def test_offgrid_points_in_the_plan(mod):
     bad = mod.Desc("burgers", (48, 96), 3, "f32", coef=(0.02,), points=[[np.nan, 0.0]],
                    point_value=np.zeros(1))
     assert nbytes(bad)[0] != 0
+    # the multi-field families take points with a field index in range
     ns2d = mod.Desc("ns2d", (16, 16), 2, "f32", coef=(100.0, 1.0), points=[[0.5, 0.5]],
-                    point_value=np.zeros(1))
-    assert nbytes(ns2d)[0] != 0
+                    point_value=np.zeros(1), point_field=np.array([1], np.int32))
+    assert nbytes(ns2d)[0] == 0
+    ns2d_bad = mod.Desc("ns2d", (16, 16), 2, "f32", coef=(100.0, 1.0), points=[[0.5, 0.5]],
+                        point_value=np.zeros(1), point_field=np.array([3], np.int32))
+    assert nbytes(ns2d_bad)[0] != 0
+    body = mod.Desc("ns3d", (8, 8, 16), 2, "f32", coef=(60.0, 0.4, 1.0, 1.0), points=[[0.5, 0.5, 1.0]],
+                    point_value=np.zeros(1), point_field=np.array([2], np.int32))
+    assert nbytes(body)[0] == 0

@@ -1,7 +1,8 @@
 """Off-grid measurement points (d-linear sampling of the composed field) on the
 GPU against the FP64 oracle: loss terms and every level gradient with points
 near walls and on tile borders, mixed with on-grid cells, in a batch, in the
-persistent launch, and Adam trajectories in FP64."""
+persistent launch, and Adam trajectories in FP64; the same for the velocity
+samples of the cavity (bilinear) and the body (trilinear) at points."""
 import numpy as np
 import pytest
 
@@ -96,8 +97,85 @@ def test_points_adam_steps_f64(modil):
             assert np.max(np.abs(p.read_level(lvl) - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
 
 
-def test_points_rejected_where_unsupported(modil):
+def _mf_case(modil, pde, shape, L, dtype, seed, n_cells=20, n_pts=40):
+    """Cavity (u, v, p) or body (u, v, w, p, chihat) with velocity samples at
+    cells and at points, points also at walls, outermost centres and tile
+    borders (cavity tiles 8 x 32, body tiles 4 x 8 x 16)."""
+    rng = np.random.default_rng(seed)
+    npd = np.float64 if dtype == "f64" else np.float32
+    rnd = lambda a: np.asarray(a, np.float64).astype(npd).astype(np.float64)  # noqa: E731
+    nf = 3 if pde == "ns2d" else 5
+    levels = [[rnd(a) for a in lv] for lv in inputs.random_levels(shape, L, nf, seed, -0.5, 0.5, 0.2)]
+    if pde == "ns3d":
+        levels[4][0] = rnd(levels[4][0] * 8.0 + 5.0)   # body fraction near 1/2
+    n = int(np.prod(shape))
+    cells = inputs.measurement_cells(n, n_cells, seed)
+    cfield = (np.arange(n_cells) % 3).astype(np.int32)
+    cval = rnd(rng.normal(0, 0.3, n_cells))
+    lengths = np.array((1.0, 1.0) if pde == "ns2d" else (1.0, 1.0, 2.0))
+    d = len(shape)
+    u01 = rng.uniform(0, 1, (n_pts, d))
+    u01[0] = 0.0
+    u01[1] = 1.0
+    u01[2] = 0.5 / np.array(shape)
+    u01[3] = np.array([8.0, 32.0][-d:] if d == 2 else [4.0, 8.0, 16.0]) / np.array(shape)
+    pts = u01 * lengths
+    pfield = rng.integers(0, 3, n_pts).astype(np.int32)
+    pval = rnd(rng.normal(0, 0.3, n_pts))
+    if pde == "ns2d":
+        coef, dcoef = {"Re": 100.0, "tau": 1.0}, (100.0, 1.0)
+    else:
+        coef, dcoef = {"Re": 60.0, "D": 0.4, "lam": 1.0, "tau": 1.0}, (60.0, 0.4, 1.0, 1.0)
+    orc = o.Problem(pde, shape, L, coef=coef, meas_cell=cells, meas_field=cfield, meas_value=cval,
+                    meas_points=pts, point_value=pval, point_field=pfield)
+    desc = modil.Desc(pde, shape, L, dtype, coef=dcoef, meas_cell=cells, meas_field=cfield,
+                      meas_value=cval, points=pts, point_value=pval, point_field=pfield, lr=2e-3)
+    return orc, desc, levels
+
+
+def _mf_check(p, orc, levels, tol):
+    terms, grads, _ = o.loss_grad_levels(orc, levels)
+    t = p.eval_grad()[0]
+    for j, name in enumerate(("total", "res", "data")):
+        assert abs(t[j] - terms[name]) <= tol * abs(terms[name]), (name, t[j], terms[name])
+    floor = orc.pde == "ns2d"   # the cavity's coarse pressure levels (reading R14)
+    for f, gf in enumerate(grads):
+        for lvl, gr in enumerate(gf):
+            g = p.read_grad(lvl, field=f).astype(np.float64)
+            scale = np.linalg.norm(gr)
+            if floor and f == 2 and lvl >= 1:
+                from _cases import abs_chain
+                scale = max(scale, 0.1 * np.linalg.norm(abs_chain(gf[0], len(gf))[lvl]))
+            assert np.linalg.norm(g - gr) <= tol * scale, (f, lvl)
+
+
+@pytest.mark.parametrize("pde,shape,L,dtype", [("ns2d", (32, 32), 3, "f32"), ("ns2d", (24, 24), 3, "f64"),
+                                               ("ns3d", (8, 16, 32), 3, "f32"), ("ns3d", (8, 8, 16), 2, "f64")])
+def test_multi_field_points_loss_grad(modil, pde, shape, L, dtype):
+    orc, desc, levels = _mf_case(modil, pde, shape, L, dtype, seed=64)
+    with modil.Problem(desc) as p:
+        p.write_fields(levels)
+        _mf_check(p, orc, levels, 1e-5 if dtype == "f32" else 1e-11)
+
+
+@pytest.mark.parametrize("pde,shape,L", [("ns2d", (16, 16), 3), ("ns3d", (8, 8, 16), 2)])
+def test_multi_field_points_adam_steps_f64(modil, pde, shape, L):
+    orc, desc, levels = _mf_case(modil, pde, shape, L, "f64", seed=65)
+    st = o.OracleState.zeros_like_levels(levels)
+    hist = [o.oracle_step(orc, st, 2e-3) for _ in range(3)]
+    with modil.Problem(desc) as p:
+        p.write_fields(levels)
+        for k in range(3):
+            t = p.step(1)[0]
+            assert abs(t[0] - hist[k]["total"]) <= 1e-11 * hist[k]["total"]
+        for f, lv in enumerate(st.levels):
+            for lvl, ref in enumerate(lv):
+                a = p.read_level(lvl, field=f)
+                assert np.max(np.abs(a - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref))), (f, lvl)
+
+
+def test_point_field_out_of_range_rejected(modil):
     pts = np.array([[0.5, 0.5]])
     with pytest.raises(modil.ModilError):
         modil.Problem(modil.Desc("ns2d", (16, 16), 2, "f32", coef=(100.0, 1.0), points=pts,
-                                 point_value=np.zeros(1)))
+                                 point_value=np.zeros(1), point_field=np.array([3], np.int32)))

@@ -100,3 +100,54 @@ def test_offgrid_level_gradient_matches_finite_differences():
     fd = (loss(eps) - loss(-eps)) / (2 * eps)
     an = sum(float(np.sum(g * b)) for g, b in zip(grads, d))
     assert abs(fd - an) <= 1e-7 * max(1.0, abs(an))
+
+
+def test_multi_field_point_at_a_centre_is_a_cell_measurement_of_that_field():
+    """Velocity samples at points (Sections 3.3, 3.5): a point at the centre
+    of cell c measuring field f contributes exactly what a measurement of
+    (c, f) does, in 2-D (cavity, bilinear) and 3-D (body, trilinear) -- the
+    field routing and the corner weights at a centre."""
+    import oracle as o
+    from paper_2303_04679_gb300 import inputs
+    rng = np.random.default_rng(12)
+    for pde, shape, L, coef, nf in (("ns2d", (8, 8), 2, {"Re": 100.0, "tau": 1.0}, 3),
+                                    ("ns3d", (4, 4, 8), 2, {"Re": 60.0, "D": 0.4, "lam": 1.0, "tau": 1.0}, 5)):
+        levels = inputs.random_levels(shape, L, nf, 12, -0.5, 0.5, 0.2)
+        n = int(np.prod(shape))
+        cells = rng.choice(n, 6, replace=False).astype(np.int32)
+        fields = np.array([0, 1, 2, 0, 1, 2], np.int32)
+        vals = rng.normal(size=6)
+        lengths = (1.0, 1.0) if pde == "ns2d" else (1.0, 1.0, 2.0)
+        idx = np.array(np.unravel_index(cells, shape)).T
+        pts = (idx + 0.5) * np.array(lengths) / np.array(shape)
+        on = o.Problem(pde, shape, L, coef=coef, meas_cell=cells, meas_field=fields, meas_value=vals)
+        off = o.Problem(pde, shape, L, coef=coef, meas_points=pts, point_value=vals, point_field=fields)
+        t1, g1, _ = o.loss_grad_levels(on, levels)
+        t2, g2, _ = o.loss_grad_levels(off, levels)
+        assert np.isclose(t1["data"], t2["data"], rtol=1e-13)
+        for f in range(nf):
+            for a, b in zip(g1[f], g2[f]):
+                assert np.allclose(a, b, rtol=1e-12, atol=1e-14)
+
+
+def test_multi_field_points_gradient_matches_finite_differences():
+    import oracle as o
+    from paper_2303_04679_gb300 import inputs
+    rng = np.random.default_rng(13)
+    for pde, shape, L, coef, nf, lengths in (
+            ("ns2d", (8, 8), 2, {"Re": 100.0, "tau": 1.0}, 3, (1.0, 1.0)),
+            ("ns3d", (4, 4, 8), 2, {"Re": 60.0, "D": 0.4, "lam": 1.0, "tau": 1.0}, 5, (1.0, 1.0, 2.0))):
+        levels = inputs.random_levels(shape, L, nf, 13, -0.5, 0.5, 0.2)
+        pts = rng.uniform(0, 1, (9, len(shape))) * np.array(lengths)
+        p = o.Problem(pde, shape, L, coef=coef, w_data=50.0, meas_points=pts,
+                      point_value=rng.normal(size=9), point_field=rng.integers(0, nf, 9).astype(np.int32))
+        _, grads, _ = o.loss_grad_levels(p, levels)
+        d = [[rng.standard_normal(a.shape) for a in lv] for lv in levels]
+        eps = 1e-6
+
+        def loss(s):
+            return o.loss_terms(p, [o.compose([a + s * b for a, b in zip(lv, dv)])
+                                    for lv, dv in zip(levels, d)])["total"]
+        fd = (loss(eps) - loss(-eps)) / (2 * eps)
+        an = sum(float(np.sum(g * b)) for gf, df in zip(grads, d) for g, b in zip(gf, df))
+        assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)), (pde, fd, an)
