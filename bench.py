@@ -659,47 +659,76 @@ def flushed_steps(step, stream, flush, K, W):
 
 
 def run_poisson(args):
-    """The paper's Poisson level sweep (2-D, cell layout, 32 x 32 cells, zero
-    initial guess, reference u_ref of the recipe): for L = 1..5 levels, 400
-    Adam steps (lr 0.005) and 400 L-BFGS iterations (history 50); relative
-    RMS error against u_ref after the run and host wall time of each run."""
+    """The paper's Poisson level sweep (Section 3.1): d = 1, 2, 3, node and cell
+    layouts, N = 32 cells per axis, zero initial guess, L = 1..5 levels; 400
+    Adam iterations (lr 0.005) and 400 L-BFGS iterations (history 50); the
+    RMS error relative to the exact solution of the discrete problem, which
+    the library itself computes first (L-BFGS with five levels until the loss
+    stops falling).  The right-hand side is the closed-form Laplacian of the
+    reference u_ref of the recipe."""
     import torch
 
     from paper_2303_04679_gb300 import inputs, modil
     torch.cuda.set_device(0)
-    w = inputs.poisson_workload(32)
-    ref = w["u_ref"]
-    rms = lambda u: float(np.sqrt(np.mean((u - ref) ** 2) / np.mean(ref ** 2)))  # noqa: E731
-    rows = []
-    for L in range(1, 6):
-        desc = modil.Desc("poisson", w["shape"], L, "f64", aux=w["f"].ravel(), lr=5e-3)
-        with modil.Problem(desc) as p:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            p.step(400, read_loss=False)
-            torch.cuda.synchronize()
-            t_adam = time.perf_counter() - t0
-            e_adam = rms(p.read_field())
-        with modil.Problem(desc) as p, modil.LBFGS(p, history=50) as opt:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            hist = opt.run(400)
-            t_lb = time.perf_counter() - t0
-            e_lb = rms(p.read_field())
-        rows.append({"levels": L, "adam": {"error": e_adam, "seconds": t_adam},
-                     "lbfgs": {"error": e_lb, "seconds": t_lb, "iterations": len(hist) - 1,
-                               "final_loss": float(hist[-1])}})
-    best = rows[-1]
+    n = 32
+    sweeps = []
+    for d in (1, 2, 3):
+        for layout in ("node", "cell"):
+            w = inputs.poisson_workload(n, d, layout)
+
+            def desc(L):
+                return modil.Desc("poisson", w["shape"], L, "f64", aux=w["f"].ravel(), layout=layout, lr=5e-3)
+
+            def solution(u):
+                # node layout: the boundary nodes hold the imposed Dirichlet value
+                if layout == "node":
+                    u = u.copy()
+                    for ax in range(d):
+                        idx = [slice(None)] * d
+                        idx[ax] = 0
+                        u[tuple(idx)] = 0.0
+                        idx[ax] = -1
+                        u[tuple(idx)] = 0.0
+                return u
+            with modil.Problem(desc(5)) as p, modil.LBFGS(p, history=50) as opt:
+                hist = opt.run(3000)
+                exact = solution(p.read_field())
+            scale = float(np.sqrt(np.mean(exact ** 2)))
+            err = lambda u: float(np.sqrt(np.mean((solution(u) - exact) ** 2)) / scale)  # noqa: E731
+            rows = []
+            for L in range(1, 6):
+                with modil.Problem(desc(L)) as p:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    p.step(400, read_loss=False)
+                    torch.cuda.synchronize()
+                    t_adam = time.perf_counter() - t0
+                    e_adam = err(p.read_field())
+                errs = []
+                t_lb = 0.0
+                with modil.Problem(desc(L)) as p, modil.LBFGS(p, history=50) as opt:
+                    for _ in range(20):  # 20 x 20 iterations; the pair history carries over
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        h = opt.run(20)
+                        t_lb += time.perf_counter() - t0
+                        errs.append(err(p.read_field()))
+                        if len(h) < 21:
+                            break
+                reach = next((20 * (k + 1) for k, e in enumerate(errs) if e < 1e-10), None)
+                rows.append({"levels": L, "adam_error": e_adam, "adam_seconds": t_adam,
+                             "lbfgs_error": errs[-1], "lbfgs_seconds": t_lb,
+                             "lbfgs_iterations_to_1e-10": reach})
+            sweeps.append({"d": d, "layout": layout, "exact_solve_loss": float(hist[-1]),
+                           "exact_vs_u_ref": float(np.sqrt(np.mean((exact - w["u_ref"]) ** 2)) / scale),
+                           "levels": rows})
     out = {
-        "metric": "relative RMS error after 400 iterations", "value": best["lbfgs"]["error"],
-        "unit": "relative RMS error", "n_gpus": 1, "steps": 400, "warmup": 0,
-        "ms_per_step": 1e3 * best["lbfgs"]["seconds"] / max(best["lbfgs"]["iterations"], 1),
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": "Poisson 2-D cell layout, 32x32, levels 1..5, zero initial guess",
-                   "rhs": "closed-form Laplacian of the reference solution"},
-        "sweep": rows,
-        "note": "error floor: the discretisation error between the discrete solution and u_ref",
+        "metric": "relative RMS error after 400 iterations (Adam, L-BFGS) against the discrete solution",
+        "unit": "relative RMS error", "n_gpus": 1, "steps": 400, "warmup": 0, "higher_is_better": False,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "Poisson, d = 1, 2, 3, node and cell layouts, 32 cells per axis, "
+                               "levels 1..5, zero initial guess"},
+        "sweep": sweeps,
     }
     print(json.dumps(out), flush=True)
 

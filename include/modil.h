@@ -75,14 +75,23 @@ enum {
                             4 = chihat with body fraction chi = 1/(1+exp(-(chihat-5)));
                             inlet x = 0 (u = (1,0,0)), outlet x = 2 (p = 0), free-slip
                             walls in y and z; ndim = 3                               */
-  MODIL_PDE_POISSON = 5  /* Poisson equation lap(u) = f on [0,1]^2, axes (y, x), cell
-                            layout: finite volumes at cell centres, zero Dirichlet
-                            walls by quadratic extrapolation from the wall and the two
-                            nearest centres (ghost = -2 u_0 + u_1 / 3); residual in
-                            every cell; f in aux; both axes >= 2 cells; Section 3.1 */
+  MODIL_PDE_POISSON = 5  /* Poisson equation lap(u) = f on [0,1]^d, d = ndim = 1, 2 or 3,
+                            axes slowest first (Section 3.1).  Cell layout: finite
+                            volumes at cell centres, zero Dirichlet walls by quadratic
+                            extrapolation from the wall and the two nearest centres
+                            (ghost = -2 u_0 + u_1 / 3), residual in every cell, every
+                            axis >= 2 cells.  Node layout: finite differences at the
+                            N + 1 nodes per axis, the Dirichlet value imposed on the
+                            boundary nodes (the stencil reads 0 there, their
+                            unknowns get no residual gradient), residual at interior
+                            nodes.  f in aux, one
+                            value per fine cell (node).  The 2-D cell layout runs in
+                            the fused tile kernel, the others in a kernel per step of
+                            the method (grids of a few tens of cells per axis)    */
 };
 
 enum { MODIL_F32 = 0, MODIL_F64 = 1 };
+enum { MODIL_CELL = 0, MODIL_NODE = 1 };
 
 #define MODIL_MAX_LEVELS 10
 #define MODIL_MAX_FIELDS 5
@@ -144,6 +153,9 @@ typedef struct {
   const int32_t* point_field; /* field sampled at each off-grid point, or NULL
                                  (field 0): the cavity's u, v or p, the body's
                                  u, v, w, p or chihat                           */
+  int layout;                 /* POISSON: MODIL_CELL (0, values at cell
+                                 centres) or MODIL_NODE (1, values at the N + 1
+                                 nodes per axis); the other families: 0       */
 } modil_desc;
 
 /* Device bytes needed for a batch of n problems described by descs[0..n-1]. */

@@ -407,9 +407,11 @@ def _heat_reg(q):
 # value b = 0 is imposed by quadratic extrapolation from the wall and the two
 # nearest centres: ghost = 8/3 b - 2 u_0 + 1/3 u_1.  Residual = discrete
 # Laplacian - f in every cell; loss w_res * h^d * sum r^2.
-# node layout: finite differences on the N+1 nodes per axis; residual at the
-# interior nodes; boundary nodes carry the term w_res * h^(d-1) * sum u^2
-# (the boundary integral of the displayed Poisson loss).
+# node layout: finite differences on the N+1 nodes per axis; the Dirichlet
+# value is imposed directly on the boundary nodes (Section 3.1), so the
+# stencil reads 0 there whatever the decomposition holds, the residual lives
+# at the interior nodes, and the boundary nodes' unknowns do not enter the
+# loss (their gradient is zero).
 
 def _poisson_ghost_pad(u, axis):
     u0 = np.take(u, [0], axis=axis)
@@ -433,6 +435,7 @@ def poisson_residual(u, f, h, layout="cell"):
                     + np.take(p, range(0, n), axis=ax)) / h[ax] ** 2
         return lap - f
     inner = tuple(slice(1, -1) for _ in range(d))
+    u = np.where(_poisson_boundary_mask(u.shape), 0.0, u)   # the Dirichlet value on the nodes
     lap = np.zeros(tuple(s - 2 for s in u.shape))
     for ax in range(d):
         sp = [slice(1, -1)] * d
@@ -490,7 +493,7 @@ def _poisson_adjoint(u, lam, h, layout):
         g[tuple(sp)] += c
         g[tuple(sm)] += c
         g[inner] += -2.0 * c
-    return g
+    return np.where(_poisson_boundary_mask(u.shape), 0.0, g)  # boundary nodes are fixed
 
 
 # ---------------------------------------------------------------------------
@@ -820,9 +823,6 @@ def loss_terms(p, u, q=None):
         reg = p.w_reg * _heat_reg(q)[0]
     elif p.pde == "poisson":
         r = poisson_residual(u, p.coef["f"], h, p.layout)
-        if p.layout == "node":
-            hb = np.prod(h[1:]) if len(h) > 1 else 1.0
-            bnd = p.w_res * hb * float(np.sum(u[_poisson_boundary_mask(u.shape)] ** 2))
     elif p.pde == "ns2d":
         ru, rv, rc, rg = ns2d_residuals(u[0], u[1], u[2], p.coef["Re"], h[0],
                                         p.coef.get("tau", 1.0))
@@ -853,10 +853,6 @@ def loss_grad_fine(p, u, q=None):
     elif p.pde == "poisson":
         r = poisson_residual(u, p.coef["f"], h, p.layout)
         g = _poisson_adjoint(u, 2.0 * p.w_res * dV * r, h, p.layout)
-        if p.layout == "node":
-            hb = np.prod(h[1:]) if len(h) > 1 else 1.0
-            m = _poisson_boundary_mask(u.shape)
-            g = g + np.where(m, 2.0 * p.w_res * hb * u, 0.0)
     elif p.pde == "ns2d":
         Re, tf = p.coef["Re"], p.coef.get("tau", 1.0)
         ru, rv, rc, rg = ns2d_residuals(u[0], u[1], u[2], Re, h[0], tf)

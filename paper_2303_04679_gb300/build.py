@@ -20,8 +20,8 @@ LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libmodil.so")
 
-SOURCES = ["modil_api.cu", "kernels_st.cu", "kernels_stream.cu", "kernels_ns2d.cu", "kernels_ns3d.cu",
-           "kernels_common.cu", "tc_gemm.cu", "unet.cu", "lbfgs.cu"]
+SOURCES = ["modil_api.cu", "kernels_st.cu", "kernels_stream.cu", "kernels_grid.cu", "kernels_ns2d.cu",
+           "kernels_ns3d.cu", "kernels_common.cu", "tc_gemm.cu", "unet.cu", "lbfgs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -20,6 +20,7 @@ constexpr int kStreamCfg = 6;
 constexpr int kSR = 32, kSW = 28;
 constexpr int kStreamNT = 128;   // threads per block of the streaming kernel (one strip per warp)
 constexpr int kComposeNT = 256;  // threads (cells) per block of the 2-D composition pass
+constexpr int kGridNT = 256;     // threads (cells) per block of the d-dimensional Poisson kernels
 // Tile of the restriction kernels (coarse levels), rows x cols.
 constexpr int kLevTY = 8, kLevTX = 32;
 
@@ -60,6 +61,16 @@ template <class T>
 cudaError_t launch_compose2(const Arena<T>& A, int level, int cur, cudaStream_t s);
 template <class T>
 cudaError_t launch_fine_stream(const Arena<T>& A, int mode, int cur, cudaStream_t s);
+// The Poisson family in d = 1, 2, 3, node or cell layout: composition of a
+// level, fine residual/adjoint/Adam, restriction/Adam of a level, loss terms.
+template <class T>
+cudaError_t launch_gcompose(const Arena<T>& A, int level, int cur, cudaStream_t s);
+template <class T>
+cudaError_t launch_gresid(const Arena<T>& A, int mode, int cur, cudaStream_t s);
+template <class T>
+cudaError_t launch_grestrict(const Arena<T>& A, int level, int mode, int cur, cudaStream_t s);
+template <class T>
+cudaError_t launch_gfinal(const Arena<T>& A, int mode, cudaStream_t s);
 // 3-D penalised Navier-Stokes: fine tile 4 x 8 x 16 cells, coarse tile 2 x 8 x 16.
 constexpr int k3TZ = 4, k3TY = 8, k3TX = 16;
 constexpr int k3LZ = 2, k3LY = 8, k3LX = 16;

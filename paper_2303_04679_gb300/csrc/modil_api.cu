@@ -83,6 +83,7 @@ struct Plan {
   std::vector<double> pt_w, pt_val, pe_w;
   size_t pyr_elems = 0;
   bool stream = false;     // warp-streaming fine kernel and composition pass (Burgers)
+  bool grid = false;       // Poisson in d = 1, 3 or the node layout: one kernel per step
   std::vector<int> cblk_inst[MODIL_MAXL], cblk_first[MODIL_MAXL];
   size_t o_cbi[MODIL_MAXL], o_cbf[MODIL_MAXL];
   // arena offsets (bytes)
@@ -114,8 +115,16 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
     return fail(MODIL_ERR_UNSUPPORTED, "unknown pde " + std::to_string(P.pde));
   if (P.dtype != MODIL_F32 && P.dtype != MODIL_F64) return fail(MODIL_ERR_ARG, "dtype");
   const bool three = P.pde == MODIL_PDE_NS3D;
-  if (P.ndim != (three ? 3 : 2))
+  if (P.pde == MODIL_PDE_POISSON) {
+    if (P.ndim < 1 || P.ndim > 3) return fail(MODIL_ERR_ARG, "Poisson: ndim 1, 2 or 3");
+    if (d[0].layout != MODIL_CELL && d[0].layout != MODIL_NODE) return fail(MODIL_ERR_ARG, "layout");
+    P.grid = P.ndim != 2 || d[0].layout == MODIL_NODE;
+  } else if (P.ndim != (three ? 3 : 2)) {
     return fail(MODIL_ERR_ARG, three ? "NS3D needs ndim = 3" : "this PDE family is 2-D (ndim = 2)");
+  } else if (d[0].layout != MODIL_CELL) {
+    return fail(MODIL_ERR_ARG, "only the Poisson family has a node layout");
+  }
+  const bool grid = P.grid;
   P.esz = P.dtype == MODIL_F64 ? 8 : 4;
   P.nfield = (P.pde == MODIL_PDE_NS2D) ? 3 : (three ? 5 : 1);
   // tile configuration (same for the batch)
@@ -151,17 +160,21 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
   long long off = 0, foff = 0, koff = 0, aoff = 0;
   for (int i = 0; i < n; ++i) {
     const modil_desc& q = d[i];
-    if (q.pde != P.pde || q.dtype != P.dtype || q.ndim != P.ndim)
-      return fail(MODIL_ERR_ARG, "a batch must share pde, dtype and ndim");
+    if (q.pde != P.pde || q.dtype != P.dtype || q.ndim != P.ndim || q.layout != d[0].layout)
+      return fail(MODIL_ERR_ARG, "a batch must share pde, dtype, ndim and layout");
     if (q.tile[0] != d[0].tile[0] || q.tile[1] != d[0].tile[1])
       return fail(MODIL_ERR_ARG, "a batch must share the tile shape");
-    // 2-D problems: (1, ny, nx); 3-D: (nz, ny, nx)
-    const int nz = three ? q.shape[0] : 1;
-    const int ny = three ? q.shape[1] : q.shape[0], nx = three ? q.shape[2] : q.shape[1];
+    // 2-D problems: (1, ny, nx); 3-D: (nz, ny, nx); the grid path also 1-D
+    // (1, 1, nx); cells per axis (the node layout stores one more per axis)
+    const int nd = P.ndim;
+    const int nz = (nd == 3) ? q.shape[0] : 1;
+    const int ny = (nd == 3) ? q.shape[1] : (nd == 2 ? q.shape[0] : 1);
+    const int nx = q.shape[nd - 1];
+    const int ex = (grid && q.layout == MODIL_NODE) ? 1 : 0;  // extra entry per real axis
     if (nz < 1 || ny < 1 || nx < 1) return fail(MODIL_ERR_ARG, "shape must be positive");
     if (q.n_levels < 1 || q.n_levels > MODIL_MAXL) return fail(MODIL_ERR_ARG, "n_levels");
     const int L = q.n_levels;
-    if ((three && (nz % (1 << (L - 1)))) || (ny % (1 << (L - 1))) || (nx % (1 << (L - 1))))
+    if ((nd == 3 && (nz % (1 << (L - 1)))) || (nd >= 2 && (ny % (1 << (L - 1)))) || (nx % (1 << (L - 1))))
       return fail(MODIL_ERR_ARG, "every axis must be divisible by 2^(n_levels-1)");
     if ((long long)nz * ny * nx > (1LL << 30)) return fail(MODIL_ERR_ARG, "grid too large");
     if (three) {
@@ -196,8 +209,13 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
         }
       }
     if (P.pde == MODIL_PDE_POISSON) {
-      if (q.n_aux != ny * nx || !q.aux) return fail(MODIL_ERR_ARG, "Poisson needs aux[ny * nx] (right-hand side)");
-      if (ny < 2 || nx < 2) return fail(MODIL_ERR_ARG, "Poisson needs >= 2 cells per axis");
+      const long long ent = (long long)(nd == 3 ? nz + ex : 1) * (nd >= 2 ? ny + ex : 1) * (nx + ex);
+      if (q.n_aux != ent || !q.aux)
+        return fail(MODIL_ERR_ARG, "Poisson needs aux[] with one right-hand side value per fine cell or node");
+      if (!ex && ((nd >= 2 && ny < 2) || nx < 2 || (nd == 3 && nz < 2)))
+        return fail(MODIL_ERR_ARG, "Poisson (cell layout) needs >= 2 cells per axis");
+      if (grid && q.n_points > 0)
+        return fail(MODIL_ERR_UNSUPPORTED, "off-grid points: the 2-D cell layout of the Poisson family only");
     }
     if (P.pde == MODIL_PDE_HEAT) {
       if (q.n_aux != nx || !q.aux) return fail(MODIL_ERR_ARG, "heat needs aux[nx] (initial profile)");
@@ -231,12 +249,12 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
     const long long tcap =
         (P.dtype == MODIL_F64 ? kTailCellsF64 : kTailCellsF32) * P.tail.cluster / (kTailC * P.nfield);
     int tail = L;
-    if (!three)
+    if (!three && !grid)
       for (int l = 1; l < L; ++l)
         if ((long long)(ny >> l) * (nx >> l) <= tcap) { tail = l; break; }
     D.tail = tail;
     P.max_tail = std::max(P.max_tail, tail);
-    {
+    if (!grid) {
       size_t tc = 0;
       for (int l = tail; l < L; ++l) tc += (size_t)(ny >> l) * (nx >> l);
       P.tail.tail_cells = std::max(P.tail.tail_cells, tc);
@@ -247,10 +265,27 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
       P.tail.smem_bytes = std::max(P.tail.smem_bytes, tail_instance_bytes(L, tail, nn, P.nfield, P.tail.cluster, (int)P.esz));
     }
     for (int l = 0; l < L; ++l) {
-      ip.n[l][0] = three ? nz >> l : 1;
-      ip.n[l][1] = ny >> l;
-      ip.n[l][2] = nx >> l;
+      ip.n[l][0] = three ? nz >> l : (nd == 3 ? (nz >> l) + ex : 1);
+      ip.n[l][1] = (nd >= 2) ? (ny >> l) + ex : 1;
+      ip.n[l][2] = (nx >> l) + ex;
       int tzl = 1, tyl, txl;
+      if (grid) {
+        // flat blocks of kGridNT cells of every level
+        const long long sz = (long long)ip.n[l][0] * ip.n[l][1] * ip.n[l][2];
+        ip.nt[l][0] = ip.nt[l][1] = 1;
+        ip.nt[l][2] = (int)((sz + kGridNT - 1) / kGridNT);
+        ip.lev_size[l] = sz;
+        for (int a = 0; a < 3; ++a) { D.n[l][a] = ip.n[l][a]; D.nt[l][a] = ip.nt[l][a]; }
+        D.tile_base[l] = (int)P.tile_inst[l].size();
+        if (l == 0) D.ntile0 = ip.nt[l][2];
+        for (int t = 0; t < ip.nt[l][2]; ++t) P.tile_inst[l].push_back(i);
+        if (l == 0 || l + 1 < L)  // composition of this level (l = 0 writes the composed field)
+          for (long long c = 0; c < sz; c += kGridNT) {
+            P.cblk_inst[l].push_back(i);
+            P.cblk_first[l].push_back((int)c);
+          }
+        continue;
+      }
       if (three) {
         tzl = l == 0 ? k3TZ : k3LZ;
         tyl = l == 0 ? k3TY : k3LY;
@@ -281,8 +316,14 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
     D.k_off = koff;
     koff += ip.nk;
     D.aux_off = aoff;
-    aoff += (P.pde == MODIL_PDE_HEAT) ? nx : (P.pde == MODIL_PDE_POISSON ? (long long)ny * nx : 0);
-    if (dom) {
+    aoff += (P.pde == MODIL_PDE_HEAT) ? nx : (P.pde == MODIL_PDE_POISSON ? ip.lev_size[0] : 0);
+    D.layout = q.layout;
+    if (grid) {
+      // [0,1]^d; unused leading axes keep spacing 1
+      D.h[0] = (nd == 3) ? 1.0 / nz : 1.0;
+      D.h[1] = (nd >= 2) ? 1.0 / ny : 1.0;
+      D.h[2] = 1.0 / nx;
+    } else if (dom) {
       D.h[0] = 1.0; D.h[1] = (q.domain_hi[0] - q.domain_lo[0]) / ny; D.h[2] = (q.domain_hi[1] - q.domain_lo[1]) / nx;
     } else if (P.pde == MODIL_PDE_BURGERS) {
       D.h[0] = 1.0; D.h[1] = 1.0 / ny; D.h[2] = 2.0 / nx;
@@ -293,12 +334,13 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
     }
     const double dV = D.h[0] * D.h[1] * D.h[2];
     for (int c = 0; c < 4; ++c) D.coef[c] = q.coef[c];
+
     D.w_res_dV = q.w_res * dV;
     D.w_data_n = (q.n_meas + q.n_points) > 0 ? q.w_data / (q.n_meas + q.n_points) : 0.0;
     D.w_reg = q.w_reg;
     D.lr = q.adam_lr; D.b1 = q.adam_beta1; D.b2 = q.adam_beta2; D.eps = q.adam_eps;
     // pyramid bound of this instance (unclipped worst case, clipped by level size)
-    if (three) {
+    if (three || grid) {
       // composition is level by level (no per-tile pyramid)
     } else {
       const int hu = (P.pde == MODIL_PDE_NS2D) ? 4 : 2;  // halo of the composed field
@@ -337,7 +379,8 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
       if (f < 0 || f >= P.nfield) return fail(MODIL_ERR_ARG, "measurement field out of range");
       if (!std::isfinite(q.meas_value[k])) return fail(MODIL_ERR_ARG, "measurement value not finite");
       const int z = c / (ny * nx), y = (c / nx) % ny, x = c % nx;
-      const int t = P.dev[i].tile_base[0] + ((z / tz) * ip.nt[0][1] + (y / ty3)) * ip.nt[0][2] + (x / tx3);
+      const int t = grid ? P.dev[i].tile_base[0] + c / kGridNT
+                         : P.dev[i].tile_base[0] + ((z / tz) * ip.nt[0][1] + (y / ty3)) * ip.nt[0][2] + (x / tx3);
       all.push_back({t, c, f, q.meas_value[k]});
     }
   }
@@ -506,7 +549,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
   P.o_v = take(8 * P.n_param);
   P.o_g = take(P.esz * P.n_param);
   P.o_uf = take(P.esz * P.n_fine);
-  P.o_wl = take((P.pde == MODIL_PDE_NS3D || P.stream) ? P.esz * P.n_param : 0);
+  P.o_wl = take((P.pde == MODIL_PDE_NS3D || P.stream || P.grid) ? P.esz * P.n_param : 0);
   P.o_kq = take(P.esz * P.n_k);
   P.o_km = take(P.esz * P.n_k);
   P.o_kv = take(8 * P.n_k);
@@ -641,6 +684,27 @@ modil_status run_pass_t(modil_problem* p, Arena<T>& A, int mode, int cur, cudaEv
   const Plan& P = p->plan;
   int k = 0;
   if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+  if (P.grid) {
+    // compose w_{L-2} .. w_0 (level 0: the composed field), the fine kernel,
+    // the restriction chain, the loss terms
+    for (int l = std::max(P.max_lev - 2, 0); l >= 0; --l) {
+      CUDA_TRY(launch_gcompose<T>(A, l, cur, p->stream));
+      if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+    }
+    if (mode != MODE_COMPOSE) {
+      CUDA_TRY(launch_gresid<T>(A, mode, cur, p->stream));
+      if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+      if (mode == MODE_GRAD || mode == MODE_STEP)
+        for (int l = 1; l < P.max_lev; ++l) {
+          CUDA_TRY(launch_grestrict<T>(A, l, mode, cur, p->stream));
+          if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+        }
+      CUDA_TRY(launch_gfinal<T>(A, mode, p->stream));
+      if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+    }
+    if (nev) *nev = k;
+    return MODIL_OK;
+  }
   if (P.pde == MODIL_PDE_NS3D) {
     // compose level by level (coarse to fine), then the fused residual pass
     // (level -1: copy of single-level instances, launched only if the batch has one)
@@ -694,6 +758,7 @@ modil_status run_pass(modil_problem* p, int mode, cudaEvent_t* ev = nullptr, int
 int kernels_per_step(const Plan& P) {
   const int compose3 = (P.max_lev - 1) + (P.min_lev == 1 ? 1 : 0);
   const int compose2 = P.stream ? std::max(P.max_lev - 2, 0) : 0;
+  if (P.grid) return std::max(P.max_lev - 1, 1) + 1 + (P.max_lev - 1) + 1;
   return (P.pde == MODIL_PDE_NS3D ? compose3 + 1 : 1 + compose2) + (P.max_tail - 1) + 1;
 }
 
@@ -908,7 +973,7 @@ modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t ar
   else if (P.pde == MODIL_PDE_NS2D)
     e = P.dtype == MODIL_F64 ? prepare_fine_ns2d<double>(P.cfg, P.pyr_elems)
                              : prepare_fine_ns2d<float>(P.cfg, P.pyr_elems);
-  else if (!P.stream)
+  else if (!P.stream && !P.grid)
     e = P.dtype == MODIL_F64 ? prepare_fine_st<double>(P.pde, P.cfg, P.pyr_elems)
                              : prepare_fine_st<float>(P.pde, P.cfg, P.pyr_elems);
   if (e == cudaSuccess)
@@ -949,6 +1014,10 @@ modil_status modil_level_shape(const modil_problem* p, int instance, int level, 
   if (level < 0 || level >= P.inst[instance].nlev) return fail(MODIL_ERR_ARG, "level out of range");
   if (P.ndim == 3) {
     for (int a = 0; a < 3; ++a) shape[a] = P.inst[instance].n[level][a];
+  } else if (P.ndim == 1) {
+    shape[0] = P.inst[instance].n[level][2];
+    shape[1] = 0;
+    shape[2] = 0;
   } else {
     shape[0] = P.inst[instance].n[level][1];
     shape[1] = P.inst[instance].n[level][2];
@@ -1089,6 +1158,14 @@ modil_status modil_profile_labels(const modil_problem* p, int* kind, int* level,
   if (max_kernels < nk) return fail(MODIL_ERR_ARG, "arrays too short");
   int k = 0;
   auto put = [&](int kd, int lv) { kind[k] = kd; level[k] = lv; ++k; };
+  if (P.grid) {
+    for (int l = std::max(P.max_lev - 2, 0); l >= 0; --l) put(0, l);
+    put(1, 0);
+    for (int l = 1; l < P.max_lev; ++l) put(2, l);
+    put(3, P.max_lev);
+    *n_kernels = k;
+    return MODIL_OK;
+  }
   if (P.pde == MODIL_PDE_NS3D) {
     const int lo = P.min_lev == 1 ? -1 : 0;
     for (int l = P.max_lev - 2; l >= lo; --l) put(0, l);
@@ -1153,7 +1230,7 @@ modil_status modil_set_persistent(modil_problem* p, int on) {
   const Plan& P = p->plan;
   if ((P.pde == MODIL_PDE_NS2D || P.pde == MODIL_PDE_NS3D) && on)
     return fail(MODIL_ERR_UNSUPPORTED, "persistent launch: Burgers/heat only");
-  if (P.stream) return MODIL_OK;  // equal strips, one warp each: nothing to balance
+  if (P.stream || P.grid) return MODIL_OK;  // equal work units: nothing to balance
   int grid = 0;
   if (on) {
     int dev = 0, sms = 0;
@@ -1633,8 +1710,9 @@ extern "C" modil_status modil_eval_grad_noalloc(const modil_desc* desc, const vo
   Plan P;
   modil_status s = make_plan(desc, 1, P, /*allow_stream=*/false);
   if (s != MODIL_OK) return s;
-  if (P.pde == MODIL_PDE_NS3D)
-    return fail(MODIL_ERR_UNSUPPORTED, "the allocation-free entry point takes the 2-D families");
+  if (P.pde == MODIL_PDE_NS3D || P.grid)
+    return fail(MODIL_ERR_UNSUPPORTED, "the allocation-free entry point takes the 2-D families "
+                "(the Poisson family in its 2-D cell layout)");
   if (P.n_points > 0)
     return fail(MODIL_ERR_UNSUPPORTED, "the allocation-free entry point takes no off-grid points");
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -32,6 +32,7 @@ struct DevInst {
   int nlev, nfield, nk, ndim;
   int tail;                    // first level finished by the per-instance tail kernel
   int ntile0;                  // fine tiles of this instance
+  int layout;                  // Poisson: 0 cell, 1 node (n[][] count the nodes)
   int n[MODIL_MAXL][3];        // cells per axis per level, slowest first (2-D: n[l][0] = 1)
   int nt[MODIL_MAXL][3];       // tiles per axis per level
   int tile_base[MODIL_MAXL];   // global tile index of this instance's first tile per level

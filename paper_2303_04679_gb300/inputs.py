@@ -385,25 +385,31 @@ def cavity_workload(n=256, n_levels=8, n_samples=1000, seed=3, Re=100.0):
 # Poisson equation (Section 3.1): the paper's reference solution on [0,1]^2
 # --------------------------------------------------------------------------
 
-def poisson_workload(n=32):
-    """Cell centres of an n x n grid on [0,1]^2, the reference solution
-    u_ref = g(prod_i 5 (1 - x_i) x_i) with g(v) = (v^5 / (1 + v^5))^(1/5), and
-    the right-hand side f = lap(u_ref) from the closed-form derivatives
-    (g' = (1 + v^5)^(-6/5), g'' = -6 v^4 (1 + v^5)^(-11/5)).  The paper takes
-    f from the discrete Laplacian so that u_ref solves the discrete problem
-    exactly; the closed form used here leaves the discretisation error
-    (second order in 1/n) between the discrete solution and u_ref."""
-    c = (np.arange(n) + 0.5) / n
-    y, x = np.meshgrid(c, c, indexing="ij")
-    phx, phy = 5.0 * (1.0 - x) * x, 5.0 * (1.0 - y) * y
-    dphx, dphy = 5.0 - 10.0 * x, 5.0 - 10.0 * y
-    v = phx * phy
+def poisson_workload(n=32, d=2, layout="cell"):
+    """The reference solution u_ref = g(prod_i 5 (1 - x_i) x_i) with
+    g(v) = (v^5 / (1 + v^5))^(1/5) of Section 3.1 on [0,1]^d, at the cell
+    centres (cell layout, n per axis) or the nodes (node layout, n + 1 per
+    axis), and the right-hand side f = lap(u_ref) from the closed-form
+    derivatives (g' = (1 + v^5)^(-6/5), g'' = -6 v^4 (1 + v^5)^(-11/5)).  The
+    paper takes f from the discrete Laplacian so that u_ref solves the
+    discrete problem exactly; the closed form used here leaves the
+    discretisation error (second order in 1/n) between the discrete solution
+    and u_ref."""
+    c = np.arange(n + 1) / n if layout == "node" else (np.arange(n) + 0.5) / n
+    X = np.meshgrid(*([c] * d), indexing="ij")
+    ph = [5.0 * (1.0 - x) * x for x in X]
+    dph = [5.0 - 10.0 * x for x in X]
+    v = np.prod(ph, axis=0)
     g = v / (1.0 + v ** 5) ** 0.2
     g1 = (1.0 + v ** 5) ** -1.2
     g2 = -6.0 * v ** 4 * (1.0 + v ** 5) ** -2.2
-    grad2 = (dphx * phy) ** 2 + (phx * dphy) ** 2
-    lapv = -10.0 * phy - 10.0 * phx
-    return dict(shape=(n, n), u_ref=g, f=g2 * grad2 + g1 * lapv)
+    grad2 = np.zeros_like(v)
+    lapv = np.zeros_like(v)
+    for i in range(d):
+        others = np.prod([ph[j] for j in range(d) if j != i], axis=0) if d > 1 else np.ones_like(v)
+        grad2 += (dph[i] * others) ** 2
+        lapv += -10.0 * others
+    return dict(shape=(n,) * d, u_ref=g, f=g2 * grad2 + g1 * lapv, layout=layout)
 
 
 def uniform_noise(values, amplitude=0.05, seed=0):

@@ -52,7 +52,7 @@ class modil_desc(C.Structure):
         ("point_value", C.POINTER(C.c_double)),
         ("tile", C.c_int * 2),
         ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3),
-        ("point_field", C.POINTER(C.c_int32)),
+        ("point_field", C.POINTER(C.c_int32)), ("layout", C.c_int),
     ]
 
 
@@ -120,12 +120,13 @@ class Desc:
     def __init__(self, pde, shape, n_levels, dtype="f32", coef=(), w_res=1.0, w_data=1.0,
                  w_reg=0.0, meas_cell=None, meas_value=None, meas_field=None, aux=None,
                  knodes=None, lr=5e-3, beta1=0.9, beta2=0.999, eps=1e-8, tile=(0, 0),
-                 points=None, point_value=None, domain=None, point_field=None):
+                 points=None, point_value=None, domain=None, point_field=None, layout="cell"):
         self.kwargs = dict(pde=pde, shape=shape, n_levels=n_levels, dtype=dtype, coef=coef,
                            w_res=w_res, w_data=w_data, w_reg=w_reg, meas_cell=meas_cell,
                            meas_value=meas_value, meas_field=meas_field, aux=aux, knodes=knodes,
                            lr=lr, beta1=beta1, beta2=beta2, eps=eps, tile=tile, points=points,
-                           point_value=point_value, domain=domain, point_field=point_field)
+                           point_value=point_value, domain=domain, point_field=point_field,
+                           layout=layout)
         self.pde = {"burgers": PDE_BURGERS, "heat": PDE_HEAT, "ns2d": PDE_NS2D,
                     "ns3d": PDE_NS3D, "poisson": PDE_POISSON}.get(pde, pde)
         self.dtype = {"f32": F32, "f64": F64}.get(dtype, dtype)
@@ -172,6 +173,8 @@ class Desc:
         d.point_coord = _dptr(self._pts, C.c_double)
         d.point_value = _dptr(self._pval, C.c_double)
         d.point_field = _dptr(self._pfield, C.c_int32)
+        self.layout = {"cell": 0, "node": 1}.get(layout, layout)
+        d.layout = self.layout
         d.tile[0], d.tile[1] = int(tile[0]), int(tile[1])
         if domain is not None:  # ((lo, hi) per axis, slowest first)
             for a, (lo, hi) in enumerate(domain):
@@ -190,10 +193,11 @@ class Desc:
         """Unknowns of the levels: fields x sum over levels of the cells of each
         level (every axis halved per level)."""
         per_field = 0
+        extra = 1 if getattr(self, "layout", 0) == 1 else 0
         for lvl in range(self.n_levels):
             n = 1
             for s in self.shape:
-                n *= s >> lvl
+                n *= (s >> lvl) + extra
             per_field += n
         return self.n_fields * per_field
 
@@ -260,7 +264,7 @@ class Problem:
     def level_shape(self, level, instance=0):
         s = (C.c_int * 3)()
         _check(LIB.modil_level_shape(self._h, instance, level, s))
-        return (s[0], s[1], s[2]) if s[2] else (s[0], s[1])
+        return tuple(v for v in (s[0], s[1], s[2]) if v)
 
     def n_levels(self, instance=0):
         return self.descs[instance].n_levels

@@ -381,7 +381,10 @@ def test_poisson_laplacian_exact_on_biquadratics(layout):
 
 
 def _quadratic_minimiser(p, shape):
-    """Minimiser of a quadratic loss from its exact gradient: H u = -g(0)."""
+    """Minimiser of a quadratic loss from its exact gradient: H u = -g(0)
+    (least squares: in the node layout the boundary nodes hold the Dirichlet
+    value and do not enter the loss, so their rows of H vanish and the
+    minimum-norm minimiser keeps them at 0)."""
     n = int(np.prod(shape))
     g0 = o.loss_grad_fine(p, np.zeros(shape))[1].reshape(-1)
     H = np.empty((n, n))
@@ -389,7 +392,28 @@ def _quadratic_minimiser(p, shape):
         e = np.zeros(n)
         e[j] = 1.0
         H[:, j] = o.loss_grad_fine(p, e.reshape(shape))[1].reshape(-1) - g0
-    return np.linalg.solve(H, -g0).reshape(shape)
+    return np.linalg.lstsq(H, -g0, rcond=None)[0].reshape(shape)
+
+
+def test_poisson_node_boundary_holds_the_dirichlet_value():
+    """Section 3.1: in the node layout the Dirichlet value is imposed on the
+    boundary nodes themselves: whatever the field holds there, the stencil
+    reads 0, the boundary values do not change the loss and get no gradient;
+    the residual lives at the (N - 1)^d interior nodes."""
+    rng = np.random.default_rng(14)
+    n = 8
+    u = rng.normal(size=(n + 1, n + 1))
+    f = rng.normal(size=(n + 1, n + 1))
+    p = o.Problem("poisson", (n, n), 1, layout="node", coef={"f": f})
+    v = u.copy()
+    v[0, :] += 3.0
+    v[:, -1] -= 1.5
+    assert o.poisson_residual(u, f, (1 / n, 1 / n), "node").shape == (n - 1, n - 1)
+    assert o.loss_terms(p, u)["total"] == o.loss_terms(p, v)["total"]
+    g = o.loss_grad_fine(p, u)[1]
+    edge = np.ones_like(g, dtype=bool)
+    edge[1:-1, 1:-1] = False
+    assert np.all(g[edge] == 0.0) and np.any(g[~edge] != 0.0)
 
 
 @pytest.mark.parametrize("layout", ["cell", "node"])
