@@ -19,6 +19,7 @@ constexpr int kTileCfg[kNumTileCfg][2] = {{16, 32}, {16, 64}, {8, 64}, {32, 32},
 constexpr int kStreamCfg = 6;
 constexpr int kSR = 32, kSW = 28;
 constexpr int kStreamNT = 128;   // threads per block of the streaming kernel (one strip per warp)
+constexpr int kStreamMinStrips = 4 * 152;  // default to the streaming kernel from this many strips
 constexpr int kComposeNT = 256;  // threads (cells) per block of the 2-D composition pass
 constexpr int kGridNT = 256;     // threads (cells) per block of the d-dimensional Poisson kernels
 // Tile of the restriction kernels (coarse levels), rows x cols.

@@ -135,8 +135,15 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
   if (ty == 0 && tx == 0) {
     ty = (P.pde == MODIL_PDE_NS2D) ? 8 : 16;
     tx = 32;
-    // Burgers: the warp-streaming kernel unless off-grid points need the tile kernel
-    if (P.pde == MODIL_PDE_BURGERS && !any_points && allow_stream) {
+    // Burgers: the warp-streaming kernel (one warp per strip) when the batch
+    // has enough strips to fill the GPU and no off-grid points need the tile
+    // kernel; small grids keep the tile kernel's 256 threads per tile
+    long long strips = 0;
+    for (int i = 0; i < n; ++i) {
+      const int sy = d[i].shape[0], sx = d[i].shape[1];
+      strips += (long long)((sy + kSR - 1) / kSR) * ((sx + kSW - 1) / kSW);
+    }
+    if (P.pde == MODIL_PDE_BURGERS && !any_points && allow_stream && strips >= kStreamMinStrips) {
       ty = kSR;
       tx = kSW;
     }

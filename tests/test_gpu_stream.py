@@ -1,5 +1,6 @@
 """The warp-streaming Burgers kernel (32-row x 28-column strips, one warp
-each; the default for Burgers problems without off-grid points) against the
+each; the default for Burgers problems and batches of at least 608 strips
+without off-grid points, requested here with tile (32, 28)) against the
 FP64 oracle on grids whose strips are ragged in both directions, on one-row
 and one-column coarse levels and single-level problems; against the tile
 kernel on the same problem; Adam trajectories in FP64; a batch of uneven
@@ -35,7 +36,7 @@ SHAPES = [((72, 100), 3), ((96, 56), 4), ((2, 64), 2), ((64, 2), 2), ((16, 40), 
 @pytest.mark.parametrize("shape,L", SHAPES)
 def test_stream_loss_grad(modil, shape, L, dtype):
     c = Case("burgers", shape, L, dtype, seed=70, n_meas=max(3, shape[0] * shape[1] // 40), nu=0.02,
-             duplicate=2)
+             duplicate=2, tile=(32, 28))
     with modil.Problem(c.desc()) as p:
         labels = p.profile_labels()
         assert labels[:max(L - 2, 0) + 1] == [f"compose_L{l}" for l in range(L - 2, 0, -1)] + ["fine"]
@@ -62,7 +63,7 @@ def test_stream_matches_tile_kernel(modil):
 
 
 def test_stream_adam_f64_matches_oracle(modil):
-    c = Case("burgers", (72, 100), 3, "f64", seed=72, n_meas=150, lr=5e-3, nu=0.01)
+    c = Case("burgers", (72, 100), 3, "f64", seed=72, n_meas=150, lr=5e-3, nu=0.01, tile=(32, 28))
     st = o.OracleState.zeros_like_levels(c.levels)
     with modil.Problem(c.desc()) as p:
         c.load(p)
@@ -78,8 +79,8 @@ def test_stream_adam_f64_matches_oracle(modil):
 def test_stream_batch_equals_single_bitwise(modil):
     specs = [((64, 512), 4, 0.01), ((512, 64), 4, 0.002), ((128, 128), 5, 0.05), ((256, 64), 4, 0.02),
              ((64, 64), 4, 0.1), ((72, 100), 3, 0.03)]
-    cases = [Case("burgers", s, L, "f32", seed=80 + i, n_meas=max(1, s[0] * s[1] // 200), nu=nu)
-             for i, (s, L, nu) in enumerate(specs)]
+    cases = [Case("burgers", s, L, "f32", seed=80 + i, n_meas=max(1, s[0] * s[1] // 200), nu=nu,
+                  tile=(32, 28)) for i, (s, L, nu) in enumerate(specs)]
     with modil.Problem([c.desc() for c in cases]) as p:
         for i, c in enumerate(cases):
             c.load(p, instance=i)
