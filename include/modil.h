@@ -156,6 +156,18 @@ typedef struct {
   int layout;                 /* POISSON: MODIL_CELL (0, values at cell
                                  centres) or MODIL_NODE (1, values at the N + 1
                                  nodes per axis); the other families: 0       */
+  int k_fixed;                /* HEAT: nonzero = the conductivity is known (the
+                                 forward problem that makes a reference record,
+                                 Section 3.4): the nodes stay at `knodes`, dL/dq
+                                 reads as zero and no optimiser moves them;
+                                 the other families: 0 (else MODIL_ERR_ARG)    */
+  double k_scale;             /* HEAT: the unit in which the optimisers move the
+                                 conductivity nodes (a diagonal preconditioner:
+                                 Adam's node step is adam_lr * k_scale, L-BFGS
+                                 works on q / k_scale); 0 = 1.  The nodes are
+                                 ~0.02 where the temperatures are ~1, so an
+                                 unscaled step overshoots them.  The other
+                                 families: 0 (else MODIL_ERR_ARG)             */
 } modil_desc;
 
 /* Device bytes needed for a batch of n problems described by descs[0..n-1]. */
@@ -315,15 +327,18 @@ modil_status modil_eval_grad_noalloc(const modil_desc* desc, const void* levels,
  * or g.d >= 0); a pair is kept only when s.y > 1e-12 y.y.  Vectors live on
  * the device in the problem's dtype; dot products are reduced in FP64 in a
  * fixed order; the loss and gradient are the problem's own kernels.
- *   modil_lbfgs_create: single-instance problems whose unknowns are their
- *     levels (Burgers, cavity, body, Poisson; not heat, whose conductivity nodes are
- *     unknowns too: MODIL_ERR_UNSUPPORTED).  Allocates (2 history + 6) level
- *     vectors of device memory.  The optimiser keeps a pointer to p, which
- *     must outlive it.
- *   modil_lbfgs_run: continues from the problem's current levels (the pair
- *     history is kept across calls) for up to `iterations` iterations; writes
- *     the final levels and their gradient back into the problem (readable
- *     with modil_read_level / modil_read_grad; Adam's state is untouched).
+ *   modil_lbfgs_create: single-instance problems (MODIL_ERR_UNSUPPORTED for
+ *     a batch).  The unknowns are the levels of every field and, for the heat
+ *     problem without k_fixed, its conductivity nodes after them (the pass
+ *     reads the nodes from, and writes their gradient to, the problem's node
+ *     arrays; Adam's node moments are untouched).  Allocates (2 history + 6)
+ *     vectors of the unknowns in device memory.  The optimiser keeps a
+ *     pointer to p, which must outlive it.
+ *   modil_lbfgs_run: continues from the problem's current levels (and nodes;
+ *     the pair history is kept across calls) for up to `iterations`
+ *     iterations; writes the final levels (and nodes) and their gradient
+ *     back into the problem (readable with modil_read_level / modil_read_grad
+ *     / modil_read_knodes / modil_read_kgrad; Adam's state is untouched).
  *     loss: host output of iterations + 1 doubles or NULL: the loss at the
  *     start and after each completed iteration.  done: iterations completed.
  *     Synchronises the problem's stream (the line search reads the loss). */
@@ -346,6 +361,10 @@ const char* modil_last_error(void);
 
 /* Library version string. */
 const char* modil_version(void);
+
+/* sizeof(modil_desc) as this library was compiled: a binding checks it
+ * against its own copy of the struct before the first call. */
+size_t modil_desc_size(void);
 
 #ifdef __cplusplus
 }

@@ -205,6 +205,13 @@ class Problem:
     domain_bounds: tuple = None
     # field sampled at each off-grid point (multi-field problems; None: 0)
     point_field: np.ndarray = None
+    # heat: the conductivity is known (the forward problem that makes the
+    # reference record of Section 3.4): q is a fixed input, dL/dq is zero and
+    # the optimiser moves only the levels
+    k_fixed: bool = False
+    # heat: the unit of the optimiser's steps on the nodes (Adam's node step
+    # is lr * k_scale; a diagonal preconditioner, not part of the loss)
+    k_scale: float = 1.0
 
     @property
     def n_fields(self):
@@ -849,7 +856,7 @@ def loss_grad_fine(p, u, q=None):
     elif p.pde == "heat":
         r = heat_residual(u, q, h[0], h[1], p.aux)
         g, gq = _heat_adjoint(u, q, 2.0 * p.w_res * dV * r, h[0], h[1])
-        gq = gq + p.w_reg * _heat_reg(q)[1]
+        gq = np.zeros_like(q) if p.k_fixed else gq + p.w_reg * _heat_reg(q)[1]
     elif p.pde == "poisson":
         r = poisson_residual(u, p.coef["f"], h, p.layout)
         g = _poisson_adjoint(u, 2.0 * p.w_res * dV * r, h, p.layout)
@@ -940,7 +947,7 @@ def oracle_step(p, st, lr, b1=0.9, b2=0.999, eps=1e-8):
         st.levels[i], st.m[i], st.v[i] = adam_step(st.levels[i], st.m[i], st.v[i],
                                                    g, st.t, lr, b1, b2, eps)
     if st.q is not None:
-        st.q, st.mq, st.vq = adam_step(st.q, st.mq, st.vq, gq, st.t, lr, b1, b2, eps)
+        st.q, st.mq, st.vq = adam_step(st.q, st.mq, st.vq, gq, st.t, lr * p.k_scale, b1, b2, eps)
     return terms
 
 

@@ -440,11 +440,15 @@ k_tail(const __grid_constant__ Arena<T> A, int mode, int cur) {
     }
     if (mode != MODE_LOSS)
       for (int j = tid; j < nk; j += kTailNT) {
-        const AdamCoef ac = acS;
+        AdamCoef ac = acS;  // the nodes move in units of k_scale
+        ac.lr *= D.k_scale;
+        ac.lrf = (float)ac.lr;
         // d/dq_j of w_reg * sum_i d2_i^2 = 2 w_reg (d2_{j-1} - 2 d2_j + d2_{j+1})
         const double dm = (j >= 1) ? d2s[j - 1] : 0.0;
         const double dp = (j + 1 < MODIL_MAXK) ? d2s[j + 1] : 0.0;
-        const double g = chunk[2 + j] + 2.0 * D.w_reg * (dm - 2.0 * d2s[j] + dp);
+        // known conductivity (forward problem): no gradient, so Adam keeps q
+        // (m and v stay 0) and L-BFGS directions have no q component
+        const double g = D.k_fixed ? 0.0 : chunk[2 + j] + 2.0 * D.w_reg * (dm - 2.0 * d2s[j] + dp);
         A.kg[D.k_off + j] = (T)g;
         if (mode == MODE_STEP) {
           T p = (T)qs[j];

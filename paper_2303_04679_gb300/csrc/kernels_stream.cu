@@ -1,11 +1,11 @@
 // Warp-streaming fine kernel of the viscous Burgers problem (paper Section
 // 3.2; axes (t, x)) and the level-by-level composition pass it reads.
 //
-// Composition pass (k_compose2, one launch per level l = L-2 .. 1, coarse to
-// fine): w_l = u_l + T_l w_{l+1} on every cell of level l of every instance,
-// w_{L-1} = u_{L-1} (Horner's scheme of Section 2.2, T the tensor product of
-// the cell-based 1-D interpolation), stored in the scratch arrays wl at the
-// offsets of the levels.
+// Composition pass, coarse to fine: w_l = u_l + T_l w_{l+1}, w_{L-1} = u_{L-1}
+// (Horner's scheme of Section 2.2, T the tensor product of the cell-based 1-D
+// interpolation), stored in the scratch arrays wl at the offsets of the
+// levels: levels L-2 .. 2 of each instance by one block (k_compose2_small),
+// then level 1 of every instance in one grid (k_compose2).
 //
 // Fine kernel (k_fine_stream): one warp owns a strip of kSW = 28 columns and
 // kSR = 32 rows of the fine grid.  Lane j holds column x = x0 - 2 + j, so the
@@ -56,24 +56,11 @@ __device__ __forceinline__ T eo_flux_s(T a, T b, T& da, T& db) {
 }
 
 // ---------------------------------------------------------------------------
-// Composition of one level of every instance that has a coarser level
+// Composition: one cell of w_l = u_l + T w_{l+1}
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(kComposeNT) k_compose2(const __grid_constant__ Arena<T> A, int l, int cur) {
-  const int b = blockIdx.x;
-  const int ii = (A.n_inst == 1) ? 0 : A.cblk_inst[l][b];
-  const DevInst& D = (A.n_inst == 1) ? A.inst0 : A.inst[ii];
-  const int ny = D.n[l][1], nx = D.n[l][2];
-  const int nyc = D.n[l + 1][1], nxc = D.n[l + 1][2];
-  const long long cell = (long long)A.cblk_first[l][b] + threadIdx.x;
-  // the levels are written by the previous step's last kernels and, for
-  // w_{l+1}, by the previous launch
-  pdl_wait();
-  pdl_trigger();
-  if (cell >= (long long)ny * nx) return;
-  const int y = (int)(cell / nx), x = (int)(cell - (long long)y * nx);
-  const T* __restrict__ P = A.p[cur];
-  const T* __restrict__ Wc = (l + 1 == D.nlev - 1) ? P + D.off[0][l + 1] : A.wl + D.off[0][l + 1];
+__device__ __forceinline__ T compose_cell(const T* __restrict__ Pl, const T* __restrict__ Wc, int y, int x,
+                                          int nx, int nyc, int nxc) {
   int jy0, jy1, jx0, jx1;
   T wy0, wy1, wx0, wx1;
   prolong_taps<T>(y, nyc, jy0, jy1, wy0, wy1);
@@ -81,7 +68,64 @@ __global__ void __launch_bounds__(kComposeNT) k_compose2(const __grid_constant__
   const T* r0 = Wc + (long long)jy0 * nxc;
   const T* r1 = Wc + (long long)jy1 * nxc;
   const T c = wy0 * (wx0 * r0[jx0] + wx1 * r0[jx1]) + wy1 * (wx0 * r1[jx0] + wx1 * r1[jx1]);
-  A.wl[D.off[0][l] + cell] = P[D.off[0][l] + cell] + c;
+  return Pl[(long long)y * nx + x] + c;
+}
+
+// Level 1 of every instance with L >= 3: four consecutive cells of a row per
+// thread (16-byte load and store where the row and the level start allow).
+template <class T>
+__global__ void __launch_bounds__(kComposeNT) k_compose2(const __grid_constant__ Arena<T> A, int l, int cur) {
+  const int b = blockIdx.x;
+  const int ii = (A.n_inst == 1) ? 0 : A.cblk_inst[l][b];
+  const DevInst& D = (A.n_inst == 1) ? A.inst0 : A.inst[ii];
+  const int ny = D.n[l][1], nx = D.n[l][2];
+  const int nyc = D.n[l + 1][1], nxc = D.n[l + 1][2];
+  const long long cell = (long long)A.cblk_first[l][b] + 4 * threadIdx.x;
+  // the levels are written by the previous step's last kernels and, for
+  // w_{l+1}, by the previous launch
+  pdl_wait();
+  pdl_trigger();
+  const long long ncell = (long long)ny * nx;
+  if (cell >= ncell) return;
+  const T* __restrict__ P = A.p[cur];
+  const T* __restrict__ Pl = P + D.off[0][l];
+  const T* __restrict__ Wc = (l + 1 == D.nlev - 1) ? P + D.off[0][l + 1] : A.wl + D.off[0][l + 1];
+  T* __restrict__ Wl = A.wl + D.off[0][l];
+  const int y = (int)(cell / nx), x = (int)(cell - (long long)y * nx);
+  if (sizeof(T) == 4 && (nx & 3) == 0 && ((D.off[0][l] + cell) & 3) == 0) {
+    T v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = compose_cell<T>(Pl, Wc, y, x + k, nx, nyc, nxc);
+    *reinterpret_cast<float4*>(Wl + cell) = make_float4(v[0], v[1], v[2], v[3]);
+    return;
+  }
+  for (int k = 0; k < 4 && cell + k < ncell; ++k) {
+    const int yy = (int)((cell + k) / nx), xx = (int)((cell + k) - (long long)yy * nx);
+    Wl[cell + k] = compose_cell<T>(Pl, Wc, yy, xx, nx, nyc, nxc);
+  }
+}
+
+// Levels L-2 .. 2 of one instance per block, coarse to fine, a barrier
+// between levels (the block's own writes of w_{l+1} are then visible).
+template <class T>
+__global__ void __launch_bounds__(kComposeSmallNT) k_compose2_small(const __grid_constant__ Arena<T> A, int cur) {
+  const int ii = (A.n_inst == 1) ? 0 : A.csmall_inst[blockIdx.x];
+  const DevInst& D = (A.n_inst == 1) ? A.inst0 : A.inst[ii];
+  pdl_wait();
+  pdl_trigger();
+  const T* __restrict__ P = A.p[cur];
+  for (int l = D.nlev - 2; l >= 2; --l) {
+    const int ny = D.n[l][1], nx = D.n[l][2];
+    const int nyc = D.n[l + 1][1], nxc = D.n[l + 1][2];
+    const T* __restrict__ Wc = (l + 1 == D.nlev - 1) ? P + D.off[0][l + 1] : A.wl + D.off[0][l + 1];
+    const T* __restrict__ Pl = P + D.off[0][l];
+    T* __restrict__ Wl = A.wl + D.off[0][l];
+    for (int c = threadIdx.x; c < ny * nx; c += kComposeSmallNT) {
+      const int y = c / nx, x = c - y * nx;
+      Wl[c] = compose_cell<T>(Pl, Wc, y, x, nx, nyc, nxc);
+    }
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -354,8 +398,13 @@ static cudaLaunchConfig_t pdl_cfg(dim3 grid, dim3 block, cudaStream_t s, cudaLau
 
 template <class T>
 cudaError_t launch_compose2(const Arena<T>& A, int level, int cur, cudaStream_t s) {
-  if (A.ncblk[level] == 0) return cudaSuccess;
   cudaLaunchAttribute at[1];
+  if (level >= 2) {  // every level from 2 up, one block per instance
+    if (A.ncsmall == 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = pdl_cfg(dim3(A.ncsmall), dim3(kComposeSmallNT), s, at);
+    return cudaLaunchKernelEx(&cfg, k_compose2_small<T>, A, cur);
+  }
+  if (A.ncblk[level] == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = pdl_cfg(dim3(A.ncblk[level]), dim3(kComposeNT), s, at);
   return cudaLaunchKernelEx(&cfg, k_compose2<T>, A, level, cur);
 }

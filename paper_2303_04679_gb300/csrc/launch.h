@@ -20,7 +20,8 @@ constexpr int kStreamCfg = 6;
 constexpr int kSR = 32, kSW = 28;
 constexpr int kStreamNT = 128;   // threads per block of the streaming kernel (one strip per warp)
 constexpr int kStreamMinStrips = 4 * 152;  // default to the streaming kernel from this many strips
-constexpr int kComposeNT = 256;  // threads (cells) per block of the 2-D composition pass
+constexpr int kComposeNT = 256;  // threads per block of the level-1 composition (4 cells each)
+constexpr int kComposeSmallNT = 512;  // threads per block composing levels >= 2 of one instance
 constexpr int kGridNT = 256;     // threads (cells) per block of the d-dimensional Poisson kernels
 // Tile of the restriction kernels (coarse levels), rows x cols.
 constexpr int kLevTY = 8, kLevTX = 32;

@@ -63,6 +63,13 @@ __global__ void k_axpby(T* __restrict__ z, const T* __restrict__ x, const T* __r
     z[i] = (T)fma(a, (double)y[i], (double)x[i]);
 }
 
+// z = a * x (host coefficient).
+template <class T>
+__global__ void k_mul(T* __restrict__ z, const T* __restrict__ x, double a, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = (T)(a * (double)x[i]);
+}
+
 // z = x - y.
 template <class T>
 __global__ void k_sub(T* __restrict__ z, const T* __restrict__ x, const T* __restrict__ y, long long n) {
@@ -103,6 +110,12 @@ cudaError_t lb_axpby(T* z, const T* x, const T* y, double a, long long n, cudaSt
 }
 
 template <class T>
+cudaError_t lb_mul(T* z, const T* x, double a, long long n, cudaStream_t s) {
+  k_mul<T><<<vec_grid(n), 256, 0, s>>>(z, x, a, n);
+  return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t lb_sub(T* z, const T* x, const T* y, long long n, cudaStream_t s) {
   k_sub<T><<<vec_grid(n), 256, 0, s>>>(z, x, y, n);
   return cudaGetLastError();
@@ -117,6 +130,7 @@ int lb_dot_partials() { return kDotBlocks; }
                                   cudaStream_t);                                                       \
   template cudaError_t lb_scale<T>(T*, const T*, const double*, const double*, long long, cudaStream_t); \
   template cudaError_t lb_axpby<T>(T*, const T*, const T*, double, long long, cudaStream_t);         \
+  template cudaError_t lb_mul<T>(T*, const T*, double, long long, cudaStream_t);                    \
   template cudaError_t lb_sub<T>(T*, const T*, const T*, long long, cudaStream_t);
 MODIL_LB_INST(float)
 MODIL_LB_INST(double)

@@ -21,6 +21,9 @@ cudaError_t lb_axpby(T* z, const T* x, const T* y, double a, long long n, cudaSt
 // z = x - y.
 template <class T>
 cudaError_t lb_sub(T* z, const T* x, const T* y, long long n, cudaStream_t s);
+// z = a * x
+template <class T>
+cudaError_t lb_mul(T* z, const T* x, double a, long long n, cudaStream_t s);
 int lb_dot_partials();
 
 }  // namespace modil

@@ -84,8 +84,8 @@ struct Plan {
   size_t pyr_elems = 0;
   bool stream = false;     // warp-streaming fine kernel and composition pass (Burgers)
   bool grid = false;       // Poisson in d = 1, 3 or the node layout: one kernel per step
-  std::vector<int> cblk_inst[MODIL_MAXL], cblk_first[MODIL_MAXL];
-  size_t o_cbi[MODIL_MAXL], o_cbf[MODIL_MAXL];
+  std::vector<int> cblk_inst[MODIL_MAXL], cblk_first[MODIL_MAXL], csmall_inst;
+  size_t o_cbi[MODIL_MAXL], o_cbf[MODIL_MAXL], o_csm;
   // arena offsets (bytes)
   size_t o_p0, o_p1, o_m, o_v, o_g, o_uf, o_wl, o_kq, o_km, o_kv, o_kg, o_aux, o_part, o_rptr, o_rcell,
       o_rfield, o_rbeg, o_mval, o_rv0, o_inst, o_st, o_cnt, o_q, o_ti[MODIL_MAXL], total;
@@ -169,6 +169,10 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
     const modil_desc& q = d[i];
     if (q.pde != P.pde || q.dtype != P.dtype || q.ndim != P.ndim || q.layout != d[0].layout)
       return fail(MODIL_ERR_ARG, "a batch must share pde, dtype, ndim and layout");
+    if (q.k_fixed && q.pde != MODIL_PDE_HEAT)
+      return fail(MODIL_ERR_ARG, "k_fixed: only the heat family has conductivity nodes");
+    if (!(q.k_scale >= 0.0 && q.k_scale < HUGE_VAL) || (q.k_scale != 0.0 && q.pde != MODIL_PDE_HEAT))
+      return fail(MODIL_ERR_ARG, "k_scale: a finite value >= 0, for the heat family only");
     if (q.tile[0] != d[0].tile[0] || q.tile[1] != d[0].tile[1])
       return fail(MODIL_ERR_ARG, "a batch must share the tile shape");
     // 2-D problems: (1, ny, nx); 3-D: (nz, ny, nx); the grid path also 1-D
@@ -207,14 +211,17 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
       if (!(q.coef[0] > 0)) return fail(MODIL_ERR_ARG, "NS2D needs coef[0] = Re > 0");
       if (!(q.coef[1] >= 0)) return fail(MODIL_ERR_ARG, "NS2D needs coef[1] = tau factor >= 0");
     }
-    if (P.stream)  // composition pass: levels 1 .. L-2, kComposeNT cells per block
-      for (int l = 1; l + 1 < L; ++l) {
-        const long long cells = (long long)(ny >> l) * (nx >> l);
-        for (long long c = 0; c < cells; c += kComposeNT) {
-          P.cblk_inst[l].push_back(i);
-          P.cblk_first[l].push_back((int)c);
+    if (P.stream) {  // composition pass: level 1 in blocks of 4 kComposeNT cells,
+                     // levels 2 .. L-2 one block per instance
+      if (L >= 3) {
+        const long long cells = (long long)(ny >> 1) * (nx >> 1);
+        for (long long c = 0; c < cells; c += 4 * kComposeNT) {
+          P.cblk_inst[1].push_back(i);
+          P.cblk_first[1].push_back((int)c);
         }
       }
+      if (L >= 4) P.csmall_inst.push_back(i);
+    }
     if (P.pde == MODIL_PDE_POISSON) {
       const long long ent = (long long)(nd == 3 ? nz + ex : 1) * (nd >= 2 ? ny + ex : 1) * (nx + ex);
       if (q.n_aux != ent || !q.aux)
@@ -345,6 +352,8 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
     D.w_res_dV = q.w_res * dV;
     D.w_data_n = (q.n_meas + q.n_points) > 0 ? q.w_data / (q.n_meas + q.n_points) : 0.0;
     D.w_reg = q.w_reg;
+    D.k_fixed = q.k_fixed != 0;
+    D.k_scale = q.k_scale > 0.0 ? q.k_scale : 1.0;
     D.lr = q.adam_lr; D.b1 = q.adam_beta1; D.b2 = q.adam_beta2; D.eps = q.adam_eps;
     // pyramid bound of this instance (unclipped worst case, clipped by level size)
     if (three || grid) {
@@ -591,6 +600,7 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
     P.o_cbi[l] = take(4 * P.cblk_inst[l].size());
     P.o_cbf[l] = take(4 * P.cblk_first[l].size());
   }
+  P.o_csm = take(4 * P.csmall_inst.size());
   P.total = o;
   return MODIL_OK;
 }
@@ -662,6 +672,8 @@ void fill_arena(modil_problem* p, Arena<T>& A) {
     A.cblk_first[l] = reinterpret_cast<const int*>(b + P.o_cbf[l]);
     A.ncblk[l] = (int)P.cblk_inst[l].size();
   }
+  A.csmall_inst = reinterpret_cast<const int*>(b + P.o_csm);
+  A.ncsmall = (int)P.csmall_inst.size();
   A.npart = P.npart;
   A.n_inst = P.n_inst;
   A.gscale = 1.0f;
@@ -730,9 +742,13 @@ modil_status run_pass_t(modil_problem* p, Arena<T>& A, int mode, int cur, cudaEv
   } else if (P.pde == MODIL_PDE_NS2D) {
     CUDA_TRY(launch_fine_ns2d<T>(A, P.cfg, mode, cur, P.pyr_elems, p->stream));
   } else if (P.stream) {
-    // compose w_{L-2} .. w_1 (coarse to fine), then the streaming fine kernel
-    for (int l = P.max_lev - 2; l >= 1; --l) {
-      CUDA_TRY(launch_compose2<T>(A, l, cur, p->stream));
+    // compose w_{L-2} .. w_2 (one launch), w_1, then the streaming fine kernel
+    if (P.max_lev >= 4) {
+      CUDA_TRY(launch_compose2<T>(A, 2, cur, p->stream));
+      if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
+    }
+    if (P.max_lev >= 3) {
+      CUDA_TRY(launch_compose2<T>(A, 1, cur, p->stream));
       if (ev) CUDA_TRY(cudaEventRecord(ev[k++], p->stream));
     }
     CUDA_TRY(launch_fine_stream<T>(A, mode, cur, p->stream));
@@ -764,7 +780,7 @@ modil_status run_pass(modil_problem* p, int mode, cudaEvent_t* ev = nullptr, int
 
 int kernels_per_step(const Plan& P) {
   const int compose3 = (P.max_lev - 1) + (P.min_lev == 1 ? 1 : 0);
-  const int compose2 = P.stream ? std::max(P.max_lev - 2, 0) : 0;
+  const int compose2 = P.stream ? (P.max_lev >= 4 ? 1 : 0) + (P.max_lev >= 3 ? 1 : 0) : 0;
   if (P.grid) return std::max(P.max_lev - 1, 1) + 1 + (P.max_lev - 1) + 1;
   return (P.pde == MODIL_PDE_NS3D ? compose3 + 1 : 1 + compose2) + (P.max_tail - 1) + 1;
 }
@@ -972,6 +988,7 @@ modil_status modil_create(const modil_desc* descs, int n, void* arena, size_t ar
     st = upload(p, P.o_cbi[l], P.cblk_inst[l].data(), 4 * P.cblk_inst[l].size());
     if (st == MODIL_OK) st = upload(p, P.o_cbf[l], P.cblk_first[l].data(), 4 * P.cblk_first[l].size());
   }
+  if (st == MODIL_OK) st = upload(p, P.o_csm, P.csmall_inst.data(), 4 * P.csmall_inst.size());
   if (st != MODIL_OK) return bail(st);
   e = P.dtype == MODIL_F64 ? launch_reset<double>(p->A64, p->stream) : launch_reset<float>(p->A32, p->stream);
   if (e != cudaSuccess) return bail(fail(MODIL_ERR_CUDA, cudaGetErrorString(e)));
@@ -1177,7 +1194,8 @@ modil_status modil_profile_labels(const modil_problem* p, int* kind, int* level,
     const int lo = P.min_lev == 1 ? -1 : 0;
     for (int l = P.max_lev - 2; l >= lo; --l) put(0, l);
   } else if (P.stream) {
-    for (int l = P.max_lev - 2; l >= 1; --l) put(0, l);
+    if (P.max_lev >= 4) put(0, 2);  // levels 2 .. L-2
+    if (P.max_lev >= 3) put(0, 1);
   }
   put(1, 0);
   for (int l = 1; l < P.max_tail; ++l) put(2, l);
@@ -1362,7 +1380,10 @@ modil_status modil_reset_optimizer(modil_problem* p) {
 struct modil_lbfgs {
   modil_problem* p = nullptr;
   int m = 0;                 // pairs kept
-  long long n = 0;           // parameters (all fields and levels)
+  long long n = 0;           // unknowns: the levels, then the heat conductivity nodes
+  long long nl = 0;          // of which the levels (all fields)
+  int nk = 0;                // and the conductivity nodes (heat without k_fixed; else 0)
+  double ks = 1.0;           // the vector holds the nodes in units of k_scale
   void* vec = nullptr;       // device: S[m], Y[m], then 6 work vectors, problem dtype
   double* dsc = nullptr;     // device: dot partials, rho[m], alpha[m], sy[m], yy[m], beta, scratch
   std::vector<int> order;    // slots of the stored pairs, oldest first
@@ -1405,11 +1426,18 @@ modil_status lbfgs_run_t(modil_lbfgs* o, int iters, double* loss, int* done) {
   double* tmp = beta + 1;
   Arena<T>& A = arena_of<T>(p);
   T* pc = A.p[p->steps & 1];  // the problem's current levels
+  const long long nl = o->nl;
+  const size_t kb = sizeof(T) * (size_t)o->nk;
+  const double ks = o->ks;
   double terms[MODIL_NTERMS];
   // loss (and gradient) at lv; a non-finite loss of a trial point counts as
-  // +inf (the line search backs off) and the problem's latch is cleared
+  // +inf (the line search backs off) and the problem's latch is cleared.  The
+  // conductivity nodes (the vector's tail) go through the problem's own node
+  // array: written before the pass, their gradient read after it.
   auto eval = [&](T* lv, T* gr, double* f) -> modil_status {
+    if (kb) CUDA_TRY(lb_mul<T>(A.kq, lv + nl, ks, o->nk, s));
     modil_status st = external_pass<T>(p, A, lv, gr, 1.0, gr ? MODE_GRAD : MODE_LOSS);
+    if (st == MODIL_OK && gr && kb) CUDA_TRY(lb_mul<T>(gr + nl, A.kg, ks, o->nk, s));
     if (st == MODIL_OK) st = read_terms(p, terms);
     *f = terms[0];
     if (st == MODIL_ERR_NONFINITE && !gr) {
@@ -1425,7 +1453,8 @@ modil_status lbfgs_run_t(modil_lbfgs* o, int iters, double* loss, int* done) {
     CUDA_TRY(cudaStreamSynchronize(s));
     return MODIL_OK;
   };
-  CUDA_TRY(cudaMemcpyAsync(x, pc, vb, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(x, pc, sizeof(T) * (size_t)nl, cudaMemcpyDeviceToDevice, s));
+  if (kb) CUDA_TRY(lb_mul<T>(x + nl, A.kq, 1.0 / ks, o->nk, s));
   double fx = 0.0;
   modil_status st = eval(x, g, &fx);
   if (st != MODIL_OK) return st;
@@ -1500,9 +1529,13 @@ modil_status lbfgs_run_t(modil_lbfgs* o, int iters, double* loss, int* done) {
     if (loss) loss[k + 1] = fx;
     o->iters++;
   }
-  // the result and its gradient become the problem's levels and gradient
-  CUDA_TRY(cudaMemcpyAsync(pc, x, vb, cudaMemcpyDeviceToDevice, s));
-  CUDA_TRY(cudaMemcpyAsync(A.g, g, vb, cudaMemcpyDeviceToDevice, s));
+  // the result and its gradient become the problem's levels (and nodes) and gradient
+  CUDA_TRY(cudaMemcpyAsync(pc, x, sizeof(T) * (size_t)nl, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(A.g, g, sizeof(T) * (size_t)nl, cudaMemcpyDeviceToDevice, s));
+  if (kb) {
+    CUDA_TRY(lb_mul<T>(A.kq, x + nl, ks, o->nk, s));
+    CUDA_TRY(lb_mul<T>(A.kg, g + nl, 1.0 / ks, o->nk, s));
+  }
   CUDA_TRY(cudaStreamSynchronize(s));
   if (done) *done = k;
   return MODIL_OK;
@@ -1518,14 +1551,15 @@ modil_status modil_lbfgs_create(modil_problem* p, int history, modil_lbfgs** out
   const Plan& P = p->plan;
   if (history < 1) return fail(MODIL_ERR_ARG, "history < 1");
   if (P.n_inst != 1) return fail(MODIL_ERR_UNSUPPORTED, "L-BFGS: single-instance problems only");
-  if (P.pde == MODIL_PDE_HEAT)
-    return fail(MODIL_ERR_UNSUPPORTED, "L-BFGS: the conductivity nodes of the heat problem are not in the level arena");
   modil_lbfgs* o = new (std::nothrow) modil_lbfgs();
   if (!o) return fail(MODIL_ERR_ARG, "out of host memory");
   o->p = p;
   o->m = history;
-  o->n = P.n_param;
-  cudaError_t e = cudaMalloc(&o->vec, P.esz * (size_t)P.n_param * (2 * (size_t)history + 6));
+  o->nl = P.n_param;
+  o->nk = (P.pde == MODIL_PDE_HEAT && !P.dev[0].k_fixed) ? P.dev[0].nk : 0;
+  o->n = o->nl + o->nk;
+  o->ks = P.dev[0].k_scale;
+  cudaError_t e = cudaMalloc(&o->vec, P.esz * (size_t)o->n * (2 * (size_t)history + 6));
   if (e == cudaSuccess)
     e = cudaMalloc(&o->dsc, sizeof(double) * ((size_t)lb_dot_partials() + 4 * (size_t)history + 2));
   if (e != cudaSuccess) {
@@ -1554,6 +1588,8 @@ void modil_lbfgs_destroy(modil_lbfgs* o) {
 const char* modil_last_error(void) { return g_err.c_str(); }
 
 const char* modil_version(void) { return "modil-gb300 0.1 (sm_103a)"; }
+
+size_t modil_desc_size(void) { return sizeof(modil_desc); }
 
 }  // extern "C"
 

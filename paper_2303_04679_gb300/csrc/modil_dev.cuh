@@ -45,6 +45,8 @@ struct DevInst {
   double w_res_dV;             // w_res * cell volume
   double w_data_n;             // w_data / n_meas
   double w_reg;                // regulariser weight (heat)
+  int k_fixed;                 // heat: conductivity nodes known (dL/dq = 0, not stepped)
+  double k_scale;              // heat: unit of the nodes' optimiser steps (Adam lr * k_scale)
   double lr, b1, b2, eps;      // Adam
 };
 
@@ -120,6 +122,8 @@ struct Arena {
   const int* cblk_inst[MODIL_MAXL];
   const int* cblk_first[MODIL_MAXL];
   int ncblk[MODIL_MAXL];
+  const int* csmall_inst;  // instances with levels >= 2 to compose (L >= 4)
+  int ncsmall;
   int npart;
   int n_inst;
   float gscale;        // factor on the written fine gradient (d loss / d output), 1 normally

@@ -180,14 +180,16 @@ def heat_k_init(value=0.02, n=HEAT_KNODES):
     return np.full(n, value, dtype=np.float64)
 
 
-def heat_workload(nt=512, nx=512, n_levels=7, seed=2):
+def heat_workload(nt=512, nx=512, n_levels=7, seed=2, field=None):
     """Conductivity inference on a 512 (x) by 512 (t) grid with 7 levels.
 
     5 % of the cells carry measurements with Gaussian noise (sigma = 1e-3) of
-    the closed-form constant-conductivity temperature record; the initial
+    the temperature record ``field`` (nt x nx): a solution of the forward
+    problem with the reference conductivity (records.heat_record), or by
+    default the closed-form constant-conductivity series; the initial
     profile is g(x) - g(0); 32 conductivity nodes start at 0.02.
     """
-    cells, vals = heat_measurements(nt, nx, 0.05, 1e-3, seed)
+    cells, vals = heat_measurements(nt, nx, 0.05, 1e-3, seed, field=field)
     return dict(shape=(nt, nx), n_levels=n_levels, meas_cell=cells, meas_value=vals,
                 aux=heat_ic(nx), knodes=heat_k_init(), w_res=1.0, w_data=1.0, w_reg=1e-4,
                 lr=1e-3)

@@ -52,7 +52,8 @@ class modil_desc(C.Structure):
         ("point_value", C.POINTER(C.c_double)),
         ("tile", C.c_int * 2),
         ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3),
-        ("point_field", C.POINTER(C.c_int32)), ("layout", C.c_int),
+        ("point_field", C.POINTER(C.c_int32)), ("layout", C.c_int), ("k_fixed", C.c_int),
+        ("k_scale", C.c_double),
     ]
 
 
@@ -94,11 +95,15 @@ def _load():
         "modil_lbfgs_destroy": ([P], None),
         "modil_last_error": ([], C.c_char_p),
         "modil_version": ([], C.c_char_p),
+        "modil_desc_size": ([], C.c_size_t),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = res
+    if lib.modil_desc_size() != C.sizeof(modil_desc):
+        raise ImportError(f"libmodil.so's modil_desc is {lib.modil_desc_size()} bytes, this binding's "
+                          f"{C.sizeof(modil_desc)}: rebuild the library")
     return lib
 
 
@@ -120,13 +125,14 @@ class Desc:
     def __init__(self, pde, shape, n_levels, dtype="f32", coef=(), w_res=1.0, w_data=1.0,
                  w_reg=0.0, meas_cell=None, meas_value=None, meas_field=None, aux=None,
                  knodes=None, lr=5e-3, beta1=0.9, beta2=0.999, eps=1e-8, tile=(0, 0),
-                 points=None, point_value=None, domain=None, point_field=None, layout="cell"):
+                 points=None, point_value=None, domain=None, point_field=None, layout="cell",
+                 k_fixed=False, k_scale=0.0):
         self.kwargs = dict(pde=pde, shape=shape, n_levels=n_levels, dtype=dtype, coef=coef,
                            w_res=w_res, w_data=w_data, w_reg=w_reg, meas_cell=meas_cell,
                            meas_value=meas_value, meas_field=meas_field, aux=aux, knodes=knodes,
                            lr=lr, beta1=beta1, beta2=beta2, eps=eps, tile=tile, points=points,
                            point_value=point_value, domain=domain, point_field=point_field,
-                           layout=layout)
+                           layout=layout, k_fixed=k_fixed, k_scale=k_scale)
         self.pde = {"burgers": PDE_BURGERS, "heat": PDE_HEAT, "ns2d": PDE_NS2D,
                     "ns3d": PDE_NS3D, "poisson": PDE_POISSON}.get(pde, pde)
         self.dtype = {"f32": F32, "f64": F64}.get(dtype, dtype)
@@ -175,6 +181,8 @@ class Desc:
         d.point_field = _dptr(self._pfield, C.c_int32)
         self.layout = {"cell": 0, "node": 1}.get(layout, layout)
         d.layout = self.layout
+        d.k_fixed = 1 if k_fixed else 0
+        d.k_scale = float(k_scale)
         d.tile[0], d.tile[1] = int(tile[0]), int(tile[1])
         if domain is not None:  # ((lo, hi) per axis, slowest first)
             for a, (lo, hi) in enumerate(domain):

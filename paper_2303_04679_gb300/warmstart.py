@@ -42,10 +42,14 @@ def zero_levels(shape, n_levels, inflow_level=0):
     return lv
 
 
-def forward_solves(cases, side, n_levels, steps, lr=1e-3, w_pin=10.0, batch=32):
+def forward_solves(cases, side, n_levels, steps, lr=1e-3, w_pin=10.0, batch=32, fractions=None,
+                   lbfgs_iters=0, history=50):
     """Plain mODIL forward solutions of the body problem around each case's
-    ellipsoid (cases: list of (centre, axes)); returns [n, 5, S, S, S] FP32
-    composed fields and the final loss terms."""
+    ellipsoid (cases: list of (centre, axes); fractions: their body fractions
+    on the grid if already computed): `steps` Adam steps on batches of cases,
+    then, with lbfgs_iters > 0, that many L-BFGS iterations per case (the
+    optimiser of Section 3.5).  Returns [n, 5, S, S, S] FP32 composed fields
+    and the final loss terms."""
     import torch  # noqa: F401  (device memory and streams)
     shape = (side,) * 3
     ncell = side ** 3
@@ -54,9 +58,13 @@ def forward_solves(cases, side, n_levels, steps, lr=1e-3, w_pin=10.0, batch=32):
     terms = np.zeros((len(cases), 4))
     cells = np.arange(ncell, dtype=np.int32)
     field4 = np.full(ncell, 4, np.int32)
+    if lbfgs_iters:
+        batch = 1  # L-BFGS runs on single-instance problems
     for b0 in range(0, len(cases), batch):
         chunk = cases[b0:b0 + batch]
-        chats = [chihat_from_fraction(inputs.ns3d_body_fraction(shape, c, a)) for c, a in chunk]
+        chats = [chihat_from_fraction(fractions[b0 + k] if fractions is not None
+                                      else inputs.ns3d_body_fraction(shape, c, a))
+                 for k, (c, a) in enumerate(chunk)]
         descs = [modil.Desc("ns3d", shape, n_levels, "f32", coef=(cf["Re"], cf["D"], cf["lam"], cf["tau"]),
                             w_res=1.0, w_data=w_pin * ncell, meas_cell=cells, meas_field=field4,
                             meas_value=ch.reshape(-1), lr=lr) for ch in chats]
@@ -65,7 +73,11 @@ def forward_solves(cases, side, n_levels, steps, lr=1e-3, w_pin=10.0, batch=32):
                 lv = zero_levels(shape, n_levels)
                 lv[4][0][:] = ch
                 p.write_fields(lv, instance=i)
-            p.step(steps, read_loss=False)
+            if steps:
+                p.step(steps, read_loss=False)
+            if lbfgs_iters:
+                with modil.LBFGS(p, history=history) as opt:
+                    opt.run(lbfgs_iters)
             t = p.eval_loss()
             for i in range(len(chunk)):
                 out[b0 + i] = np.stack([p.read_field(f, instance=i) for f in range(FIELDS)])
@@ -182,26 +194,36 @@ def inverse_problem(shape, n_levels, cells, fidx, vals, lr=1e-3):
                       w_res=1.0, w_data=1.0, meas_cell=cells, meas_field=fidx, meas_value=vals, lr=lr)
 
 
-def steps_to_losses(desc, levels, thresholds, max_steps, chunk=100, chi_ref=None, run_all=False):
-    """Run mODIL from the given levels; for every threshold the first step
-    count (multiple of chunk) and wall time at which the loss is at or below
-    it (None if never).  Returns (hits, loss history per chunk), and with
+def steps_to_losses(desc, levels, thresholds, max_steps, chunk=100, chi_ref=None, run_all=False,
+                    optimizer="adam", history=50):
+    """Run mODIL from the given levels with Adam or L-BFGS (Section 3.5 uses
+    L-BFGS); for every threshold the first step (iteration) count, a
+    multiple of chunk, and the wall time at which the loss is at or below it
+    (None if never).  Returns (hits, loss history per chunk), and with
     chi_ref also the mean absolute body-fraction error per chunk (the
     composed chihat read back outside the timed steps).  Stops once every
-    threshold is reached unless run_all."""
+    threshold is reached unless run_all, and when L-BFGS stops early."""
     import torch
     hits = {t: None for t in thresholds}
     hist, chi_err = [], []
     with modil.Problem(desc) as p:
         p.write_fields(levels)
+        opt = modil.LBFGS(p, history=history) if optimizer == "lbfgs" else None
         torch.cuda.synchronize()
         el = 0.0
         done = 0
-        while done < max_steps:
+        stalled = False
+        while done < max_steps and not stalled:
             t0 = time.perf_counter()
-            loss = float(p.step(chunk)[0][0])
+            if opt is None:
+                loss = float(p.step(chunk)[0][0])
+                done += chunk
+            else:
+                h = opt.run(chunk)
+                loss = float(h[-1])
+                done += len(h) - 1
+                stalled = len(h) - 1 < chunk
             el += time.perf_counter() - t0
-            done += chunk
             hist.append(loss)
             if chi_ref is not None:
                 chi_err.append(float(np.mean(np.abs(fraction_from_chihat(p.read_field(4)) - chi_ref))))
@@ -210,6 +232,8 @@ def steps_to_losses(desc, levels, thresholds, max_steps, chunk=100, chi_ref=None
                     hits[t] = (done, el)
             if not run_all and hits and all(v is not None for v in hits.values()):
                 break
+        if opt is not None:
+            opt.close()
     if chi_ref is not None:
         return hits, hist, chi_err
     return hits, hist

@@ -18,7 +18,7 @@ class Case:
     def __init__(self, pde, shape, L, dtype="f32", seed=0, n_meas=50, nu=0.01, w_res=1.0,
                  w_data=1.0, w_reg=0.0, lr=5e-3, tile=(0, 0), duplicate=0, n_knodes=32,
                  fine_lo=None, fine_hi=None, coarse_scale=None, Re=100.0, tau=1.0, D=0.4,
-                 lam=1.0, chi_shift=5.0):
+                 lam=1.0, chi_shift=5.0, k_fixed=False, k_scale=1.0):
         self.pde, self.shape, self.L, self.dtype = pde, tuple(shape), L, dtype
         self.npd = np.float64 if dtype == "f64" else np.float32
         nx = shape[-1]
@@ -62,12 +62,13 @@ class Case:
                 "ns3d": {"Re": Re, "D": D, "lam": lam, "tau": tau}}.get(pde, {})
         self.oracle = o.Problem(pde, self.shape, L, coef=coef, w_res=w_res, w_data=w_data,
                                 w_reg=w_reg, meas_cell=cells, meas_value=vals, aux=self.aux,
-                                meas_field=mfield)
+                                meas_field=mfield, k_fixed=k_fixed, k_scale=k_scale)
         dcoef = {"burgers": (nu,), "ns2d": (Re, tau), "ns3d": (Re, D, lam, tau)}.get(pde, ())
         self.desc_kw = dict(pde=pde, shape=self.shape, n_levels=L, dtype=dtype,
                             coef=dcoef, w_res=w_res, w_data=w_data,
                             w_reg=w_reg, meas_cell=cells, meas_value=vals, meas_field=mfield,
-                            aux=self.aux, knodes=self.q, lr=lr, tile=tile)
+                            aux=self.aux, knodes=self.q, lr=lr, tile=tile, k_fixed=k_fixed,
+                            k_scale=0.0 if k_scale == 1.0 else k_scale)
         self.lr = lr
 
     def desc(self):

@@ -38,6 +38,18 @@ def test_version_string(mod):
     assert "sm_103a" in mod.version()
 
 
+def test_descriptor_struct_matches_the_header(mod):
+    import ctypes as C
+    assert mod.LIB.modil_desc_size() == C.sizeof(mod.modil_desc)
+
+
+def test_k_fixed_only_for_the_heat_family(mod):
+    assert mod.arena_bytes([_heat(mod, k_fixed=True)]) > 0
+    with pytest.raises(mod.ModilError) as e:
+        mod.arena_bytes([mod.Desc("burgers", (16, 16), 2, coef=(0.01,), k_fixed=True)])
+    assert e.value.code == mod.ERR_ARG
+
+
 def _heat(mod, shape=(64, 64), L=4, **kw):
     nt, nx = shape
     return mod.Desc("heat", shape, L, aux=np.zeros(nx), knodes=np.full(32, 0.02), **kw)

@@ -1,0 +1,130 @@
+"""The heat family with a known conductivity (k_fixed, the forward problem
+that makes the reference record of Section 3.4) on the GPU against the FP64
+oracle: Adam moves the levels exactly as the oracle does and never the
+nodes; the device L-BFGS on the levels alone reaches the oracle's row-by-row
+implicit solve of the same discrete problem.  With the conductivity unknown,
+L-BFGS over the levels and the nodes follows the oracle's L-BFGS."""
+import numpy as np
+import pytest
+
+import oracle as o
+from oracle import lbfgs_oracle as lb
+from paper_2303_04679_gb300 import inputs
+
+from _cases import Case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def modil():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_04679_gb300 import build
+    build.build()
+    from paper_2303_04679_gb300 import modil as m
+    return m
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_known_conductivity_adam_keeps_the_nodes(modil, dtype):
+    c = Case("heat", (64, 128), 5, dtype, seed=40, n_meas=300, w_reg=0.1, lr=5e-3, k_fixed=True)
+    st = o.OracleState.zeros_like_levels(c.levels, c.q)
+    hist = [o.oracle_step(c.oracle, st, c.lr) for _ in range(5)]
+    tol = 1e-11 if dtype == "f64" else 2e-5
+    with modil.Problem(c.desc()) as p:
+        c.load(p)
+        for k in range(5):
+            t = p.step(1)[0]
+            assert abs(t[0] - hist[k]["total"]) <= tol * hist[k]["total"]
+        assert np.array_equal(p.read_knodes(), c.q)      # bit for bit
+        p.eval_grad()
+        assert not np.any(p.read_kgrad())
+        if dtype == "f64":
+            for lvl in range(c.L):
+                ref = st.levels[lvl]
+                assert np.max(np.abs(p.read_level(lvl) - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_known_conductivity_lbfgs_reaches_the_implicit_solve(modil):
+    n, L = 64, 4
+    q = inputs.heat_k_true(np.arange(32) / 31)
+    init = inputs.heat_ic(n)
+    ref = o.heat_implicit_solve(init, n, 1.0 / n, 1.0 / n, lambda uf: o.heat_conductivity(uf, q)[0])
+    d = modil.Desc("heat", (n, n), L, "f64", w_res=1.0, w_data=0.0, aux=init, knodes=q, k_fixed=True)
+    with modil.Problem(d) as p, modil.LBFGS(p, history=50) as opt:
+        hist = opt.run(3000)
+        u = p.read_field()
+        assert np.array_equal(p.read_knodes(), q)
+    assert np.max(np.abs(u - ref)) < 1e-8, (np.max(np.abs(u - ref)), hist[-1], len(hist))
+
+
+def _heat_inverse(n, L, dtype, seed=3):
+    """Conductivity inference on n x n (Section 3.4): 5 % of the cells of the
+    oracle's implicit solve with the reference k, N(0, 1e-3^2) noise, 32
+    nodes starting at 0.02."""
+    u = o.heat_implicit_solve(inputs.heat_ic(n), n, 1.0 / n, 1.0 / n, inputs.heat_k_true)
+    cells, vals = inputs.heat_measurements(n, n, 0.05, 1e-3, seed, field=u)
+    npd = np.float64 if dtype == "f64" else np.float32
+    vals = vals.astype(npd).astype(np.float64)
+    init = inputs.heat_ic(n).astype(npd).astype(np.float64)
+    orc = o.Problem("heat", (n, n), L, w_res=1.0, w_data=1.0, w_reg=1e-4, meas_cell=cells, meas_value=vals,
+                    aux=init)
+    return u, cells, vals, init, orc
+
+
+def k_error(q):
+    """RMS error of the node interpolant against the reference k over u in
+    (0, 1), normalised by the reference's maximum (Section 3.4's measure)."""
+    uu = (np.arange(1000) + 0.5) / 1000
+    return float(np.sqrt(np.mean((o.heat_conductivity(uu, q)[0] - inputs.heat_k_true(uu)) ** 2)) / 0.02)
+
+
+def test_node_step_unit_adam_f64(modil):
+    """k_scale: Adam moves the nodes by lr * k_scale units, as the oracle."""
+    c = Case("heat", (64, 96), 4, "f64", seed=41, n_meas=300, w_reg=0.01, lr=5e-3, k_scale=0.05)
+    st = o.OracleState.zeros_like_levels(c.levels, c.q)
+    hist = [o.oracle_step(c.oracle, st, c.lr) for _ in range(5)]
+    with modil.Problem(c.desc()) as p:
+        c.load(p)
+        for k in range(5):
+            t = p.step(1)[0]
+            assert abs(t[0] - hist[k]["total"]) <= 1e-11 * hist[k]["total"]
+        np.testing.assert_allclose(p.read_knodes(), st.q, rtol=1e-12, atol=1e-15)
+        for lvl in range(c.L):
+            ref = st.levels[lvl]
+            assert np.max(np.abs(p.read_level(lvl) - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_conductivity_lbfgs_follows_the_oracle(modil):
+    """L-BFGS over the levels and the nodes (the nodes in units of k_scale):
+    the device follows the oracle's iterations on a 32 x 32, three-level
+    problem."""
+    n, L, ks = 32, 3, 0.02
+    _, cells, vals, init, orc = _heat_inverse(n, L, "f64")
+    q0 = inputs.heat_k_init()
+    shapes = o.level_shapes((n, n), L)
+    sizes = [int(np.prod(s)) for s in shapes]
+    nl = sum(sizes)
+
+    def unpack(z):  # the vector's tail holds q / ks
+        return [z[a:a + m].reshape(s) for a, m, s in zip(np.cumsum([0] + sizes[:-1]), sizes, shapes)], ks * z[nl:]
+
+    def fg(z):
+        lv, q = unpack(z)
+        t, g, gq = o.loss_grad_levels(orc, lv, q)
+        return t["total"], np.concatenate([a.ravel() for a in g] + [ks * gq])
+
+    def f(z):
+        lv, q = unpack(z)
+        return o.loss_terms(orc, o.compose(lv), q)["total"]
+    x, want, _ = lb.lbfgs(fg, f, np.concatenate([np.zeros(nl), q0 / ks]), 50, 25)
+    d = modil.Desc("heat", (n, n), L, "f64", w_res=1.0, w_data=1.0, w_reg=1e-4, meas_cell=cells,
+                   meas_value=vals, aux=init, knodes=q0, k_scale=ks)
+    with modil.Problem(d) as p, modil.LBFGS(p, history=50) as opt:
+        hist = opt.run(25)
+        q = p.read_knodes()
+    np.testing.assert_allclose(hist[:21], want[:21], rtol=1e-8)
+    if len(hist) == len(want):
+        np.testing.assert_allclose(q, ks * x[nl:], rtol=1e-6, atol=1e-9)

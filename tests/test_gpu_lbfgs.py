@@ -87,11 +87,7 @@ def test_lbfgs_descends_and_continues(modil):
         assert t[0] == pytest.approx(b[-1], rel=1e-6)
 
 
-def test_lbfgs_rejects_heat_and_batches(modil):
-    c = Case("heat", (32, 64), 3, "f32", seed=42, n_meas=50)
-    with modil.Problem(c.desc()) as p:
-        with pytest.raises(modil.ModilError):
-            modil.LBFGS(p)
+def test_lbfgs_rejects_batches(modil):
     cs = [Case("burgers", (32, 32), 2, "f32", seed=43 + i, n_meas=20) for i in range(2)]
     with modil.Problem([x.desc() for x in cs]) as p:
         with pytest.raises(modil.ModilError):

@@ -321,6 +321,67 @@ def test_heat_implicit_solve_zeroes_residual():
     assert u.max() <= init.max() + 1e-12 and u.min() >= -1e-12
 
 
+def test_heat_known_conductivity_forward_problem_is_the_implicit_solve():
+    """With the conductivity known (k_fixed: the forward problem that makes the
+    reference record of Section 3.4) dL/dq is zero, an Adam step leaves q
+    alone, and minimising the loss over the levels alone (library L-BFGS, no
+    data) reaches the row-by-row implicit solve of the same discrete problem
+    with k the nodes' piecewise-linear interpolant.  A dropped k_fixed (q
+    moves) or a residual that is not the implicit scheme fails."""
+    from scipy.optimize import minimize
+    n, L = 16, 2
+    q = inputs.heat_k_true(np.arange(32) / 31)
+    init = inputs.heat_ic(n)
+    p = o.Problem("heat", (n, n), L, w_res=1.0, w_data=0.0, w_reg=1e-3, aux=init, k_fixed=True)
+    shapes = o.level_shapes((n, n), L)
+    sizes = [int(np.prod(s)) for s in shapes]
+
+    def unpack(z):
+        return [z[a:a + m].reshape(s) for a, m, s in zip(np.cumsum([0] + sizes[:-1]), sizes, shapes)]
+
+    def fg(z):
+        t, g, gq = o.loss_grad_levels(p, unpack(z), q)
+        assert not np.any(gq)
+        return t["total"], np.concatenate([a.ravel() for a in g])
+    r = minimize(fg, np.zeros(sum(sizes)), jac=True, method="L-BFGS-B",
+                 options=dict(maxiter=5000, maxcor=30, ftol=0.0, gtol=1e-14))
+    u = o.compose(unpack(r.x))
+    ref = o.heat_implicit_solve(init, n, 1.0 / n, 1.0 / n, lambda uf: o.heat_conductivity(uf, q)[0])
+    assert np.max(np.abs(u - ref)) < 1e-7, np.max(np.abs(u - ref))
+    st = o.OracleState.zeros_like_levels(unpack(r.x), q=q)
+    o.oracle_step(p, st, 1e-2)
+    assert np.array_equal(st.q, q)
+    free = o.Problem("heat", (n, n), L, w_res=1.0, w_data=0.0, w_reg=1e-3, aux=init)
+    assert np.any(o.loss_grad_levels(free, unpack(r.x), q)[2])
+
+
+def test_heat_node_step_unit():
+    """k_scale only rescales the optimiser's steps on the nodes: Adam's first
+    step from zero moments moves every node by lr * k_scale * sign(dL/dq)
+    (to within eps), and the levels move exactly as with k_scale = 1."""
+    n, L = 16, 2
+    rng = np.random.default_rng(5)
+    lv = [rng.uniform(0.0, 1.0, s) for s in o.level_shapes((n, n), L)]
+    q = inputs.heat_k_true(np.arange(32) / 31) + 0.005
+    cells = inputs.measurement_cells(n * n, 20, 1)
+    kw = dict(w_res=1.0, w_data=1.0, w_reg=1e-3, aux=inputs.heat_ic(n), meas_cell=cells,
+              meas_value=rng.uniform(0.0, 1.0, 20))
+    lr, ks = 1e-2, 0.05
+    gq = o.loss_grad_levels(o.Problem("heat", (n, n), L, **kw), lv, q)[2]
+    out = []
+    for k_scale in (1.0, ks):
+        st = o.OracleState.zeros_like_levels(lv, q=q)
+        o.oracle_step(o.Problem("heat", (n, n), L, k_scale=k_scale, **kw), st, lr)
+        out.append(st)
+    big = np.abs(gq) > 1e-6  # nodes far from the data have gradients near eps
+    assert big.sum() >= 16
+    np.testing.assert_allclose((out[1].q - q)[big], -lr * ks * np.sign(gq[big]), rtol=1e-5)
+    np.testing.assert_allclose((out[0].q - q)[big], -lr * np.sign(gq[big]), rtol=1e-5)
+    np.testing.assert_allclose(out[1].q - q, ks * (out[0].q - q), rtol=1e-9, atol=1e-18)
+    for a, b in zip(out[0].levels, out[1].levels):
+        assert np.array_equal(a, b)
+
+
 def test_heat_regulariser_closed_forms():
     """Second difference of the conductivity nodes (Section 3.4 reading R7):
     zero for nodes on a line; for q_j = j^2 every second difference is 2, so
