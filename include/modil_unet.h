@@ -83,6 +83,12 @@ modil_status modil_unet_train_step(modil_unet* net, const float* input, const fl
 modil_status modil_unet_profile_step(modil_unet* net, const float* input, const float* target,
                                      float* ms, int max, int* n);
 
+/* How the 3x3x3 convolutions and their input gradients run: implicit = 1
+ * (the default) as implicit GEMMs whose A operand TMA reads as shifted boxes
+ * of the activations; 0 through explicit im2col / col2im buffers around the
+ * same GEMM.  Both give the same sums up to the order of FP32 accumulation. */
+modil_status modil_unet_set_implicit(modil_unet* net, int implicit);
+
 /* D (+)= A B^T on the tensor cores: A [M][K] and B [N][K] BF16 row-major with
  * row pitches lda, ldb (elements, multiples of 8, 16-byte aligned bases);
  * FP32 accumulation.  mode 0: D BF16 = relu?(acc + bias); mode 1: D FP32 =

@@ -21,11 +21,18 @@
 //   4. finishes the previous row: dL/du(n-1, x) gathers lambda dr/du of the
 //      residuals that read u(n-1, x) -- its own, those of x-1 and x+1 of row
 //      n-1 (shuffles) and that of (n, x) -- writes it and applies Adam.
-// Everything stays in registers: no shared memory and no block barriers.
-// Level 0's parameters and Adam moments stream through a per-warp ring of
-// kRing rows in shared memory, copied asynchronously kRing - 1 rows ahead;
-// the rows of w_1 are loaded one fine row ahead.  Each warp writes its FP64 partial sums (r^2 and the data
-// misfit, compensated FP32 in between) for the per-instance tail kernel.
+// Everything stays in registers: no shared-memory tiles and no block
+// barriers.  Level 0's parameters and Adam moments stream through a per-warp
+// ring of kRing rows in shared memory, copied asynchronously kRing - 1 rows
+// ahead.  Rows go in pairs (2k+1, 2k+2), which interpolate between the same
+// two rows k, k+1 of w_1 with the fixed weights (3/4, 1/4) and (1/4, 3/4);
+// inside the strip a pair runs with every row condition known to hold (no
+// bounds checks, no weight arithmetic), the pairs at the strip's edges and
+// the level's ends take the general path.  The next row of w_1 is loaded one
+// pair ahead.  The kernel is compiled per mode (loss, gradient, step,
+// compose).  Each lane sums its r^2 (at most 32 rows) in FP32, the warp
+// combines the lanes in compensated FP32, and each warp writes FP64 partial
+// sums (r^2 and the data misfit) for the per-instance tail kernel.
 // The stencil (rows n >= 1, the implicit step of the reading of Section 3.2):
 //   r = (u^n_i - u^{n-1}_i)/dt + (F_{i+1/2} - F_{i-1/2})/dx
 //       - nu (u^n_{i+1} - 2u^n_i + u^n_{i-1})/dx^2,
@@ -41,6 +48,13 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRing = 4;  // rows of level 0 in flight per warp (a power of two)
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Asynchronous 4- or 8-byte copy to a shared-memory address.
+__device__ __forceinline__ void cp_async_at(unsigned saddr, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_at(unsigned saddr, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr), "l"(src) : "memory");
+}
 template <int N>
 __device__ __forceinline__ void cp_async_wait_group() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
@@ -145,8 +159,9 @@ struct StreamCoef {
   T idt, idx1, idx2, nu, lam_scale, wd2, gscale;
 };
 
-template <class T>
-__global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stream(const __grid_constant__ Arena<T> A, int mode, int cur) {
+template <class T, int MODE>
+__global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stream(const __grid_constant__ Arena<T> A, int cur) {
+  constexpr bool step = (MODE == MODE_STEP), adj = (MODE != MODE_LOSS), comp_only = (MODE == MODE_COMPOSE);
   // per warp: a ring of kRing rows of level 0's parameters and Adam moments,
   // filled with asynchronous copies kRing - 1 rows ahead of their use
   __shared__ __align__(16) T sP[kStreamNT / 32][kRing][32];
@@ -169,30 +184,40 @@ __global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stre
   const bool own_x = x >= x0 && x < xo1;
   const bool res_x = xin && x >= x0 - 1 && x <= xo1;  // residual columns [x0 - 1, xo1]
   const bool hw = x > 0, he = x < nx - 1;
-  const bool step = (mode == MODE_STEP), adj = (mode != MODE_LOSS);
   // per-instance bases; indices within an instance's level fit 32 bits
   const long long o0 = D.off[0][0];
   const T* __restrict__ P0 = A.p[cur] + o0;
   const T* __restrict__ M0 = A.m + o0;
   const double* __restrict__ V0 = A.v + o0;
   const int nstart = max(y0 - 1, 0);
-  // level 0 of rows [nstart, y1] (and m, v of the owned rows) -> ring slot r % kRing;
-  // one copy group per row, committed even when empty
-  auto issue = [&](int r) {
-    if (r <= y1 && r < ny && xin) {
-      const int sl = r & (kRing - 1);
-      const int e = r * nx + x;
-      cp_async(&sP[w][sl][lane], P0 + e);
-      if (step && r >= y0 && own_x) {
-        cp_async(&sM[w][sl][lane], M0 + e);
-        cp_async(&sV[w][sl][lane], V0 + e);
+  T* __restrict__ G0 = A.g + o0;               // level 0's gradient
+  T* __restrict__ Pn = A.p[cur ^ 1] + o0;      // level 0 after the step
+  const int rmax = min(y1, ny - 1);  // last row of level 0 the strip reads
+  // level 0 of row r (and m, v of owned rows) -> ring slot r % kRing; one copy
+  // group per row, committed even when empty.  chk = false: the caller knows
+  // y0 <= r <= rmax.  Shared addresses of the lane's ring column and global
+  // pointers of its column are formed once; a row adds offsets only.
+  const unsigned sPa = (unsigned)__cvta_generic_to_shared(&sP[w][0][lane]);
+  const unsigned sMa = (unsigned)__cvta_generic_to_shared(&sM[w][0][lane]);
+  const unsigned sVa = (unsigned)__cvta_generic_to_shared(&sV[w][0][lane]);
+  const T* gP = P0 + x;
+  const T* gM = M0 + x;
+  const double* gV = V0 + x;
+  auto issue = [&](int r, bool chk) {
+    if ((!chk || r <= rmax) && xin) {
+      const unsigned so = (unsigned)(r & (kRing - 1)) * 32u;  // slot offset in elements
+      const int ro = r * nx;
+      cp_async_at(sPa + so * (unsigned)sizeof(T), gP + ro);
+      if (step && (!chk || r >= y0) && own_x) {
+        cp_async_at(sMa + so * (unsigned)sizeof(T), gM + ro);
+        cp_async_at(sVa + so * 8u, gV + ro);
       }
     }
     cp_async_commit();
   };
   // level 0, m and v were last written by this kernel one step earlier
 #pragma unroll
-  for (int k = 0; k < kRing - 1; ++k) issue(nstart + k);
+  for (int k = 0; k < kRing - 1; ++k) issue(nstart + k, true);
   const T cdiag = T(-2) - (hw ? T(0) : T(1)) - (he ? T(0) : T(1));
   // level 1 composed (w_1; the coarsest level itself when L == 2) and the
   // lane's column taps into it
@@ -204,8 +229,8 @@ __global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stre
   // fine row n lies between rows lo(n) and lo(n) + 1 of w_1
   auto lo_of = [&](int n) { return nyc > 1 ? min(max((n - 1) >> 1, 0), nyc - 2) : 0; };
   const int rb = A.run_ptr[gt], re = A.run_ptr[gt + 1];
-  // the row of the next measurement run (runs sorted by cell)
-  auto run_row = [&](int r) { return r < re ? A.run_cell[r] / nx : 0x7fffffff; };
+  // the cell of the next measurement run (runs sorted by cell)
+  auto run_cell = [&](int r) { return r < re ? A.run_cell[r] : 0x7fffffff; };
 
   pdl_wait();  // w_1 (previous launch) and the step state (previous step's tail)
   pdl_trigger();
@@ -226,75 +251,69 @@ __global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stre
   const StreamCoef<T>& cf = sC[w];
   const AdamCoef& ac = cf.ac;
 
-  // x-interpolated rows lo(n), lo(n) + 1 of w_1; the next row's new one is
-  // loaded one row ahead
+  // va, vb: rows clo and clo + 1 of w_1 interpolated in x (zero when L == 1);
+  // wa, wb: the raw taps of row clo + 2, loaded one shift ahead
+  int clo = lo_of(nstart);
   T va = T(0), vb = T(0), wa = T(0), wb = T(0);
-  bool pend = false;
-  if (L >= 2 && xin) {
-    const int lo = lo_of(nstart), hi = nyc > 1 ? lo + 1 : 0;
-    va = wx0 * W1[lo * nxc + jx0] + wx1 * W1[lo * nxc + jx1];
+  const bool w1x = L >= 2 && xin;
+  if (w1x) {
+    const int hi = nyc > 1 ? clo + 1 : 0;
+    va = wx0 * W1[clo * nxc + jx0] + wx1 * W1[clo * nxc + jx1];
     vb = wx0 * W1[hi * nxc + jx0] + wx1 * W1[hi * nxc + jx1];
+    if (clo + 2 <= nyc - 1) {
+      wa = W1[(clo + 2) * nxc + jx0];
+      wb = W1[(clo + 2) * nxc + jx1];
+    }
   }
-  float rh = 0.f, rl = 0.f, dh = 0.f, dl = 0.f;  // compensated FP32 sums (FP32 problems)
+  auto shift = [&]() {  // advance to rows clo + 1, clo + 2 of w_1
+    va = vb;
+    vb = wx0 * wa + wx1 * wb;
+    ++clo;
+    if (w1x && clo + 2 <= nyc - 1) {
+      wa = W1[(clo + 2) * nxc + jx0];
+      wb = W1[(clo + 2) * nxc + jx1];
+    }
+  };
+  // FP32 problems: r^2 per lane in plain FP32 (<= 32 terms), data misfit compensated
+  float rh = 0.f, rl = 0.f, dh = 0.f, dl = 0.f;
   double rd = 0.0, dd = 0.0;                     // FP64 problems
   T lJ0p = T(0), lJ1p = T(0), lJ2p = T(0), datp = T(0);  // row n-1 (pending gradient)
   T p0p = T(0), mp = T(0);
   double vp = 0.0;
-  int rr = rb, nr = run_row(rb);
-  int lon = lo_of(nstart);
+  int rr = rb, nc = run_cell(rb);
   T uo = T(0);  // u(n-1, x)
-  // row n: the field, the residual and the data term of row n; the gradient
+
+  // Row n: the field, the residual and the data term of row n; the gradient
   // and the Adam update of row n - 1.  Row y1 (< ny) supplies the residual
   // that reads the last owned row; the pass with n == ny only finishes rows.
-  for (int n = nstart; n <= y1; ++n) {
-    issue(n + kRing - 1);
+  // gen = false: a row of the strip's interior (y0 < n, n + kRing - 1 <=
+  // rmax), where every row condition holds and the copies need no check.
+  auto row = [&](const int n, const T wlo, const T whi, const bool gen) {
+    issue(n + kRing - 1, gen);
     cp_async_wait_group<kRing - 1>();  // this lane's copies of row n have landed
-    const bool row_ok = n < ny;
-    const bool own_row = n >= y0 && n < y1;
+    const bool row_ok = !gen || n < ny;
+    const bool own_row = !gen || (n >= y0 && n < y1);
+    const bool res_row = !gen || (n >= 1 && n >= y0 && n < ny);
+    const bool grad_row = !gen || (n - 1 >= y0 && n - 1 < y1);
     const int sl = n & (kRing - 1);
     T p0 = T(0), u = T(0), mn = T(0);
     double vn = 0.0;
-    if (pend) {
-      va = vb;
-      vb = wx0 * wa + wx1 * wb;
-      pend = false;
-    }
     if (row_ok && xin) {
       p0 = sP[w][sl][lane];
       if (step && own_row && own_x) {
         mn = sM[w][sl][lane];
         vn = sV[w][sl][lane];
       }
-      u = p0;
-      if (L >= 2) {
-        // weights 5/4 - t/2 and t/2 - 1/4 with t = n - 2 lo (3/4, 1/4 inside;
-        // 5/4, -1/4 at the ends); one row of w_1: a copy
-        T wlo = T(1), whi = T(0);
-        if (nyc > 1) {
-          wlo = T(1.25) - T(0.5) * (T)(n - 2 * lon);
-          whi = T(1) - wlo;
-        }
-        u = p0 + (wlo * va + whi * vb);
-      }
+      u = p0 + (wlo * va + whi * vb);
     }
-    {
-      const int lo1 = lo_of(n + 1);
-      if (L >= 2 && xin && lo1 != lon && n + 1 < ny) {
-        const int h1 = (lo1 + 1) * nxc;
-        wa = W1[h1 + jx0];
-        wb = W1[h1 + jx1];
-        pend = true;
-      }
-      lon = lo1;
-    }
-    if (mode == MODE_COMPOSE) {
+    if (comp_only) {
       if (row_ok && own_row && own_x) A.ufine[D.fine_off[0] + n * nx + x] = u;
-      continue;
+      return;
     }
     const T uW = __shfl_up_sync(kFull, u, 1);
     const T uE = __shfl_down_sync(kFull, u, 1);
     T lJ0 = T(0), lJ1 = T(0), lJ2 = T(0), lJ3 = T(0);
-    if (row_ok && res_x && n >= 1 && n >= y0) {
+    if (res_row && res_x) {
       const T uw = hw ? uW : -u;
       const T ue = he ? uE : -u;
       // the flux through a wall is the upwind flux against the zero wall value
@@ -309,14 +328,14 @@ __global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stre
       lJ2 = he ? lam * (dFEe * cf.idx1 - cf.nu * cf.idx2) : T(0);
       lJ3 = lam * (-cf.idt);
       if (own_row && own_x) {
-        if (sizeof(T) == 4) acc_add(rh, rl, r * r);
+        if (sizeof(T) == 4) rh += (float)(r * r);
         else rd += (double)(r * r);
       }
     }
     // data term of the measured cells of row n (runs sorted by cell)
     T dat = T(0);
-    if (n == nr && own_row) {
-      const int rowbase = n * nx;
+    const int rowbase = n * nx;
+    if (nc < rowbase + nx && own_row) {
       for (; rr < re; ++rr) {
         const int off = A.run_cell[rr] - rowbase;
         if (off >= nx) break;
@@ -334,21 +353,20 @@ __global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stre
           dat = cf.wd2 * sd;
         }
       }
-      nr = run_row(rr);
+      nc = run_cell(rr);
     }
     // gradient and Adam of row n - 1
     const T fromE = __shfl_down_sync(kFull, lJ0p, 1);  // lambda dr/du of residual (n-1, x+1)
     const T fromW = __shfl_up_sync(kFull, lJ2p, 1);    // lambda dr/du of residual (n-1, x-1)
-    const int m1 = n - 1;
-    if (adj && m1 >= y0 && m1 < y1 && own_x) {
+    if (adj && grad_row && own_x) {
       const T g = ((lJ1p + datp) + fromE + fromW + lJ3) * cf.gscale;
-      const int em = m1 * nx + x;
-      A.g[o0 + em] = g;
+      const int em = rowbase - nx + x;
+      G0[em] = g;
       if (step) {
         T p = p0p, m = mp;
         double v = vp;
         adam_update(p, m, v, g, ac);
-        A.p[cur ^ 1][o0 + em] = p;
+        Pn[em] = p;
         const_cast<T*>(M0)[em] = m;
         const_cast<double*>(V0)[em] = v;
       }
@@ -356,9 +374,35 @@ __global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stre
     lJ0p = lJ0; lJ1p = lJ1; lJ2p = lJ2; datp = dat;
     p0p = p0; mp = mn; vp = vn;
     uo = u;
+  };
+  // a row at the strip's edges: weights of w_1 rows clo, clo + 1 from its
+  // position (3/4, 1/4 inside; 5/4, -1/4 at the level's ends; a copy when
+  // w_1 has one row)
+  auto edge_row = [&](const int n) {
+    T wlo = T(1), whi = T(0);
+    if (nyc > 1) {
+      wlo = T(1.25) - T(0.5) * (T)(n - 2 * clo);
+      whi = T(1) - wlo;
+    }
+    row(n, wlo, whi, true);
+  };
+  int n = nstart;
+  if (n == 0) edge_row(n++);  // row 0 has no partner row -1
+  // rows in pairs (2k + 1, 2k + 2), both between rows k and k + 1 of w_1
+  for (; n <= y1; n += 2) {
+    const int k = (n - 1) >> 1;
+    if (k > clo && k <= nyc - 2) shift();
+    const bool inner = n > y0 && n + kRing <= rmax && (L < 2 || k <= nyc - 2);
+    if (inner) {
+      row(n, T(0.75), T(0.25), false);
+      row(n + 1, T(0.25), T(0.75), false);
+    } else {
+      edge_row(n);
+      if (n + 1 <= y1) edge_row(n + 1);
+    }
   }
   cp_async_wait_all();  // the ring's trailing (empty or unused) copies
-  if (mode == MODE_COMPOSE) return;
+  if (comp_only) return;
   double rs, ds;
   if (sizeof(T) == 4) {
 #pragma unroll
@@ -415,7 +459,12 @@ cudaError_t launch_fine_stream(const Arena<T>& A, int mode, int cur, cudaStream_
   constexpr int wpb = kStreamNT / 32;
   cudaLaunchAttribute at[1];
   cudaLaunchConfig_t cfg = pdl_cfg(dim3((A.ntiles[0] + wpb - 1) / wpb), dim3(kStreamNT), s, at);
-  return cudaLaunchKernelEx(&cfg, k_fine_stream<T>, A, mode, cur);
+  switch (mode) {
+    case MODE_LOSS: return cudaLaunchKernelEx(&cfg, k_fine_stream<T, MODE_LOSS>, A, cur);
+    case MODE_GRAD: return cudaLaunchKernelEx(&cfg, k_fine_stream<T, MODE_GRAD>, A, cur);
+    case MODE_STEP: return cudaLaunchKernelEx(&cfg, k_fine_stream<T, MODE_STEP>, A, cur);
+    default: return cudaLaunchKernelEx(&cfg, k_fine_stream<T, MODE_COMPOSE>, A, cur);
+  }
 }
 
 template cudaError_t launch_compose2<float>(const Arena<float>&, int, int, cudaStream_t);

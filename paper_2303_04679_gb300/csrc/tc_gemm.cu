@@ -68,6 +68,24 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes (64 BF16), 8-row swizzle atoms 1024 bytes apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -179,9 +197,22 @@ k_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorM
         if (*abort_flag) break;
         unsigned char* st = smem + s * Smem<BN>::STAGE;
         mbar_expect_tx(full + s, Smem<BN>::STAGE);
-        const int kx = (kc0 + i) * BK;
-        tma_load_2d(st, &ta, full + s, kx, m0);
-        tma_load_2d(st + Smem<BN>::A_BYTES, &tb, full + s, kx, n0);
+        if (g.conv) {
+          // chunk -> (tap, channel block); the output tile's first voxel
+          const int kc = kc0 + i, tap = kc / g.cc, c0 = (kc - tap * g.cc) * BK;
+          const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+          const int S = g.S;
+          const int x0 = m0 % S, r1 = m0 / S, y0 = r1 % S, r2 = r1 / S, z0 = r2 % S, b0 = r2 / S;
+          tma_load_5d(st, &ta, full + s, c0, x0 + g.sign * dx, y0 + g.sign * dy, z0 + g.sign * dz, b0);
+          if (g.b_tap_mid)
+            tma_load_3d(st + Smem<BN>::A_BYTES, &tb, full + s, c0, tap, n0);
+          else
+            tma_load_3d(st + Smem<BN>::A_BYTES, &tb, full + s, c0, n0, tap);
+        } else {
+          const int kx = (kc0 + i) * BK;
+          tma_load_2d(st, &ta, full + s, kx, m0);
+          tma_load_2d(st + Smem<BN>::A_BYTES, &tb, full + s, kx, n0);
+        }
       }
     } else if (warp == 1 && lane == 0) {
       // MMA issuer
@@ -221,7 +252,11 @@ k_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorM
       const int col = n0 + c;
       if (row >= g.M || col >= g.N) continue;
       const int ncol = min(16, g.N - col);
-      if (g.mode == GEMM_STORE_BF16) {
+      if (g.mode == GEMM_STORE_BF16_MASK) {
+        const __nv_bfloat16* a = static_cast<const __nv_bfloat16*>(g.act) + (long long)row * g.ldd + col;
+        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(g.D) + (long long)row * g.ldd + col;
+        for (int j = 0; j < ncol; ++j) d[j] = __float2bfloat16_rn(__bfloat162float(a[j]) > 0.f ? v[j] : 0.f);
+      } else if (g.mode == GEMM_STORE_BF16) {
         if (g.bias)
 #pragma unroll
           for (int j = 0; j < 16; ++j) v[j] += (col + j < g.N) ? g.bias[col + j] : 0.f;
@@ -323,6 +358,38 @@ int make_kmajor_map(CUtensorMap* m, const void* base, long long rows, long long 
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -3;
+}
+
+int make_act_map(CUtensorMap* m, const void* base, int C, int S, int B) {
+  EncodeTiled enc = encoder();
+  if (!enc) return -1;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (C % 8) || S < 8 || C > 65536) return -2;
+  const int bx = S < BM ? S : BM, by = (BM / bx) < S ? BM / bx : S, bz = BM / (bx * by);
+  if (bx * by * bz != BM || bz > S) return -2;
+  const cuuint64_t cs = (cuuint64_t)C * 2;
+  cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)S, (cuuint64_t)S, (cuuint64_t)S, (cuuint64_t)B};
+  cuuint64_t strides[4] = {cs, cs * S, cs * S * S, cs * S * S * S};
+  cuuint32_t box[5] = {(cuuint32_t)BK, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -3;
+}
+
+int make_3d_map(CUtensorMap* m, const void* base, long long d0, long long d1, long long d2, long long s1,
+                long long s2, int b1, int b2) {
+  EncodeTiled enc = encoder();
+  if (!enc) return -1;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((s1 * 2) & 15) || ((s2 * 2) & 15)) return -2;
+  cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+  cuuint64_t strides[2] = {(cuuint64_t)(s1 * 2), (cuuint64_t)(s2 * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)b1, (cuuint32_t)b2};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -3;

@@ -6,7 +6,7 @@
 
 namespace modil_tc {
 
-enum GemmMode { GEMM_STORE_BF16 = 0, GEMM_STORE_F32 = 1, GEMM_ATOMIC_F32 = 2 };
+enum GemmMode { GEMM_STORE_BF16 = 0, GEMM_STORE_F32 = 1, GEMM_ATOMIC_F32 = 2, GEMM_STORE_BF16_MASK = 3 };
 
 struct GemmArgs {
   int M, N, K;        // D is M x N, the contraction runs over K
@@ -17,7 +17,25 @@ struct GemmArgs {
   void* D;            // row-major output, ldd elements per row
   int ldd;
   int* err;           // device word: set non-zero when a wait timed out
+  // BF16_MASK store: D = (act > 0 ? acc : 0) as BF16, act row-major like D
+  const void* act;
+  // Implicit 3x3x3 convolution (conv != 0): A is a 5-D activation map
+  // (channels, x, y, z, sample) of S^3-voxel samples, a tile of 128 output
+  // voxels its box; K chunk i is tap i / cc, channels 64 (i % cc) ..; the A box
+  // sits at voxel + sign * tap offset (zero outside the grid).  B is a 3-D
+  // weight map: b_tap_mid ? (channels, tap, row) : (channels, row, tap).
+  int conv, S, cc, sign, b_tap_mid;
 };
+
+// Tensor map of BF16 activations [B][S][S][S][C] (channels innermost) in
+// boxes of 64 channels x 128 voxels (x fastest; 128B swizzle; channels past C
+// and voxels outside the grid read as zero).  C % 8 == 0, S >= 8.  0 on success.
+int make_act_map(CUtensorMap* m, const void* base, int C, int S, int B);
+
+// Tensor map of a BF16 3-D array (d0 innermost, strides in elements) in boxes
+// of 64 x b1 x b2 (128B swizzle; reads past d0 are zero).  0 on success.
+int make_3d_map(CUtensorMap* m, const void* base, long long d0, long long d1, long long d2, long long s1,
+                long long s2, int b1, int b2);
 
 // Tensor map of a row-major BF16 matrix (rows x k used, row pitch ld
 // elements) in 64-column tiles of box_rows rows.  0 on success.

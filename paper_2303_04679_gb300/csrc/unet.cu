@@ -376,6 +376,7 @@ struct modil_unet {
   // profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev;
+  bool implicit = true;  // 3x3x3 convolutions as implicit GEMMs (else im2col / col2im)
 };
 
 namespace {
@@ -419,7 +420,35 @@ modil_status gemm(modil_unet* n, const bf16* A, long long lda, const bf16* B, lo
 
 unsigned gs(long long n) { return (unsigned)std::min<long long>((n + kNT - 1) / kNT, 152LL * 16); }
 
+// A 3x3x3 convolution as an implicit GEMM: the A operand is read by TMA as
+// 128-voxel boxes of the channels-innermost activations X (Ca channels),
+// shifted by each tap (sign +1: the forward convolution; -1: its input
+// gradient), 64 channels at a time, zeros outside the grid and past Ca; the
+// B operand is the weight array w viewed in 3-D (see GemmArgs).
+modil_status conv_gemm(modil_unet* n, const bf16* X, int Ca, int S, long long M, const bf16* w, long long d1,
+                       long long d2, long long s1, long long s2, bool b_tap_mid, int sign, void* D, int ldd, int N,
+                       int mode, int relu, const float* bias, const bf16* act) {
+  CUtensorMap ta, tb;
+  const int bn = pick_bn(N);
+  const long long S3 = (long long)S * S * S;
+  if (M % S3 || M % 128) return fail(MODIL_ERR_ARG, "implicit convolution: voxel count");
+  if (modil_tc::make_act_map(&ta, X, Ca, S, (int)(M / S3)) != 0 ||
+      modil_tc::make_3d_map(&tb, w, Ca, d1, d2, s1, s2, b_tap_mid ? 1 : bn, b_tap_mid ? bn : 1) != 0)
+    return fail(MODIL_ERR_ARG, "tensor map of an implicit convolution");
+  GemmArgs g{};
+  g.cc = (Ca + 63) / 64;
+  g.M = (int)M; g.N = N; g.K = 27 * g.cc * 64; g.mode = mode; g.relu = relu; g.bias = bias; g.D = D;
+  g.ldd = ldd; g.err = n->err; g.act = act;
+  g.conv = 1; g.S = S; g.sign = sign; g.b_tap_mid = b_tap_mid ? 1 : 0;
+  g.kchunks = 27 * g.cc;
+  UCUDA(modil_tc::launch_gemm(ta, tb, g, bn, 1, n->s));
+  return rec(n);
+}
+
 modil_status conv_fwd(modil_unet* n, Conv& cv, const bf16* X, long long M, bf16* Y) {
+  if (cv.taps == 27 && n->implicit && cv.S >= 8)  // Wf [co][27][cin]; a tile of 128 voxels
+    return conv_gemm(n, X, cv.cin, cv.S, M, cv.Wf, 27, cv.co, cv.cin, 27LL * cv.cin, true, 1, Y, cv.cout, cv.cout,
+                     modil_tc::GEMM_STORE_BF16, 1, cv.bm, nullptr);
   k_im2col<<<gs(M * 27 * (cv.cin / 8)), kNT, 0, n->s>>>(X, cv.cin, cv.S, M, n->col);
   UCUDA(cudaGetLastError());
   modil_status st = rec(n);
@@ -454,6 +483,10 @@ modil_status conv_bwd(modil_unet* n, Conv& cv, const bf16* X, long long M, const
                  nullptr, true)))
     return st;
   if (!dx_f32 && !dx_bf16) return MODIL_OK;
+  if (cv.taps == 27 && n->implicit && cv.S >= 8)  // Wb [27][cin][co]; g has cout channels
+    return conv_gemm(n, g, cv.cout, cv.S, M, cv.Wb, cv.cin, 27, cv.co, (long long)cv.cin * cv.co, false, -1,
+                     dx_f32 ? static_cast<void*>(dx_f32) : static_cast<void*>(dx_bf16), cv.cin, cv.cin,
+                     dx_f32 ? modil_tc::GEMM_STORE_F32 : modil_tc::GEMM_STORE_BF16_MASK, 0, nullptr, act);
   if ((st = gemm(n, g, cv.cout, cv.Wb, cv.co, n->dcol, cv.K, (int)M, cv.K, cv.cout, modil_tc::GEMM_STORE_F32, 0,
                  nullptr, false)))
     return st;
@@ -844,6 +877,12 @@ modil_status modil_unet_train_step(modil_unet* n, const float* input, const floa
   modil_status st = eval_grad(n, input, target, loss);
   if (st) return st;
   return adam(n);
+}
+
+modil_status modil_unet_set_implicit(modil_unet* n, int implicit) {
+  if (!n) return fail(MODIL_ERR_ARG, "NULL argument");
+  n->implicit = implicit != 0;
+  return MODIL_OK;
 }
 
 modil_status modil_unet_profile_step(modil_unet* n, const float* input, const float* target, float* ms, int max,

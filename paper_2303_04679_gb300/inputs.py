@@ -180,19 +180,20 @@ def heat_k_init(value=0.02, n=HEAT_KNODES):
     return np.full(n, value, dtype=np.float64)
 
 
-def heat_workload(nt=512, nx=512, n_levels=7, seed=2, field=None):
+def heat_workload(nt=512, nx=512, n_levels=7, seed=2, field=None, frac=0.05, sigma=1e-3):
     """Conductivity inference on a 512 (x) by 512 (t) grid with 7 levels.
 
-    5 % of the cells carry measurements with Gaussian noise (sigma = 1e-3) of
-    the temperature record ``field`` (nt x nx): a solution of the forward
+    A fraction ``frac`` of the cells (5 %) carry measurements with Gaussian
+    noise (``sigma`` = 1e-3) of the temperature record ``field`` (nt x nx):
+    a solution of the forward
     problem with the reference conductivity (records.heat_record), or by
     default the closed-form constant-conductivity series; the initial
     profile is g(x) - g(0); 32 conductivity nodes start at 0.02.
     """
-    cells, vals = heat_measurements(nt, nx, 0.05, 1e-3, seed, field=field)
+    cells, vals = heat_measurements(nt, nx, frac, sigma, seed, field=field)
     return dict(shape=(nt, nx), n_levels=n_levels, meas_cell=cells, meas_value=vals,
                 aux=heat_ic(nx), knodes=heat_k_init(), w_res=1.0, w_data=1.0, w_reg=1e-4,
-                lr=1e-3)
+                lr=1e-3, k_scale=0.02)
 
 
 def burgers_workload(nt=64, nx=64, n_levels=4, seed=0, n_meas=200, nu=0.01):
@@ -371,13 +372,15 @@ def cavity_velocity(n):
     return u, v
 
 
-def cavity_workload(n=256, n_levels=8, n_samples=1000, seed=3, Re=100.0):
+def cavity_workload(n=256, n_levels=8, n_samples=1000, seed=3, Re=100.0, field=None):
     """Cavity at Re = 100 on n^2 cells with 8 levels: 1000 velocity samples
-    (u or v at seeded distinct cells) of the closed-form recirculating flow."""
+    (u or v at seeded distinct cells) of ``field`` = (u, v), a forward
+    solution (records.cavity_record), or by default of the closed-form
+    recirculating flow."""
     rng = make_rng(seed)
     cells = measurement_cells(n * n, n_samples, seed)
     fields = rng.integers(0, 2, size=n_samples).astype(np.int32)
-    u, v = cavity_velocity(n)
+    u, v = cavity_velocity(n) if field is None else field
     vals = np.where(fields == 0, u.reshape(-1)[cells], v.reshape(-1)[cells])
     return dict(shape=(n, n), n_levels=n_levels, meas_cell=cells, meas_field=fields,
                 meas_value=vals, coef=(Re, 1.0), lr=1e-3)

@@ -93,11 +93,16 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("levels,base,side,batch", [(2, 8, 8, 1), (4, 8, 16, 2), (4, 32, 16, 1)])
-def test_unet_forward_and_gradients(unet, levels, base, side, batch):
+@pytest.mark.parametrize("implicit", [True, False])
+@pytest.mark.parametrize("levels,base,side,batch", [(2, 8, 8, 1), (4, 8, 16, 2), (4, 32, 16, 1), (3, 16, 32, 1)])
+def test_unet_forward_and_gradients(unet, levels, base, side, batch, implicit):
+    """Forward pass, loss and every parameter gradient against the oracle,
+    with the 3x3x3 convolutions as implicit GEMMs (grids of 8^3 and more) or
+    through im2col."""
     import torch
     spec = U.Spec(levels=levels, base=base, in_ch=4, out_ch=5)
     net, params = _net(unet, spec, side, batch, seed=10 + levels + base)
+    net.set_implicit(implicit)
     rng = np.random.default_rng(20)
     x = rng.normal(size=(batch, side, side, side, 4)).astype(np.float32)
     y = rng.normal(size=(batch, side, side, side, 5)).astype(np.float32)
