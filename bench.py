@@ -289,7 +289,7 @@ def heat_inference(modil, w, args, chunk=250):
     constant nodes on the workload w, the conductivity error read every chunk
     of steps (wall time includes the reads)."""
     import torch
-    tols = (0.5, 0.3, 0.2, 0.15)
+    tols = (0.5, 0.3, 0.2, 0.1, 0.06)
     hits = {t: None for t in tols}
     hist = []
     with modil.Problem(make_desc(modil, w, "0x0")) as p:

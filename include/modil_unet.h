@@ -75,7 +75,11 @@ modil_status modil_unet_forward(modil_unet* net, const float* input, float* outp
  * synchronises) if not NULL. */
 modil_status modil_unet_eval_grad(modil_unet* net, const float* input, const float* target,
                                   double* loss);
-/* eval_grad followed by one Adam step on every parameter. */
+/* eval_grad followed by one Adam step on every parameter.  The first call
+ * captures the step (launches and memsets, the input and target copied into
+ * the network's own buffers first) as a CUDA graph that later calls replay;
+ * Adam's step counter and bias corrections are kept on the device.  If the
+ * capture fails the call falls back to direct launches. */
 modil_status modil_unet_train_step(modil_unet* net, const float* input, const float* target,
                                    double* loss);
 /* Per-launch device times of one training step (ms), launch by launch;
@@ -83,11 +87,17 @@ modil_status modil_unet_train_step(modil_unet* net, const float* input, const fl
 modil_status modil_unet_profile_step(modil_unet* net, const float* input, const float* target,
                                      float* ms, int max, int* n);
 
-/* How the 3x3x3 convolutions and their input gradients run: implicit = 1
- * (the default) as implicit GEMMs whose A operand TMA reads as shifted boxes
- * of the activations; 0 through explicit im2col / col2im buffers around the
- * same GEMM.  Both give the same sums up to the order of FP32 accumulation. */
+/* How the 3x3x3 convolutions and their input and weight gradients run on
+ * grids of 8^3 and more: implicit = 1 (the default) as implicit GEMMs whose
+ * operands TMA reads as shifted boxes of the activations; 0 through explicit
+ * im2col / col2im buffers around the same GEMM.  Both give the same sums up to
+ * the order of FP32 accumulation. */
 modil_status modil_unet_set_implicit(modil_unet* net, int implicit);
+
+/* Whether modil_unet_train_step replays a captured CUDA graph (1, the
+ * default) or launches every kernel directly (0); the two give bit-identical
+ * results. */
+modil_status modil_unet_set_graph(modil_unet* net, int on);
 
 /* D (+)= A B^T on the tensor cores: A [M][K] and B [N][K] BF16 row-major with
  * row pitches lda, ldb (elements, multiples of 8, 16-byte aligned bases);

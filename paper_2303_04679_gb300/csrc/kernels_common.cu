@@ -97,13 +97,16 @@ __device__ __forceinline__ void cp_async16_lv(void* dst, const void* src) {
 
 // One kLevTY x kLevTX tile of coarse level l (NF fields) over all instances:
 // dL/du_l = T^T dL/du_{l-1} from a staged region of the finer level's
-// gradient, then Adam on the tile.  Each thread finishes one coarse cell:
-// away from the level's ends its weights are the 4 x 4 tensor product of
-// (1/4, 3/4, 3/4, 1/4); within two cells of an end, the 6-tap windows.
+// gradient, then Adam on the tile.  Each thread finishes two coarse cells
+// (twice the loads in flight per thread as one cell: the kernel is bound by
+// memory latency): away from the level's ends their weights are the 4 x 4
+// tensor product of (1/4, 3/4, 3/4, 1/4); within two cells of an end, the
+// 6-tap windows.
 template <class T, int NF>
 __global__ void __launch_bounds__(MODIL_NT)
 k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
-  static_assert(kLevTY * kLevTX == MODIL_NT, "one coarse cell per thread");
+  constexpr int CPT = kLevTY * kLevTX / MODIL_NT;  // coarse cells per thread
+  static_assert(CPT * MODIL_NT == kLevTY * kLevTX, "whole cells per thread");
   // staged finer-level rows 2 y0 - 2 .., columns 2 x0 - 4 .. (4-element aligned)
   constexpr int FH = 2 * kLevTY + 4, FW = 2 * kLevTX + 8;
   __shared__ __align__(16) T fineS[NF * FH * FW];  // all fields staged at once
@@ -119,23 +122,32 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   const int y0 = ty * kLevTY, x0 = tx * kLevTX;
   const int ch = min(kLevTY, ny - y0), cw = min(kLevTX, nx - x0);
   const bool store_g = (mode != MODE_STEP) || (l < D.nlev - 1);
-  // cells packed as k = oy * cw + ox so that a ragged tile keeps the low threads busy
-  const int oy = threadIdx.x / cw, ox = threadIdx.x - (threadIdx.x / cw) * cw;
-  const bool mine = threadIdx.x < ch * cw;
-  const int Y = y0 + oy, X = x0 + ox;
-  const long long e = (long long)Y * nx + X;
+  // cells k = threadIdx.x + j * MODIL_NT packed as k = oy * cw + ox so that a
+  // ragged tile keeps the low threads busy
+  int Yc[CPT], Xc[CPT];
+  bool mine[CPT];
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    const int k = threadIdx.x + j * MODIL_NT;
+    const int oy = k / cw;
+    Yc[j] = y0 + oy;
+    Xc[j] = x0 + (k - oy * cw);
+    mine[j] = k < ch * cw;
+  }
   // Prologue: this level's parameters and moments were last written by the
   // same kernel one step earlier, two or more launches back.
-  T pv[NF], mv[NF];
-  double vv[NF];
+  T pv[CPT][NF], mv[CPT][NF];
+  double vv[CPT][NF];
+#pragma unroll
+  for (int j = 0; j < CPT; ++j)
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    pv[f] = T(0); mv[f] = T(0); vv[f] = 0.0;
-    if (mode == MODE_STEP && mine) {
-      const long long o = D.off[f][l] + e;
-      pv[f] = A.p[cur][o];
-      mv[f] = A.m[o];
-      vv[f] = A.v[o];
+    pv[j][f] = T(0); mv[j][f] = T(0); vv[j][f] = 0.0;
+    if (mode == MODE_STEP && mine[j]) {
+      const long long o = D.off[f][l] + (long long)Yc[j] * nx + Xc[j];
+      pv[j][f] = A.p[cur][o];
+      mv[j][f] = A.m[o];
+      vv[j][f] = A.v[o];
     }
   }
   if (threadIdx.x == 0) acS = adam_coef(D, A.st[ii]);  // once per block: no per-thread FP64
@@ -173,9 +185,12 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   cp_async_wait_all();
   __syncthreads();
 #pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    const T* fs = fineS + f * FH * FW;
-    if (mine) {
+  for (int j = 0; j < CPT; ++j) {
+    const int Y = Yc[j], X = Xc[j];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const T* fs = fineS + f * FH * FW;
+      if (!mine[j]) continue;
       T g;
       if (Y >= 2 && Y <= ny - 3 && X >= 2 && X <= nx - 3) {
         const T* s = fs + (2 * Y - 1 - oY) * FW + (2 * X - 1 - oX);
@@ -204,14 +219,14 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
           g += wy[i] * h;
         }
       }
-      const long long o = D.off[f][l] + e;
+      const long long o = D.off[f][l] + (long long)Y * nx + X;
       if (store_g) A.g[o] = g;
       if (mode == MODE_STEP) {
         const AdamCoef ac = acS;
-        adam_update(pv[f], mv[f], vv[f], g, ac);
-        A.p[cur ^ 1][o] = pv[f];
-        A.m[o] = mv[f];
-        A.v[o] = vv[f];
+        adam_update(pv[j][f], mv[j][f], vv[j][f], g, ac);
+        A.p[cur ^ 1][o] = pv[j][f];
+        A.m[o] = mv[j][f];
+        A.v[o] = vv[j][f];
       }
     }
   }

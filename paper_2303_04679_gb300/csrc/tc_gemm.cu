@@ -77,6 +77,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
                                             int c2, int c3, int c4) {
   asm volatile(
@@ -158,7 +167,9 @@ k_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorM
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int nk_total = (g.K + BK - 1) / BK;
-  const int kc0 = blockIdx.z * g.kchunks;
+  // weight gradient of a convolution: blockIdx.z = tap * wsplits + split
+  const int wtap = g.conv == 2 ? (int)blockIdx.z / g.wsplits : 0;
+  const int kc0 = (g.conv == 2 ? (int)blockIdx.z - wtap * g.wsplits : (int)blockIdx.z) * g.kchunks;
   const int kc1 = min(nk_total, kc0 + g.kchunks);
   const int nk = max(0, kc1 - kc0);
 
@@ -197,7 +208,16 @@ k_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorM
         if (*abort_flag) break;
         unsigned char* st = smem + s * Smem<BN>::STAGE;
         mbar_expect_tx(full + s, Smem<BN>::STAGE);
-        if (g.conv) {
+        if (g.conv == 2) {
+          // chunk -> its first voxel (x and y flattened: a y shift is an
+          // offset of S, 16-byte aligned for S >= 8, and rows past the plane's
+          // ends read as zero); the tap's x-shifted copy
+          const int v0 = (kc0 + i) * BK, S = g.S, S2 = S * S;
+          const int xy0 = v0 % S2, r2 = v0 / S2, z0 = r2 % S, b0 = r2 / S;
+          const int dz = wtap / 9 - 1, dy = (wtap / 3) % 3 - 1, dx = wtap % 3 - 1;
+          tma_load_4d(st, &ta, full + s, xy0 + dy * S, z0 + dz, b0, (dx + 1) * g.wC + m0);
+          tma_load_2d(st + Smem<BN>::A_BYTES, &tb, full + s, v0, n0);
+        } else if (g.conv) {
           // chunk -> (tap, channel block); the output tile's first voxel
           const int kc = kc0 + i, tap = kc / g.cc, c0 = (kc - tap * g.cc) * BK;
           const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
@@ -284,8 +304,8 @@ k_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorM
         } else {
           for (int j = 0; j < ncol; ++j) d[j] = v[j];
         }
-      } else {  // GEMM_ATOMIC_F32
-        float* d = static_cast<float*>(g.D) + (long long)row * g.ldd + col;
+      } else {  // GEMM_ATOMIC_F32 (weight gradients: rows of the tap)
+        float* d = static_cast<float*>(g.D) + ((long long)wtap * g.wC + row) * g.ldd + col;
         for (int j = 0; j < ncol; ++j) atomicAdd(d + j, v[j]);
       }
     }
@@ -300,18 +320,41 @@ k_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorM
 }
 
 template <int BN>
-static cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits,
-                             cudaStream_t s) {
-  const size_t smem = Smem<BN>::BYTES;
+static cudaError_t set_smem_attr() {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Smem<BN>::BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  return cudaSuccess;
+}
+
+template <int BN>
+static cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int splits,
+                             cudaStream_t s) {
+  const size_t smem = Smem<BN>::BYTES;
+  cudaError_t e = set_smem_attr<BN>();
+  if (e != cudaSuccess) return e;
   dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, splits);
   k_gemm<BN><<<grid, NTHREADS, smem, s>>>(ta, tb, g);
   return cudaGetLastError();
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiled encoder();
+
+cudaError_t prepare_gemm() {
+  if (!encoder()) return cudaErrorNotSupported;
+  cudaError_t e = set_smem_attr<16>();
+  if (e == cudaSuccess) e = set_smem_attr<32>();
+  if (e == cudaSuccess) e = set_smem_attr<64>();
+  if (e == cudaSuccess) e = set_smem_attr<128>();
+  if (e == cudaSuccess) e = set_smem_attr<256>();
+  return e;
 }
 
 cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& g, int bn, int splits,
@@ -329,10 +372,6 @@ cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const Gemm
 // ---------------------------------------------------------------------------
 // Tensor maps (driver entry point fetched through the runtime once)
 // ---------------------------------------------------------------------------
-typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 static EncodeTiled encoder() {
   static EncodeTiled fn = nullptr;
   if (!fn) {
@@ -375,6 +414,23 @@ int make_act_map(CUtensorMap* m, const void* base, int C, int S, int B) {
   cuuint32_t box[5] = {(cuuint32_t)BK, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -3;
+}
+
+int make_shift3_map(CUtensorMap* m, const void* base, int C, int S, int B) {
+  EncodeTiled enc = encoder();
+  if (!enc) return -1;
+  // x and y flattened into one axis of S^2 voxels, so that a K chunk is one
+  // 64-voxel (128-byte) line: the 128B swizzle pattern assumes 128-byte rows
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || S < 8 || (S * S) % BK) return -2;
+  const cuuint64_t ps = (cuuint64_t)S * S * 2;  // bytes of one z plane
+  cuuint64_t dims[4] = {(cuuint64_t)S * S, (cuuint64_t)S, (cuuint64_t)B, (cuuint64_t)3 * C};
+  cuuint64_t strides[3] = {ps, ps * S, ps * S * B};
+  cuuint32_t box[4] = {(cuuint32_t)BK, 1, 1, (cuuint32_t)BM};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -3;

@@ -1,8 +1,13 @@
 // Learned warm start: a 3-D convolutional U-Net trained and evaluated by this
-// library's kernels.  Every convolution is an im2col GEMM on the tensor cores
-// (tc_gemm.cu); the rest (im2col and its transpose, col2im, pooling,
-// upsampling, masks, loss, bias gradients, Adam) are the small streaming
-// kernels below.  Network, arithmetic and layouts: include/modil_unet.h.
+// library's kernels.  Every convolution is a GEMM on the tensor cores
+// (tc_gemm.cu): on grids of 8^3 and more the 3x3x3 convolutions, their input
+// gradients and their weight gradients are implicit GEMMs whose operands TMA
+// reads as shifted boxes of the activations (the weight gradient from three
+// x-shifted transposed copies, the innermost axis admitting no odd offset);
+// smaller grids and the 1x1x1 head go through im2col.  The rest (transposes,
+// pooling, upsampling, masks, loss, bias gradients, Adam) are the small
+// streaming kernels below.  Network, arithmetic and layouts:
+// include/modil_unet.h.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -94,6 +99,29 @@ __global__ void k_transpose(const bf16* __restrict__ X, long long R, int Cc, bf1
     const int c = c0 + j;
     const long long r = r0 + threadIdx.x;
     if (c < Cc && r < R) Y[(long long)c * ldy + r] = tile[threadIdx.x][j];
+  }
+}
+
+// xt3[(d + 1) C + c][v] = X[v + d e_x][c] for d = -1, 0, 1 (zero where x + d
+// leaves the grid): three x-shifted transposed copies, rows of pitch ld >= M.
+// A 32-voxel x 32-channel tile with one voxel of halo on each side.
+__global__ void k_shift3(const bf16* __restrict__ X, long long M, int C, int S, bf16* __restrict__ xt3, long long ld) {
+  __shared__ bf16 tile[34][33];
+  const long long v0 = (long long)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 34; j += 8) {
+    const long long v = v0 - 1 + j;
+    const int c = c0 + threadIdx.x;
+    tile[j][threadIdx.x] = (v >= 0 && v < M && c < C) ? X[v * C + c] : __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  const long long v = v0 + threadIdx.x;
+  const int x = (int)(v % S);
+  for (int j = threadIdx.y; j < 96; j += 8) {
+    const int d = j >> 5, cl = j & 31, c = c0 + cl;
+    if (c >= C || v >= M) continue;
+    const int xs = x + d - 1;
+    xt3[((long long)d * C + c) * ld + v] = (xs >= 0 && xs < S) ? tile[threadIdx.x + d][cl] : __float2bfloat16_rn(0.f);
   }
 }
 
@@ -287,25 +315,51 @@ __global__ void k_head_loss(const float* __restrict__ outp, int oc, long long M,
 }
 
 // db[c] += sum over rows of g[r][c]
+// db[c] += sum over the block's kBiasRows rows of g[r][c]: 16-byte loads of 8
+// channels, the block's partial sums combined in shared memory, one atomic per
+// channel and block.  C a multiple of 8, at most 8 kNT.
+constexpr int kBiasRows = 4096;
 __global__ void k_bias_grad(const bf16* __restrict__ g, long long M, int C, float* __restrict__ db) {
-  const int groups = max(1, kNT / C);
-  const int c = threadIdx.x % C, grp = threadIdx.x / C;
-  if (grp >= groups || threadIdx.x >= groups * C) return;
-  const long long r0 = (long long)blockIdx.x * 1024;
-  const long long r1 = min(M, r0 + 1024);
-  for (int cc = c; cc < C; cc += kNT) {
+  __shared__ float red[kNT * 8];
+  const int vpr = C / 8;        // 16-byte vectors per row
+  const int rpi = kNT / vpr;    // rows per pass of the block
+  const int l8 = threadIdx.x % vpr, rs = threadIdx.x / vpr;
+  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const long long r0 = (long long)blockIdx.x * kBiasRows, r1 = min(M, r0 + kBiasRows);
+  for (long long r = r0 + rs; rs < rpi && r < r1; r += rpi) {  // threads past rpi * vpr idle
+    const uint4 q = *reinterpret_cast<const uint4*>(g + r * C + l8 * 8);
+    const bf16* h = reinterpret_cast<const bf16*>(&q);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] += __bfloat162float(h[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) red[threadIdx.x * 8 + k] = a[k];
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += kNT) {
+    const int v = c / 8, k = c % 8;
     float s = 0.f;
-    for (long long r = r0 + grp; r < r1; r += groups) s += __bfloat162float(g[r * C + cc]);
-    atomicAdd(db + cc, s);
-    if (C <= kNT) break;
+    for (int j = 0; j < rpi; ++j) s += red[(j * vpr + v) * 8 + k];
+    atomicAdd(db + c, s);
   }
 }
 
+// The step counter and Adam's bias corrections live on the device, so that a
+// captured training step replays with the right coefficients:
+// st[0] = step (as double), st[1] = 1 / (1 - b1^step), st[2] = 1 / (1 - b2^step).
+__global__ void k_adam_step(double* st, double b1, double b2) {
+  if (threadIdx.x != 0) return;
+  const double t = st[0] + 1.0;
+  st[0] = t;
+  st[1] = 1.0 / (1.0 - pow(b1, t));
+  st[2] = 1.0 / (1.0 - pow(b2, t));
+}
+
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
-                       float c2) {
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps,
+                       const double* __restrict__ st) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const float c1 = (float)st[1], c2 = (float)st[2];
   const float gi = g[i];
   const float mi = b1 * m[i] + (1.f - b1) * gi;
   const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
@@ -372,6 +426,11 @@ struct modil_unet {
   double* loss = nullptr;
   int* err = nullptr;
   long long step = 0;
+  double* adam_st = nullptr;        // device: step, bias corrections (k_adam_step)
+  // the training step as one CUDA graph (inputs copied into owned buffers)
+  bool use_graph = true;
+  cudaGraphExec_t exec = nullptr;
+  float *in_buf = nullptr, *tgt_buf = nullptr;
   std::vector<Conv*> convs;  // parameter order
   // profiling
   bool prof = false;
@@ -463,7 +522,7 @@ modil_status conv_fwd(modil_unet* n, Conv& cv, const bf16* X, long long M, bf16*
 modil_status conv_bwd(modil_unet* n, Conv& cv, const bf16* X, long long M, const bf16* g, float* dx_f32,
                       const bf16* act, bf16* dx_bf16) {
   modil_status st;
-  k_bias_grad<<<blocks(M, 1024), kNT, 0, n->s>>>(g, M, cv.cout, cv.db);
+  k_bias_grad<<<blocks(M, kBiasRows), kNT, 0, n->s>>>(g, M, cv.cout, cv.db);
   UCUDA(cudaGetLastError());
   if ((st = rec(n))) return st;
   // voxel-major operands of the weight gradient; row pitch padded to 8 for TMA
@@ -471,17 +530,40 @@ modil_status conv_bwd(modil_unet* n, Conv& cv, const bf16* X, long long M, const
   dim3 tb(32, 8);
   k_transpose<<<dim3((unsigned)((M + 31) / 32), (cv.cout + 31) / 32), tb, 0, n->s>>>(g, M, cv.cout, n->gt, Mp);
   UCUDA(cudaGetLastError());
-  k_transpose<<<dim3((unsigned)((M + 31) / 32), (cv.cin + 31) / 32), tb, 0, n->s>>>(X, M, cv.cin, n->xt, Mp);
-  UCUDA(cudaGetLastError());
-  if (cv.S % 8 == 0)
-    k_shift_t8<<<dim3(blocks(M / 8), cv.K), kNT, 0, n->s>>>(n->xt, cv.cin, cv.S, M, Mp, n->colT);
-  else
-    k_shift_t<<<dim3(blocks(M), cv.K), kNT, 0, n->s>>>(n->xt, cv.cin, cv.S, M, Mp, n->colT);
-  UCUDA(cudaGetLastError());
-  if ((st = rec(n))) return st;
-  if ((st = gemm(n, n->colT, Mp, n->gt, Mp, cv.dW, cv.co, cv.K, cv.cout, (int)M, modil_tc::GEMM_ATOMIC_F32, 0,
-                 nullptr, true)))
-    return st;
+  if (cv.taps == 27 && n->implicit && cv.S >= 8) {
+    // implicit: the A operand is read by TMA from three x-shifted transposed
+    // copies of X (y and z shifts are box offsets), per tap in blockIdx.z
+    k_shift3<<<dim3((unsigned)((M + 31) / 32), (cv.cin + 31) / 32), tb, 0, n->s>>>(X, M, cv.cin, cv.S, n->xt, Mp);
+    UCUDA(cudaGetLastError());
+    if ((st = rec(n))) return st;
+    CUtensorMap ta, tmb;
+    const int bn = pick_bn(cv.cout);
+    const long long S3 = (long long)cv.S * cv.S * cv.S;
+    if (Mp != M || M % S3 || modil_tc::make_shift3_map(&ta, n->xt, cv.cin, cv.S, (int)(M / S3)) != 0 ||
+        modil_tc::make_kmajor_map(&tmb, n->gt, cv.cout, M, Mp, bn) != 0)
+      return fail(MODIL_ERR_ARG, "tensor map of a weight gradient");
+    GemmArgs ga{};
+    ga.M = cv.cin; ga.N = cv.cout; ga.K = (int)M; ga.mode = modil_tc::GEMM_ATOMIC_F32; ga.D = cv.dW; ga.ldd = cv.co;
+    ga.err = n->err; ga.conv = 2; ga.S = cv.S; ga.wC = cv.cin;
+    const long long nk = M / 64, tiles = (long long)((cv.cin + 127) / 128) * ((cv.cout + bn - 1) / bn);
+    const long long want = std::max<long long>(1, (2 * 152 + 27 * tiles - 1) / (27 * tiles));
+    ga.kchunks = (int)((nk + want - 1) / want);
+    ga.wsplits = (int)((nk + ga.kchunks - 1) / ga.kchunks);
+    UCUDA(modil_tc::launch_gemm(ta, tmb, ga, bn, 27 * ga.wsplits, n->s));
+    if ((st = rec(n))) return st;
+  } else {
+    k_transpose<<<dim3((unsigned)((M + 31) / 32), (cv.cin + 31) / 32), tb, 0, n->s>>>(X, M, cv.cin, n->xt, Mp);
+    UCUDA(cudaGetLastError());
+    if (cv.S % 8 == 0)
+      k_shift_t8<<<dim3(blocks(M / 8), cv.K), kNT, 0, n->s>>>(n->xt, cv.cin, cv.S, M, Mp, n->colT);
+    else
+      k_shift_t<<<dim3(blocks(M), cv.K), kNT, 0, n->s>>>(n->xt, cv.cin, cv.S, M, Mp, n->colT);
+    UCUDA(cudaGetLastError());
+    if ((st = rec(n))) return st;
+    if ((st = gemm(n, n->colT, Mp, n->gt, Mp, cv.dW, cv.co, cv.K, cv.cout, (int)M, modil_tc::GEMM_ATOMIC_F32, 0,
+                   nullptr, true)))
+      return st;
+  }
   if (!dx_f32 && !dx_bf16) return MODIL_OK;
   if (cv.taps == 27 && n->implicit && cv.S >= 8)  // Wb [27][cin][co]; g has cout channels
     return conv_gemm(n, g, cv.cout, cv.S, M, cv.Wb, cv.cin, 27, cv.co, (long long)cv.cin * cv.co, false, -1,
@@ -530,7 +612,7 @@ modil_status backward(modil_unet* n) {
   const int L = n->L;
   const long long M0 = n->M[0];
   // head
-  k_bias_grad<<<blocks(M0, 1024), kNT, 0, n->s>>>(n->dout, M0, kHeadPad, n->head.db);
+  k_bias_grad<<<blocks(M0, kBiasRows), kNT, 0, n->s>>>(n->dout, M0, kHeadPad, n->head.db);
   UCUDA(cudaGetLastError());
   dim3 tb(32, 8);
   k_transpose<<<dim3((unsigned)((M0 + 31) / 32), 1), tb, 0, n->s>>>(n->dout, M0, kHeadPad, n->gt, M0);
@@ -619,14 +701,14 @@ modil_status eval_grad(modil_unet* n, const float* input, const float* target, d
 modil_status adam(modil_unet* n) {
   n->step += 1;
   const double b1 = n->d.adam_beta1, b2 = n->d.adam_beta2;
-  const float c1 = (float)(1.0 / (1.0 - std::pow(b1, (double)n->step)));
-  const float c2 = (float)(1.0 / (1.0 - std::pow(b2, (double)n->step)));
+  k_adam_step<<<1, 32, 0, n->s>>>(n->adam_st, b1, b2);
+  UCUDA(cudaGetLastError());
   for (Conv* cv : n->convs) {
     const long long nw = (long long)cv->K * cv->co;
     k_adam<<<blocks(nw), kNT, 0, n->s>>>(cv->Wm, cv->dW, cv->mW, cv->vW, nw, (float)n->d.adam_lr, (float)b1,
-                                         (float)b2, (float)n->d.adam_eps, c1, c2);
+                                         (float)b2, (float)n->d.adam_eps, n->adam_st);
     k_adam<<<blocks(cv->co), kNT, 0, n->s>>>(cv->bm, cv->db, cv->mb, cv->vb, cv->co, (float)n->d.adam_lr,
-                                             (float)b1, (float)b2, (float)n->d.adam_eps, c1, c2);
+                                             (float)b1, (float)b2, (float)n->d.adam_eps, n->adam_st);
     UCUDA(cudaGetLastError());
     modil_status st = refresh(n, *cv);
     if (st) return st;
@@ -685,6 +767,10 @@ modil_status modil_unet_create(const modil_unet_desc* d, void* stream, modil_une
   modil_unet* n = new modil_unet();
   n->d = *d;
   n->s = static_cast<cudaStream_t>(stream);
+  if (modil_tc::prepare_gemm() != cudaSuccess) {
+    delete n;
+    return fail(MODIL_ERR_CUDA, "tensor-core GEMM setup (shared-memory attributes, tensor-map encoder)");
+  }
   n->L = d->levels;
   const int L = n->L;
   for (int l = 0; l < L; ++l) {
@@ -698,7 +784,7 @@ modil_status modil_unet_create(const modil_unet_desc* d, void* stream, modil_une
     const size_t Mp = (size_t)((M + 7) & ~7LL);
     col = std::max(col, Mp * cv.K);
     dcol = std::max(dcol, (size_t)M * cv.K);
-    xt = std::max(xt, Mp * cv.cin);
+    xt = std::max(xt, 3 * Mp * cv.cin);  // three shifted copies (implicit weight gradient)
     gt = std::max(gt, Mp * cv.cout);
   };
   n->enc_a.resize(L); n->enc_b.resize(L); n->dec_c.resize(L); n->dec_d.resize(L);
@@ -757,8 +843,11 @@ modil_status modil_unet_create(const modil_unet_desc* d, void* stream, modil_une
   n->gt = dalloc<bf16>(P, gt);
   n->loss = dalloc<double>(P, 1);
   n->err = dalloc<int>(P, 1);
+  n->adam_st = dalloc<double>(P, 3);
+  n->in_buf = dalloc<float>(P, (size_t)M0 * d->in_ch);
+  n->tgt_buf = dalloc<float>(P, (size_t)M0 * d->out_ch);
   ok &= n->x0 && n->out && n->dout && n->ghead && n->g1 && n->g2 && n->col && n->colT && n->dcol && n->xt && n->gt &&
-        n->loss && n->err;
+        n->loss && n->err && n->adam_st && n->in_buf && n->tgt_buf;
   if (!ok) {
     modil_unet_destroy(n);
     return fail(MODIL_ERR_OOM, "device allocation of the network failed");
@@ -772,6 +861,7 @@ modil_status modil_unet_create(const modil_unet_desc* d, void* stream, modil_une
     cudaMemsetAsync(cv->Wb, 0, nw * sizeof(bf16), n->s);
   }
   cudaMemsetAsync(n->err, 0, sizeof(int), n->s);
+  cudaMemsetAsync(n->adam_st, 0, 3 * sizeof(double), n->s);
   cudaError_t e = cudaStreamSynchronize(n->s);
   if (e != cudaSuccess) {
     modil_unet_destroy(n);
@@ -784,6 +874,7 @@ modil_status modil_unet_create(const modil_unet_desc* d, void* stream, modil_une
 void modil_unet_destroy(modil_unet* n) {
   if (!n) return;
   cudaStreamSynchronize(n->s);
+  if (n->exec) cudaGraphExecDestroy(n->exec);
   for (void* p : n->pool) cudaFree(p);
   for (cudaEvent_t e : n->ev) cudaEventDestroy(e);
   delete n;
@@ -872,8 +963,58 @@ modil_status modil_unet_eval_grad(modil_unet* n, const float* input, const float
   return eval_grad(n, input, target, loss);
 }
 
+// One training step as a captured CUDA graph: the ~150 launches and memsets
+// of a step cost more host time than the GPU spends on a 32^3 step.  The
+// caller's input and target are copied into owned buffers first, so that the
+// graph (captured once) reads fixed addresses; Adam's coefficients are on the
+// device.  Any capture failure falls back to direct launches for good.
+modil_status train_graph(modil_unet* n, const float* input, const float* target, double* loss) {
+  const long long M0 = n->M[0];
+  UCUDA(cudaMemcpyAsync(n->in_buf, input, sizeof(float) * (size_t)M0 * n->d.in_ch, cudaMemcpyDeviceToDevice, n->s));
+  UCUDA(cudaMemcpyAsync(n->tgt_buf, target, sizeof(float) * (size_t)M0 * n->d.out_ch, cudaMemcpyDeviceToDevice,
+                        n->s));
+  if (!n->exec) {
+    cudaGraph_t g = nullptr;
+    UCUDA(cudaStreamBeginCapture(n->s, cudaStreamCaptureModeThreadLocal));
+    modil_status st = eval_grad(n, n->in_buf, n->tgt_buf, nullptr);
+    if (!st) st = adam(n);
+    n->step -= 1;  // counted when the graph runs
+    cudaError_t e = cudaStreamEndCapture(n->s, &g);
+    if (st || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      n->use_graph = false;
+      return st ? st : fail(MODIL_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&n->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      n->exec = nullptr;
+      n->use_graph = false;
+      return fail(MODIL_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+  }
+  UCUDA(cudaGraphLaunch(n->exec, n->s));
+  n->step += 1;
+  if (loss) {
+    double l = 0;
+    int e = 0;
+    UCUDA(cudaMemcpyAsync(&l, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->s));
+    UCUDA(cudaMemcpyAsync(&e, n->err, sizeof(int), cudaMemcpyDeviceToHost, n->s));
+    UCUDA(cudaStreamSynchronize(n->s));
+    if (e) return fail(MODIL_ERR_TIMEOUT, "tensor-core GEMM wait timed out (code " + std::to_string(e) + ")");
+    *loss = l / ((double)M0 * n->d.out_ch);
+  }
+  return MODIL_OK;
+}
+
 modil_status modil_unet_train_step(modil_unet* n, const float* input, const float* target, double* loss) {
   if (!n || !input || !target) return fail(MODIL_ERR_ARG, "NULL argument");
+  if (n->use_graph) {
+    modil_status st = train_graph(n, input, target, loss);
+    if (st == MODIL_OK || n->use_graph) return st;
+    // capture failed: run this step directly (the copies above are harmless)
+  }
   modil_status st = eval_grad(n, input, target, loss);
   if (st) return st;
   return adam(n);
@@ -881,7 +1022,18 @@ modil_status modil_unet_train_step(modil_unet* n, const float* input, const floa
 
 modil_status modil_unet_set_implicit(modil_unet* n, int implicit) {
   if (!n) return fail(MODIL_ERR_ARG, "NULL argument");
+  if (n->implicit != (implicit != 0) && n->exec) {  // the captured step used the other path
+    UCUDA(cudaStreamSynchronize(n->s));
+    cudaGraphExecDestroy(n->exec);
+    n->exec = nullptr;
+  }
   n->implicit = implicit != 0;
+  return MODIL_OK;
+}
+
+modil_status modil_unet_set_graph(modil_unet* n, int on) {
+  if (!n) return fail(MODIL_ERR_ARG, "NULL argument");
+  n->use_graph = on != 0;
   return MODIL_OK;
 }
 

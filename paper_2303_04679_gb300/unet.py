@@ -26,6 +26,7 @@ _SIG = {
     "modil_unet_create": ([C.POINTER(unet_desc), _P, C.POINTER(_P)], C.c_int),
     "modil_unet_destroy": ([_P], None),
     "modil_unet_set_implicit": ([_P, C.c_int], C.c_int),
+    "modil_unet_set_graph": ([_P, C.c_int], C.c_int),
     "modil_unet_param_count": ([_P, C.POINTER(C.c_int)], C.c_int),
     "modil_unet_param_shape": ([_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "modil_unet_write_param": ([_P, C.c_int, C.POINTER(C.c_float), C.c_size_t], C.c_int),
@@ -80,6 +81,10 @@ class UNet:
     def set_implicit(self, on=True):
         """3x3x3 convolutions as implicit GEMMs (default) or through im2col."""
         _check(LIB.modil_unet_set_implicit(self._h, 1 if on else 0))
+
+    def set_graph(self, on=True):
+        """Training steps replayed from a captured CUDA graph (default) or launched directly."""
+        _check(LIB.modil_unet_set_graph(self._h, 1 if on else 0))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -174,3 +174,35 @@ def test_unet_training_reduces_loss(unet):
     # the FP64 oracle with the same Adam settings goes from 0.48 to 0.15 here
     assert last < 0.45 * first, (first, last)
     net.close()
+
+
+def test_graph_replayed_steps_equal_direct_steps(unet):
+    """Training steps replayed from the captured graph (inputs copied into the
+    network's buffers, Adam's coefficients on the device) match the same steps
+    launched directly, with a new input tensor every step.  The loss and the
+    split-K weight gradients are summed with atomics, so the two agree to the
+    order of those sums: the losses to 1e-12, the parameters within 1e-6
+    except where Adam's sign step flips on a near-zero gradient (a stale input
+    would change the loss, a wrong bias correction every parameter)."""
+    import torch
+    spec = U.Spec(levels=3, base=8, in_ch=4, out_ch=5)
+    nets = []
+    for graph in (True, False):
+        net, _ = _net(unet, spec, 16, 1, seed=60)
+        net.set_graph(graph)
+        nets.append(net)
+    rng = np.random.default_rng(61)
+    for _ in range(4):
+        x = torch.from_numpy(rng.normal(size=(1, 16, 16, 16, 4)).astype(np.float32)).cuda()
+        y = torch.from_numpy(rng.normal(size=(1, 16, 16, 16, 5)).astype(np.float32)).cuda()
+        losses = [net.train_step(x.clone(), y.clone()) for net in nets]
+        assert abs(losses[0] - losses[1]) <= 1e-12 * abs(losses[1]), losses
+    close = total = 0
+    for a, b in zip(nets[0].read_params(), nets[1].read_params()):
+        d = np.abs(a - b)
+        assert np.all(d <= 8e-3), float(d.max())  # at most one sign flip per step (lr 1e-3)
+        close += int(np.sum(d <= 1e-6))
+        total += d.size
+    assert close >= 0.99 * total, (close, total)
+    for net in nets:
+        net.close()
