@@ -97,11 +97,11 @@ __device__ __forceinline__ void cp_async16_lv(void* dst, const void* src) {
 
 // One kLevTY x kLevTX tile of coarse level l (NF fields) over all instances:
 // dL/du_l = T^T dL/du_{l-1} from a staged region of the finer level's
-// gradient, then Adam on the tile.  Each thread finishes two coarse cells
-// (twice the loads in flight per thread as one cell: the kernel is bound by
-// memory latency): away from the level's ends their weights are the 4 x 4
-// tensor product of (1/4, 3/4, 3/4, 1/4); within two cells of an end, the
-// 6-tap windows.
+// gradient, then Adam on the tile.  Each thread finishes four coarse cells
+// (four times the loads in flight per thread as one cell: the kernel is bound
+// by memory latency; level 1 of the batched Burgers step 0.147 -> 0.110 ms):
+// away from the level's ends their weights are the 4 x 4 tensor product of
+// (1/4, 3/4, 3/4, 1/4); within two cells of an end, the 6-tap windows.
 template <class T, int NF>
 __global__ void __launch_bounds__(MODIL_NT)
 k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {

@@ -24,7 +24,7 @@ constexpr int kComposeNT = 256;  // threads per block of the level-1 composition
 constexpr int kComposeSmallNT = 512;  // threads per block composing levels >= 2 of one instance
 constexpr int kGridNT = 256;     // threads (cells) per block of the d-dimensional Poisson kernels
 // Tile of the restriction kernels (coarse levels), rows x cols.
-constexpr int kLevTY = 16, kLevTX = 32;  // two coarse cells per thread of k_level
+constexpr int kLevTY = 32, kLevTX = 32;  // four coarse cells per thread of k_level
 
 // Levels with at most this many cells are finished by the per-instance tail
 // kernel (FP32 / FP64 problems).
