@@ -319,9 +319,11 @@ modil_status modil_eval_grad_noalloc(const modil_desc* desc, const void* levels,
 /* Limited-memory BFGS on the levels of a problem: the optimiser the paper
  * uses for most of its results (SciPy's L-BFGS-B without bounds, Section 2.1;
  * a history of 50 pairs in Section 3.1).  The paper gives no algorithmic
- * detail; this is the textbook method: direction -H g by the two-loop
- * recursion over the newest `history` pairs (s, y) with H0 = (s.y / y.y) I of
- * the newest pair; the first direction -g with a first trial step of
+ * detail; this is the textbook method: direction -H g over the newest
+ * `history` pairs (s, y) with H0 = (s.y / y.y) I of the newest pair, H g
+ * evaluated in the compact representation (Byrd, Nocedal and Schnabel 1994;
+ * the same H g as the two-loop recursion) from batched dot products and one
+ * pass over the stored vectors; the first direction -g with a first trial step of
  * 1 / ||g||; backtracking on the Armijo condition f(x + t d) <= f(x) +
  * 1e-4 t g.d, halving t, at most 40 trials (the run stops when none passes
  * or g.d >= 0); a pair is kept only when s.y > 1e-12 y.y.  Vectors live on

@@ -25,5 +25,15 @@ cudaError_t lb_sub(T* z, const T* x, const T* y, long long n, cudaStream_t s);
 template <class T>
 cudaError_t lb_mul(T* z, const T* x, double a, long long n, cudaStream_t s);
 int lb_dot_partials();
+// out[d] = va[d] . vb[d] for d < ndots (device pointer arrays); part:
+// lb_mdot_partials(ndots) doubles of scratch.
+template <class T>
+cudaError_t lb_mdot(const T* const* va, const T* const* vb, int ndots, long long n, double* part, double* out,
+                    cudaStream_t s);
+int lb_mdot_partials(int ndots);
+// r = c0 g + sum_k coef[k] v[k] (device pointer and coefficient arrays).
+template <class T>
+cudaError_t lb_combine(T* r, const T* g, double c0, const T* const* v, const double* coef, int nv, long long n,
+                       cudaStream_t s);
 
 }  // namespace modil

@@ -1384,13 +1384,18 @@ struct modil_lbfgs {
   long long nl = 0;          // of which the levels (all fields)
   int nk = 0;                // and the conductivity nodes (heat without k_fixed; else 0)
   double ks = 1.0;           // the vector holds the nodes in units of k_scale
-  void* vec = nullptr;       // device: S[m], Y[m], then 6 work vectors, problem dtype
-  double* dsc = nullptr;     // device: dot partials, rho[m], alpha[m], sy[m], yy[m], beta, scratch
+  void* vec = nullptr;       // device: S[m], Y[m], then 7 work vectors, problem dtype
+  double* dsc = nullptr;     // device: dot partials, batched-dot partials and results, coefficients, scratch
+  void** ptrs = nullptr;     // device: vector-pointer arrays of the batched dots and of the combination
   std::vector<int> order;    // slots of the stored pairs, oldest first
+  std::vector<double> SY, YY;  // host, m x m by slot: s_i . y_j and y_i . y_j of stored pairs
+  std::vector<double> a, b;    // host, by slot: s_i . g and y_i . g at the current gradient
   long long iters = 0;       // iterations completed over the optimiser's life
 };
 
 namespace {
+
+int lbfgs_max_dots(int m) { return 5 + 4 * m; }
 
 template <class T>
 Arena<T>& arena_of(modil_problem* p);
@@ -1399,6 +1404,15 @@ Arena<float>& arena_of<float>(modil_problem* p) { return p->A32; }
 template <>
 Arena<double>& arena_of<double>(modil_problem* p) { return p->A64; }
 
+// L-BFGS in the compact representation (Byrd, Nocedal and Schnabel 1994):
+// with the stored pairs oldest first as the columns of S and Y, R the upper
+// triangle of S^T Y, D its diagonal and gamma = s.y / y.y of the newest pair,
+//   H g = gamma g + S u + gamma Y w,  w = -R^{-1} S^T g,
+//   u = R^{-T} ((D + gamma Y^T Y) R^{-1} S^T g - gamma Y^T g),
+// the same H g as the two-loop recursion (H0 = gamma I).  The products S^T g,
+// Y^T g and the new entries of S^T Y and Y^T Y are batched dot products, the
+// small triangular solves run on the host, and H g is one pass over the
+// vectors: a few launches per iteration instead of four per stored pair.
 template <class T>
 modil_status lbfgs_run_t(modil_lbfgs* o, int iters, double* loss, int* done) {
   constexpr double kC1 = 1e-4, kCurv = 1e-12;
@@ -1415,15 +1429,18 @@ modil_status lbfgs_run_t(modil_lbfgs* o, int iters, double* loss, int* done) {
   T* xt = x + n;
   T* g = xt + n;
   T* gn = g + n;
-  T* q = gn + n;
-  T* r = q + n;
+  T* q = gn + n;  // s of the candidate pair
+  T* r = q + n;   // H g
+  T* yv = r + n;  // y of the candidate pair
+  const int maxd = lbfgs_max_dots(m);
   double* part = o->dsc;
-  double* rho = part + lb_dot_partials();
-  double* alpha = rho + m;
-  double* sy = alpha + m;
-  double* yy = sy + m;
-  double* beta = yy + m;
-  double* tmp = beta + 1;
+  double* mpart = part + lb_dot_partials();
+  double* mout = mpart + lb_mdot_partials(maxd);
+  double* coef = mout + maxd;
+  double* tmp = coef + 2 * m;
+  const T** dva = reinterpret_cast<const T**>(static_cast<void*>(o->ptrs));
+  const T** dvb = dva + maxd;
+  const T** dvc = dvb + maxd;
   Arena<T>& A = arena_of<T>(p);
   T* pc = A.p[p->steps & 1];  // the problem's current levels
   const long long nl = o->nl;
@@ -1440,10 +1457,10 @@ modil_status lbfgs_run_t(modil_lbfgs* o, int iters, double* loss, int* done) {
     if (st == MODIL_OK && gr && kb) CUDA_TRY(lb_mul<T>(gr + nl, A.kg, ks, o->nk, s));
     if (st == MODIL_OK) st = read_terms(p, terms);
     *f = terms[0];
-    if (st == MODIL_ERR_NONFINITE && !gr) {
+    if (st == MODIL_ERR_NONFINITE) {
       CUDA_TRY(cudaMemsetAsync(reinterpret_cast<char*>(A.st) + offsetof(InstState, nonfinite), 0, sizeof(int), s));
       *f = HUGE_VAL;
-      return MODIL_OK;
+      return gr ? MODIL_ERR_NONFINITE : MODIL_OK;
     }
     return st;
   };
@@ -1453,74 +1470,160 @@ modil_status lbfgs_run_t(modil_lbfgs* o, int iters, double* loss, int* done) {
     CUDA_TRY(cudaStreamSynchronize(s));
     return MODIL_OK;
   };
+  // batched dots of the listed vector pairs (enqueued; results in mout)
+  std::vector<const T*> la, lb;
+  auto mdot = [&]() -> modil_status {
+    CUDA_TRY(cudaMemcpyAsync(dva, la.data(), sizeof(T*) * la.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(dvb, lb.data(), sizeof(T*) * lb.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(lb_mdot<T>(dva, dvb, (int)la.size(), n, mpart, mout, s));
+    return MODIL_OK;
+  };
+  std::vector<double> h;
+  auto read_mout = [&]() -> modil_status {  // on the problem's stream (it may not block the legacy one)
+    h.resize(la.size());
+    CUDA_TRY(cudaMemcpyAsync(h.data(), mout, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return MODIL_OK;
+  };
+  // the dots of a trial point: g.r; the candidate pair's s.y, y.y; the new
+  // column of S^T Y and row of Y^T Y; S^T gn, Y^T gn of the stored pairs and
+  // of the candidate
+  auto trial_list = [&]() {
+    la.clear();
+    lb.clear();
+    la.push_back(g); lb.push_back(r);
+    la.push_back(q); lb.push_back(yv);
+    la.push_back(yv); lb.push_back(yv);
+    for (int i : o->order) { la.push_back(Sv(i)); lb.push_back(yv); la.push_back(Yv(i)); lb.push_back(yv); }
+    for (int i : o->order) { la.push_back(Sv(i)); lb.push_back(gn); la.push_back(Yv(i)); lb.push_back(gn); }
+    la.push_back(q); lb.push_back(gn);
+    la.push_back(yv); lb.push_back(gn);
+  };
+  modil_status st;
   CUDA_TRY(cudaMemcpyAsync(x, pc, sizeof(T) * (size_t)nl, cudaMemcpyDeviceToDevice, s));
   if (kb) CUDA_TRY(lb_mul<T>(x + nl, A.kq, 1.0 / ks, o->nk, s));
   double fx = 0.0;
-  modil_status st = eval(x, g, &fx);
-  if (st != MODIL_OK) return st;
+  if ((st = eval(x, g, &fx)) != MODIL_OK) return st;
   if (loss) loss[0] = fx;
+  if (!o->order.empty()) {  // S^T g and Y^T g at this run's starting point
+    la.clear();
+    lb.clear();
+    for (int i : o->order) { la.push_back(Sv(i)); lb.push_back(g); la.push_back(Yv(i)); lb.push_back(g); }
+    if ((st = mdot()) != MODIL_OK) return st;
+    if ((st = read_mout()) != MODIL_OK) return st;
+    for (size_t j = 0; j < o->order.size(); ++j) {
+      o->a[o->order[j]] = h[2 * j];
+      o->b[o->order[j]] = h[2 * j + 1];
+    }
+  }
+  std::vector<double> R, t, z, cu;
+  std::vector<const T*> vecs;
   int k = 0;
   for (; k < iters; ++k) {
-    // r = H g by the two-loop recursion, newest pair first; d = -r
     const int np = (int)o->order.size();
     if (np == 0) {
       CUDA_TRY(cudaMemcpyAsync(r, g, vb, cudaMemcpyDeviceToDevice, s));
     } else {
-      CUDA_TRY(cudaMemcpyAsync(q, g, vb, cudaMemcpyDeviceToDevice, s));
-      for (int j = np - 1; j >= 0; --j) {
-        const int i = o->order[j];
-        CUDA_TRY(lb_dot<T>(Sv(i), q, n, part, rho + i, alpha + i, s));   // alpha_i = rho_i s_i.q
-        CUDA_TRY(lb_axpy<T>(q, Yv(i), alpha + i, nullptr, -1.0, n, s));  // q -= alpha_i y_i
+      // coefficients of H g on the host (np <= m small triangular systems)
+      const std::vector<int>& od = o->order;
+      auto SYo = [&](int i, int j) { return o->SY[(size_t)od[i] * m + od[j]]; };
+      auto YYo = [&](int i, int j) { return o->YY[(size_t)od[i] * m + od[j]]; };
+      const int nw = od.back();
+      const double gamma = o->SY[(size_t)nw * m + nw] / o->YY[(size_t)nw * m + nw];
+      t.assign(np, 0.0);
+      for (int i = np - 1; i >= 0; --i) {  // R t = S^T g
+        double v = o->a[od[i]];
+        for (int j = i + 1; j < np; ++j) v -= SYo(i, j) * t[j];
+        t[i] = v / SYo(i, i);
       }
-      const int nw = o->order.back();
-      CUDA_TRY(lb_scale<T>(r, q, sy + nw, yy + nw, n, s));  // r = (s.y / y.y) q
-      for (int j = 0; j < np; ++j) {
-        const int i = o->order[j];
-        CUDA_TRY(lb_dot<T>(Yv(i), r, n, part, rho + i, beta, s));       // beta = rho_i y_i.r
-        CUDA_TRY(lb_axpy<T>(r, Sv(i), alpha + i, beta, 1.0, n, s));    // r += (alpha_i - beta) s_i
+      z.assign(np, 0.0);
+      for (int i = 0; i < np; ++i) {  // z = (D + gamma Y^T Y) t - gamma Y^T g
+        double v = SYo(i, i) * t[i] - gamma * o->b[od[i]];
+        for (int j = 0; j < np; ++j) v += gamma * YYo(i, j) * t[j];
+        z[i] = v;
       }
+      cu.assign(2 * np, 0.0);
+      for (int i = 0; i < np; ++i) {  // R^T u = z
+        double v = z[i];
+        for (int j = 0; j < i; ++j) v -= SYo(j, i) * cu[j];
+        cu[i] = v / SYo(i, i);
+      }
+      for (int i = 0; i < np; ++i) cu[np + i] = -gamma * t[i];  // gamma w
+      vecs.clear();
+      for (int i = 0; i < np; ++i) vecs.push_back(Sv(od[i]));
+      for (int i = 0; i < np; ++i) vecs.push_back(Yv(od[i]));
+      CUDA_TRY(cudaMemcpyAsync(coef, cu.data(), sizeof(double) * cu.size(), cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(dvc, vecs.data(), sizeof(T*) * vecs.size(), cudaMemcpyHostToDevice, s));
+      CUDA_TRY(lb_combine<T>(r, g, gamma, dvc, coef, 2 * np, n, s));
     }
-    double gr = 0.0;
-    if ((st = dot_host(g, r, &gr)) != MODIL_OK) return st;
-    const double gd = -gr;  // g.d
-    if (!(gd < 0.0)) break;
-    double t = 1.0;
+    double step = 1.0;
     if (o->iters == 0) {
       double gg = 0.0;
       if ((st = dot_host(g, g, &gg)) != MODIL_OK) return st;
-      t = 1.0 / std::sqrt(gg);
+      step = 1.0 / std::sqrt(gg);
     }
-    // backtracking on the Armijo condition
-    bool ok = false;
+    // The first trial point with its gradient and every dot product the
+    // iteration needs, read back once: the first trial is accepted in most
+    // iterations, and then one loss-and-gradient pass and one host round trip
+    // make the iteration.
+    CUDA_TRY(lb_axpby<T>(xt, x, r, -step, n, s));  // xt = x + step d
     double ft = 0.0;
-    for (int trial = 0; trial < kTrials; ++trial) {
-      CUDA_TRY(lb_axpby<T>(xt, x, r, -t, n, s));  // xt = x + t d
-      if ((st = eval(xt, nullptr, &ft)) != MODIL_OK) return st;
-      if (ft <= fx + kC1 * t * gd) { ok = true; break; }
-      t *= 0.5;
-    }
-    if (!ok) break;
-    if ((st = eval(xt, gn, &ft)) != MODIL_OK) return st;
-    // candidate pair in the work vectors q (s) and r (y)
+    st = eval(xt, gn, &ft);
+    if (st != MODIL_OK && st != MODIL_ERR_NONFINITE) return st;
     CUDA_TRY(lb_sub<T>(q, xt, x, n, s));
-    CUDA_TRY(lb_sub<T>(r, gn, g, n, s));
-    double sy_h = 0.0, yy_h = 0.0;
-    if ((st = dot_host(q, r, &sy_h)) != MODIL_OK) return st;
-    if ((st = dot_host(r, r, &yy_h)) != MODIL_OK) return st;
+    CUDA_TRY(lb_sub<T>(yv, gn, g, n, s));
+    trial_list();
+    if ((st = mdot()) != MODIL_OK) return st;
+    if ((st = read_mout()) != MODIL_OK) return st;
+    const double gd = -h[0];  // g.d
+    if (!(gd < 0.0)) break;
+    if (!(ft <= fx + kC1 * step * gd)) {
+      // backtracking on the Armijo condition (loss only), then the gradient
+      // and the dots at the accepted point
+      bool ok = false;
+      for (int trial = 1; trial < kTrials; ++trial) {
+        step *= 0.5;
+        CUDA_TRY(lb_axpby<T>(xt, x, r, -step, n, s));
+        if ((st = eval(xt, nullptr, &ft)) != MODIL_OK) return st;
+        if (ft <= fx + kC1 * step * gd) { ok = true; break; }
+      }
+      if (!ok) break;
+      if ((st = eval(xt, gn, &ft)) != MODIL_OK) return st;
+      CUDA_TRY(lb_sub<T>(q, xt, x, n, s));
+      CUDA_TRY(lb_sub<T>(yv, gn, g, n, s));
+      trial_list();
+      if ((st = mdot()) != MODIL_OK) return st;
+      if ((st = read_mout()) != MODIL_OK) return st;
+    }
+    // the new point; the candidate pair if its curvature is positive
+    const double sy_h = h[1], yy_h = h[2];
+    const std::vector<int> old = o->order;
+    const int no = (int)old.size();
+    for (int j = 0; j < no; ++j) {  // S^T g and Y^T g at the new point
+      o->a[old[j]] = h[3 + 2 * no + 2 * j];
+      o->b[old[j]] = h[4 + 2 * no + 2 * j];
+    }
     if (sy_h > kCurv * yy_h) {
-      int slot;
-      if ((int)o->order.size() < m) {
-        slot = (int)o->order.size();
+      int slot, first = 0;
+      if (no < m) {
+        slot = no;
       } else {
-        slot = o->order.front();
+        slot = o->order.front();  // the oldest pair makes room
         o->order.erase(o->order.begin());
+        first = 1;
       }
       CUDA_TRY(cudaMemcpyAsync(Sv(slot), q, vb, cudaMemcpyDeviceToDevice, s));
-      CUDA_TRY(cudaMemcpyAsync(Yv(slot), r, vb, cudaMemcpyDeviceToDevice, s));
-      const double sc[3] = {sy_h, yy_h, 1.0 / sy_h};
-      CUDA_TRY(cudaMemcpy(sy + slot, &sc[0], sizeof(double), cudaMemcpyHostToDevice));
-      CUDA_TRY(cudaMemcpy(yy + slot, &sc[1], sizeof(double), cudaMemcpyHostToDevice));
-      CUDA_TRY(cudaMemcpy(rho + slot, &sc[2], sizeof(double), cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpyAsync(Yv(slot), yv, vb, cudaMemcpyDeviceToDevice, s));
+      for (int j = first; j < no; ++j) {
+        const int i = old[j];
+        o->SY[(size_t)i * m + slot] = h[3 + 2 * j];
+        o->YY[(size_t)i * m + slot] = h[4 + 2 * j];
+        o->YY[(size_t)slot * m + i] = h[4 + 2 * j];
+      }
+      o->SY[(size_t)slot * m + slot] = sy_h;
+      o->YY[(size_t)slot * m + slot] = yy_h;
+      o->a[slot] = h[3 + 4 * no];
+      o->b[slot] = h[4 + 4 * no];
       o->order.push_back(slot);
     }
     std::swap(x, xt);
@@ -1559,9 +1662,16 @@ modil_status modil_lbfgs_create(modil_problem* p, int history, modil_lbfgs** out
   o->nk = (P.pde == MODIL_PDE_HEAT && !P.dev[0].k_fixed) ? P.dev[0].nk : 0;
   o->n = o->nl + o->nk;
   o->ks = P.dev[0].k_scale;
-  cudaError_t e = cudaMalloc(&o->vec, P.esz * (size_t)o->n * (2 * (size_t)history + 6));
+  o->SY.assign((size_t)history * history, 0.0);
+  o->YY.assign((size_t)history * history, 0.0);
+  o->a.assign(history, 0.0);
+  o->b.assign(history, 0.0);
+  const int maxd = lbfgs_max_dots(history);
+  cudaError_t e = cudaMalloc(&o->vec, P.esz * (size_t)o->n * (2 * (size_t)history + 7));
   if (e == cudaSuccess)
-    e = cudaMalloc(&o->dsc, sizeof(double) * ((size_t)lb_dot_partials() + 4 * (size_t)history + 2));
+    e = cudaMalloc(&o->dsc, sizeof(double) * ((size_t)lb_dot_partials() + (size_t)lb_mdot_partials(maxd) + maxd +
+                                              2 * (size_t)history + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&o->ptrs, sizeof(void*) * (2 * (size_t)maxd + 2 * (size_t)history));
   if (e != cudaSuccess) {
     modil_lbfgs_destroy(o);
     return fail(MODIL_ERR_CUDA, std::string("L-BFGS buffers: ") + cudaGetErrorString(e));
@@ -1582,6 +1692,7 @@ void modil_lbfgs_destroy(modil_lbfgs* o) {
   if (!o) return;
   if (o->vec) cudaFree(o->vec);
   if (o->dsc) cudaFree(o->dsc);
+  if (o->ptrs) cudaFree(o->ptrs);
   delete o;
 }
 

@@ -73,6 +73,24 @@ def test_lbfgs_matches_oracle_f64(modil, pde, shape, L, kw):
                 assert np.max(np.abs(a - ref)) <= 1e-7 * max(1.0, np.max(np.abs(ref))), (f, lvl)
 
 
+@pytest.mark.parametrize("pde,shape,L,kw", [("burgers", (64, 64), 4, dict(n_meas=200, nu=0.01)),
+                                            ("ns2d", (16, 16), 3, dict(n_meas=40, Re=100.0))])
+def test_lbfgs_f32_tracks_oracle(modil, pde, shape, L, kw):
+    """FP32 problems: the device's L-BFGS (FP32 vectors, FP64 dot products)
+    follows the FP64 oracle's iterations to FP32 rounding for the first
+    iterations and ends no higher."""
+    c = Case(pde, shape, L, "f32", seed=44, **kw)
+    m, iters = 4, 12
+    _, loss_ref, _ = _oracle_run(c, m, iters)
+    with modil.Problem(c.desc()) as p:
+        c.load(p)
+        with modil.LBFGS(p, history=m) as opt:
+            loss = opt.run(iters)
+    k = min(5, len(loss), len(loss_ref))
+    np.testing.assert_allclose(loss[:k], loss_ref[:k], rtol=1e-4)
+    assert loss[-1] <= 1.05 * loss_ref[-1], (loss, loss_ref)
+
+
 def test_lbfgs_descends_and_continues(modil):
     """FP32 Burgers: monotone loss, and a second run continues from the first."""
     c = Case("burgers", (64, 128), 4, "f32", seed=41, n_meas=300, nu=0.02)
