@@ -4,9 +4,10 @@
 Default workload (the largest configuration on one GPU): 512 viscous Burgers
 instances of uneven size (paper Section 3.2 discretisation; N_x, N_t drawn
 from {64, 128, 256, 512}, nu log-uniform in [1e-3, 1e-1], 0.5 % of the cells
-measured), all stepped together: one persistent launch per phase of the step
-(fused fine tile kernel, restriction + Adam of the coarse levels, per-instance
-tail), replayed as one CUDA graph.  A step is one loss+gradient evaluation of
+measured), all stepped together: one launch per phase of the step for all
+instances (composition of the coarse levels, the warp-streaming fine kernel,
+restriction + Adam of the coarse levels, per-instance tail), replayed as one
+CUDA graph.  A step is one loss+gradient evaluation of
 every instance followed by the Adam update of every level of every instance;
 the metric is instance evaluations per second.  The ~1.3 GB working set is
 larger than L2, so no flush is needed.
@@ -332,8 +333,8 @@ def batched_config(args, tile, pers, fine, params, nmeas):
     """The `config` of the batched line, identical in both arms."""
     return {"workload": f"batched Burgers x{args.instances}: N_x, N_t uniform in {{64,128,256,512}}, "
                         "nu log-uniform in [1e-3, 1e-1], 0.5 % measured cells, "
-                        "L = log2(min(N_x, N_t)/8) + 1, FP32, Adam, one persistent launch per phase "
-                        "in one CUDA graph",
+                        "L = log2(min(N_x, N_t)/8) + 1, FP32, Adam, one launch per phase of the step "
+                        "for all instances, the step captured in one CUDA graph",
             "instances": args.instances, "tile": list(tile), "persistent": pers,
             "fine_cells": fine, "params": params, "measurements": nmeas,
             "l2": "working set (about 1.3 GB) larger than L2 (no flush)",
