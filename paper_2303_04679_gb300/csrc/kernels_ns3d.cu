@@ -737,7 +737,15 @@ k_resid3(const __grid_constant__ Arena<T> A, int mode, int cur, const __grid_con
 // 3-D restriction with Adam for one level: coarse tile 2 x 8 x 16, staged
 // fine region, separable x, y, z passes of the transposed interpolation.
 constexpr int L3Z = k3LZ, L3Y = k3LY, L3X = k3LX;
-constexpr int L3FZ = 2 * L3Z + 4, L3FY = 2 * L3Y + 4, L3FX = 2 * L3X + 4;
+// staged finer region: rows 2 Z0 - 2 .. and 2 Y0 - 2 .., columns 2 X0 - 4 ..
+// (a 4-element boundary, so that rows copy in 16-byte chunks)
+constexpr int L3FZ = 2 * L3Z + 4, L3FY = 2 * L3Y + 4, L3FX = 2 * L3X + 8;
+
+// 16-byte asynchronous copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16_3(void* dst, const void* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
+}
 
 template <class T>
 __device__ __forceinline__ void rwin3(int X, int nc, T* w) {
@@ -796,15 +804,31 @@ k_level3(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   const int fz0 = max(0, 2 * Z0 - 2), fz1 = min(fz, 2 * (Z0 + cz) + 2);
   const int fy0 = max(0, 2 * Y0 - 2), fy1 = min(fy, 2 * (Y0 + cy) + 2);
   const int fx0 = max(0, 2 * X0 - 2), fx1 = min(fx, 2 * (X0 + cx) + 2);
-  const int dz = fz1 - fz0, dy = fy1 - fy0, dx = fx1 - fx0;
+  const int dz = fz1 - fz0, dy = fy1 - fy0;
   if (f >= D.nfield) return;
   {
-    const T* __restrict__ gf = A.g + D.off[f][l - 1];
-    // loops run over the constant-size boxes (divisions by constants) with bounds checks
-    for (int i = t; i < L3FZ * L3FY * L3FX; i += MODIL_NT) {
-      const int a = i / (L3FY * L3FX), b = (i / L3FX) % L3FY, c = i % L3FX;
-      if (a < dz && b < dy && c < dx)
-        cp_async(S + i, gf + ((long long)(fz0 + a) * fy + (fy0 + b)) * fx + (fx0 + c));
+    const long long fo = D.off[f][l - 1];
+    const T* __restrict__ gf = A.g + fo;
+    const int oX = 2 * X0 - 4;  // x of the region's first column
+    // loops run over the constant-size boxes (divisions by constants) with bounds
+    // checks; 4-element chunks wholly inside the level where rows and the level
+    // start are 16-byte aligned, single elements otherwise
+    const bool vec = ((fx & 3) == 0) && ((fo & 3) == 0) && (sizeof(T) == 4);
+    if (vec) {
+      constexpr int CW = L3FX / 4;
+      for (int i = t; i < L3FZ * L3FY * CW; i += MODIL_NT) {
+        const int a = i / (L3FY * CW), b = (i / CW) % L3FY, c = 4 * (i % CW);
+        const int xx = oX + c;
+        if (a < dz && b < dy && xx >= 0 && xx + 3 < fx && xx + 3 >= fx0 && xx < fx1)
+          cp_async16_3(S + (a * L3FY + b) * L3FX + c, gf + ((long long)(fz0 + a) * fy + (fy0 + b)) * fx + xx);
+      }
+    } else {
+      for (int i = t; i < L3FZ * L3FY * L3FX; i += MODIL_NT) {
+        const int a = i / (L3FY * L3FX), b = (i / L3FX) % L3FY, c = i % L3FX;
+        const int xx = oX + c;
+        if (a < dz && b < dy && xx >= fx0 && xx < fx1)
+          cp_async(S + i, gf + ((long long)(fz0 + a) * fy + (fy0 + b)) * fx + xx);
+      }
     }
     cp_async_wait_all();
     __syncthreads();
@@ -817,8 +841,8 @@ k_level3(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
       rwin3<T>(X, nx, w);
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const int q = min(max(2 * X - 2 + k - fx0, 0), dx - 1);
+      for (int k = 0; k < 6; ++k) {  // taps outside the level have zero weight: clamp them into it
+        const int q = min(max(2 * X - 2 + k, fx0), fx1 - 1) - oX;
         acc += w[k] * S[(a * L3FY + b) * L3FX + q];
       }
       Hx[(a * L3FY + b) * L3X + c] = acc;
