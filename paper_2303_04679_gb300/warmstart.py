@@ -43,13 +43,15 @@ def zero_levels(shape, n_levels, inflow_level=0):
 
 
 def forward_solves(cases, side, n_levels, steps, lr=1e-3, w_pin=10.0, batch=32, fractions=None,
-                   lbfgs_iters=0, history=50):
+                   lbfgs_iters=0, history=50, schedule=None):
     """Plain mODIL forward solutions of the body problem around each case's
     ellipsoid (cases: list of (centre, axes); fractions: their body fractions
-    on the grid if already computed): `steps` Adam steps on batches of cases,
-    then, with lbfgs_iters > 0, that many L-BFGS iterations per case (the
-    optimiser of Section 3.5).  Returns [n, 5, S, S, S] FP32 composed fields
-    and the final loss terms."""
+    on the grid if already computed): `steps` Adam steps on batches of cases
+    (or, with schedule = [(steps, lr), ...], Adam by learning-rate phases,
+    each phase a new problem from the levels the last one reached), then,
+    with lbfgs_iters > 0, that many L-BFGS iterations per case (the optimiser
+    of Section 3.5).  Returns [n, 5, S, S, S] FP32 composed fields and the
+    final loss terms."""
     import torch  # noqa: F401  (device memory and streams)
     shape = (side,) * 3
     ncell = side ** 3
@@ -65,16 +67,28 @@ def forward_solves(cases, side, n_levels, steps, lr=1e-3, w_pin=10.0, batch=32, 
         chats = [chihat_from_fraction(fractions[b0 + k] if fractions is not None
                                       else inputs.ns3d_body_fraction(shape, c, a))
                  for k, (c, a) in enumerate(chunk)]
-        descs = [modil.Desc("ns3d", shape, n_levels, "f32", coef=(cf["Re"], cf["D"], cf["lam"], cf["tau"]),
-                            w_res=1.0, w_data=w_pin * ncell, meas_cell=cells, meas_field=field4,
-                            meas_value=ch.reshape(-1), lr=lr) for ch in chats]
-        with modil.Problem(descs) as p:
-            for i, ch in enumerate(chats):
-                lv = zero_levels(shape, n_levels)
-                lv[4][0][:] = ch
+        def make(rate):
+            return [modil.Desc("ns3d", shape, n_levels, "f32", coef=(cf["Re"], cf["D"], cf["lam"], cf["tau"]),
+                               w_res=1.0, w_data=w_pin * ncell, meas_cell=cells, meas_field=field4,
+                               meas_value=ch.reshape(-1), lr=rate) for ch in chats]
+        starts = []
+        for ch in chats:
+            lv = zero_levels(shape, n_levels)
+            lv[4][0][:] = ch
+            starts.append(lv)
+        phases = list(schedule) if schedule else []
+        for steps_k, rate in phases[:-1]:  # all but the last phase
+            with modil.Problem(make(rate)) as p:
+                for i, lv in enumerate(starts):
+                    p.write_fields(lv, instance=i)
+                p.step(steps_k, read_loss=False)
+                starts = [[p.read_levels(field=f, instance=i) for f in range(FIELDS)] for i in range(len(chats))]
+        last_steps, last_rate = phases[-1] if phases else (steps, lr)
+        with modil.Problem(make(last_rate)) as p:
+            for i, lv in enumerate(starts):
                 p.write_fields(lv, instance=i)
-            if steps:
-                p.step(steps, read_loss=False)
+            if last_steps:
+                p.step(last_steps, read_loss=False)
             if lbfgs_iters:
                 with modil.LBFGS(p, history=history) as opt:
                     opt.run(lbfgs_iters)
@@ -195,25 +209,36 @@ def inverse_problem(shape, n_levels, cells, fidx, vals, lr=1e-3):
 
 
 def steps_to_losses(desc, levels, thresholds, max_steps, chunk=100, chi_ref=None, run_all=False,
-                    optimizer="adam", history=50):
+                    optimizer="adam", history=50, schedule=None):
     """Run mODIL from the given levels with Adam or L-BFGS (Section 3.5 uses
     L-BFGS); for every threshold the first step (iteration) count, a
     multiple of chunk, and the wall time at which the loss is at or below it
-    (None if never).  Returns (hits, loss history per chunk), and with
+    (None if never).  schedule: Adam's learning rate by phases, [(steps, lr),
+    ...] (each phase a new problem from the levels the last one reached, its
+    moments restarted; the switch counts in the wall time; max_steps is then
+    the schedule's total).  Returns (hits, loss history per chunk), and with
     chi_ref also the mean absolute body-fraction error per chunk (the
     composed chihat read back outside the timed steps).  Stops once every
     threshold is reached unless run_all, and when L-BFGS stops early."""
     import torch
     hits = {t: None for t in thresholds}
     hist, chi_err = [], []
-    with modil.Problem(desc) as p:
+    phases = [(max_steps, None)] if schedule is None else list(schedule)
+    el = 0.0
+    done = 0
+    stalled = False
+    for steps, lr in phases:
+        if stalled or (not run_all and hits and all(v is not None for v in hits.values())):
+            break
+        t0 = time.perf_counter()
+        d = desc if lr is None else modil.Desc(**{**desc.kwargs, "lr": lr})
+        p = modil.Problem(d)
         p.write_fields(levels)
         opt = modil.LBFGS(p, history=history) if optimizer == "lbfgs" else None
         torch.cuda.synchronize()
-        el = 0.0
-        done = 0
-        stalled = False
-        while done < max_steps and not stalled:
+        el += time.perf_counter() - t0
+        end = done + steps
+        while done < end and not stalled:
             t0 = time.perf_counter()
             if opt is None:
                 loss = float(p.step(chunk)[0][0])
@@ -234,6 +259,10 @@ def steps_to_losses(desc, levels, thresholds, max_steps, chunk=100, chi_ref=None
                 break
         if opt is not None:
             opt.close()
+        t0 = time.perf_counter()
+        levels = [p.read_levels(field=f) for f in range(desc.n_fields)]
+        p.close()
+        el += time.perf_counter() - t0
     if chi_ref is not None:
         return hits, hist, chi_err
     return hits, hist
