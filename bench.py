@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="modil", choices=["modil", "reference"])
     ap.add_argument("--tile", default=None,
-                    help="fine tile 'ROWSxCOLS' (heat default 32x32; batched default 32x28, the "
+                    help="fine tile 'ROWSxCOLS' (heat default 32x32; batched default 32x60, the "
                          "warp-streaming strip) or 'auto' (autotuner)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -398,7 +398,7 @@ def run_reference_batched(args):
         return
     batch = inputs.burgers_batch(args.instances)
     fine, params, nmeas = batch_sizes(batch)
-    tile = tuple(int(v) for v in (args.tile or "32x28").split("x")) if args.tile != "auto" else (32, 28)
+    tile = tuple(int(v) for v in (args.tile or "32x60").split("x")) if args.tile != "auto" else (32, 60)
     per = 16
     for w in range(max(args.warmup, 0)):
         o, prob, st = oracle_burgers(batch[w % len(batch)])
@@ -418,7 +418,7 @@ def run_reference_batched(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": batched_config(args, tile, tile != (32, 28), fine, params, nmeas),
+        "config": batched_config(args, tile, tile != (32, 60), fine, params, nmeas),
         "cpu_baseline": {"value": value, "unit": BATCH_METRIC_UNIT, "cores": blas_threads(),
                          "kind": "oracle",
                          "sample": f"{per} instances of the batch per step (cycling, {n} in all), one "
@@ -457,7 +457,7 @@ def run_batched(args):
         tile, pers, _ = autotune.autotune(
             descs((16, 32)), measure=lambda d, t, q: autotune.time_steps(d, t, q, steps=10, warmup=3))
     else:
-        tile = tuple(int(v) for v in (args.tile or "32x28").split("x"))
+        tile = tuple(int(v) for v in (args.tile or "32x60").split("x"))
         pers = tile != autotune.STREAM_TILE
     ds = descs(tile)
     fine, params, nmeas = batch_sizes(batch)

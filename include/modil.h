@@ -140,7 +140,7 @@ typedef struct {
   const double* point_value;
   int tile[2];               /* fine tile (rows, cols); 0 = library default.
                                 Burgers/heat/Poisson: 16x32 16x64 8x64 32x32 8x128;
-                                Burgers without off-grid points also 32x28 (the
+                                Burgers without off-grid points also 32x60 (the
                                 warp-streaming kernel, its default);
                                 NS2D: 8x32 16x32.  NS3D: 0 only (4x8x16 cells)  */
   double domain_lo[3], domain_hi[3];

@@ -13,7 +13,7 @@ import json
 import os
 
 ST_TILES = ((16, 32), (16, 64), (8, 64), (32, 32), (8, 128))
-STREAM_TILE = (32, 28)   # Burgers: the warp-streaming kernel's strip (no persistent variant)
+STREAM_TILE = (32, 60)   # Burgers: the warp-streaming kernel's strip (no persistent variant)
 NS2D_TILES = ((8, 32), (16, 32))
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "modil_gb300", "autotune.json")
 

@@ -7,20 +7,24 @@
 // levels: levels L-2 .. 2 of each instance by one block (k_compose2_small),
 // then level 1 of every instance in one grid (k_compose2).
 //
-// Fine kernel (k_fine_stream): one warp owns a strip of kSW = 28 columns and
-// kSR = 32 rows of the fine grid.  Lane j holds column x = x0 - 2 + j, so the
-// warp covers the owned columns plus two on each side: the composed field is
-// needed two columns out, the residuals one column out.  The warp walks down
-// the rows of its strip (from one row above it to one row below); per row it
+// Fine kernel (k_fine_stream): one warp owns a strip of kSW = 60 columns and
+// kSR = 32 rows of the fine grid.  Lane j holds the two columns
+// a = x0 - 2 + 2j and b = a + 1, so the warp covers the owned columns plus two
+// on each side: the composed field is needed two columns out, the residuals
+// one column out.  Two columns per lane share the per-row work (copies,
+// shuffles, addresses, bookkeeping) and move as one 8- or 16-byte access.
+// The warp walks down the rows of its strip (from one row above it to one row
+// below); per row it
 //   1. composes u = u_0 + T w_1 (level 0 of the row, the two rows of w_1 it
 //      interpolates between, interpolated in x once per row of w_1);
 //   2. evaluates the residual of the row and lambda * dr/du at its four
-//      stencil points (lambda = 2 w_res dV r), the neighbours u(x-1), u(x+1)
-//      taken from the adjacent lanes by shuffles;
+//      stencil points (lambda = 2 w_res dV r), the neighbours u(a-1) and
+//      u(b+1) taken from the adjacent lanes by shuffles;
 //   3. adds the data term of the measured cells of the row;
 //   4. finishes the previous row: dL/du(n-1, x) gathers lambda dr/du of the
 //      residuals that read u(n-1, x) -- its own, those of x-1 and x+1 of row
-//      n-1 (shuffles) and that of (n, x) -- writes it and applies Adam.
+//      n-1 (one of them in the adjacent lane) and that of (n, x) -- writes it
+//      and applies Adam.
 // Everything stays in registers: no shared-memory tiles and no block
 // barriers.  Level 0's parameters and Adam moments stream through a per-warp
 // ring of kRing rows in shared memory, copied asynchronously kRing - 1 rows
@@ -30,7 +34,7 @@
 // bounds checks, no weight arithmetic), the pairs at the strip's edges and
 // the level's ends take the general path.  The next row of w_1 is loaded one
 // pair ahead.  The kernel is compiled per mode (loss, gradient, step,
-// compose).  Each lane sums its r^2 (at most 32 rows) in FP32, the warp
+// compose).  Each lane sums its r^2 (at most 64 cells) in FP32, the warp
 // combines the lanes in compensated FP32, and each warp writes FP64 partial
 // sums (r^2 and the data misfit) for the per-instance tail kernel.
 // The stencil (rows n >= 1, the implicit step of the reading of Section 3.2):
@@ -150,6 +154,18 @@ __device__ __forceinline__ void acc_add(float& hi, float& lo, T x) {
   ff_add(hi, lo, (float)x, 0.f);
 }
 
+template <class T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
+// Asynchronous copy of two consecutive elements (8 bytes of FP32, 16 of FP64).
+__device__ __forceinline__ void cp_async_pair(unsigned saddr, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_pair(unsigned saddr, const double* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(src) : "memory");
+}
+
 // Loop-invariant coefficients of a strip in the working precision, computed
 // once per warp into shared memory: under register pressure the compiler
 // reloads them from there instead of recomputing conversions and divisions.
@@ -159,14 +175,41 @@ struct StreamCoef {
   T idt, idx1, idx2, nu, lam_scale, wd2, gscale;
 };
 
+// Residual of cell (n, x) and lambda dr/du (lambda = 2 w_res dV r) at its
+// four stencil points: (n, x-1) -> lJ0, (n, x) -> lJ1, (n, x+1) -> lJ2,
+// (n-1, x) -> lJ3.  uW, uE: the neighbours in the row (unused at a wall, where
+// the odd ghost -u stands in for the viscous term and the flux through the
+// wall is the upwind flux against the zero wall value).  ls = 2 w_res dV, or
+// 0 for a column without a residual (every lambda dr/du then vanishes, so
+// that both columns of a lane run the same instructions without branches).
+template <class T>
+__device__ __forceinline__ T burgers_cell(T u, T uo, T uW, T uE, bool hw, bool he, T cdiag, T ls,
+                                          const StreamCoef<T>& cf, T& lJ0, T& lJ1, T& lJ2, T& lJ3) {
+  const T uw = hw ? uW : -u;
+  const T ue = he ? uE : -u;
+  T dFEc, dFEe, dFWw, dFWc;
+  const T FE = eo_flux_s(u, he ? ue : T(0), dFEc, dFEe);
+  const T FW = eo_flux_s(hw ? uw : T(0), u, dFWw, dFWc);
+  const T lap = (ue - T(2) * u + uw) * cf.idx2;
+  const T r = (u - uo) * cf.idt + (FE - FW) * cf.idx1 - cf.nu * lap;
+  const T lam = ls * r;
+  lJ1 = lam * (cf.idt + (dFEc - dFWc) * cf.idx1 - cf.nu * cdiag * cf.idx2);
+  lJ0 = hw ? lam * (-dFWw * cf.idx1 - cf.nu * cf.idx2) : T(0);
+  lJ2 = he ? lam * (dFEe * cf.idx1 - cf.nu * cf.idx2) : T(0);
+  lJ3 = lam * (-cf.idt);
+  return r;
+}
+
 template <class T, int MODE>
-__global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stream(const __grid_constant__ Arena<T> A, int cur) {
+__global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? kStreamBlocksF32 : kStreamBlocksF64)
+k_fine_stream(const __grid_constant__ Arena<T> A, int cur) {
   constexpr bool step = (MODE == MODE_STEP), adj = (MODE != MODE_LOSS), comp_only = (MODE == MODE_COMPOSE);
-  // per warp: a ring of kRing rows of level 0's parameters and Adam moments,
-  // filled with asynchronous copies kRing - 1 rows ahead of their use
-  __shared__ __align__(16) T sP[kStreamNT / 32][kRing][32];
-  __shared__ __align__(16) T sM[kStreamNT / 32][kRing][32];
-  __shared__ __align__(16) double sV[kStreamNT / 32][kRing][32];
+  using T2 = typename Pair<T>::type;
+  // per warp: a ring of kRing rows (64 columns) of level 0's parameters and
+  // Adam moments, filled with asynchronous copies kRing - 1 rows ahead of use
+  __shared__ __align__(16) T sP[kStreamNT / 32][kRing][64];
+  __shared__ __align__(16) T sM[kStreamNT / 32][kRing][64];
+  __shared__ __align__(16) double sV[kStreamNT / 32][kRing][64];
   __shared__ StreamCoef<T> sC[kStreamNT / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int gt = blockIdx.x * (kStreamNT / 32) + w;
@@ -179,38 +222,63 @@ __global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stre
   const int sty = local / D.nt[0][2], stx = local - sty * D.nt[0][2];
   const int y0 = sty * kSR, x0 = stx * kSW;
   const int y1 = min(y0 + kSR, ny), xo1 = min(x0 + kSW, nx);  // owned rows [y0, y1), columns [x0, xo1)
-  const int x = x0 - 2 + lane;
-  const bool xin = x >= 0 && x < nx;
-  const bool own_x = x >= x0 && x < xo1;
-  const bool res_x = xin && x >= x0 - 1 && x <= xo1;  // residual columns [x0 - 1, xo1]
-  const bool hw = x > 0, he = x < nx - 1;
+  // the lane's two columns: a = x0 - 2 + 2 lane, b = a + 1
+  const int xa = x0 - 2 + 2 * lane, xb = xa + 1;
+  const bool ina = xa >= 0 && xa < nx, inb = xb >= 0 && xb < nx;
+  const bool owna = xa >= x0 && xa < xo1, ownb = xb >= x0 && xb < xo1;
+  // residual columns [x0 - 1, xo1]
+  const bool resa = ina && xa >= x0 - 1 && xa <= xo1, resb = inb && xb >= x0 - 1 && xb <= xo1;
+  const bool hwa = xa > 0, hea = xa < nx - 1, hwb = xb > 0, heb = xb < nx - 1;
   // per-instance bases; indices within an instance's level fit 32 bits
   const long long o0 = D.off[0][0];
   const T* __restrict__ P0 = A.p[cur] + o0;
   const T* __restrict__ M0 = A.m + o0;
   const double* __restrict__ V0 = A.v + o0;
-  const int nstart = max(y0 - 1, 0);
   T* __restrict__ G0 = A.g + o0;               // level 0's gradient
   T* __restrict__ Pn = A.p[cur ^ 1] + o0;      // level 0 after the step
+  // both columns of a lane move as one 8- or 16-byte access when every row
+  // and array starts on a pair boundary (x0 and a are even); else element by
+  // element
+  const bool vec = (nx % 2 == 0) &&
+                   ((reinterpret_cast<uintptr_t>(P0) | reinterpret_cast<uintptr_t>(Pn) |
+                     reinterpret_cast<uintptr_t>(M0) | reinterpret_cast<uintptr_t>(G0)) % (2 * sizeof(T))) == 0 &&
+                   reinterpret_cast<uintptr_t>(V0) % 16 == 0;
+  const int nstart = max(y0 - 1, 0);
   const int rmax = min(y1, ny - 1);  // last row of level 0 the strip reads
   // level 0 of row r (and m, v of owned rows) -> ring slot r % kRing; one copy
   // group per row, committed even when empty.  chk = false: the caller knows
-  // y0 <= r <= rmax.  Shared addresses of the lane's ring column and global
-  // pointers of its column are formed once; a row adds offsets only.
-  const unsigned sPa = (unsigned)__cvta_generic_to_shared(&sP[w][0][lane]);
-  const unsigned sMa = (unsigned)__cvta_generic_to_shared(&sM[w][0][lane]);
-  const unsigned sVa = (unsigned)__cvta_generic_to_shared(&sV[w][0][lane]);
-  const T* gP = P0 + x;
-  const T* gM = M0 + x;
-  const double* gV = V0 + x;
+  // y0 <= r <= rmax.  Shared addresses of the lane's ring columns and global
+  // pointers of its columns are formed once; a row adds offsets only.
+  const unsigned sPa = (unsigned)__cvta_generic_to_shared(&sP[w][0][2 * lane]);
+  const unsigned sMa = (unsigned)__cvta_generic_to_shared(&sM[w][0][2 * lane]);
+  const unsigned sVa = (unsigned)__cvta_generic_to_shared(&sV[w][0][2 * lane]);
+  const T* gP = P0 + xa;
+  const T* gM = M0 + xa;
+  const double* gV = V0 + xa;
   auto issue = [&](int r, bool chk) {
-    if ((!chk || r <= rmax) && xin) {
-      const unsigned so = (unsigned)(r & (kRing - 1)) * 32u;  // slot offset in elements
+    if (!chk || r <= rmax) {
+      const unsigned so = (unsigned)(r & (kRing - 1)) * 64u;  // slot offset in elements
       const int ro = r * nx;
-      cp_async_at(sPa + so * (unsigned)sizeof(T), gP + ro);
-      if (step && (!chk || r >= y0) && own_x) {
-        cp_async_at(sMa + so * (unsigned)sizeof(T), gM + ro);
-        cp_async_at(sVa + so * 8u, gV + ro);
+      const bool mv = step && (!chk || r >= y0);
+      if (vec) {  // ina == inb and owna == ownb
+        if (ina) {
+          cp_async_pair(sPa + so * (unsigned)sizeof(T), gP + ro);
+          if (mv && owna) {
+            cp_async_pair(sMa + so * (unsigned)sizeof(T), gM + ro);
+            cp_async_pair(sVa + so * 8u, gV + ro);
+          }
+        }
+      } else {
+        if (ina) cp_async_at(sPa + so * (unsigned)sizeof(T), gP + ro);
+        if (inb) cp_async_at(sPa + (so + 1u) * (unsigned)sizeof(T), gP + ro + 1);
+        if (mv && owna) {
+          cp_async_at(sMa + so * (unsigned)sizeof(T), gM + ro);
+          cp_async_at(sVa + so * 8u, gV + ro);
+        }
+        if (mv && ownb) {
+          cp_async_at(sMa + (so + 1u) * (unsigned)sizeof(T), gM + ro + 1);
+          cp_async_at(sVa + (so + 1u) * 8u, gV + ro + 1);
+        }
       }
     }
     cp_async_commit();
@@ -218,13 +286,17 @@ __global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stre
   // level 0, m and v were last written by this kernel one step earlier
 #pragma unroll
   for (int k = 0; k < kRing - 1; ++k) issue(nstart + k, true);
-  const T cdiag = T(-2) - (hw ? T(0) : T(1)) - (he ? T(0) : T(1));
+  const T cdga = T(-2) - (hwa ? T(0) : T(1)) - (hea ? T(0) : T(1));
+  const T cdgb = T(-2) - (hwb ? T(0) : T(1)) - (heb ? T(0) : T(1));
   // level 1 composed (w_1; the coarsest level itself when L == 2) and the
-  // lane's column taps into it
+  // column taps into it of the lane's two columns
   const int nyc = L >= 2 ? D.n[1][1] : 1, nxc = L >= 2 ? D.n[1][2] : 1;
-  int jx0 = 0, jx1 = 0;
-  T wx0 = T(0), wx1 = T(0);
-  if (L >= 2 && xin) prolong_taps<T>(x, nxc, jx0, jx1, wx0, wx1);
+  int ja0 = 0, ja1 = 0, jb0 = 0, jb1 = 0;
+  T wa0 = T(0), wa1 = T(0), wb0 = T(0), wb1 = T(0);
+  if (L >= 2) {
+    if (ina) prolong_taps<T>(xa, nxc, ja0, ja1, wa0, wa1);
+    if (inb) prolong_taps<T>(xb, nxc, jb0, jb1, wb0, wb1);
+  }
   const T* __restrict__ W1 = (L >= 3) ? A.wl + D.off[0][1] : A.p[cur] + D.off[0][1];
   // fine row n lies between rows lo(n) and lo(n) + 1 of w_1
   auto lo_of = [&](int n) { return nyc > 1 ? min(max((n - 1) >> 1, 0), nyc - 2) : 0; };
@@ -250,38 +322,51 @@ __global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stre
   __syncwarp();
   const StreamCoef<T>& cf = sC[w];
   const AdamCoef& ac = cf.ac;
+  // per column: lambda scale (0 without a residual), 1 for an owned cell
+  const T lsa = resa ? cf.lam_scale : T(0), lsb = resb ? cf.lam_scale : T(0);
+  const T ooa = owna ? T(1) : T(0), oob = ownb ? T(1) : T(0);
 
-  // va, vb: rows clo and clo + 1 of w_1 interpolated in x (zero when L == 1);
-  // wa, wb: the raw taps of row clo + 2, loaded one shift ahead
+  // per column (a, b): va, vb the rows clo and clo + 1 of w_1 interpolated in
+  // x (zero when L == 1); ca, cb the raw taps of row clo + 2, loaded one shift
+  // ahead
   int clo = lo_of(nstart);
-  T va = T(0), vb = T(0), wa = T(0), wb = T(0);
-  const bool w1x = L >= 2 && xin;
-  if (w1x) {
+  T vaa = T(0), vba = T(0), caa = T(0), cba = T(0);  // column a
+  T vab = T(0), vbb = T(0), cab = T(0), cbb = T(0);  // column b
+  if (L >= 2) {
     const int hi = nyc > 1 ? clo + 1 : 0;
-    va = wx0 * W1[clo * nxc + jx0] + wx1 * W1[clo * nxc + jx1];
-    vb = wx0 * W1[hi * nxc + jx0] + wx1 * W1[hi * nxc + jx1];
+    const T* r0 = W1 + clo * nxc;
+    const T* r1 = W1 + hi * nxc;
+    vaa = wa0 * r0[ja0] + wa1 * r0[ja1];
+    vba = wa0 * r1[ja0] + wa1 * r1[ja1];
+    vab = wb0 * r0[jb0] + wb1 * r0[jb1];
+    vbb = wb0 * r1[jb0] + wb1 * r1[jb1];
     if (clo + 2 <= nyc - 1) {
-      wa = W1[(clo + 2) * nxc + jx0];
-      wb = W1[(clo + 2) * nxc + jx1];
+      const T* r2 = W1 + (clo + 2) * nxc;
+      caa = r2[ja0]; cba = r2[ja1];
+      cab = r2[jb0]; cbb = r2[jb1];
     }
   }
   auto shift = [&]() {  // advance to rows clo + 1, clo + 2 of w_1
-    va = vb;
-    vb = wx0 * wa + wx1 * wb;
+    vaa = vba;
+    vab = vbb;
+    vba = wa0 * caa + wa1 * cba;
+    vbb = wb0 * cab + wb1 * cbb;
     ++clo;
-    if (w1x && clo + 2 <= nyc - 1) {
-      wa = W1[(clo + 2) * nxc + jx0];
-      wb = W1[(clo + 2) * nxc + jx1];
+    if (L >= 2 && clo + 2 <= nyc - 1) {
+      const T* r2 = W1 + (clo + 2) * nxc;
+      caa = r2[ja0]; cba = r2[ja1];
+      cab = r2[jb0]; cbb = r2[jb1];
     }
   };
-  // FP32 problems: r^2 per lane in plain FP32 (<= 32 terms), data misfit compensated
+  // FP32 problems: r^2 per lane in plain FP32 (<= 64 terms), data misfit compensated
   float rh = 0.f, rl = 0.f, dh = 0.f, dl = 0.f;
   double rd = 0.0, dd = 0.0;                     // FP64 problems
-  T lJ0p = T(0), lJ1p = T(0), lJ2p = T(0), datp = T(0);  // row n-1 (pending gradient)
-  T p0p = T(0), mp = T(0);
-  double vp = 0.0;
+  // row n - 1 (pending gradient) of columns a and b
+  T lJ0pa = T(0), lJ1pa = T(0), lJ2pa = T(0), datpa = T(0), p0pa = T(0), mpa = T(0);
+  T lJ0pb = T(0), lJ1pb = T(0), lJ2pb = T(0), datpb = T(0), p0pb = T(0), mpb = T(0);
+  double vpa = 0.0, vpb = 0.0;
   int rr = rb, nc = run_cell(rb);
-  T uo = T(0);  // u(n-1, x)
+  T uoa = T(0), uob = T(0);  // u(n-1, a), u(n-1, b)
 
   // Row n: the field, the residual and the data term of row n; the gradient
   // and the Adam update of row n - 1.  Row y1 (< ny) supplies the residual
@@ -296,50 +381,60 @@ __global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stre
     const bool res_row = !gen || (n >= 1 && n >= y0 && n < ny);
     const bool grad_row = !gen || (n - 1 >= y0 && n - 1 < y1);
     const int sl = n & (kRing - 1);
-    T p0 = T(0), u = T(0), mn = T(0);
-    double vn = 0.0;
-    if (row_ok && xin) {
-      p0 = sP[w][sl][lane];
-      if (step && own_row && own_x) {
-        mn = sM[w][sl][lane];
-        vn = sV[w][sl][lane];
-      }
-      u = p0 + (wlo * va + whi * vb);
+    // No branches on the lane's columns: slots of columns outside the level
+    // (or of rows not copied) hold stale values, which are selected away
+    // (level 0) or used only in results that are never stored (m, v).  A
+    // column outside the level has u = 0 (its w_1 taps have weight 0).
+    const T2 pp = *reinterpret_cast<const T2*>(&sP[w][sl][2 * lane]);
+    const T p0a = (row_ok && ina) ? pp.x : T(0), p0b = (row_ok && inb) ? pp.y : T(0);
+    const T ua = p0a + (wlo * vaa + whi * vba);
+    const T ub = p0b + (wlo * vab + whi * vbb);
+    T mna = T(0), mnb = T(0);
+    double vna = 0.0, vnb = 0.0;
+    if (step) {
+      const T2 mm = *reinterpret_cast<const T2*>(&sM[w][sl][2 * lane]);
+      const double2 vv = *reinterpret_cast<const double2*>(&sV[w][sl][2 * lane]);
+      mna = mm.x; mnb = mm.y;
+      vna = vv.x; vnb = vv.y;
     }
     if (comp_only) {
-      if (row_ok && own_row && own_x) A.ufine[D.fine_off[0] + n * nx + x] = u;
+      if (row_ok && own_row) {
+        T* uf = A.ufine + D.fine_off[0] + n * nx;
+        if (owna) uf[xa] = ua;
+        if (ownb) uf[xb] = ub;
+      }
       return;
     }
-    const T uW = __shfl_up_sync(kFull, u, 1);
-    const T uE = __shfl_down_sync(kFull, u, 1);
-    T lJ0 = T(0), lJ1 = T(0), lJ2 = T(0), lJ3 = T(0);
-    if (res_row && res_x) {
-      const T uw = hw ? uW : -u;
-      const T ue = he ? uE : -u;
-      // the flux through a wall is the upwind flux against the zero wall value
-      T dFEc, dFEe, dFWw, dFWc;
-      const T FE = eo_flux_s(u, he ? ue : T(0), dFEc, dFEe);
-      const T FW = eo_flux_s(hw ? uw : T(0), u, dFWw, dFWc);
-      const T lap = (ue - T(2) * u + uw) * cf.idx2;
-      const T r = (u - uo) * cf.idt + (FE - FW) * cf.idx1 - cf.nu * lap;
-      const T lam = cf.lam_scale * r;
-      lJ1 = lam * (cf.idt + (dFEc - dFWc) * cf.idx1 - cf.nu * cdiag * cf.idx2);
-      lJ0 = hw ? lam * (-dFWw * cf.idx1 - cf.nu * cf.idx2) : T(0);
-      lJ2 = he ? lam * (dFEe * cf.idx1 - cf.nu * cf.idx2) : T(0);
-      lJ3 = lam * (-cf.idt);
-      if (own_row && own_x) {
-        if (sizeof(T) == 4) rh += (float)(r * r);
-        else rd += (double)(r * r);
+    const T uWa = __shfl_up_sync(kFull, ub, 1);    // u(n, a - 1): column b of lane - 1
+    const T uEb = __shfl_down_sync(kFull, ua, 1);  // u(n, b + 1): column a of lane + 1
+    T lJ0a, lJ1a, lJ2a, lJ3a, lJ0b, lJ1b, lJ2b, lJ3b;
+    {
+      const T ra = burgers_cell<T>(ua, uoa, uWa, ub, hwa, hea, cdga, res_row ? lsa : T(0), cf,
+                                   lJ0a, lJ1a, lJ2a, lJ3a);
+      const T rb = burgers_cell<T>(ub, uob, ua, uEb, hwb, heb, cdgb, res_row ? lsb : T(0), cf,
+                                   lJ0b, lJ1b, lJ2b, lJ3b);
+      // r^2 of the owned cells of residual rows (x 1) and of the others (x 0)
+      const bool rrow = own_row && res_row;
+      const T oa = rrow ? ooa : T(0), ob = rrow ? oob : T(0);
+      if (sizeof(T) == 4) {
+        rh = fmaf((float)oa, (float)(ra * ra), rh);
+        rh = fmaf((float)ob, (float)(rb * rb), rh);
+      } else {
+        rd = fma((double)oa, (double)(ra * ra), rd);
+        rd = fma((double)ob, (double)(rb * rb), rd);
       }
     }
-    // data term of the measured cells of row n (runs sorted by cell)
-    T dat = T(0);
+    // data term of the measured cells of row n (runs sorted by cell; every
+    // run of this strip lies in its owned columns)
+    T data = T(0), datb = T(0);
     const int rowbase = n * nx;
     if (nc < rowbase + nx && own_row) {
       for (; rr < re; ++rr) {
         const int off = A.run_cell[rr] - rowbase;
         if (off >= nx) break;
-        if (x == off) {
+        const bool ha = xa == off;
+        if (ha || xb == off) {
+          const T u = ha ? ua : ub;
           const int e0 = A.run_beg[rr], e1 = A.run_beg[rr + 1];
           T d = u - A.run_v0[rr];
           T sd = d, sq = d * d;
@@ -350,30 +445,59 @@ __global__ void __launch_bounds__(kStreamNT, sizeof(T) == 4 ? 6 : 4) k_fine_stre
           }
           if (sizeof(T) == 4) acc_add(dh, dl, sq);
           else dd += (double)sq;
-          dat = cf.wd2 * sd;
+          if (ha) data = cf.wd2 * sd;
+          else datb = cf.wd2 * sd;
         }
       }
       nc = run_cell(rr);
     }
-    // gradient and Adam of row n - 1
-    const T fromE = __shfl_down_sync(kFull, lJ0p, 1);  // lambda dr/du of residual (n-1, x+1)
-    const T fromW = __shfl_up_sync(kFull, lJ2p, 1);    // lambda dr/du of residual (n-1, x-1)
-    if (adj && grad_row && own_x) {
-      const T g = ((lJ1p + datp) + fromE + fromW + lJ3) * cf.gscale;
-      const int em = rowbase - nx + x;
-      G0[em] = g;
+    // gradient and Adam of row n - 1: dL/du(n-1, x) gathers lambda dr/du of
+    // the residuals (n-1, x-1), (n-1, x), (n-1, x+1) and (n, x)
+    const T fromWa = __shfl_up_sync(kFull, lJ2pb, 1);    // residual (n-1, a-1): lane - 1
+    const T fromEb = __shfl_down_sync(kFull, lJ0pa, 1);  // residual (n-1, b+1): lane + 1
+    if (adj && grad_row) {
+      const T ga = ((lJ1pa + datpa) + lJ0pb + fromWa + lJ3a) * cf.gscale;
+      const T gb = ((lJ1pb + datpb) + fromEb + lJ2pa + lJ3b) * cf.gscale;
+      const int em = rowbase - nx + xa;
+      T pa = p0pa, ma = mpa, pb = p0pb, mb = mpb;
+      double va = vpa, vb = vpb;
       if (step) {
-        T p = p0p, m = mp;
-        double v = vp;
-        adam_update(p, m, v, g, ac);
-        Pn[em] = p;
-        const_cast<T*>(M0)[em] = m;
-        const_cast<double*>(V0)[em] = v;
+        adam_update(pa, ma, va, ga, ac);
+        adam_update(pb, mb, vb, gb, ac);
+      }
+      if (vec) {
+        if (owna) {  // == ownb
+          *reinterpret_cast<T2*>(G0 + em) = T2{ga, gb};
+          if (step) {
+            *reinterpret_cast<T2*>(Pn + em) = T2{pa, pb};
+            *reinterpret_cast<T2*>(const_cast<T*>(M0) + em) = T2{ma, mb};
+            *reinterpret_cast<double2*>(const_cast<double*>(V0) + em) = double2{va, vb};
+          }
+        }
+      } else {
+        if (owna) {
+          G0[em] = ga;
+          if (step) {
+            Pn[em] = pa;
+            const_cast<T*>(M0)[em] = ma;
+            const_cast<double*>(V0)[em] = va;
+          }
+        }
+        if (ownb) {
+          G0[em + 1] = gb;
+          if (step) {
+            Pn[em + 1] = pb;
+            const_cast<T*>(M0)[em + 1] = mb;
+            const_cast<double*>(V0)[em + 1] = vb;
+          }
+        }
       }
     }
-    lJ0p = lJ0; lJ1p = lJ1; lJ2p = lJ2; datp = dat;
-    p0p = p0; mp = mn; vp = vn;
-    uo = u;
+    lJ0pa = lJ0a; lJ1pa = lJ1a; lJ2pa = lJ2a; datpa = data;
+    lJ0pb = lJ0b; lJ1pb = lJ1b; lJ2pb = lJ2b; datpb = datb;
+    p0pa = p0a; mpa = mna; vpa = vna;
+    p0pb = p0b; mpb = mnb; vpb = vnb;
+    uoa = ua; uob = ub;
   };
   // a row at the strip's edges: weights of w_1 rows clo, clo + 1 from its
   // position (3/4, 1/4 inside; 5/4, -1/4 at the level's ends; a copy when

@@ -15,10 +15,11 @@ namespace modil {
 // is the strip of the warp-streaming Burgers kernel (kSR rows, kSW owned
 // columns per warp).
 constexpr int kNumTileCfg = 7;
-constexpr int kTileCfg[kNumTileCfg][2] = {{16, 32}, {16, 64}, {8, 64}, {32, 32}, {8, 128}, {8, 32}, {32, 28}};
+constexpr int kTileCfg[kNumTileCfg][2] = {{16, 32}, {16, 64}, {8, 64}, {32, 32}, {8, 128}, {8, 32}, {32, 60}};
 constexpr int kStreamCfg = 6;
-constexpr int kSR = 32, kSW = 28;
+constexpr int kSR = 32, kSW = 60;
 constexpr int kStreamNT = 128;   // threads per block of the streaming kernel (one strip per warp)
+constexpr int kStreamBlocksF32 = 4, kStreamBlocksF64 = 3;  // its resident blocks per SM (register cap)
 constexpr int kStreamMinStrips = 4 * 152;  // default to the streaming kernel from this many strips
 constexpr int kComposeNT = 256;  // threads per block of the level-1 composition (4 cells each)
 constexpr int kComposeSmallNT = 512;  // threads per block composing levels >= 2 of one instance

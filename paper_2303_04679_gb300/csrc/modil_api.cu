@@ -151,8 +151,8 @@ modil_status make_plan(const modil_desc* d, int n, Plan& P, bool allow_stream = 
   P.cfg = find_cfg(ty, tx);
   if (P.cfg < 0) return fail(MODIL_ERR_ARG, "unsupported tile shape");
   if (P.cfg == kStreamCfg) {
-    if (P.pde != MODIL_PDE_BURGERS) return fail(MODIL_ERR_ARG, "the 32 x 28 strip is the Burgers streaming kernel's");
-    if (any_points) return fail(MODIL_ERR_UNSUPPORTED, "off-grid points need a tile kernel shape (not 32 x 28)");
+    if (P.pde != MODIL_PDE_BURGERS) return fail(MODIL_ERR_ARG, "the 32 x 60 strip is the Burgers streaming kernel's");
+    if (any_points) return fail(MODIL_ERR_UNSUPPORTED, "off-grid points need a tile kernel shape (not 32 x 60)");
     if (!allow_stream) P.cfg = 0;
   }
   P.stream = (P.cfg == kStreamCfg);
