@@ -318,6 +318,52 @@ def heat_inference(modil, w, args, chunk=250):
             "k_max_over_min": float(np.max(q) / max(np.min(np.abs(q)), 1e-30))}
 
 
+# Config 2's inference with the paper's optimiser (Section 3.4 runs mODIL with
+# L-BFGS-B): the data weight and the node unit are readings (the paper states
+# neither): the data term weighted 1e4 against the residual integral, the
+# nodes in their own units (k_scale = 1).  With the data weight 1 the joint
+# optimum at 512 x 512 lies far from the reference conductivity.
+HEAT_LBFGS = dict(w_data=1e4, k_scale=1.0, history=50, chunk=100, iterations=2000)
+
+
+def heat_inference_lbfgs(modil, w, args):
+    """Conductivity inference to a tolerance by the device L-BFGS on the
+    workload w (zero levels, constant nodes), the conductivity error read
+    every chunk of iterations (wall time includes the reads)."""
+    import torch
+    c = HEAT_LBFGS
+    tols = (0.5, 0.3, 0.2, 0.1, 0.05, 0.02, 0.01)
+    hits = {t: None for t in tols}
+    hist = []
+    w2 = dict(w, w_data=c["w_data"], k_scale=c["k_scale"])
+    with modil.Problem(make_desc(modil, w2, "0x0")) as p, modil.LBFGS(p, history=c["history"]) as opt:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = 0
+        loss = None
+        while done < c["iterations"]:
+            h = opt.run(c["chunk"])
+            done += len(h) - 1
+            loss = float(h[-1])
+            e = k_error(p.read_knodes())
+            el = time.perf_counter() - t0
+            hist.append((done, e))
+            for t in tols:
+                if hits[t] is None and e <= t:
+                    hits[t] = {"iterations": done, "seconds": el}
+            if len(h) - 1 < c["chunk"]:
+                break
+        q = p.read_knodes()
+    return {"metric": "conductivity error (RMS over u in (0,1) / max k, Section 3.4)",
+            "optimizer": f"device L-BFGS (history {c['history']}, Armijo backtracking)",
+            "grid": list(w["shape"]), "levels": w["n_levels"], "measurements": len(w["meas_cell"]),
+            "w_data": c["w_data"], "k_scale": c["k_scale"], "dtype": "f32",
+            "k_error_initial": k_error(w["knodes"]), "k_error_final": hist[-1][1], "iterations": done,
+            "to_tolerance": {str(t): hits[t] for t in tols}, "loss_final": loss,
+            "k_error_every_500": [round(e, 4) for s, e in hist if s % 500 == 0],
+            "k_over_0.02_every_3rd_node": [round(float(v) / 0.02, 3) for v in q[::3]]}
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -1371,14 +1417,16 @@ def main():
     out["record"] = {"kind": "library forward solve (k_fixed, L-BFGS nested from 64^2)",
                      "finest_iterations": len(rec_hist) - 1, "loss": float(rec_hist[-1]), "seconds": t_rec}
     # conductivity inference to a tolerance in the setting of Section 3.4: the
-    # inverse problem on 64 x 64 cells, 500 measured cells without noise; on
-    # the 512 x 512 configuration with seven levels Adam does not identify k
-    # within 10 000 steps (reported beside it)
+    # inverse problem on 64 x 64 cells, 500 measured cells without noise, by
+    # Adam; on the 512 x 512 configuration with seven levels and noisy data
+    # Adam does not identify k within 10 000 steps (reported beside it), the
+    # device L-BFGS does (HEAT_LBFGS)
     rec64, _ = records.heat_record(64, 64, 4, depth=1)
     w64 = inputs.heat_workload(64, 64, 4, field=rec64, frac=500 / 4096, sigma=0.0)
     w64["lr"] = 3e-3
     out["inference"] = heat_inference(modil, w64, args)
     out["inference_512"] = heat_inference(modil, w, args)
+    out["inference_512_lbfgs"] = heat_inference_lbfgs(modil, w, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, el = time_oracle(w, args.cpu_seconds)
         out["cpu_baseline"] = {"value": n / el, "unit": UNIT, "cores": blas_threads(),
