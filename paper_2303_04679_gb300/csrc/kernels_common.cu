@@ -98,10 +98,12 @@ __device__ __forceinline__ void cp_async16_lv(void* dst, const void* src) {
 // One kLevTY x kLevTX tile of coarse level l (NF fields) over all instances:
 // dL/du_l = T^T dL/du_{l-1} from a staged region of the finer level's
 // gradient, then Adam on the tile.  Each thread finishes four coarse cells
-// (four times the loads in flight per thread as one cell: the kernel is bound
-// by memory latency; level 1 of the batched Burgers step 0.147 -> 0.110 ms):
-// away from the level's ends their weights are the 4 x 4 tensor product of
-// (1/4, 3/4, 3/4, 1/4); within two cells of an end, the 6-tap windows.
+// (four times the loads in flight per thread as one cell; level 1 of the
+// batched Burgers step 0.147 -> 0.110 ms).  One FP32 field: two separable
+// passes over the staged region that every cell runs alike (6-tap windows,
+// zero weights padding the interior's (1/4, 3/4, 3/4, 1/4)).  Otherwise:
+// away from the level's ends the 4 x 4 tensor product of (1/4, 3/4, 3/4,
+// 1/4); within two cells of an end, the 6-tap windows.
 template <class T, int NF>
 __global__ void __launch_bounds__(MODIL_NT)
 k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
@@ -170,20 +172,80 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
       if (yy < ry0 || yy >= ry1) continue;
       T* dst = fs + r * FW + c;
       const T* src = gf + (long long)yy * fx + xx;
+      // staged positions without a copy are zeroed: the windows of the
+      // level's end columns read them with weight 0
       if (vec) {
         if (xx + 3 >= rx0 && xx < rx1) {  // whole 4-element chunks inside the level
           cp_async16_lv(dst, src);
           if (sizeof(T) == 8) cp_async16_lv(dst + 2, src + 2);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) dst[j] = T(0);
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 4; ++j) {
           if (xx + j >= rx0 && xx + j < rx1) cp_async(dst + j, src + j);
+          else dst[j] = T(0);
+        }
       }
     }
   }
   cp_async_wait_all();
   __syncthreads();
+  if constexpr (NF == 1 && sizeof(T) == 4) {
+    // One FP32 field: the restriction in two passes that every cell runs alike
+    // (6-tap windows of zero-padded weights; near the level's ends the
+    // windows carry the extrapolation taps), so no warp splits into an
+    // interior and an end path.  x pass: each staged row r, coarse column c;
+    // the window's six fine values are three aligned pairs.
+    static_assert(kLevTX == 32 && MODIL_NT % 32 == 0, "one coarse column per lane");
+    __shared__ __align__(16) float hx[FH * kLevTX];
+    {
+      const int c = threadIdx.x & 31;
+      const int X = x0 + c;
+      T wx[6];
+      rwin<T>(min(X, nx - 1), nx, wx);
+      const float2* win = reinterpret_cast<const float2*>(fineS + (2 * X - 2 - oX));
+      for (int r = threadIdx.x >> 5; r < FH; r += MODIL_NT / 32) {
+        const int yy = oY + r;
+        T h = T(0);
+        if (c < cw && yy >= ry0 && yy < ry1) {
+          const float2* q = win + r * (FW / 2);
+          const float2 a = q[0], b = q[1], e = q[2];
+          h += wx[0] * a.x;
+          h += wx[1] * a.y;
+          h += wx[2] * b.x;
+          h += wx[3] * b.y;
+          h += wx[4] * e.x;
+          h += wx[5] * e.y;
+        }
+        hx[r * kLevTX + c] = h;
+      }
+    }
+    __syncthreads();
+    // y pass, then Adam, per owned cell
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      if (!mine[j]) continue;
+      const int Y = Yc[j], X = Xc[j];
+      T wy[6];
+      rwin<T>(Y, ny, wy);
+      const T* col = hx + (2 * Y - 2 - oY) * kLevTX + (X - x0);
+      T g = T(0);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) g += wy[i] * col[i * kLevTX];
+      const long long o = D.off[0][l] + (long long)Y * nx + X;
+      if (store_g) A.g[o] = g;
+      if (mode == MODE_STEP) {
+        const AdamCoef ac = acS;
+        adam_update(pv[j][0], mv[j][0], vv[j][0], g, ac);
+        A.p[cur ^ 1][o] = pv[j][0];
+        A.m[o] = mv[j][0];
+        A.v[o] = vv[j][0];
+      }
+    }
+  } else {
 #pragma unroll
   for (int j = 0; j < CPT; ++j) {
     const int Y = Yc[j], X = Xc[j];
@@ -229,6 +291,7 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
         A.v[o] = vv[j][f];
       }
     }
+  }
   }
 }
 
