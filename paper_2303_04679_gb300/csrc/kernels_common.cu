@@ -124,17 +124,35 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   const int y0 = ty * kLevTY, x0 = tx * kLevTX;
   const int ch = min(kLevTY, ny - y0), cw = min(kLevTX, nx - x0);
   const bool store_g = (mode != MODE_STEP) || (l < D.nlev - 1);
+  // level offsets in registers: the descriptor is memory that the stores
+  // below could alias, and would otherwise be re-read after each of them
+  long long offl[NF], offp[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    offl[f] = D.off[f][l];
+    offp[f] = D.off[f][l - 1];
+  }
   // cells k = threadIdx.x + j * MODIL_NT packed as k = oy * cw + ox so that a
-  // ragged tile keeps the low threads busy
+  // ragged tile keeps the low threads busy (a full-width tile: shifts)
   int Yc[CPT], Xc[CPT];
   bool mine[CPT];
+  if (cw == kLevTX) {
 #pragma unroll
-  for (int j = 0; j < CPT; ++j) {
-    const int k = threadIdx.x + j * MODIL_NT;
-    const int oy = k / cw;
-    Yc[j] = y0 + oy;
-    Xc[j] = x0 + (k - oy * cw);
-    mine[j] = k < ch * cw;
+    for (int j = 0; j < CPT; ++j) {
+      const int k = threadIdx.x + j * MODIL_NT;
+      Yc[j] = y0 + k / kLevTX;
+      Xc[j] = x0 + k % kLevTX;
+      mine[j] = k < ch * kLevTX;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      const int k = threadIdx.x + j * MODIL_NT;
+      const int oy = k / cw;
+      Yc[j] = y0 + oy;
+      Xc[j] = x0 + (k - oy * cw);
+      mine[j] = k < ch * cw;
+    }
   }
   // Prologue: this level's parameters and moments were last written by the
   // same kernel one step earlier, two or more launches back.
@@ -146,7 +164,7 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   for (int f = 0; f < NF; ++f) {
     pv[j][f] = T(0); mv[j][f] = T(0); vv[j][f] = 0.0;
     if (mode == MODE_STEP && mine[j]) {
-      const long long o = D.off[f][l] + (long long)Yc[j] * nx + Xc[j];
+      const long long o = offl[f] + (long long)Yc[j] * nx + Xc[j];
       pv[j][f] = A.p[cur][o];
       mv[j][f] = A.m[o];
       vv[j][f] = A.v[o];
@@ -162,7 +180,7 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
   constexpr int CW = FW / 4;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    const long long fo = D.off[f][l - 1];
+    const long long fo = offp[f];
     const T* __restrict__ gf = A.g + fo;
     T* fs = fineS + f * FH * FW;
     const bool vec = ((fx & 3) == 0) && ((fo & 3) == 0);
@@ -224,7 +242,9 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
       }
     }
     __syncthreads();
-    // y pass, then Adam, per owned cell
+    // y pass, then Adam, per owned cell (the coefficients read once: the
+    // stores below could alias shared memory)
+    const AdamCoef ac = acS;
 #pragma unroll
     for (int j = 0; j < CPT; ++j) {
       if (!mine[j]) continue;
@@ -235,10 +255,9 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
       T g = T(0);
 #pragma unroll
       for (int i = 0; i < 6; ++i) g += wy[i] * col[i * kLevTX];
-      const long long o = D.off[0][l] + (long long)Y * nx + X;
+      const long long o = offl[0] + (long long)Y * nx + X;
       if (store_g) A.g[o] = g;
       if (mode == MODE_STEP) {
-        const AdamCoef ac = acS;
         adam_update(pv[j][0], mv[j][0], vv[j][0], g, ac);
         A.p[cur ^ 1][o] = pv[j][0];
         A.m[o] = mv[j][0];
@@ -281,7 +300,7 @@ k_level(const __grid_constant__ Arena<T> A, int l, int mode, int cur) {
           g += wy[i] * h;
         }
       }
-      const long long o = D.off[f][l] + (long long)Y * nx + X;
+      const long long o = offl[f] + (long long)Y * nx + X;
       if (store_g) A.g[o] = g;
       if (mode == MODE_STEP) {
         const AdamCoef ac = acS;
