@@ -151,3 +151,22 @@ def test_offgrid_points_in_the_plan(mod):
     body = mod.Desc("ns3d", (8, 8, 16), 2, "f32", coef=(60.0, 0.4, 1.0, 1.0), points=[[0.5, 0.5, 1.0]],
                     point_value=np.zeros(1), point_field=np.array([2], np.int32))
     assert nbytes(body)[0] == 0
+
+
+def test_streaming_strip_tile(mod):
+    """The warp-streaming Burgers kernel's strip is 32 rows x 60 columns (two
+    columns per lane of a warp): that tile is accepted for Burgers, also with
+    odd widths and a single level, and refused for other families and with
+    off-grid points; the former 32 x 28 strip is no tile shape any more
+    (host only)."""
+    from paper_2303_04679_gb300 import autotune
+    assert autotune.STREAM_TILE == (32, 60)
+    for shape, L in (((64, 512), 4), ((45, 61), 1), ((40, 33), 1)):
+        assert mod.arena_bytes([mod.Desc("burgers", shape, L, "f32", coef=(0.01,), tile=(32, 60))]) > 0
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([mod.Desc("burgers", (64, 64), 3, "f32", coef=(0.01,), tile=(32, 28))])
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([_heat(mod, (64, 64), 3, tile=(32, 60))])
+    with pytest.raises(mod.ModilError):
+        mod.arena_bytes([mod.Desc("burgers", (64, 64), 3, "f32", coef=(0.01,), tile=(32, 60),
+                                  points=[[0.5, 0.0]], point_value=np.zeros(1))])
